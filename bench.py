@@ -1,0 +1,424 @@
+#!/usr/bin/env python
+"""Throughput of the GB300 PI-RRT# exploitation path (edge relaxations/s).
+
+One step = the whole Batched-Extension schedule of one roadmap (Alg. 3):
+starting from an empty graph, insert block after block (vertices plus the
+edges whose other endpoint is present) and exploit to convergence after each
+(Alg. 2: Improve / Evaluate until no parent switches).  The default workload
+is the 6-D roadmap: [-pi, pi]^6 with 64 hyperspheres, N = 4,000,000
+collision-free samples, k = 30 nearest neighbours, 16-point edge checks, FP32
+costs, FP64 g, blocks of 50,000 vertices (80 exploitation rounds per step).
+
+value      = edge relaxations (CSR entries scanned by Improve) / device time,
+             inputs resident in HBM, summed over ranks (replicas).
+e2e        = the same through the C ABI with pinned host inputs: every step
+             copies the COO blocks host->device inside insert_batch and reads
+             g and the parents back to the host.
+roofline   = the dominant kernel's algorithmic bytes / its CUDA-event time,
+             against the measured HBM copy bandwidth.
+cpu_baseline / --impl reference = the CPU oracle (serial policy iteration,
+             Alg. 2, one core) on a bounded prefix of the same schedule.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+from paper_2003_04920_gb300 import workloads as W  # noqa: E402
+
+METRIC = "edge relaxations/sec and ms to converged exploitation per batch; % of HBM roofline"
+UNIT = "relaxations/s"
+L2_BYTES = 129 * 1024 * 1024
+
+WORKLOADS = {
+    "c3": ("roadmap_c3", "6-D [-pi,pi]^6, 64 hyperspheres r~U[0.3,0.8], N=4e6, k=30, "
+                         "16-point edge check, FP32 costs, FP64 g, blocks of 5e4"),
+    "c2": ("roadmap_c2", "2-D unit square, 200 circles r~U[0.02,0.08], N=1e6, k=76, FP32 costs, "
+                         "FP64 g, blocks of 1e4"),
+    "c2-companion": ("roadmap_c2", "2-D unit square, 200 circles r~U[0.01,0.04], N=1e6, k=76, "
+                                   "FP32 costs, FP64 g, blocks of 1e4"),
+}
+
+
+def load_roadmap(name: str, n: int | None, block: int | None, trial: int):
+    fn_name, _ = WORKLOADS[name]
+    kw = dict(trial=trial)
+    if n:
+        kw["n"] = n
+    if block:
+        kw["block"] = block
+    if name == "c2-companion":
+        kw["companion"] = True
+    return W.cached(name, getattr(W, fn_name), **kw)
+
+
+def measured_peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(path):
+        with open(path) as f:
+            d = json.load(f)
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+class ClockSampler:
+    """nvidia-smi samples of SM clock and throttle reasons during a region."""
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.path = None
+
+    def __enter__(self):
+        fd, self.path = tempfile.mkstemp(suffix=".csv")
+        os.close(fd)
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--id={self.device}", f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=open(self.path, "w"), stderr=subprocess.DEVNULL)
+        except (FileNotFoundError, OSError):
+            self.proc = None
+        time.sleep(0.3)
+        return self
+
+    def __exit__(self, *exc):
+        if self.proc is not None:
+            time.sleep(0.25)
+            self.proc.terminate()
+            try:
+                self.proc.wait(timeout=5)
+            except subprocess.TimeoutExpired:
+                self.proc.kill()
+
+    def summary(self, busy_sm_floor: float = 0.0) -> dict:
+        rows = []
+        if self.path and os.path.exists(self.path):
+            for line in open(self.path):
+                parts = [p.strip() for p in line.split(",")]
+                if len(parts) < 9:
+                    continue
+                try:
+                    rows.append(dict(sm=float(parts[1]), smax=float(parts[2]),
+                                     hw=parts[5], hwt=parts[6], swt=parts[7], pcap=parts[8]))
+                except ValueError:
+                    continue
+            os.unlink(self.path)
+        if not rows:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unavailable"], "samples": 0}
+        reasons = set()
+        for r in rows:
+            for key, name in (("hw", "hw_slowdown"), ("hwt", "hw_thermal_slowdown"),
+                              ("swt", "sw_thermal_slowdown"), ("pcap", "sw_power_cap")):
+                if r[key].lower().startswith("active"):
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(r["sm"] for r in rows),
+                "sm_max_mhz": max(r["smax"] for r in rows),
+                "reasons": sorted(reasons), "samples": len(rows)}
+
+
+def improve_bytes(prof: dict, n: int, entry_bytes: int, cost_bytes: int) -> float:
+    """Algorithmic (compulsory) HBM bytes of all Improve launches: every CSR
+    entry scanned (col + cost), per processed vertex its row offset, parent,
+    parent-edge cost and the parent's g, the list id in sparse sweeps, g of
+    every vertex once per dense sweep, and the parent / cost writes of each
+    switch.  Gathers of g(u) in sparse sweeps are not counted (lower bound)."""
+    entries = prof["improve_entries"]
+    verts = prof["improve_vertices"]
+    dense_v = prof["improve_dense_vertices"]
+    sparse_v = verts - dense_v
+    per_vertex = 8 + 4 + cost_bytes + 8
+    return (entries * entry_bytes + verts * per_vertex + sparse_v * 4 + dense_v * 8
+            + prof["improve_switches"] * (4 + cost_bytes + 4))
+
+
+def evaluate_bytes(prof: dict, cost_bytes: int) -> float:
+    """Evaluate: read p and the parent-edge cost, write g, per vertex."""
+    return prof["evaluate_vertices"] * (4 + cost_bytes + 8)
+
+
+def run_ours(args) -> None:
+    import torch
+    import torch.distributed as dist
+
+    import paper_2003_04920_gb300 as P
+
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    if world > 1:
+        dist.init_process_group("nccl", device_id=torch.device("cuda", local))
+    P.load_library()
+
+    rm = load_roadmap(args.workload, args.n, args.block, args.trial)
+    n_blocks = rm.n_blocks()
+    stream = torch.cuda.current_stream()
+    dev_u = torch.from_numpy(rm.u).cuda()
+    dev_v = torch.from_numpy(rm.v).cuda()
+    dev_c = torch.from_numpy(rm.cost).cuda()
+    cost_bytes = rm.cost.dtype.itemsize
+    entry_bytes = 8 if cost_bytes == 4 else 16
+    G = P.Graph(rm.n, rm.m, 0, rm.cost.dtype, device=local, stream=stream.cuda_stream)
+    flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+
+    def step(device_inputs=True):
+        G.reset()
+        relax = 0
+        iters = 0
+        for v0, v1, e0, e1 in rm.blocks():
+            if device_inputs:
+                G.insert_batch(v1 - v0, dev_u[e0:e1], dev_v[e0:e1], dev_c[e0:e1])
+            else:
+                G.insert_batch(v1 - v0, host_u[e0:e1], host_v[e0:e1], host_c[e0:e1])
+            st = G.exploit(group=args.group, dense_fraction=args.dense_fraction)
+            relax += st["relaxations"]
+            iters += st["iterations"]
+        return relax, iters
+
+    def barrier():
+        torch.cuda.synchronize()
+        if world > 1:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    for _ in range(args.warmup):
+        step()
+    barrier()
+
+    # device-resident inputs, one CUDA-event pair per step, L2 flushed between
+    # steps outside the timed spans (the CSR is also ~8x larger than L2)
+    G.set_profiling(True)
+    times, relaxes, iters_all = [], [], []
+    with ClockSampler(local) as clk:
+        for _ in range(args.steps):
+            flush.fill_(1)
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(stream)
+            r, it = step()
+            e1.record(stream)
+            e1.synchronize()
+            times.append(e0.elapsed_time(e1))
+            relaxes.append(r)
+            iters_all.append(it)
+    prof = G.get_profile()
+    G.set_profiling(False)
+    barrier()
+    clocks = clk.summary()
+
+    total_ms = float(sum(times))
+    total_relax = float(sum(relaxes))
+    if world > 1:
+        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        total_ms = float(t.item())
+        r = torch.tensor([total_relax], dtype=torch.float64, device="cuda")
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        total_relax = float(r.item())
+    value = total_relax / (total_ms / 1e3)
+    ms_per_step = total_ms / args.steps
+
+    # end to end through the C ABI with pinned host buffers
+    pin_u = torch.from_numpy(rm.u).pin_memory()
+    pin_v = torch.from_numpy(rm.v).pin_memory()
+    pin_c = torch.from_numpy(rm.cost).pin_memory()
+    host_u, host_v, host_c = pin_u.numpy(), pin_v.numpy(), pin_c.numpy()
+    out_g = torch.empty(rm.n, dtype=torch.float64).pin_memory().numpy()
+    out_p = torch.empty(rm.n, dtype=torch.int32).pin_memory().numpy()
+    barrier()
+    t0 = time.perf_counter()
+    e2e_relax = 0
+    for _ in range(args.steps):
+        r, _ = step(device_inputs=False)
+        G.get_costs(out_g)
+        G.get_parents(out_p)
+        e2e_relax += r
+    torch.cuda.synchronize()
+    e2e_s = time.perf_counter() - t0
+    if world > 1:
+        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+        e2e_s = float(t.item())
+        r = torch.tensor([float(e2e_relax)], dtype=torch.float64, device="cuda")
+        dist.all_reduce(r, op=dist.ReduceOp.SUM)
+        e2e_relax = float(r.item())
+    h2d = rm.m * (4 + 4 + cost_bytes)
+    d2h = rm.n * (8 + 4)
+
+    peak, peak_src = measured_peaks()
+    kernels = {}
+    for name, ms_key, launches_key, nbytes in (
+            ("improve", "improve_ms", "improve_launches", improve_bytes(prof, rm.n, entry_bytes, cost_bytes)),
+            ("evaluate", "evaluate_ms", "evaluate_launches", evaluate_bytes(prof, cost_bytes)),
+            ("mark_frontier", "mark_ms", "mark_launches", None),
+            ("insert", "insert_ms", "insert_calls", prof["insert_new_entries"] * entry_bytes)):
+        ms = prof[ms_key]
+        k = {"ms": round(ms, 3), "launches": prof[launches_key],
+             "share_of_step": round(ms / total_ms, 4) if total_ms else None}
+        if nbytes is not None and ms > 0:
+            k["algorithmic_gbs"] = round(nbytes / (ms / 1e3) / 1e9, 1)
+        kernels[name] = k
+    imp_bytes = improve_bytes(prof, rm.n, entry_bytes, cost_bytes)
+    launches = max(1, prof["improve_launches"])
+    imp_ms_avg = prof["improve_ms"] / launches
+    achieved = (imp_bytes / launches) / (imp_ms_avg / 1e3) / 1e9 if imp_ms_avg > 0 else 0.0
+    traffic = None
+    tpath = os.path.join(ROOT, "profiles", "improve_traffic.json")
+    if os.path.exists(tpath):
+        with open(tpath) as f:
+            tj = json.load(f)
+        if tj.get("workload") == args.workload and tj.get("kernel_hash") == kernel_hash():
+            traffic = tj.get("traffic_bytes_per_launch")
+
+    line = {
+        "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
+        "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
+        "ms_per_batch": round(ms_per_step / n_blocks, 4),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded roadmap generator)",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][1]}",
+                   "vertices": rm.n, "undirected_edges": rm.m, "csr_entries": 2 * rm.m,
+                   "blocks_per_step": n_blocks, "block_size": rm.block,
+                   "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
+                   "parallelism": f"replicas x{world}",
+                   "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
+                         % (2 * rm.m * entry_bytes / 1e9)},
+        "roofline": {"bound": "hbm", "kernel": "improve", "achieved": round(achieved, 1),
+                     "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
+                     "peak_source": f"{peak_src} copy bandwidth",
+                     "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
+                     "traffic": traffic,
+                     "bytes_per_launch": round(imp_bytes / launches, 1),
+                     "avg_launch_ms": round(imp_ms_avg, 5)},
+        "kernels": kernels,
+        "e2e": {"value": round(e2e_relax / e2e_s, 1), "unit": UNIT,
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+        "gpu_launches": int(prof["launches"]),
+        "clocks": clocks,
+    }
+    if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        line["cpu_baseline"] = cpu_baseline(rm, args.cpu_seconds)
+    G.close()
+    if rank == 0:
+        print(json.dumps(line), flush=True)
+    if world > 1:
+        dist.barrier()
+        dist.destroy_process_group()
+
+
+def kernel_hash() -> str:
+    import hashlib
+    h = hashlib.sha1()
+    for f in ("graph_kernels.cuh", "device_common.cuh"):
+        with open(os.path.join(ROOT, "paper_2003_04920_gb300", "csrc", f), "rb") as fh:
+            h.update(fh.read())
+    return h.hexdigest()[:12]
+
+
+def oracle_prefix(rm, seconds: float) -> dict:
+    """Serial policy iteration (the oracle, Alg. 2) on a prefix of the same
+    Batched-Extension schedule, block by block, until `seconds` have passed."""
+    import oracle as O
+    G = O.OracleGraph(rm.n)
+    relax = 0
+    blocks = 0
+    t_exploit = 0.0
+    t0 = time.perf_counter()
+    for v0, v1, e0, e1 in rm.blocks():
+        G.insert(v1 - v0, rm.u[e0:e1], rm.v[e0:e1], rm.cost[e0:e1].astype(np.float64))
+        t = time.perf_counter()
+        st = G.replan()
+        t_exploit += time.perf_counter() - t
+        relax += st["relaxations"]
+        blocks += 1
+        if time.perf_counter() - t0 > seconds:
+            break
+    G.close()
+    return dict(relax=relax, blocks=blocks, seconds=t_exploit, n_present=min(rm.n, blocks * rm.block))
+
+
+def cpu_baseline(rm, seconds: float) -> dict:
+    r = oracle_prefix(rm, seconds)
+    return {"value": round(r["relax"] / r["seconds"], 1), "unit": UNIT, "cores": 1,
+            "kind": "oracle",
+            "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
+            "sample": f"serial policy iteration (Alg. 2) on the first {r['blocks']} of "
+                      f"{rm.n_blocks()} blocks of the same schedule ({r['n_present']} vertices), "
+                      f"Improve sweeping every vertex each round; {r['relax']} relaxations "
+                      f"in {r['seconds']:.2f} s"}
+
+
+def run_reference(args) -> None:
+    world = int(os.environ.get("WORLD_SIZE", "1"))
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return
+    rm = load_roadmap(args.workload, args.n, args.block, args.trial)
+    per_step = args.cpu_seconds
+    for _ in range(args.warmup):
+        oracle_prefix(rm, per_step / 4)
+    relax, secs, blocks = 0, 0.0, 0
+    for _ in range(args.steps):
+        r = oracle_prefix(rm, per_step)
+        relax += r["relax"]
+        secs += r["seconds"]
+        blocks += r["blocks"]
+    value = relax / secs
+    line = {
+        "impl": "reference", "metric": METRIC, "value": round(value, 1), "unit": UNIT,
+        "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": round(1e3 * secs / args.steps, 3),
+        "ms_per_batch": round(1e3 * secs / blocks, 3),
+        "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+        "data": "synthetic (seeded roadmap generator)",
+        "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][1]}",
+                   "vertices": rm.n, "undirected_edges": rm.m},
+        "cpu_baseline": {"value": round(value, 1), "unit": UNIT, "cores": 1, "kind": "oracle",
+                         "sample": f"each step: serial policy iteration (Alg. 2) on the first "
+                                   f"blocks of the schedule for ~{per_step:.0f} s "
+                                   f"({blocks / args.steps:.1f} blocks per step)"},
+        "e2e": {"value": round(value, 1), "unit": UNIT, "h2d_bytes_per_step": 0,
+                "d2h_bytes_per_step": 0},
+    }
+    print(json.dumps(line), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=3)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS), default="c3")
+    ap.add_argument("--n", type=int, default=None, help="override the vertex count")
+    ap.add_argument("--block", type=int, default=None, help="override the block size S")
+    ap.add_argument("--trial", type=int, default=0)
+    ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--dense-fraction", type=float, default=0.0)
+    ap.add_argument("--cpu-seconds", type=float, default=15.0)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        run_reference(args)
+    else:
+        run_ours(args)
+
+
+if __name__ == "__main__":
+    main()

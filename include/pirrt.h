@@ -1,0 +1,201 @@
+/*
+ * pirrt.h -- C ABI of the GB300 exploitation path of PI-RRT#
+ * (Policy Iteration RRT#, Lawson, Wills and Tsiotras, "GPU Parallelization
+ * of Policy Iteration RRT#").
+ *
+ * Problem (Sec. III): an undirected graph G = (V, E) with positive edge
+ * costs c : E -> R+, a root x_init, a policy pi : V -> E (each vertex's
+ * parent edge) and the cost-to-come g_pi : V -> R+ along the policy tree.
+ * The library keeps G, pi and g resident on one GPU and runs
+ *   - Batched-Extension insertion of a block of vertices and edges (Alg. 3;
+ *     Sec. IV-A, the edge list is merged into a CSR on the device),
+ *   - Replan (Alg. 2): Improve (every vertex re-selects its parent as the
+ *     argmin over neighbours u of g(u) + c(u, v)) and Evaluate (recompute g
+ *     under the new parent tree), repeated until no parent changes.
+ *
+ * Conventions shared by every entry point:
+ *   - Vertex ids are dense int32: insert_batch appends ids [n, n + n_new).
+ *     The root is fixed at create time; g(root) = 0.
+ *   - Edges are undirected: one (src, dst, cost) triple is stored in both
+ *     directions.  Parallel edges are allowed; the cheapest one wins.
+ *   - Costs are FP32 or FP64 (pirrt_config.cost_dtype); g is always FP64.
+ *   - Pointers flagged "on_device" are CUDA device pointers (any allocator,
+ *     e.g. PyTorch's); otherwise they are host pointers.  The caller owns
+ *     every buffer it passes; the library reads inputs before the call
+ *     returns and never retains caller pointers.
+ *   - All device work is ordered on the stream given at create time
+ *     (NULL = legacy default stream).  Calls that return results to the
+ *     host (exploit, get_*) synchronise that stream before returning.
+ *   - Errors are returned as pirrt_status; no exception crosses the ABI.
+ *     Device kernels report errors through a status word, never by trapping.
+ *     pirrt_graph_last_error() gives a human-readable detail string.
+ *   - A handle is not thread-safe; the caller serialises calls on it.
+ */
+#ifndef PIRRT_H
+#define PIRRT_H
+
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef enum {
+    PIRRT_OK = 0,
+    PIRRT_ERR_INVALID_ARG = 1,     /* NULL handle/pointer, negative size, bad option */
+    PIRRT_ERR_CAPACITY = 2,        /* max_vertices or max_edges would be exceeded */
+    PIRRT_ERR_OOM = 3,             /* device or host allocation failed */
+    PIRRT_ERR_CUDA = 4,            /* a CUDA runtime call failed */
+    PIRRT_ERR_NOT_CONVERGED = 5,   /* max_iters Improve rounds ran with parents still switching */
+    PIRRT_ERR_DEVICE_TIMEOUT = 6,  /* a device-side wait ran out (grid barrier) */
+    PIRRT_ERR_BAD_INPUT = 7,       /* id out of range, self loop, cost <= 0 / NaN / Inf,
+                                      or a policy edge that is not in G */
+    PIRRT_ERR_BAD_TREE = 8         /* parent pointers contain a cycle */
+} pirrt_status;
+
+enum { PIRRT_COST_F32 = 0, PIRRT_COST_F64 = 1 };
+
+/* Fixed at create time. */
+typedef struct {
+    int64_t max_vertices;  /* capacity of V */
+    int64_t max_edges;     /* capacity of E in undirected edges (each uses two CSR entries) */
+    int32_t root;          /* x_init, in [0, max_vertices) */
+    int32_t cost_dtype;    /* PIRRT_COST_F32 or PIRRT_COST_F64 */
+    int32_t device;        /* CUDA device ordinal */
+    int32_t reserved;
+    void *stream;          /* cudaStream_t for all work; NULL = legacy default stream */
+} pirrt_config;
+
+/* Per exploit call.  Zero-initialised gives the defaults. */
+typedef struct {
+    double eps;             /* Replan stops once Delta g <= eps (Alg. 2); 0 = until no
+                               parent switches */
+    int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
+    int32_t group;          /* threads per vertex in Improve: 0 = tuned, else 4, 8, 16 or 32 */
+    double dense_fraction;  /* frontier size, as a fraction of |V|, above which the next
+                               Improve sweeps every vertex instead of a list; 0 = tuned */
+} pirrt_exploit_opts;
+
+/* Filled by pirrt_graph_exploit. */
+typedef struct {
+    int32_t iterations;     /* Improve rounds run (the last one switched nothing if converged) */
+    int32_t converged;      /* 1 if the policy is stable */
+    int64_t relaxations;    /* adjacency entries scanned by Improve, i.e. candidates g(u)+c(u,v) */
+    int64_t improved;       /* vertices processed by Improve, summed over rounds */
+    int64_t switches;       /* parent switches, summed over rounds */
+    int64_t evaluated;      /* vertices whose g Evaluate recomputed, summed over rounds */
+    int32_t jump_rounds;    /* pointer-jumping rounds, summed over Evaluate calls */
+    int32_t dense_sweeps;   /* Improve rounds that swept every vertex */
+    float ms_exploit;       /* device time of the call, CUDA events on the graph's stream */
+    float reserved;
+} pirrt_exploit_stats;
+
+typedef struct pirrt_graph pirrt_graph;   /* opaque, library-owned */
+
+/* Allocate an empty graph (no vertices) with the given capacities on
+ * cfg->device.  Device memory: about 2 x 8 B x (max_vertices + 1) row offsets,
+ * 2 x (8 or 16 B) x 2 x max_edges CSR entries, and about 80 B per vertex of
+ * policy and work arrays.  *out is set to NULL on failure. */
+pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out);
+
+/* Free every allocation of the handle (NULL is ignored). */
+void pirrt_graph_destroy(pirrt_graph *g);
+
+/* Drop every vertex and edge, keeping the allocations. */
+pirrt_status pirrt_graph_reset(pirrt_graph *g);
+
+/* Batched-Extension insertion (Alg. 3 "repeat S times: Extend"; Sec. IV-A:
+ * new edges arrive as a coordinate list and are merged into the device CSR
+ * once per Replan).  Appends n_new_vertices vertices (ids n .. n+n_new-1;
+ * g = +inf and no parent, except g(root) = 0) and n_edges undirected edges
+ * src[e] -- dst[e] with cost[e] (float or double per cost_dtype).  Endpoints
+ * may be old or new vertices.  The new vertices and the endpoints of the
+ * new edges seed the next exploit's Improve frontier.
+ * Errors: PIRRT_ERR_CAPACITY, PIRRT_ERR_BAD_INPUT (ids outside
+ * [0, n + n_new), src == dst, cost <= 0, NaN or Inf); on error the graph is
+ * unchanged.  Synchronises the stream once to read the validation result. */
+pirrt_status pirrt_graph_insert_batch(pirrt_graph *g, int64_t n_new_vertices, int64_t n_edges,
+                                      const int32_t *src, const int32_t *dst, const void *cost,
+                                      int on_device);
+
+/* Replace the policy: parent[v] for v in [0, n) (-1 = none; parent[root]
+ * must be -1), n = current vertex count.  Each parent edge must exist; its
+ * cost is the cheapest parallel edge.  Evaluates g under the new policy
+ * (Alg. 2 Evaluate) and makes the next Improve sweep every vertex.
+ * Errors: PIRRT_ERR_INVALID_ARG (n mismatch), PIRRT_ERR_BAD_INPUT,
+ * PIRRT_ERR_BAD_TREE (the parents contain a cycle). */
+pirrt_status pirrt_graph_set_policy(pirrt_graph *g, const int32_t *parent, int64_t n,
+                                    int on_device);
+
+/* Replan (Alg. 2): loop { Improve; stop if no parent switched (Delta g <=
+ * eps); Evaluate }.  Improve is a Jacobi sweep: each vertex v != root takes
+ * the lexicographic minimum over its neighbours u of (g(u) + c(u, v), u)
+ * and switches to it only if that value is strictly below g(p(v)) +
+ * c(p(v), v) computed the same way, so a current parent attaining the
+ * minimum is kept and otherwise the lowest id wins.  Only vertices with a
+ * neighbour whose g changed (or seeded by insertion) are re-examined.
+ * Evaluate recomputes g(v) = g(p(v)) + c(p(v), v) from the root by pointer
+ * jumping in FP64.  Blocks until done; stats may be NULL.
+ * Errors: PIRRT_ERR_NOT_CONVERGED (max_iters reached; the state stays
+ * consistent and exploit may be called again), PIRRT_ERR_BAD_TREE,
+ * PIRRT_ERR_DEVICE_TIMEOUT, PIRRT_ERR_CUDA. */
+pirrt_status pirrt_graph_exploit(pirrt_graph *g, const pirrt_exploit_opts *opts,
+                                 pirrt_exploit_stats *stats);
+
+/* Copy g (FP64, +inf for vertices not connected to the root) into g_out[0..n),
+ * n = current vertex count.  Synchronises the stream. */
+pirrt_status pirrt_graph_get_costs(const pirrt_graph *g, double *g_out, int64_t n, int on_device);
+
+/* Copy the parents (-1 for the root and for unreached vertices) into
+ * p_out[0..n), n = current vertex count.  This is the tree E' = {pi(v)} that
+ * Alg. 1 and Alg. 3 output.  Synchronises the stream. */
+pirrt_status pirrt_graph_get_parents(const pirrt_graph *g, int32_t *p_out, int64_t n,
+                                     int on_device);
+
+/* Copy the device CSR: row_off[0..n] (int64), col[0..m) (int32) and
+ * cost[0..m) (float or double), m = pirrt_graph_num_entries().  Entries of
+ * a row are in no particular order.  Any output pointer may be NULL. */
+pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *g, int64_t *row_off, int32_t *col,
+                                       void *cost, int on_device);
+
+/* Per-kernel accounting of one handle (tracing).  Launch counts are always
+ * kept; device times are measured with CUDA events on the handle's stream
+ * only while profiling is enabled.  Work units let a caller turn times into
+ * bandwidth: Improve scanned `improve_entries` CSR entries over
+ * `improve_vertices` vertices (of which `improve_dense_vertices` in dense
+ * sweeps) and switched `improve_switches` parents; Evaluate finished
+ * `evaluate_vertices` vertices in `evaluate_visits` work-list visits;
+ * insertion wrote `insert_new_entries` new and copied `insert_copied_entries`
+ * old CSR entries. */
+typedef struct {
+    int64_t launches;             /* every kernel launch of this handle */
+    int64_t improve_launches, evaluate_launches, mark_launches, insert_calls;
+    double improve_ms, evaluate_ms, mark_ms, insert_ms;
+    int64_t improve_entries, improve_vertices, improve_dense_vertices, improve_switches;
+    int64_t evaluate_vertices, evaluate_visits, mark_vertices;
+    int64_t insert_new_entries, insert_copied_entries;
+} pirrt_profile;
+
+/* Clear the profile and turn event timing on (enable = 1) or off (0). */
+pirrt_status pirrt_graph_set_profiling(pirrt_graph *g, int enable);
+
+/* Copy the profile accumulated since the last pirrt_graph_set_profiling. */
+pirrt_status pirrt_graph_get_profile(const pirrt_graph *g, pirrt_profile *out);
+
+/* Current vertex count, or -1 for a NULL handle. */
+int64_t pirrt_graph_num_vertices(const pirrt_graph *g);
+
+/* Current number of directed CSR entries (2 per undirected edge), or -1. */
+int64_t pirrt_graph_num_entries(const pirrt_graph *g);
+
+/* Detail of the last error on this handle ("" if none). */
+const char *pirrt_graph_last_error(const pirrt_graph *g);
+
+/* Static name of a status code. */
+const char *pirrt_status_string(pirrt_status s);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PIRRT_H */

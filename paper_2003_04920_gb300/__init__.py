@@ -1,0 +1,279 @@
+"""GB300 exploitation path of PI-RRT# (Policy Iteration RRT#).
+
+A thin ctypes binding over the C ABI declared in ``include/pirrt.h``
+(``libpirrt.so``, hand-written sm_103a CUDA kernels).  The functions keep the
+C names (``pirrt_graph_create`` ... ``pirrt_graph_get_parents``) and only
+marshal arguments: every step of insertion, Improve and Evaluate runs in the
+library's kernels.  There is no CPU fallback: if the library is not built,
+loading fails loudly.
+
+:class:`Graph` wraps a handle for Python callers.  Device buffers may be
+PyTorch CUDA tensors (PyTorch supplies device memory and the stream); host
+buffers are NumPy arrays.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+_HERE = os.path.dirname(os.path.abspath(__file__))
+LIB_PATH = os.path.join(_HERE, "libpirrt.so")
+
+PIRRT_OK = 0
+PIRRT_ERR_INVALID_ARG = 1
+PIRRT_ERR_CAPACITY = 2
+PIRRT_ERR_OOM = 3
+PIRRT_ERR_CUDA = 4
+PIRRT_ERR_NOT_CONVERGED = 5
+PIRRT_ERR_DEVICE_TIMEOUT = 6
+PIRRT_ERR_BAD_INPUT = 7
+PIRRT_ERR_BAD_TREE = 8
+PIRRT_COST_F32 = 0
+PIRRT_COST_F64 = 1
+
+
+class pirrt_config(ctypes.Structure):
+    _fields_ = [("max_vertices", ctypes.c_int64), ("max_edges", ctypes.c_int64),
+                ("root", ctypes.c_int32), ("cost_dtype", ctypes.c_int32),
+                ("device", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("stream", ctypes.c_void_p)]
+
+
+class pirrt_exploit_opts(ctypes.Structure):
+    _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int32),
+                ("group", ctypes.c_int32), ("dense_fraction", ctypes.c_double)]
+
+
+class pirrt_exploit_stats(ctypes.Structure):
+    _fields_ = [("iterations", ctypes.c_int32), ("converged", ctypes.c_int32),
+                ("relaxations", ctypes.c_int64), ("improved", ctypes.c_int64),
+                ("switches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
+                ("jump_rounds", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
+                ("ms_exploit", ctypes.c_float), ("reserved", ctypes.c_float)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+
+
+class pirrt_profile(ctypes.Structure):
+    _fields_ = [("launches", ctypes.c_int64), ("improve_launches", ctypes.c_int64),
+                ("evaluate_launches", ctypes.c_int64), ("mark_launches", ctypes.c_int64),
+                ("insert_calls", ctypes.c_int64), ("improve_ms", ctypes.c_double),
+                ("evaluate_ms", ctypes.c_double), ("mark_ms", ctypes.c_double),
+                ("insert_ms", ctypes.c_double), ("improve_entries", ctypes.c_int64),
+                ("improve_vertices", ctypes.c_int64), ("improve_dense_vertices", ctypes.c_int64),
+                ("improve_switches", ctypes.c_int64), ("evaluate_vertices", ctypes.c_int64),
+                ("evaluate_visits", ctypes.c_int64), ("mark_vertices", ctypes.c_int64),
+                ("insert_new_entries", ctypes.c_int64), ("insert_copied_entries", ctypes.c_int64)]
+
+    def as_dict(self) -> dict:
+        return {name: getattr(self, name) for name, _ in self._fields_}
+
+
+_lib = None
+
+
+def load_library(path: str = LIB_PATH):
+    """Load libpirrt.so (raises if it has not been built)."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    if not os.path.exists(path):
+        raise RuntimeError(
+            f"CUDA library {path} is missing: build it with "
+            "`python -c 'import __graft_entry__ as g; g.build()'` (no CPU fallback exists)")
+    lib = ctypes.CDLL(path)
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int
+    st = ctypes.c_int
+    sig = {
+        "pirrt_graph_create": (st, [ctypes.POINTER(pirrt_config), ctypes.POINTER(vp)]),
+        "pirrt_graph_destroy": (None, [vp]),
+        "pirrt_graph_reset": (st, [vp]),
+        "pirrt_graph_insert_batch": (st, [vp, i64, i64, vp, vp, vp, i32]),
+        "pirrt_graph_set_policy": (st, [vp, vp, i64, i32]),
+        "pirrt_graph_exploit": (st, [vp, ctypes.POINTER(pirrt_exploit_opts),
+                                     ctypes.POINTER(pirrt_exploit_stats)]),
+        "pirrt_graph_get_costs": (st, [vp, vp, i64, i32]),
+        "pirrt_graph_get_parents": (st, [vp, vp, i64, i32]),
+        "pirrt_graph_get_adjacency": (st, [vp, vp, vp, vp, i32]),
+        "pirrt_graph_set_profiling": (st, [vp, i32]),
+        "pirrt_graph_get_profile": (st, [vp, ctypes.POINTER(pirrt_profile)]),
+        "pirrt_graph_num_vertices": (i64, [vp]),
+        "pirrt_graph_num_entries": (i64, [vp]),
+        "pirrt_graph_last_error": (ctypes.c_char_p, [vp]),
+        "pirrt_status_string": (ctypes.c_char_p, [st]),
+    }
+    for name, (res, args) in sig.items():
+        fn = getattr(lib, name)
+        fn.restype = res
+        fn.argtypes = args
+    _lib = lib
+    return lib
+
+
+class PirrtError(RuntimeError):
+    def __init__(self, call: str, status: int, detail: str = ""):
+        lib = load_library()
+        name = lib.pirrt_status_string(status).decode()
+        super().__init__(f"{call}: {name}" + (f" ({detail})" if detail else ""))
+        self.status = status
+
+
+def _buf(x, dtype):
+    """(pointer, on_device, keepalive) for a torch tensor or array-like."""
+    if hasattr(x, "data_ptr") and hasattr(x, "is_cuda"):
+        assert x.is_contiguous(), "tensor must be contiguous"
+        if x.is_cuda:
+            return x.data_ptr(), 1, x
+        x = x.numpy()
+    a = np.ascontiguousarray(x, dtype=dtype)
+    return a.ctypes.data, 0, a
+
+
+def _current_stream_ptr(device: int):
+    try:
+        import torch
+        if torch.cuda.is_available():
+            return torch.cuda.current_stream(device).cuda_stream
+    except ImportError:
+        pass
+    return None
+
+
+class Graph:
+    """One planning graph resident on a GPU (wraps a ``pirrt_graph*``)."""
+
+    def __init__(self, max_vertices: int, max_edges: int, root: int = 0,
+                 cost_dtype=np.float32, device: int = 0, stream=None):
+        self._lib = load_library()
+        self.cost_dtype = np.dtype(cost_dtype)
+        if self.cost_dtype not in (np.float32, np.float64):
+            raise ValueError("cost_dtype must be float32 or float64")
+        if stream is None:
+            stream = _current_stream_ptr(device)
+        cfg = pirrt_config(int(max_vertices), int(max_edges), int(root),
+                           PIRRT_COST_F32 if self.cost_dtype == np.float32 else PIRRT_COST_F64,
+                           int(device), 0, stream)
+        h = ctypes.c_void_p()
+        rc = self._lib.pirrt_graph_create(ctypes.byref(cfg), ctypes.byref(h))
+        if rc:
+            raise PirrtError("pirrt_graph_create", rc)
+        self._h = h
+        self.root = int(root)
+        self.device = int(device)
+
+    def _check(self, call: str, rc: int):
+        if rc:
+            detail = self._lib.pirrt_graph_last_error(self._h).decode()
+            raise PirrtError(call, rc, detail)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pirrt_graph_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    @property
+    def n(self) -> int:
+        return int(self._lib.pirrt_graph_num_vertices(self._h))
+
+    @property
+    def m(self) -> int:
+        return int(self._lib.pirrt_graph_num_entries(self._h))
+
+    def reset(self):
+        self._check("pirrt_graph_reset", self._lib.pirrt_graph_reset(self._h))
+
+    def insert_batch(self, n_new: int, src, dst, cost):
+        ps, ds, ks = _buf(src, np.int32)
+        pd, dd, kd = _buf(dst, np.int32)
+        pc, dc, kc = _buf(cost, self.cost_dtype)
+        if not (ds == dd == dc):
+            raise ValueError("src, dst and cost must all be host or all be device buffers")
+        n_edges = len(ks) if ds == 0 else ks.numel()
+        rc = self._lib.pirrt_graph_insert_batch(self._h, int(n_new), int(n_edges), ps, pd, pc, ds)
+        self._check("pirrt_graph_insert_batch", rc)
+
+    def set_policy(self, parent):
+        pp, dev, keep = _buf(parent, np.int32)
+        n = len(keep) if dev == 0 else keep.numel()
+        self._check("pirrt_graph_set_policy",
+                    self._lib.pirrt_graph_set_policy(self._h, pp, int(n), dev))
+
+    def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0,
+                dense_fraction: float = 0.0, check: bool = True) -> dict:
+        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group), float(dense_fraction))
+        st = pirrt_exploit_stats()
+        rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))
+        out = st.as_dict()
+        out["status"] = int(rc)
+        if check:
+            self._check("pirrt_graph_exploit", rc)
+        return out
+
+    def set_profiling(self, enable: bool = True):
+        self._check("pirrt_graph_set_profiling",
+                    self._lib.pirrt_graph_set_profiling(self._h, 1 if enable else 0))
+
+    def get_profile(self) -> dict:
+        pr = pirrt_profile()
+        self._check("pirrt_graph_get_profile",
+                    self._lib.pirrt_graph_get_profile(self._h, ctypes.byref(pr)))
+        return pr.as_dict()
+
+    def get_costs(self, out=None) -> np.ndarray:
+        n = self.n
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        p, dev, keep = _buf(out, np.float64)
+        self._check("pirrt_graph_get_costs", self._lib.pirrt_graph_get_costs(self._h, p, n, dev))
+        return out
+
+    def get_parents(self, out=None) -> np.ndarray:
+        n = self.n
+        if out is None:
+            out = np.empty(n, dtype=np.int32)
+        p, dev, keep = _buf(out, np.int32)
+        self._check("pirrt_graph_get_parents",
+                    self._lib.pirrt_graph_get_parents(self._h, p, n, dev))
+        return out
+
+    def get_adjacency(self):
+        n, m = self.n, self.m
+        off = np.empty(n + 1, dtype=np.int64)
+        col = np.empty(m, dtype=np.int32)
+        cost = np.empty(m, dtype=self.cost_dtype)
+        self._check("pirrt_graph_get_adjacency",
+                    self._lib.pirrt_graph_get_adjacency(self._h, off.ctypes.data, col.ctypes.data,
+                                                        cost.ctypes.data, 0))
+        return off, col, cost
+
+
+def pirrt_status_string(status: int) -> str:
+    return load_library().pirrt_status_string(int(status)).decode()
+
+
+def run_schedule(graph: Graph, roadmap, block: int | None = None, on_device_inputs=None,
+                 **exploit_kw) -> list[dict]:
+    """Batched-Extension schedule (Alg. 3): for each block, insert its
+    vertices and edges, then exploit to convergence.  ``on_device_inputs``
+    may hold (u, v, cost) device tensors of the whole roadmap."""
+    stats = []
+    for v0, v1, e0, e1 in roadmap.blocks(block):
+        if on_device_inputs is not None:
+            u, v, c = on_device_inputs
+            graph.insert_batch(v1 - v0, u[e0:e1], v[e0:e1], c[e0:e1])
+        else:
+            graph.insert_batch(v1 - v0, roadmap.u[e0:e1], roadmap.v[e0:e1], roadmap.cost[e0:e1])
+        stats.append(graph.exploit(**exploit_kw))
+    return stats

@@ -1,0 +1,129 @@
+// Device-side building blocks shared by the PI-RRT# kernels: CSR entry
+// layouts, streaming loads, warp-aggregated list appends, the bounded grid
+// barrier and the device counter block.
+#pragma once
+
+#include <cstdint>
+#include <cuda_runtime.h>
+
+namespace pirrt {
+
+// Status bits a kernel may raise (never a trap).
+constexpr unsigned kStatusBadInput = 1u;
+constexpr unsigned kStatusTimeout = 2u;
+constexpr unsigned kStatusBadTree = 4u;
+
+// A grid barrier gives up after this many polls (each followed by a short
+// sleep), i.e. well over a second: it then raises kStatusTimeout.
+constexpr unsigned long long kBarrierSpinLimit = 1ull << 25;
+
+// Evaluate stops pointer jumping after this many rounds: a parent chain of
+// length L finishes in about log2(L) + 1 rounds, so anything left over after
+// 40 rounds sits on a cycle.
+constexpr int kMaxJumpRounds = 40;
+
+// One adjacency entry of the device CSR.  FP32 costs pack (col, c) into 8 B
+// so one 8-byte load fetches both; FP64 costs use a 16 B entry.
+template <typename CT>
+struct Entry;
+template <>
+struct __align__(8) Entry<float> {
+    int32_t col;
+    float w;
+};
+template <>
+struct __align__(16) Entry<double> {
+    int32_t col;
+    int32_t pad;
+    double w;
+};
+
+// Streaming (evict-first) load of a CSR entry: each entry is read once per
+// sweep, so it should not displace g from L2.
+__device__ __forceinline__ Entry<float> ld_stream(const Entry<float> *p) {
+    int2 r = __ldcs(reinterpret_cast<const int2 *>(p));
+    Entry<float> e;
+    e.col = r.x;
+    e.w = __int_as_float(r.y);
+    return e;
+}
+__device__ __forceinline__ Entry<double> ld_stream(const Entry<double> *p) {
+    int4 r = __ldcs(reinterpret_cast<const int4 *>(p));
+    Entry<double> e;
+    e.col = r.x;
+    e.pad = 0;
+    e.w = __hiloint2double(r.w, r.z);
+    return e;
+}
+
+// Device counters of one graph.  The host copies the block back once per
+// Replan iteration.
+struct DevCounters {
+    unsigned long long relax;     // adjacency entries scanned by Improve (whole exploit)
+    unsigned long long improved;  // vertices processed by Improve (whole exploit)
+    unsigned long long evaluated; // vertices whose g was recomputed (whole exploit)
+    unsigned long long switches;  // parent switches (whole exploit)
+    unsigned long long dj_bits;   // Delta g of the current Improve (bits of a double >= 0)
+    unsigned n_active;            // size of the current Improve list
+    unsigned n_next;              // size of the list being built for the next Improve
+    unsigned n_switched;          // switches in the current iteration
+    unsigned n_dg;                // vertices whose g changed in the current Evaluate
+    unsigned rounds;              // pointer-jumping rounds of the current Evaluate
+    unsigned status;              // kStatus* bits
+    unsigned dense;               // current Improve sweeps every vertex
+    unsigned dense_next;          // next Improve sweeps every vertex
+    unsigned bar_count;           // grid barrier: arrivals
+    unsigned bar_gen;             // grid barrier: generation
+    unsigned pad[2];
+    unsigned wl_count[kMaxJumpRounds + 2];  // Evaluate work-list sizes per round
+};
+
+// Append `value` to `list` for every lane with `pred`, one atomic per warp.
+// Every lane of the warp must call this (warp-uniform control flow).
+__device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t *list,
+                                            unsigned *counter) {
+    const unsigned lane = threadIdx.x & 31u;
+    const unsigned ballot = __ballot_sync(0xffffffffu, pred);
+    if (ballot == 0u) return;
+    const int leader = __ffs(ballot) - 1;
+    unsigned base = 0;
+    if (lane == (unsigned)leader) base = atomicAdd(counter, (unsigned)__popc(ballot));
+    base = __shfl_sync(0xffffffffu, base, leader);
+    if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
+}
+
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
+// wait is bounded: on timeout the block raises kStatusTimeout and the
+// caller returns.  Returns false on timeout.
+__device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        volatile unsigned *gen = &c->bar_gen;
+        const unsigned my_gen = *gen;
+        __threadfence();
+        const unsigned prev = atomicAdd(&c->bar_count, 1u);
+        int ok = 1;
+        if (prev == nblocks - 1u) {
+            atomicExch(&c->bar_count, 0u);
+            __threadfence();
+            atomicAdd(&c->bar_gen, 1u);
+        } else {
+            unsigned long long spins = 0;
+            while (*gen == my_gen) {
+                if (++spins > kBarrierSpinLimit) {
+                    atomicOr(&c->status, kStatusTimeout);
+                    ok = 0;
+                    break;
+                }
+                __nanosleep(100);
+            }
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+}  // namespace pirrt

@@ -1,0 +1,570 @@
+// Kernels of the single-graph exploitation path of PI-RRT#:
+//   Batched-Extension insertion (Alg. 3; Sec. IV-A coordinate list merged
+//   into a device CSR), Improve (Alg. 2; Sec. IV-B), Evaluate (Alg. 2;
+//   Sec. IV-C) and the changed-vertex frontier.
+#pragma once
+
+#include <cfloat>
+#include <climits>
+#include <cmath>
+
+#include <math_constants.h>
+
+#include "device_common.cuh"
+
+namespace pirrt {
+
+constexpr int kThreads = 256;
+
+// ---------------------------------------------------------------------------
+// Insertion
+// ---------------------------------------------------------------------------
+
+// Validate the new undirected edges and count, per endpoint, how many CSR
+// entries the block adds.  Invalid input raises kStatusBadInput and is not
+// counted (the host then discards the whole block).
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+insert_validate_count(int64_t n_edges, const int32_t *__restrict__ src,
+                      const int32_t *__restrict__ dst, const CT *__restrict__ cost,
+                      int64_t n_after, int32_t *__restrict__ deg, DevCounters *ctr) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_edges;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        const double c = (double)cost[e];
+        const bool ok = a >= 0 && b >= 0 && a < n_after && b < n_after && a != b &&
+                        c > 0.0 && c <= DBL_MAX;  // rejects NaN, +inf, <= 0
+        if (!ok) {
+            atomicOr(&ctr->status, kStatusBadInput);
+            continue;
+        }
+        atomicAdd(&deg[a], 1);
+        atomicAdd(&deg[b], 1);
+    }
+}
+
+// Exclusive scan, first pass: one partial sum per tile of kScanTile entries.
+constexpr int kScanItems = 8;
+constexpr int kScanTile = kThreads * kScanItems;
+
+__device__ __forceinline__ long long block_exclusive_scan(long long x, long long *total) {
+    __shared__ long long warp_sums[kThreads / 32];
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    long long incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        long long y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) warp_sums[warp] = incl;
+    __syncthreads();
+    if (warp == 0) {
+        long long w = (lane < kThreads / 32) ? warp_sums[lane] : 0;
+#pragma unroll
+        for (int off = 1; off < 32; off <<= 1) {
+            long long y = __shfl_up_sync(0xffffffffu, w, off);
+            if (lane >= off) w += y;
+        }
+        if (lane < kThreads / 32) warp_sums[lane] = w;  // inclusive over warps
+    }
+    __syncthreads();
+    const long long warp_base = warp > 0 ? warp_sums[warp - 1] : 0;
+    *total = warp_sums[kThreads / 32 - 1];
+    __syncthreads();
+    return warp_base + incl - x;
+}
+
+__global__ void __launch_bounds__(kThreads)
+scan_tile_reduce(const int32_t *__restrict__ deg, int64_t len, long long *__restrict__ tile_sums) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i)
+        if (base + i < len) s += deg[base + i];
+    long long total;
+    block_exclusive_scan(s, &total);
+    if (threadIdx.x == 0) tile_sums[blockIdx.x] = total;
+}
+
+// Second pass: exclusive scan of the tile sums in one block.
+__global__ void __launch_bounds__(kThreads)
+scan_tile_sums(long long *__restrict__ tile_sums, int64_t n_tiles) {
+    __shared__ long long carry;
+    if (threadIdx.x == 0) carry = 0;
+    __syncthreads();
+    for (int64_t b = 0; b < n_tiles; b += kThreads) {
+        const int64_t i = b + threadIdx.x;
+        const long long x = i < n_tiles ? tile_sums[i] : 0;
+        long long total;
+        const long long ex = block_exclusive_scan(x, &total);
+        if (i < n_tiles) tile_sums[i] = carry + ex;
+        __syncthreads();
+        if (threadIdx.x == 0) carry += total;
+        __syncthreads();
+    }
+}
+
+// Third pass: new_off[v] = old_off[min(v, n_old)] + (entries added to rows < v).
+// len = n_after + 1 and deg[n_after] = 0, so new_off[n_after] is the new total.
+__global__ void __launch_bounds__(kThreads)
+scan_tile_apply(const int32_t *__restrict__ deg, int64_t len,
+                const long long *__restrict__ tile_sums, const int64_t *__restrict__ old_off,
+                int64_t n_old, int64_t *__restrict__ new_off) {
+    const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
+    long long v[kScanItems];
+    long long s = 0;
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        v[i] = (base + i < len) ? deg[base + i] : 0;
+        s += v[i];
+    }
+    long long total;
+    long long run = block_exclusive_scan(s, &total) + tile_sums[blockIdx.x];
+#pragma unroll
+    for (int i = 0; i < kScanItems; ++i) {
+        const int64_t x = base + i;
+        if (x < len) new_off[x] = old_off[x < n_old ? x : n_old] + run;
+        run += v[i];
+    }
+}
+
+// Copy every old row to its new position (the new row keeps its old entries
+// first).  One warp per row.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+insert_copy_rows(int64_t n_old, const int64_t *__restrict__ old_off,
+                 const Entry<CT> *__restrict__ old_adj, const int64_t *__restrict__ new_off,
+                 Entry<CT> *__restrict__ new_adj) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n_old;
+         v += warps) {
+        const int64_t b = old_off[v], e = old_off[v + 1], dst = new_off[v];
+        for (int64_t i = b + lane; i < e; i += 32) new_adj[dst + (i - b)] = ld_stream(&old_adj[i]);
+    }
+}
+
+// Place both directions of every new edge at the tail of its rows (filled
+// from the row end, order within a row is irrelevant) and seed the next
+// Improve frontier with both endpoints.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
+               const CT *__restrict__ cost, const int64_t *__restrict__ new_off,
+               int32_t *__restrict__ deg, Entry<CT> *__restrict__ adj, unsigned *__restrict__ stamp,
+               unsigned epoch, int32_t root, int32_t *__restrict__ active, DevCounters *ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_edges; base += stride) {
+        const int64_t e = base + threadIdx.x;
+        bool pa = false, pb = false;
+        int32_t a = 0, b = 0;
+        if (e < n_edges) {
+            a = src[e];
+            b = dst[e];
+            const CT w = cost[e];
+            const int64_t sa = new_off[a + 1] - atomicSub(&deg[a], 1);
+            const int64_t sb = new_off[b + 1] - atomicSub(&deg[b], 1);
+            Entry<CT> ea{}, eb{};
+            ea.col = b;
+            ea.w = w;
+            eb.col = a;
+            eb.w = w;
+            adj[sa] = ea;
+            adj[sb] = eb;
+            pa = a != root && atomicExch(&stamp[a], epoch) != epoch;
+            pb = b != root && atomicExch(&stamp[b], epoch) != epoch;
+        }
+        warp_append(pa, a, active, &ctr->n_active);
+        warp_append(pb, b, active, &ctr->n_active);
+    }
+}
+
+// Seed the new vertices: g = +inf (0 for the root), no parent, and put them
+// on the next Improve frontier.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__restrict__ g,
+                     int32_t *__restrict__ p, CT *__restrict__ pc, unsigned *__restrict__ stamp,
+                     unsigned epoch, int32_t *__restrict__ active, DevCounters *ctr) {
+    const int64_t stride = (int64_t)gridDim.x * blockDim.x;
+    for (int64_t base = n_old + (int64_t)blockIdx.x * blockDim.x; base < n_after; base += stride) {
+        const int64_t v = base + threadIdx.x;
+        bool pred = false;
+        if (v < n_after) {
+            g[v] = (v == root) ? 0.0 : CUDART_INF;
+            p[v] = -1;
+            pc[v] = CT(0);
+            pred = v != root && atomicExch(&stamp[v], epoch) != epoch;
+        }
+        warp_append(pred, (int32_t)v, active, &ctr->n_active);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Improve (Alg. 2; Sec. IV-B) -- Jacobi relaxation, G threads per vertex.
+// ---------------------------------------------------------------------------
+
+// Candidate order: smaller value, then smaller id, then smaller cost (parallel
+// edges).  The order is total, so the result does not depend on scan order.
+template <typename CT>
+__device__ __forceinline__ bool cand_less(double v1, int32_t u1, CT w1, double v2, int32_t u2,
+                                          CT w2) {
+    return v1 < v2 || (v1 == v2 && (u1 < u2 || (u1 == u2 && w1 < w2)));
+}
+
+template <typename CT>
+struct ImproveArgs {
+    const int64_t *row_off;
+    const Entry<CT> *adj;
+    const double *g;
+    int32_t *p;
+    CT *pc;
+    const int32_t *active;
+    int32_t *switched;  // list of vertices whose parent changed
+    DevCounters *ctr;
+    int64_t n;
+    int32_t root;
+};
+
+// G lanes cooperate on one vertex: each lane scans every G-th entry of the
+// row, four entries in flight at a time (loads first, then the g gathers),
+// then the group reduces (value, id, cost) lexicographically with shuffles.
+// Lane 0 compares the winner with the current parent's candidate, computed
+// by the same expression g(p) + c, and switches only on a strict decrease.
+template <typename CT, int G>
+__global__ void __launch_bounds__(kThreads)
+improve_kernel(ImproveArgs<CT> a) {
+    constexpr int kUnroll = 4;
+    const int lane_g = threadIdx.x & (G - 1);
+    const unsigned group_mask =
+        G == 32 ? 0xffffffffu : (((1u << G) - 1u) << ((threadIdx.x & 31) & ~(G - 1)));
+    const int groups_per_block = kThreads / G;
+    const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
+    const bool dense = a.ctr->dense != 0u;
+    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
+
+    unsigned long long relax = 0, improved = 0;
+    for (int64_t item = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G; item < count;
+         item += gstride) {
+        const int32_t v = dense ? (int32_t)item : a.active[item];
+        if (v == a.root) continue;  // uniform within the group
+        const int64_t b = a.row_off[v], e = a.row_off[v + 1];
+        double best = CUDART_INF;
+        int32_t bu = INT_MAX;
+        CT bw = CT(0);
+        for (int64_t i0 = b + lane_g; i0 < e; i0 += (int64_t)G * kUnroll) {
+            Entry<CT> en[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * G;
+                if (i < e) en[k] = ld_stream(&a.adj[i]);
+            }
+            double gv[kUnroll];
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * G;
+                gv[k] = (i < e) ? __ldg(&a.g[en[k].col]) : CUDART_INF;
+            }
+#pragma unroll
+            for (int k = 0; k < kUnroll; ++k) {
+                const int64_t i = i0 + (int64_t)k * G;
+                if (i < e) {
+                    const double cand = gv[k] + (double)en[k].w;
+                    if (cand_less(cand, en[k].col, en[k].w, best, bu, bw)) {
+                        best = cand;
+                        bu = en[k].col;
+                        bw = en[k].w;
+                    }
+                }
+            }
+        }
+#pragma unroll
+        for (int off = G / 2; off > 0; off >>= 1) {
+            const double ob = __shfl_xor_sync(group_mask, best, off, G);
+            const int32_t ou = __shfl_xor_sync(group_mask, bu, off, G);
+            const CT ow = __shfl_xor_sync(group_mask, bw, off, G);
+            if (cand_less(ob, ou, ow, best, bu, bw)) {
+                best = ob;
+                bu = ou;
+                bw = ow;
+            }
+        }
+        if (lane_g == 0) {
+            const int32_t pv = a.p[v];
+            const double cur = pv >= 0 ? a.g[pv] + (double)a.pc[v] : CUDART_INF;
+            if (best < cur) {
+                a.p[v] = bu;
+                a.pc[v] = bw;
+                const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
+                a.switched[slot] = v;
+                // Delta g = max over switches of cur - best (> 0, or +inf for a
+                // vertex reached for the first time); non-negative doubles order
+                // like their bit patterns
+                atomicMax(&a.ctr->dj_bits, (unsigned long long)__double_as_longlong(cur - best));
+            }
+            relax += (unsigned long long)(e - b);
+            improved += 1;
+        }
+    }
+    // block totals -> one atomic per block
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        relax += __shfl_down_sync(0xffffffffu, relax, off);
+        improved += __shfl_down_sync(0xffffffffu, improved, off);
+    }
+    __shared__ unsigned long long s_relax[kThreads / 32], s_imp[kThreads / 32];
+    if ((threadIdx.x & 31) == 0) {
+        s_relax[threadIdx.x >> 5] = relax;
+        s_imp[threadIdx.x >> 5] = improved;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long r = 0, m = 0;
+        for (int w = 0; w < kThreads / 32; ++w) {
+            r += s_relax[w];
+            m += s_imp[w];
+        }
+        if (r) atomicAdd(&a.ctr->relax, r);
+        if (m) atomicAdd(&a.ctr->improved, m);
+    }
+}
+
+// ---------------------------------------------------------------------------
+// Evaluate (Alg. 2; Sec. IV-C) -- g(v) = g(p(v)) + c(p(v), v) from the root,
+// by pointer jumping over the parent tree in FP64.
+// ---------------------------------------------------------------------------
+
+template <typename CT>
+struct EvaluateArgs {
+    const int32_t *p;
+    const CT *pc;
+    double *g;
+    int32_t *anc[2];  // current ancestor of each unfinished vertex
+    double *acc[2];   // sum of policy-edge costs from the vertex up to anc
+    int32_t *done;    // round in which the vertex's g became final
+    int32_t *wl[2];   // work lists of unfinished vertices
+    int32_t *dg;      // vertices whose g changed
+    DevCounters *ctr;
+    int64_t n;
+    int32_t root;
+    int32_t force;    // run even if Improve switched nothing
+};
+
+// Rounds are separated by a grid barrier.  Round 0 links every vertex to its
+// parent.  In round r an unfinished vertex w with ancestor a either finishes,
+// if a's g became final in an earlier round (g(w) = acc(w) + g(a)), or
+// jumps: acc(w) += acc(a), anc(w) = anc(a).  Every value read in round r was
+// written before round r, so the sums, hence g, do not depend on scheduling.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+evaluate_kernel(EvaluateArgs<CT> a) {
+    DevCounters *c = a.ctr;
+    if (!a.force && c->n_switched == 0u) return;
+    const unsigned nblocks = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t wstride = (int64_t)gridDim.x * kThreads;
+    const int64_t tid0 = (int64_t)blockIdx.x * kThreads;
+    unsigned long long finished = 0;
+
+    // round 0
+    for (int64_t base = tid0; base < a.n; base += wstride) {
+        const int64_t v = base + threadIdx.x;
+        bool keep = false;
+        if (v < a.n) {
+            const int32_t pv = a.p[v];
+            if (v == a.root || pv < 0) {
+                a.done[v] = 0;  // g(root) = 0, unreached = +inf: already in g
+            } else {
+                a.anc[0][v] = pv;
+                a.acc[0][v] = (double)a.pc[v];
+                a.done[v] = INT_MAX;
+                keep = true;
+            }
+        }
+        warp_append(keep, (int32_t)v, a.wl[0], &c->wl_count[1]);
+    }
+    if (!grid_barrier(c, nblocks)) return;
+
+    int r = 1;
+    for (;; ++r) {
+        const int64_t count = (int64_t)(*(volatile unsigned *)&c->wl_count[r]);
+        if (count == 0) break;
+        if (r > kMaxJumpRounds) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) atomicOr(&c->status, kStatusBadTree);
+            break;
+        }
+        const int rd = (r - 1) & 1, wr = r & 1;
+        const int32_t *wl_in = rd ? a.wl[1] : a.wl[0];
+        int32_t *wl_out = wr ? a.wl[1] : a.wl[0];
+        const int32_t *anc_r = rd ? a.anc[1] : a.anc[0];
+        const double *acc_r = rd ? a.acc[1] : a.acc[0];
+        int32_t *anc_w = wr ? a.anc[1] : a.anc[0];
+        double *acc_w = wr ? a.acc[1] : a.acc[0];
+        for (int64_t base = tid0; base < count; base += wstride) {
+            const int64_t i = base + threadIdx.x;
+            bool keep = false, changed = false;
+            int32_t w = 0;
+            if (i < count) {
+                w = __ldcg(&wl_in[i]);
+                const int32_t anc = __ldcg(&anc_r[w]);
+                const double s = __ldcg(&acc_r[w]);
+                if (__ldcg(&a.done[anc]) < r) {
+                    const double gw = s + __ldcg(&a.g[anc]);
+                    const double old = __ldcg(&a.g[w]);
+                    changed = __double_as_longlong(gw) != __double_as_longlong(old);
+                    a.g[w] = gw;
+                    a.done[w] = r;
+                    ++finished;
+                } else {
+                    anc_w[w] = __ldcg(&anc_r[anc]);
+                    acc_w[w] = s + __ldcg(&acc_r[anc]);
+                    keep = true;
+                }
+            }
+            warp_append(keep, w, wl_out, &c->wl_count[r + 1]);
+            warp_append(changed, w, a.dg, &c->n_dg);
+        }
+        if (!grid_barrier(c, nblocks)) return;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) finished += __shfl_down_sync(0xffffffffu, finished, off);
+    if (lane == 0 && finished) atomicAdd(&c->evaluated, finished);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->rounds = (unsigned)(r - 1);
+}
+
+// ---------------------------------------------------------------------------
+// Changed-vertex frontier: the next Improve examines the neighbours of every
+// vertex whose g changed (only they can find a better parent), or every
+// vertex when that set is large.
+// ---------------------------------------------------------------------------
+
+template <typename CT>
+struct MarkArgs {
+    const int64_t *row_off;
+    const Entry<CT> *adj;
+    const int32_t *dg;
+    unsigned *stamp;
+    int32_t *next;
+    DevCounters *ctr;
+    unsigned epoch;
+    int32_t root;
+    unsigned dense_limit;  // |dg| above this -> dense sweep next
+};
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+mark_frontier_kernel(MarkArgs<CT> a) {
+    DevCounters *c = a.ctr;
+    const unsigned n_dg = c->n_dg;
+    if (c->n_switched == 0u || n_dg == 0u) return;
+    if (n_dg > a.dense_limit) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->dense_next = 1u;
+        return;
+    }
+    // one warp per changed vertex; lanes stride over its row
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n_dg;
+         j += warps) {
+        const int32_t x = a.dg[j];
+        const int64_t b = a.row_off[x], e = a.row_off[x + 1];
+        for (int64_t i0 = b; i0 < e; i0 += 32) {
+            const int64_t i = i0 + lane;
+            bool pred = false;
+            int32_t u = 0;
+            if (i < e) {
+                u = __ldg(&a.adj[i].col);
+                pred = u != a.root && atomicExch(&a.stamp[u], a.epoch) != a.epoch;
+            }
+            warp_append(pred, u, a.next, &c->n_next);
+        }
+    }
+}
+
+// Clear the per-iteration fields (not the current list or the dense flag).
+__device__ __forceinline__ void clear_iteration(DevCounters *c) {
+    c->n_next = 0u;
+    c->n_switched = 0u;
+    c->dj_bits = 0ull;
+    c->n_dg = 0u;
+    c->rounds = 0u;
+    c->bar_count = 0u;
+    for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
+}
+
+// Between iterations: the list built by mark becomes the current list.
+__global__ void advance_kernel(DevCounters *c) {
+    c->n_active = c->dense_next ? 0u : c->n_next;
+    c->dense = c->dense_next;
+    c->dense_next = 0u;
+    clear_iteration(c);
+}
+
+// Before an exploit or a forced Evaluate: clear the per-iteration fields and
+// the whole-exploit totals.
+__global__ void begin_exploit_kernel(DevCounters *c) {
+    clear_iteration(c);
+    c->relax = 0ull;
+    c->improved = 0ull;
+    c->evaluated = 0ull;
+    c->switches = 0ull;
+    c->dense_next = 0u;
+}
+
+// ---------------------------------------------------------------------------
+// Policy replacement (set_policy): look up each parent edge's cost.
+// ---------------------------------------------------------------------------
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+policy_lookup_kernel(int64_t n, int32_t root, const int32_t *__restrict__ parent,
+                     const int64_t *__restrict__ row_off, const Entry<CT> *__restrict__ adj,
+                     int32_t *__restrict__ p_out, CT *__restrict__ pc_out, DevCounters *c) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = parent[v];
+        if (v == root) {
+            if (q != -1) atomicOr(&c->status, kStatusBadInput);
+            p_out[v] = -1;
+            pc_out[v] = CT(0);
+            continue;
+        }
+        if (q == -1) {
+            p_out[v] = -1;
+            pc_out[v] = CT(0);
+            continue;
+        }
+        if (q < 0 || q >= n) {
+            atomicOr(&c->status, kStatusBadInput);
+            continue;
+        }
+        bool found = false;
+        CT best = CT(0);
+        for (int64_t i = row_off[v]; i < row_off[v + 1]; ++i) {
+            const Entry<CT> en = adj[i];
+            if (en.col == q && (!found || en.w < best)) {
+                best = en.w;
+                found = true;
+            }
+        }
+        if (!found) atomicOr(&c->status, kStatusBadInput);
+        p_out[v] = q;
+        pc_out[v] = best;
+    }
+}
+
+// Commit a looked-up policy and clear g (Evaluate refills it).
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+policy_commit_kernel(int64_t n, int32_t root, const int32_t *__restrict__ p_in,
+                     const CT *__restrict__ pc_in, int32_t *__restrict__ p, CT *__restrict__ pc,
+                     double *__restrict__ g) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        p[v] = p_in[v];
+        pc[v] = pc_in[v];
+        g[v] = (v == root) ? 0.0 : CUDART_INF;
+    }
+}
+
+}  // namespace pirrt

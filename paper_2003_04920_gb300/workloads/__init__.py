@@ -363,3 +363,30 @@ def random_graph(seed: int, n: int, m: int, cost_dtype=np.float64, connected: bo
     pts = np.zeros((n, 1))
     return Roadmap(f"random{seed}", pts, u, v, cost, start, n, None,
                    dict(seed=seed, n=n, m_undirected=len(u)))
+
+
+def cached(name: str, fn, **kw) -> Roadmap:
+    """``fn(**kw)`` memoised on disk (``$PIRRT_CACHE`` or /tmp/pirrt_cache), so
+    several processes of one session share an expensive generation."""
+    import hashlib
+    import json
+    import tempfile
+    root = os.environ.get("PIRRT_CACHE", os.path.join(tempfile.gettempdir(), "pirrt_cache"))
+    os.makedirs(root, exist_ok=True)
+    key = hashlib.sha1(json.dumps([name, sorted(kw.items())], default=str).encode()).hexdigest()[:16]
+    path = os.path.join(root, f"{name}-{key}.npz")
+    if os.path.exists(path):
+        d = np.load(path, allow_pickle=False)
+        meta = json.loads(str(d["meta"]))
+        sc = Scene(int(d["dim"]), float(d["lo"]), float(d["hi"]), d["centers"], d["radii"])
+        return Roadmap(str(d["name"]), d["points"], d["u"], d["v"], d["cost"], d["edge_start"],
+                       int(d["block"]), sc, meta)
+    rm = fn(**kw)
+    tmp = f"{path}.{os.getpid()}.tmp.npz"
+    sc = rm.scene
+    np.savez(tmp, name=rm.name, points=rm.points, u=rm.u, v=rm.v, cost=rm.cost,
+             edge_start=rm.edge_start, block=rm.block, meta=json.dumps(rm.meta, default=str),
+             dim=sc.dim, lo=sc.lo, hi=sc.hi, centers=sc.centers, radii=sc.radii)
+    os.replace(tmp, path)
+    return rm
+

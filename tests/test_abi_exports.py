@@ -1,0 +1,62 @@
+"""The C ABI library builds for sm_103a, loads without a GPU and exports every
+entry point that include/pirrt.h declares (no compute call is made here)."""
+import ctypes
+import os
+import re
+
+import pytest
+
+from paper_2003_04920_gb300 import build as B
+
+HEADER_DIR = os.path.join(os.path.dirname(os.path.dirname(os.path.abspath(__file__))), "include")
+
+
+def _declared_symbols():
+    names = set()
+    for f in os.listdir(HEADER_DIR):
+        if f.endswith(".h"):
+            text = open(os.path.join(HEADER_DIR, f)).read()
+            text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+            names |= set(re.findall(r"\b(pirrt_\w+)\s*\(", text))
+    return sorted(names)
+
+
+@pytest.fixture(scope="module")
+def lib():
+    path = B.build()
+    return ctypes.CDLL(path)
+
+
+def test_header_declares_the_boundary():
+    names = _declared_symbols()
+    for want in ("pirrt_graph_create", "pirrt_graph_insert_batch", "pirrt_graph_exploit",
+                 "pirrt_graph_get_costs", "pirrt_graph_get_parents", "pirrt_graph_destroy",
+                 "pirrt_status_string"):
+        assert want in names
+
+
+def test_every_declared_symbol_is_exported(lib):
+    missing = [n for n in _declared_symbols() if not hasattr(lib, n)]
+    assert not missing, f"not exported: {missing}"
+
+
+def test_status_strings(lib):
+    lib.pirrt_status_string.restype = ctypes.c_char_p
+    assert lib.pirrt_status_string(0) == b"PIRRT_OK"
+    assert lib.pirrt_status_string(8) == b"PIRRT_ERR_BAD_TREE"
+    assert lib.pirrt_status_string(99) == b"PIRRT_UNKNOWN_STATUS"
+
+
+def test_null_handles_are_rejected(lib):
+    lib.pirrt_graph_num_vertices.restype = ctypes.c_int64
+    assert lib.pirrt_graph_num_vertices(None) == -1
+    assert lib.pirrt_graph_exploit(None, None, None) == 1
+    assert lib.pirrt_graph_create(None, None) == 1
+    lib.pirrt_graph_destroy(None)
+
+
+def test_library_links_no_driver_library():
+    path = B.build()
+    import subprocess
+    out = subprocess.run(["ldd", path], capture_output=True, text=True).stdout
+    assert "libcuda.so" not in out

@@ -1,0 +1,328 @@
+"""Parity of the CUDA exploitation path (through the C ABI) with the CPU oracle.
+
+Sizes here finish on the oracle in seconds yet span many CUDA blocks, several
+Improve groups per row, multi-round pointer jumping and ragged tails.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2003_04920_gb300 as P
+from paper_2003_04920_gb300 import workloads as W
+from tests import golden_io
+from tests.gpu_util import assert_parity, gpu_schedule
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _cuda():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load_library()
+
+
+# ------------------------------------------------------------ golden ---
+
+@pytest.mark.parametrize("name", golden_io.names())
+@pytest.mark.parametrize("dtype", [np.float64, np.float32])
+def test_golden(name, dtype):
+    gd = golden_io.load(name)
+    with P.Graph(gd["n"], len(gd["u"]), gd["root"], dtype) as G:
+        G.insert_batch(gd["n"], gd["u"], gd["v"], gd["c"].astype(dtype))
+        if gd["init"] is not None:
+            G.set_policy(gd["init"])
+        st = G.exploit()
+        np.testing.assert_array_equal(G.get_costs(), gd["g"])
+        np.testing.assert_array_equal(G.get_parents(), gd["parent"])
+        assert st["converged"] == 1
+        assert st["iterations"] == gd["iterations"]
+
+
+# ------------------------------------------- oracle-sized roadmap (C1) ---
+
+def _o1(rm, init=None, block=None):
+    return O.replan_schedule(rm, block=block, init_parent=init)
+
+
+def test_c1_bfs_start_matches_oracle():
+    rm = W.roadmap_c1()
+    init = W.bfs_tree_parents(rm)
+    g_ref, p_ref, st_ref = _o1(rm, init)
+    g, p, st = gpu_schedule(rm, init_parent=init)
+    assert_parity(rm, g, p, g_ref, p_ref)
+    assert st[0]["iterations"] == st_ref[0]["iterations"]
+    assert st[0]["switches"] == st_ref[0]["switches"]
+
+
+@pytest.mark.parametrize("trial", [0, 1, 2])
+def test_c1_unreached_start_matches_oracle(trial):
+    rm = W.roadmap_c1(trial=trial)
+    g_ref, p_ref, st_ref = _o1(rm)
+    g, p, st = gpu_schedule(rm)
+    assert_parity(rm, g, p, g_ref, p_ref)
+    assert st[0]["iterations"] == st_ref[0]["iterations"]
+
+
+@pytest.mark.parametrize("seed", range(6))
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_random_graphs(seed, dtype):
+    n = [1, 2, 17, 300, 2049, 5000][seed]
+    rm = W.random_graph(500 + seed, n, 3 * n, cost_dtype=dtype, connected=seed % 2 == 0)
+    g_ref, p_ref, _ = _o1(rm)
+    g, p, _ = gpu_schedule(rm)
+    assert_parity(rm, g, p, g_ref, p_ref)
+
+
+# ------------------------------------ Batched-Extension schedules (C2/C3) ---
+
+@pytest.fixture(scope="module")
+def c2_small():
+    return W.roadmap_c2(n=30_000, block=1_000, companion=True)
+
+
+@pytest.fixture(scope="module")
+def c3_small():
+    return W.roadmap_c3(n=40_000, block=5_000)
+
+
+def test_c2_schedule_matches_oracle_every_block(c2_small):
+    rm = c2_small
+    G = O.OracleGraph(rm.n)
+    with P.Graph(rm.n, rm.m, 0, np.float32) as D:
+        for v0, v1, e0, e1 in rm.blocks():
+            G.insert(v1 - v0, rm.u[e0:e1], rm.v[e0:e1], rm.cost[e0:e1].astype(np.float64))
+            st_ref = G.replan()
+            D.insert_batch(v1 - v0, rm.u[e0:e1], rm.v[e0:e1], rm.cost[e0:e1])
+            st = D.exploit()
+            g_ref, p_ref = G.get()
+            g, p = D.get_costs(), D.get_parents()
+            sub = W.Roadmap(rm.name, rm.points[:v1], rm.u[:e1], rm.v[:e1], rm.cost[:e1],
+                            rm.edge_start[:v1 + 1], rm.block)
+            assert_parity(sub, g, p, g_ref, p_ref)
+            assert st["converged"] == 1
+    G.close()
+
+
+def test_c3_schedule_matches_dijkstra(c3_small):
+    rm = c3_small
+    g, p, stats = gpu_schedule(rm)
+    assert all(s["converged"] for s in stats)
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    d, _ = A.dijkstra()
+    assert_parity(rm, g, p, d, csr=A)
+
+
+def test_c2_as_specified_small_reachable_set():
+    rm = W.roadmap_c2(n=20_000, block=2_000)
+    g, p, _ = gpu_schedule(rm)
+    d, _ = O.dijkstra(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    assert_parity(rm, g, p, d)
+
+
+# ------------------------------------------------------ invariances ---
+
+@pytest.mark.parametrize("group", [4, 8, 16, 32])
+def test_group_size_does_not_change_results(c3_small, group):
+    rm = c3_small
+    g0, p0, _ = gpu_schedule(rm, group=8)
+    g, p, _ = gpu_schedule(rm, group=group)
+    np.testing.assert_array_equal(g, g0)
+    np.testing.assert_array_equal(p, p0)
+
+
+@pytest.mark.parametrize("frac", [1e-9, 0.05, 1.0])
+def test_dense_threshold_does_not_change_results(c2_small, frac):
+    rm = c2_small
+    g0, p0, _ = gpu_schedule(rm)
+    g, p, st = gpu_schedule(rm, dense_fraction=frac)
+    np.testing.assert_array_equal(g, g0)
+    np.testing.assert_array_equal(p, p0)
+    if frac == 1e-9:
+        assert sum(s["dense_sweeps"] for s in st) > 0
+
+
+def test_block_size_does_not_change_results(c3_small):
+    """Alg. 3: the final policy is independent of S (Sec. IV "Correctness")."""
+    rm = c3_small
+    g1, p1, _ = gpu_schedule(rm, block=rm.n)
+    g2, p2, _ = gpu_schedule(rm, block=997)
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    d, _ = A.dijkstra()
+    m1 = assert_parity(rm, g1, p1, d, csr=A)
+    assert_parity(rm, g2, p2, d, csr=A)
+    np.testing.assert_array_equal(p1[m1], p2[m1])
+
+
+def test_device_and_host_inputs_agree(c2_small):
+    rm = c2_small
+    g0, p0, _ = gpu_schedule(rm)
+    g1, p1, _ = gpu_schedule(rm, device_inputs=True)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+
+
+def test_runs_are_deterministic(c3_small):
+    a = gpu_schedule(c3_small)
+    b = gpu_schedule(c3_small)
+    np.testing.assert_array_equal(a[0], b[0])
+    np.testing.assert_array_equal(a[1], b[1])
+
+
+# ---------------------------------------------------------- insertion ---
+
+def test_csr_equals_host_sort_of_union(c2_small):
+    rm = c2_small
+    with P.Graph(rm.n, rm.m, 0, np.float32) as D:
+        for k, (v0, v1, e0, e1) in enumerate(rm.blocks()):
+            D.insert_batch(v1 - v0, rm.u[e0:e1], rm.v[e0:e1], rm.cost[e0:e1])
+            if k in (0, 3):
+                off, col, cost = D.get_adjacency()
+                uu = np.r_[rm.u[:e1], rm.v[:e1]].astype(np.int64)
+                vv = np.r_[rm.v[:e1], rm.u[:e1]].astype(np.int64)
+                cc = np.r_[rm.cost[:e1], rm.cost[:e1]]
+                o = np.lexsort((cc, vv, uu))
+                want_off = np.searchsorted(uu[o], np.arange(v1 + 1))
+                np.testing.assert_array_equal(off, want_off)
+                rows = np.repeat(np.arange(v1), np.diff(off))
+                o2 = np.lexsort((cost, col, rows))
+                np.testing.assert_array_equal(col[o2], vv[o])
+                np.testing.assert_array_equal(cost[o2], cc[o])
+
+
+# --------------------------------------------------------- edge cases ---
+
+def test_empty_and_vertex_only_batches():
+    with P.Graph(10, 10, 0, np.float64) as D:
+        D.insert_batch(0, [], [], [])
+        assert D.exploit()["converged"] == 1
+        D.insert_batch(1, [], [], [])          # the root alone
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0.0])
+        D.insert_batch(3, [], [], [])          # isolated vertices
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0, np.inf, np.inf, np.inf])
+        np.testing.assert_array_equal(D.get_parents(), [-1, -1, -1, -1])
+        D.insert_batch(0, [0, 2], [2, 3], [1.5, 0.25])   # edges between old vertices
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0, np.inf, 1.5, 1.75])
+        np.testing.assert_array_equal(D.get_parents(), [-1, -1, 0, 2])
+        D.insert_batch(0, [3], [0], [1.0])     # a cheaper route to 3 appears later
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0, np.inf, 1.5, 1.0])
+        np.testing.assert_array_equal(D.get_parents(), [-1, -1, 0, 0])
+
+
+def test_nonzero_root():
+    gd = golden_io.load("chain_shortcut.txt")
+    # relabel: root becomes vertex 6
+    perm = np.array([6, 5, 4, 3, 2, 1, 0])
+    u, v = perm[gd["u"]], perm[gd["v"]]
+    with P.Graph(7, 7, 6, np.float64) as D:
+        D.insert_batch(7, u, v, gd["c"])
+        D.exploit()
+        g = D.get_costs()
+    d, _ = O.dijkstra(7, u, v, gd["c"], root=6)
+    np.testing.assert_array_equal(g, d)
+
+
+@pytest.mark.parametrize("bad", ["range", "negative", "self", "zero", "neg_cost", "nan", "inf"])
+def test_bad_input_rejected_graph_unchanged(bad):
+    u, v, c = [0, 1], [1, 2], [1.0, 1.0]
+    if bad == "range":
+        v = [1, 3]
+    elif bad == "negative":
+        u = [-1, 1]
+    elif bad == "self":
+        v = [1, 1]
+    elif bad == "zero":
+        c = [1.0, 0.0]
+    elif bad == "neg_cost":
+        c = [1.0, -2.0]
+    elif bad == "nan":
+        c = [np.nan, 1.0]
+    elif bad == "inf":
+        c = [1.0, np.inf]
+    with P.Graph(8, 8, 0, np.float32) as D:
+        D.insert_batch(2, [0], [1], [0.5])
+        D.exploit()
+        with pytest.raises(P.PirrtError) as e:
+            D.insert_batch(1, u, v, c)
+        assert e.value.status == P.PIRRT_ERR_BAD_INPUT
+        assert D.n == 2 and D.m == 2
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0.0, 0.5])
+
+
+def test_capacity_errors():
+    with P.Graph(3, 2, 0, np.float32) as D:
+        with pytest.raises(P.PirrtError) as e:
+            D.insert_batch(4, [], [], [])
+        assert e.value.status == P.PIRRT_ERR_CAPACITY
+        with pytest.raises(P.PirrtError) as e:
+            D.insert_batch(3, [0, 1, 0], [1, 2, 2], [1, 1, 1])
+        assert e.value.status == P.PIRRT_ERR_CAPACITY
+        D.insert_batch(3, [0, 1], [1, 2], [1, 1])
+        D.exploit()
+        np.testing.assert_array_equal(D.get_costs(), [0, 1, 2])
+
+
+def test_set_policy_rejects_missing_edge_and_root_parent():
+    gd = golden_io.load("triangle_switch.txt")
+    with P.Graph(3, 3, 0, np.float64) as D:
+        D.insert_batch(3, gd["u"], gd["v"], gd["c"])
+        with pytest.raises(P.PirrtError) as e:
+            D.set_policy([1, 0, 0])
+        assert e.value.status == P.PIRRT_ERR_BAD_INPUT
+        with pytest.raises(P.PirrtError) as e:
+            D.set_policy([-1, 0, 5])
+        assert e.value.status == P.PIRRT_ERR_BAD_INPUT
+        with pytest.raises(P.PirrtError) as e:
+            D.set_policy([-1, 0])
+        assert e.value.status == P.PIRRT_ERR_INVALID_ARG
+
+
+def test_set_policy_cycle_is_reported():
+    # 1 <-> 2 point at each other: no chain reaches the root
+    with P.Graph(3, 3, 0, np.float64) as D:
+        D.insert_batch(3, [0, 1, 0], [1, 2, 2], [1.0, 1.0, 1.0])
+        with pytest.raises(P.PirrtError) as e:
+            D.set_policy([-1, 2, 1])
+        assert e.value.status == P.PIRRT_ERR_BAD_TREE
+
+
+def test_max_iters_then_resume():
+    gd = golden_io.load("path5.txt")
+    with P.Graph(5, 4, 0, np.float64) as D:
+        D.insert_batch(5, gd["u"], gd["v"], gd["c"])
+        st = D.exploit(max_iters=2, check=False)
+        assert st["status"] == P.PIRRT_ERR_NOT_CONVERGED and st["converged"] == 0
+        st = D.exploit()
+        assert st["converged"] == 1
+        np.testing.assert_array_equal(D.get_costs(), gd["g"])
+        np.testing.assert_array_equal(D.get_parents(), gd["parent"])
+
+
+def test_reset_reuses_allocations(c3_small):
+    rm = c3_small
+    with P.Graph(rm.n, rm.m, 0, np.float32) as D:
+        g0, p0, _ = gpu_schedule(rm, graph=D)
+        D.reset()
+        assert D.n == 0
+        g1, p1, _ = gpu_schedule(rm, graph=D)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+
+
+def test_outputs_into_device_tensors(c2_small):
+    import torch
+    rm = c2_small
+    with P.Graph(rm.n, rm.m, 0, np.float32) as D:
+        gpu_schedule(rm, graph=D)
+        gt = torch.empty(rm.n, dtype=torch.float64, device="cuda")
+        pt = torch.empty(rm.n, dtype=torch.int32, device="cuda")
+        D.get_costs(gt)
+        D.get_parents(pt)
+        np.testing.assert_array_equal(gt.cpu().numpy(), D.get_costs())
+        np.testing.assert_array_equal(pt.cpu().numpy(), D.get_parents())

@@ -208,10 +208,10 @@ def test_empty_and_vertex_only_batches():
         D.exploit()
         np.testing.assert_array_equal(D.get_costs(), [0, np.inf, 1.5, 1.75])
         np.testing.assert_array_equal(D.get_parents(), [-1, -1, 0, 2])
-        D.insert_batch(0, [3], [0], [1.0])     # a cheaper route to 3 appears later
+        D.insert_batch(0, [3], [0], [1.0])     # a cheaper route to 3 (and via 3 to 2)
         D.exploit()
-        np.testing.assert_array_equal(D.get_costs(), [0, np.inf, 1.5, 1.0])
-        np.testing.assert_array_equal(D.get_parents(), [-1, -1, 0, 0])
+        np.testing.assert_array_equal(D.get_costs(), [0, np.inf, 1.25, 1.0])
+        np.testing.assert_array_equal(D.get_parents(), [-1, -1, 3, 0])
 
 
 def test_nonzero_root():

@@ -185,7 +185,8 @@ def run_ours(args) -> None:
                 G.insert_batch(v1 - v0, dev_u[e0:e1], dev_v[e0:e1], dev_c[e0:e1])
             else:
                 G.insert_batch(v1 - v0, host_u[e0:e1], host_v[e0:e1], host_c[e0:e1])
-            st = G.exploit(group=args.group, dense_fraction=args.dense_fraction)
+            st = G.exploit(group=args.group, dense_fraction=args.dense_fraction,
+                           evaluate=args.evaluate, wave_levels=args.wave_levels)
             relax += st["relaxations"]
             iters += st["iterations"]
         return relax, iters
@@ -295,6 +296,7 @@ def run_ours(args) -> None:
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][1]}",
                    "vertices": rm.n, "undirected_edges": rm.m, "csr_entries": 2 * rm.m,
                    "blocks_per_step": n_blocks, "block_size": rm.block,
+                   "evaluate": args.evaluate,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
@@ -411,6 +413,8 @@ def main():
     ap.add_argument("--trial", type=int, default=0)
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--dense-fraction", type=float, default=0.0)
+    ap.add_argument("--evaluate", choices=("auto", "wave", "jump"), default="auto")
+    ap.add_argument("--wave-levels", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -72,9 +72,23 @@ typedef struct {
                                parent switches */
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
     int32_t group;          /* threads per vertex in Improve: 0 = tuned, else 4, 8, 16 or 32 */
-    double dense_fraction;  /* frontier size, as a fraction of |V|, above which the next
+    int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
+    int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
+                               pointer jumping; 0 = tuned */
+    double dense_fraction;  /* changed vertices, as a fraction of |V|, above which the next
                                Improve sweeps every vertex instead of a list; 0 = tuned */
 } pirrt_exploit_opts;
+
+/* Evaluate strategies.  Both compute g(v) = g(p(v)) + c(p(v), v) from the root
+ * in FP64 (Alg. 2 Evaluate):
+ *   WAVE -- top-down over the policy tree, level by level, only below the
+ *           vertices whose parent switched, pruning where g is unchanged; the
+ *           next Improve frontier is marked in the same row scan.  Sums are
+ *           taken root-to-leaf, one addition per edge, as in Alg. 2.
+ *   JUMP -- pointer jumping (parent doubling) over every vertex in about
+ *           log2(depth) rounds; the sums are reassociated (within a few ulp).
+ *   AUTO -- WAVE, handing over to JUMP when a wave exceeds its level cap. */
+enum { PIRRT_EVAL_AUTO = 0, PIRRT_EVAL_WAVE = 1, PIRRT_EVAL_JUMP = 2 };
 
 /* Filled by pirrt_graph_exploit. */
 typedef struct {
@@ -86,6 +100,8 @@ typedef struct {
     int64_t evaluated;      /* vertices whose g Evaluate recomputed, summed over rounds */
     int32_t jump_rounds;    /* pointer-jumping rounds, summed over Evaluate calls */
     int32_t dense_sweeps;   /* Improve rounds that swept every vertex */
+    int32_t wave_levels;    /* top-down Evaluate levels, summed over Evaluate calls */
+    int32_t jump_evaluates; /* Evaluate calls done (or finished) by pointer jumping */
     float ms_exploit;       /* device time of the call, CUDA events on the graph's stream */
     float reserved;
 } pirrt_exploit_stats;

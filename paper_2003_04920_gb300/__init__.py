@@ -32,6 +32,10 @@ PIRRT_ERR_BAD_INPUT = 7
 PIRRT_ERR_BAD_TREE = 8
 PIRRT_COST_F32 = 0
 PIRRT_COST_F64 = 1
+PIRRT_EVAL_AUTO = 0
+PIRRT_EVAL_WAVE = 1
+PIRRT_EVAL_JUMP = 2
+EVALUATE_MODES = {"auto": PIRRT_EVAL_AUTO, "wave": PIRRT_EVAL_WAVE, "jump": PIRRT_EVAL_JUMP}
 
 
 class pirrt_config(ctypes.Structure):
@@ -43,7 +47,8 @@ class pirrt_config(ctypes.Structure):
 
 class pirrt_exploit_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("dense_fraction", ctypes.c_double)]
+                ("group", ctypes.c_int32), ("evaluate", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("dense_fraction", ctypes.c_double)]
 
 
 class pirrt_exploit_stats(ctypes.Structure):
@@ -51,6 +56,7 @@ class pirrt_exploit_stats(ctypes.Structure):
                 ("relaxations", ctypes.c_int64), ("improved", ctypes.c_int64),
                 ("switches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("jump_rounds", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("jump_evaluates", ctypes.c_int32),
                 ("ms_exploit", ctypes.c_float), ("reserved", ctypes.c_float)]
 
     def as_dict(self) -> dict:
@@ -211,8 +217,11 @@ class Graph:
                     self._lib.pirrt_graph_set_policy(self._h, pp, int(n), dev))
 
     def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0,
-                dense_fraction: float = 0.0, check: bool = True) -> dict:
-        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group), float(dense_fraction))
+                dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
+                check: bool = True) -> dict:
+        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group),
+                                  EVALUATE_MODES[evaluate], int(wave_levels),
+                                  float(dense_fraction))
         st = pirrt_exploit_stats()
         rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))
         out = st.as_dict()

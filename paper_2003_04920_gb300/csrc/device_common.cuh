@@ -74,7 +74,10 @@ struct DevCounters {
     unsigned dense_next;          // next Improve sweeps every vertex
     unsigned bar_count;           // grid barrier: arrivals
     unsigned bar_gen;             // grid barrier: generation
-    unsigned pad[2];
+    unsigned wave_cnt[3];         // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
+    unsigned wave_levels;         // levels run by the last top-down Evaluate
+    unsigned wave_incomplete;     // the top-down Evaluate stopped at its level cap
+    unsigned pad[3];
     unsigned wl_count[kMaxJumpRounds + 2];  // Evaluate work-list sizes per round
 };
 

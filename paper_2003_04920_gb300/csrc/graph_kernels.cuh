@@ -481,11 +481,135 @@ mark_frontier_kernel(MarkArgs<CT> a) {
     }
 }
 
+// ---------------------------------------------------------------------------
+// Evaluate, top-down form: recompute g only below the vertices Improve
+// switched, level by level, and mark the next Improve frontier in the same
+// row scan.
+// ---------------------------------------------------------------------------
+
+template <typename CT>
+struct WaveArgs {
+    const int64_t *row_off;
+    const Entry<CT> *adj;
+    const int32_t *p;
+    const CT *pc;
+    double *g;
+    const int32_t *switched;  // level 0: vertices whose parent changed
+    int32_t *lvl[2];          // vertices to recompute at levels t (mod 2)
+    unsigned *wstamp;         // dedups a child listed twice (parallel edges)
+    unsigned wave_epoch;      // wstamp value of level 1 (level t uses + t - 1)
+    unsigned *stamp;          // Improve-list stamps
+    unsigned epoch;           // stamp value of the list being built
+    int32_t *next;            // next Improve list
+    DevCounters *ctr;
+    int32_t root;
+    unsigned dense_limit;     // |changed| above this -> dense sweep next, stop marking
+    unsigned max_levels;      // give up (wave_incomplete) after this many levels
+};
+
+// A vertex u on level t takes g(u) = g(p(u)) + c(p(u), u), one FP64 addition
+// along the path exactly as Alg. 2's Evaluate walks the policy tree.  If g(u)
+// changed, u's row is scanned once: every neighbour joins the next Improve
+// list (only neighbours of changed vertices can find a better parent) and
+// every child (neighbour w with p(w) = u) joins level t + 1.  g(u) unchanged
+// means its whole subtree is unchanged, so the walk is pruned there.
+//
+// A switched vertex below another switched vertex is first computed from a
+// stale parent value and recomputed when the upper wave reaches it; the last
+// write of every vertex comes one level after its parent's last change, so
+// the result does not depend on scheduling.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+wave_evaluate_kernel(WaveArgs<CT> a) {
+    DevCounters *c = a.ctr;
+    const unsigned n_sw = c->n_switched;
+    if (n_sw == 0u) return;
+    const unsigned nblocks = gridDim.x;
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t warp_id = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    unsigned long long recomputed = 0, changed_total = 0;
+    unsigned t = 0;
+    for (;; ++t) {
+        const int64_t count =
+            t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
+        if (count == 0) break;
+        if (t >= a.max_levels) {
+            if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_incomplete = 1u;
+            break;
+        }
+        const int32_t *in = t == 0 ? a.switched : (((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0]);
+        int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
+        unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
+        if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_cnt[(t + 2) % 3] = 0u;
+        const unsigned wtag = a.wave_epoch + t;  // stamp of level t + 1
+        const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
+        for (int64_t j = warp_id; j < count; j += warps) {
+            const int32_t u = __ldcg(&in[j]);
+            int changed = 0;
+            if (lane == 0) {
+                const int32_t pu = __ldcg(&a.p[u]);
+                const double gn = __ldcg(&a.g[pu]) + (double)a.pc[u];
+                const double go = __ldcg(&a.g[u]);
+                if (__double_as_longlong(gn) != __double_as_longlong(go)) {
+                    __stcg(&a.g[u], gn);
+                    changed = 1;
+                }
+            }
+            changed = __shfl_sync(0xffffffffu, changed, 0);
+            if (lane == 0) {
+                ++recomputed;
+                changed_total += (unsigned long long)changed;
+            }
+            if (!changed) continue;
+            const int64_t b = a.row_off[u], e = a.row_off[u + 1];
+            for (int64_t i0 = b; i0 < e; i0 += 32) {
+                const int64_t i = i0 + lane;
+                bool child = false, mark = false;
+                int32_t w = 0;
+                if (i < e) {
+                    w = ld_stream(&a.adj[i]).col;
+                    child = __ldcg(&a.p[w]) == u && atomicExch(&a.wstamp[w], wtag) != wtag;
+                    mark = marking && w != a.root && __ldcg(&a.stamp[w]) != a.epoch &&
+                           atomicExch(&a.stamp[w], a.epoch) != a.epoch;
+                }
+                warp_append(child, w, out, out_cnt);
+                warp_append(mark, w, a.next, &c->n_next);
+            }
+        }
+        // changed-vertex count decides between a list and a dense sweep next
+        if (lane == 0 && changed_total) {
+            const unsigned total = atomicAdd(&c->n_dg, (unsigned)changed_total) +
+                                   (unsigned)changed_total;
+            if (total > a.dense_limit) c->dense_next = 1u;
+        }
+        changed_total = 0;
+        if (!grid_barrier(c, nblocks)) return;
+    }
+    // lane 0 of each warp counted every vertex the warp processed
+    if (lane == 0 && recomputed) atomicAdd(&c->evaluated, recomputed);
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_levels = t;
+}
+
 // Clear the per-iteration fields (not the current list or the dense flag).
 __device__ __forceinline__ void clear_iteration(DevCounters *c) {
+    c->wave_cnt[0] = 0u;
+    c->wave_cnt[1] = 0u;
+    c->wave_cnt[2] = 0u;
+    c->wave_levels = 0u;
+    c->wave_incomplete = 0u;
     c->n_next = 0u;
     c->n_switched = 0u;
     c->dj_bits = 0ull;
+    c->n_dg = 0u;
+    c->rounds = 0u;
+    c->bar_count = 0u;
+    for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
+}
+
+// Before pointer jumping takes over from an unfinished wave: its changed
+// list starts empty (the wave counted changes without listing them).
+__global__ void pre_jump_kernel(DevCounters *c) {
     c->n_dg = 0u;
     c->rounds = 0u;
     c->bar_count = 0u;

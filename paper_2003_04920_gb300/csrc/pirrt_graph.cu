@@ -43,13 +43,16 @@ struct pirrt_graph {
     int32_t *anc[2] = {nullptr, nullptr};
     double *acc[2] = {nullptr, nullptr};
     int32_t *done = nullptr;
-    int32_t *wl[2] = {nullptr, nullptr};
+    int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
+    unsigned *wstamp = nullptr;           // wave child dedup
+    unsigned wave_epoch = 1;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned mirror
     void *stage = nullptr;            // device staging for host-side inputs
     size_t stage_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int eval_blocks = 0;
+    int wave_blocks = 0;
     int profiling = 0;
     pirrt_profile prof{};
     cudaEvent_t pev[8] = {};          // improve, evaluate, mark, insert: (start, end) pairs
@@ -183,6 +186,32 @@ pirrt_status launch_evaluate(pirrt_graph *G, int force) {
 }
 
 template <typename CT>
+pirrt_status launch_wave(pirrt_graph *G, unsigned dense_limit, unsigned max_levels) {
+    WaveArgs<CT> a;
+    a.row_off = G->row_off[G->cur];
+    a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
+    a.p = G->p;
+    a.pc = static_cast<const CT *>(G->pc);
+    a.g = G->g;
+    a.switched = G->switched;
+    a.lvl[0] = G->wl[0];
+    a.lvl[1] = G->wl[1];
+    a.wstamp = G->wstamp;
+    a.wave_epoch = G->wave_epoch;
+    a.stamp = G->stamp;
+    a.epoch = G->epoch + 1u;
+    a.next = G->list[G->la ^ 1];
+    a.ctr = G->ctr;
+    a.root = G->cfg.root;
+    a.dense_limit = dense_limit;
+    a.max_levels = max_levels;
+    void *args[] = {&a};
+    CK(cudaLaunchCooperativeKernel((const void *)wave_evaluate_kernel<CT>, dim3(G->wave_blocks),
+                                   dim3(kThreads), args, 0, G->stream));
+    return PIRRT_OK;
+}
+
+template <typename CT>
 pirrt_status launch_mark(pirrt_graph *G, unsigned dense_limit) {
     MarkArgs<CT> a;
     a.row_off = G->row_off[G->cur];
@@ -278,12 +307,19 @@ template <typename CT>
 pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_exploit_stats *st) {
     pirrt_exploit_opts o{};
     if (opts) o = *opts;
-    if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0)
-        return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: negative max_iters/eps or dense_fraction > 1");
+    if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
+        o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP)
+        return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = group_for<CT>(G, o.group);
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
     const unsigned dense_limit = (unsigned)std::min<double>(4.0e9, frac * (double)G->n);
+    const int mode = o.evaluate;
+    // a wave deeper than the cap hands over to pointer jumping (AUTO); a WAVE
+    // run is only capped at |V| + 2 levels, beyond which the tree has a cycle
+    const unsigned cap_any = (unsigned)std::min<int64_t>(G->n + 2, 0x7fffffff);
+    const unsigned max_levels = mode == PIRRT_EVAL_WAVE ? cap_any
+                                : (o.wave_levels > 0 ? (unsigned)o.wave_levels : 192u);
 
     CK(cudaEventRecord(G->ev0, G->stream));
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
@@ -294,63 +330,93 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     bool converged = false;
     unsigned long long prev_relax = 0, prev_improved = 0, prev_eval = 0;
     const bool prof = G->profiling != 0;
+    pirrt_profile &P = G->prof;
     for (int64_t it = 0; it < max_iters; ++it) {
+        // Improve, then Evaluate (+ frontier marking), then one counter read
         if (prof) CK(cudaEventRecord(G->pev[0], G->stream));
         if ((rc = launch_improve<CT>(G, gs))) return rc;
         if (prof) CK(cudaEventRecord(G->pev[1], G->stream));
-        if ((rc = launch_evaluate<CT>(G, 0))) return rc;
-        if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
-        if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
+        bool jumped = false;
+        if (mode == PIRRT_EVAL_JUMP) {
+            if ((rc = launch_evaluate<CT>(G, 0))) return rc;
+            if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
+            if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
+            P.launches += 2;
+            jumped = true;
+        } else {
+            if ((rc = launch_wave<CT>(G, dense_limit, max_levels))) return rc;
+            if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
+            P.launches += 1;
+        }
         if (prof) CK(cudaEventRecord(G->pev[3], G->stream));
         if ((rc = pull_counters(G))) return rc;
-        G->prof.launches += 3;
-        const DevCounters &h = *G->ctr_host;
-        s.iterations += 1;
-        s.switches += h.n_switched;
-        s.jump_rounds += (int32_t)h.rounds;
-        if (h.dense) s.dense_sweeps += 1;
-        {
-            pirrt_profile &P = G->prof;
-            P.improve_launches += 1;
-            P.improve_entries += (int64_t)(h.relax - prev_relax);
-            P.improve_vertices += (int64_t)(h.improved - prev_improved);
-            if (h.dense) P.improve_dense_vertices += (int64_t)(h.improved - prev_improved);
-            P.improve_switches += h.n_switched;
-            prev_relax = h.relax;
-            prev_improved = h.improved;
-            if (h.n_switched) {
-                P.evaluate_launches += 1;
-                P.evaluate_vertices += (int64_t)(h.evaluated - prev_eval);
-                for (int r = 1; r <= kMaxJumpRounds + 1; ++r) P.evaluate_visits += h.wl_count[r];
-                P.evaluate_visits += G->n;  // round 0 touches every vertex
-                if (h.n_dg && h.n_dg <= dense_limit) {
-                    P.mark_launches += 1;
-                    P.mark_vertices += h.n_dg;
-                }
-            }
-            prev_eval = h.evaluated;
-            if (prof) {
-                float a = 0.f, b = 0.f, c = 0.f;
-                CK(cudaEventElapsedTime(&a, G->pev[0], G->pev[1]));
-                CK(cudaEventElapsedTime(&b, G->pev[1], G->pev[2]));
-                CK(cudaEventElapsedTime(&c, G->pev[2], G->pev[3]));
-                P.improve_ms += a;
-                if (h.n_switched) {
-                    P.evaluate_ms += b;
-                    if (h.n_dg && h.n_dg <= dense_limit) P.mark_ms += c;
+        P.launches += 1;
+        const DevCounters *h = G->ctr_host;
+        float t_imp = 0.f, t_eval = 0.f, t_mark = 0.f;
+        if (prof) {
+            CK(cudaEventElapsedTime(&t_imp, G->pev[0], G->pev[1]));
+            CK(cudaEventElapsedTime(&t_eval, G->pev[1], G->pev[2]));
+            CK(cudaEventElapsedTime(&t_mark, G->pev[2], G->pev[3]));
+        }
+        if (mode != PIRRT_EVAL_JUMP) {
+            G->wave_epoch += h->wave_levels + 1u;
+            s.wave_levels += (int32_t)h->wave_levels;
+            if (h->wave_incomplete) {
+                // finish this Evaluate by pointer jumping from p and pc
+                if (prof) CK(cudaEventRecord(G->pev[4], G->stream));
+                pre_jump_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
+                CKL();
+                if ((rc = launch_evaluate<CT>(G, 0))) return rc;
+                if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
+                if (prof) CK(cudaEventRecord(G->pev[5], G->stream));
+                if ((rc = pull_counters(G))) return rc;
+                P.launches += 3;
+                jumped = true;
+                if (prof) {
+                    float t = 0.f;
+                    CK(cudaEventElapsedTime(&t, G->pev[4], G->pev[5]));
+                    t_eval += t;
                 }
             }
         }
-        if ((rc = status_from_bits(G, h.status))) break;
+        s.iterations += 1;
+        s.switches += h->n_switched;
+        s.jump_rounds += (int32_t)h->rounds;
+        if (jumped && h->n_switched) s.jump_evaluates += 1;
+        if (h->dense) s.dense_sweeps += 1;
+        P.improve_launches += 1;
+        P.improve_entries += (int64_t)(h->relax - prev_relax);
+        P.improve_vertices += (int64_t)(h->improved - prev_improved);
+        if (h->dense) P.improve_dense_vertices += (int64_t)(h->improved - prev_improved);
+        P.improve_switches += h->n_switched;
+        P.improve_ms += t_imp;
+        prev_relax = h->relax;
+        prev_improved = h->improved;
+        if (h->n_switched) {
+            P.evaluate_launches += 1;
+            P.evaluate_vertices += (int64_t)(h->evaluated - prev_eval);
+            P.evaluate_ms += t_eval;
+            if (mode == PIRRT_EVAL_JUMP) {
+                for (int r = 1; r <= kMaxJumpRounds + 1; ++r) P.evaluate_visits += h->wl_count[r];
+                P.evaluate_visits += G->n;  // round 0 touches every vertex
+            }
+            if (jumped && h->n_dg && h->n_dg <= dense_limit) {
+                P.mark_launches += 1;
+                P.mark_vertices += h->n_dg;
+                P.mark_ms += t_mark;
+            }
+        }
+        prev_eval = h->evaluated;
+        if ((rc = status_from_bits(G, h->status))) break;
         // Alg. 2: stop once Delta g <= eps; with eps = 0 that is "no switch".
         // (The Evaluate of this iteration has already run, so g always
         // matches the returned policy.)
         double dj = 0.0;
-        std::memcpy(&dj, &h.dj_bits, sizeof(dj));
-        const bool stop = h.n_switched == 0u || dj <= o.eps;
+        std::memcpy(&dj, &h->dj_bits, sizeof(dj));
+        const bool stop = h->n_switched == 0u || dj <= o.eps;
         advance_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
         CKL();
-        G->prof.launches += 1;
+        P.launches += 1;
         G->la ^= 1;
         G->epoch += 1u;
         if (stop) {
@@ -421,7 +487,7 @@ void free_all(pirrt_graph *G) {
     void *bufs[] = {G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
-                    G->wl[1], G->ctr, G->stage};
+                    G->wl[1], G->wstamp, G->ctr, G->stage};
     for (void *q : bufs)
         if (q) cudaFree(q);
     if (G->ctr_host) cudaFreeHost(G->ctr_host);
@@ -523,6 +589,7 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->done, sizeof(int32_t) * nv);
     ALLOC(G->wl[0], sizeof(int32_t) * nv);
     ALLOC(G->wl[1], sizeof(int32_t) * nv);
+    ALLOC(G->wstamp, sizeof(unsigned) * nv);
     ALLOC(G->ctr, sizeof(DevCounters));
 #undef ALLOC
     if (cudaMallocHost((void **)&G->ctr_host, sizeof(DevCounters)) != cudaSuccess)
@@ -542,6 +609,15 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     occ = std::min(occ, occ64);
     if (occ < 1) return bail(PIRRT_ERR_CUDA);
     G->eval_blocks = G->num_sms * occ;
+    int wocc = 0, wocc64 = 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, wave_evaluate_kernel<float>, kThreads,
+                                                      0) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc64, wave_evaluate_kernel<double>,
+                                                      kThreads, 0) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
+    wocc = std::min(wocc, wocc64);
+    if (wocc < 1) return bail(PIRRT_ERR_CUDA);
+    G->wave_blocks = G->num_sms * std::min(wocc, 4);
     pirrt_status rc = pirrt_graph_reset(G);
     if (rc) return bail(rc);
     *out = G;
@@ -554,6 +630,7 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemsetAsync(G->row_off[0], 0, sizeof(int64_t), G->stream));
     CK(cudaMemsetAsync(G->row_off[1], 0, sizeof(int64_t), G->stream));
     CK(cudaMemsetAsync(G->stamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
+    CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->ctr, 0, sizeof(DevCounters), G->stream));
     CK(cudaStreamSynchronize(G->stream));
     G->n = 0;
@@ -561,6 +638,7 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     G->cur = 0;
     G->la = 0;
     G->epoch = 1;
+    G->wave_epoch = 1;
     G->last_error.clear();
     return PIRRT_OK;
 }

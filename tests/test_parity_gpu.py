@@ -326,3 +326,50 @@ def test_outputs_into_device_tensors(c2_small):
         D.get_parents(pt)
         np.testing.assert_array_equal(gt.cpu().numpy(), D.get_costs())
         np.testing.assert_array_equal(pt.cpu().numpy(), D.get_parents())
+
+
+# ------------------------------------------------- Evaluate strategies ---
+
+@pytest.mark.parametrize("mode,levels", [("wave", 0), ("jump", 0), ("auto", 0), ("auto", 1),
+                                         ("auto", 3)])
+def test_evaluate_strategies_agree(c2_small, mode, levels):
+    """Top-down waves, pointer jumping and a wave handing over to pointer
+    jumping after `levels` levels reach the same policy (Alg. 2 Evaluate)."""
+    rm = c2_small
+    g_ref, p_ref, _ = O.replan_schedule(rm)
+    g, p, st = gpu_schedule(rm, evaluate=mode, wave_levels=levels)
+    assert_parity(rm, g, p, g_ref, p_ref)
+    if mode == "jump" or (mode == "auto" and levels == 1):
+        assert sum(s["jump_evaluates"] for s in st) > 0
+    if mode == "wave":
+        assert sum(s["jump_evaluates"] for s in st) == 0
+
+
+def test_wave_sums_match_oracle_bitwise():
+    """The top-down Evaluate adds one edge cost per level from the root, the
+    order of Alg. 2's breadth-first Evaluate, so with the same tree g agrees
+    with the oracle to the last bit."""
+    rm = W.roadmap_c1(trial=4)
+    g_ref, p_ref, _ = O.replan_schedule(rm)
+    g, p, _ = gpu_schedule(rm, evaluate="wave")
+    same = p == p_ref
+    assert same.mean() > 0.99
+    # vertices whose whole root path agrees
+    ok = np.zeros(rm.n, dtype=bool)
+    ok[0] = True
+    for x in np.argsort(g_ref):
+        if x != 0 and p_ref[x] >= 0:
+            ok[x] = same[x] and ok[p_ref[x]]
+    np.testing.assert_array_equal(g[ok], g_ref[ok])
+    assert ok.mean() > 0.9
+
+
+def test_c3_wave_and_jump_identical_parents(c3_small):
+    rm = c3_small
+    gw, pw, _ = gpu_schedule(rm, evaluate="wave")
+    gj, pj, _ = gpu_schedule(rm, evaluate="jump")
+    np.testing.assert_allclose(gw, gj, rtol=1e-12)
+    d, _ = O.dijkstra(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    mask, _ = A.unambiguous(d)
+    np.testing.assert_array_equal(pw[mask], pj[mask])

@@ -71,7 +71,8 @@ typedef struct {
     double eps;             /* Replan stops once Delta g <= eps (Alg. 2); 0 = until no
                                parent switches */
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
-    int32_t group;          /* threads per vertex in Improve: 0 = tuned, else 4, 8, 16 or 32 */
+    int32_t group;          /* Improve kernel: 0 = tiled (a CTA streams the concatenated rows
+                               of 64 vertices), or 4, 8, 16, 32 threads per vertex */
     int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
     int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
                                pointer jumping; 0 = tuned */

@@ -329,6 +329,188 @@ improve_kernel(ImproveArgs<CT> a) {
     }
 }
 
+// Tiled Improve: a CTA takes a tile of kTileV vertices (a slice of the active
+// list, or of 0..n-1 in a dense sweep), lays their rows end to end and
+// streams the concatenation kChunk entries at a time, eight independent
+// entry loads per thread followed by eight independent g gathers, so the
+// memory system sees whole tiles in flight instead of one row per group.
+// The lexicographic argmin of (g(u) + c, u, c) per vertex is taken in shared
+// memory in three phases (min value, then min id among those, then min cost
+// among those -- parallel edges), each an atomicMin on order-preserving bits
+// of non-negative numbers.  Chunks of one tile are merged in order.
+constexpr int kTileV = 64;
+constexpr int kPerThread = 8;
+constexpr int kChunk = kThreads * kPerThread;
+
+template <typename CT>
+struct CostBits;
+template <>
+struct CostBits<float> {
+    using T = unsigned;
+    static __device__ __forceinline__ unsigned of(float w) { return __float_as_uint(w); }
+    static __device__ __forceinline__ float back(unsigned b) { return __uint_as_float(b); }
+    static constexpr unsigned kMax = 0xffffffffu;
+};
+template <>
+struct CostBits<double> {
+    using T = unsigned long long;
+    static __device__ __forceinline__ unsigned long long of(double w) {
+        return (unsigned long long)__double_as_longlong(w);
+    }
+    static __device__ __forceinline__ double back(unsigned long long b) {
+        return __longlong_as_double((long long)b);
+    }
+    static constexpr unsigned long long kMax = 0xffffffffffffffffull;
+};
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads, 3)
+improve_tile_kernel(ImproveArgs<CT> a) {
+    using WB = typename CostBits<CT>::T;
+    constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+    __shared__ int32_t s_v[kTileV];
+    __shared__ long long s_base[kTileV];
+    __shared__ int32_t s_seg[kTileV + 1];
+    __shared__ unsigned long long s_cv[kTileV];  // chunk minimum: value bits
+    __shared__ int32_t s_cid[kTileV];            //   id
+    __shared__ WB s_cw[kTileV];                  //   cost bits
+    __shared__ unsigned long long s_bv[kTileV];  // tile minimum so far
+    __shared__ int32_t s_bid[kTileV];
+    __shared__ WB s_bw[kTileV];
+    __shared__ int32_t s_wsum[2];
+
+    const int tid = threadIdx.x;
+    const bool dense = a.ctr->dense != 0u;
+    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
+    const int64_t n_tiles = (count + kTileV - 1) / kTileV;
+    unsigned long long relax = 0, improved = 0;
+
+    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
+        const int64_t t0 = tile * kTileV;
+        const int nv = (count - t0) < (int64_t)kTileV ? (int)(count - t0) : kTileV;
+        // 1. vertices of the tile, their row extents, exclusive scan of degrees
+        int deg = 0;
+        if (tid < kTileV) {
+            int32_t v = -1;
+            if (tid < nv) {
+                v = dense ? (int32_t)(t0 + tid) : __ldg(&a.active[t0 + tid]);
+                if (v != a.root) {
+                    const long long b = a.row_off[v];
+                    deg = (int)(a.row_off[v + 1] - b);
+                    s_base[tid] = b;
+                } else {
+                    v = -1;
+                }
+            }
+            s_v[tid] = v;
+            s_bv[tid] = kInfBits + 1ull;  // above +inf: "no candidate yet"
+            s_bid[tid] = INT_MAX;
+            s_bw[tid] = CostBits<CT>::kMax;
+            int incl = deg;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if ((tid & 31) >= off) incl += y;
+            }
+            if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
+            s_seg[tid + 1] = incl;  // fixed up below for the second warp
+        }
+        if (tid == 0) s_seg[0] = 0;
+        __syncthreads();
+        if (tid >= 32 && tid < kTileV) s_seg[tid + 1] += s_wsum[0];
+        __syncthreads();
+        const int total = s_seg[kTileV];
+
+        // 2. stream the concatenated rows
+        for (int c0 = 0; c0 < total; c0 += kChunk) {
+            if (tid < kTileV) {
+                s_cv[tid] = kInfBits + 1ull;
+                s_cid[tid] = INT_MAX;
+                s_cw[tid] = CostBits<CT>::kMax;
+            }
+            __syncthreads();
+            Entry<CT> en[kPerThread];
+            int kk[kPerThread];
+#pragma unroll
+            for (int i = 0; i < kPerThread; ++i) {
+                const int pos = c0 + tid + i * kThreads;
+                kk[i] = -1;
+                if (pos < total) {
+                    int lo = 0, hi = kTileV;  // last k with s_seg[k] <= pos
+                    while (hi - lo > 1) {
+                        const int mid = (lo + hi) >> 1;
+                        if (s_seg[mid] <= pos) lo = mid; else hi = mid;
+                    }
+                    kk[i] = lo;
+                    en[i] = ld_stream(&a.adj[s_base[lo] + (pos - s_seg[lo])]);
+                }
+            }
+            unsigned long long vb[kPerThread];
+#pragma unroll
+            for (int i = 0; i < kPerThread; ++i) {
+                if (kk[i] >= 0) {
+                    const double val = __ldg(&a.g[en[i].col]) + (double)en[i].w;
+                    vb[i] = (unsigned long long)__double_as_longlong(val);
+                    atomicMin(&s_cv[kk[i]], vb[i]);
+                }
+            }
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kPerThread; ++i)
+                if (kk[i] >= 0 && vb[i] == s_cv[kk[i]]) atomicMin(&s_cid[kk[i]], en[i].col);
+            __syncthreads();
+#pragma unroll
+            for (int i = 0; i < kPerThread; ++i)
+                if (kk[i] >= 0 && vb[i] == s_cv[kk[i]] && en[i].col == s_cid[kk[i]])
+                    atomicMin(&s_cw[kk[i]], CostBits<CT>::of(en[i].w));
+            __syncthreads();
+            if (tid < kTileV) {  // merge the chunk into the tile minimum
+                const unsigned long long cv = s_cv[tid], bv = s_bv[tid];
+                const int32_t cid = s_cid[tid], bid = s_bid[tid];
+                const WB cw = s_cw[tid], bw = s_bw[tid];
+                if (cv < bv || (cv == bv && (cid < bid || (cid == bid && cw < bw)))) {
+                    s_bv[tid] = cv;
+                    s_bid[tid] = cid;
+                    s_bw[tid] = cw;
+                }
+            }
+            __syncthreads();
+        }
+
+        // 3. switch where the best candidate beats the current parent
+        if (tid < nv) {
+            const int32_t v = s_v[tid];
+            if (v >= 0) {
+                const int32_t pv = a.p[v];
+                const double cur = pv >= 0 ? a.g[pv] + (double)a.pc[v] : CUDART_INF;
+                if (s_bv[tid] <= kInfBits) {
+                    const double best = __longlong_as_double((long long)s_bv[tid]);
+                    if (best < cur) {
+                        a.p[v] = s_bid[tid];
+                        a.pc[v] = CostBits<CT>::back(s_bw[tid]);
+                        const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
+                        a.switched[slot] = v;
+                        atomicMax(&a.ctr->dj_bits,
+                                  (unsigned long long)__double_as_longlong(cur - best));
+                    }
+                }
+                relax += (unsigned long long)(s_seg[tid + 1] - s_seg[tid]);
+                improved += 1;
+            }
+        }
+        __syncthreads();
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        relax += __shfl_down_sync(0xffffffffu, relax, off);
+        improved += __shfl_down_sync(0xffffffffu, improved, off);
+    }
+    if ((tid & 31) == 0 && (relax || improved)) {
+        atomicAdd(&a.ctr->relax, relax);
+        atomicAdd(&a.ctr->improved, improved);
+    }
+}
+
 // ---------------------------------------------------------------------------
 // Evaluate (Alg. 2; Sec. IV-C) -- g(v) = g(p(v)) + c(p(v), v) from the root,
 // by pointer jumping over the parent tree in FP64.

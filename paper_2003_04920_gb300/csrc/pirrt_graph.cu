@@ -117,14 +117,23 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
     return PIRRT_OK;
 }
 
-template <typename CT>
-int group_for(const pirrt_graph *G, int requested) {
+// 0 = the tiled kernel; 4, 8, 16, 32 = G threads per vertex.
+int group_for(int requested) {
     if (requested == 4 || requested == 8 || requested == 16 || requested == 32) return requested;
-    const double avg = G->n > 0 ? (double)G->m / (double)G->n : 0.0;
-    if (avg <= 12.0) return 4;
-    if (avg <= 40.0) return 8;
-    if (avg <= 100.0) return 16;
-    return 32;
+    return 0;
+}
+
+template <typename CT>
+pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a) {
+    static int occ = -1;
+    if (occ < 0) {
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tile_kernel<CT>, kThreads, 0));
+        occ = nb > 0 ? nb : 1;
+    }
+    improve_tile_kernel<CT><<<G->num_sms * occ, kThreads, 0, G->stream>>>(a);
+    CKL();
+    return PIRRT_OK;
 }
 
 template <typename CT, int GS>
@@ -154,6 +163,7 @@ pirrt_status launch_improve(pirrt_graph *G, int gs) {
     a.n = G->n;
     a.root = G->cfg.root;
     switch (gs) {
+        case 0: return launch_improve_tile<CT>(G, a);
         case 4: return launch_improve_g<CT, 4>(G, a);
         case 8: return launch_improve_g<CT, 8>(G, a);
         case 16: return launch_improve_g<CT, 16>(G, a);
@@ -311,7 +321,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP)
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
-    const int gs = group_for<CT>(G, o.group);
+    const int gs = group_for(o.group);
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
     const unsigned dense_limit = (unsigned)std::min<double>(4.0e9, frac * (double)G->n);
     const int mode = o.evaluate;

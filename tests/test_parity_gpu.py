@@ -75,6 +75,35 @@ def test_random_graphs(seed, dtype):
     assert_parity(rm, g, p, g_ref, p_ref)
 
 
+def test_high_degree_rows_span_chunks():
+    """A hub joined to thousands of vertices: its row spans several
+    2048-entry chunks of the tiled Improve; plus a long path hanging off it."""
+    n = 6000
+    rng = np.random.default_rng(11)
+    hub_u = np.zeros(4999, dtype=np.int32)
+    hub_v = np.arange(1, 5000, dtype=np.int32)
+    hub_c = rng.uniform(1.0, 2.0, 4999)
+    path_u = np.arange(4999, n - 1, dtype=np.int32)
+    path_v = path_u + 1
+    path_c = rng.uniform(0.1, 0.2, len(path_u))
+    extra_u = rng.integers(1, 5000, 3000).astype(np.int32)
+    extra_v = rng.integers(5000, n, 3000).astype(np.int32)
+    extra_c = rng.uniform(0.5, 3.0, 3000)
+    u = np.r_[hub_u, path_u, extra_u]
+    v = np.r_[hub_v, path_v, extra_v]
+    c = np.r_[hub_c, path_c, extra_c]
+    order = np.argsort(np.maximum(u, v), kind="stable")
+    u, v, c = u[order], v[order], c[order]
+    lo, hi = np.minimum(u, v), np.maximum(u, v)
+    rm = W.Roadmap("hub", np.zeros((n, 1)), lo, hi, c,
+                   np.searchsorted(hi, np.arange(n + 1)).astype(np.int64), n)
+    for dtype in (np.float64, np.float32):
+        rmd = W.Roadmap(rm.name, rm.points, rm.u, rm.v, rm.cost.astype(dtype), rm.edge_start, n)
+        g_ref, p_ref, _ = _o1(rmd)
+        g, p, _ = gpu_schedule(rmd)
+        assert_parity(rmd, g, p, g_ref, p_ref)
+
+
 # ------------------------------------ Batched-Extension schedules (C2/C3) ---
 
 @pytest.fixture(scope="module")
@@ -124,9 +153,11 @@ def test_c2_as_specified_small_reachable_set():
 # ------------------------------------------------------ invariances ---
 
 @pytest.mark.parametrize("group", [4, 8, 16, 32])
-def test_group_size_does_not_change_results(c3_small, group):
+def test_improve_kernels_agree(c3_small, group):
+    """The tiled Improve (default) and the G-threads-per-vertex kernels take
+    the same lexicographic argmin, so whole schedules agree bit for bit."""
     rm = c3_small
-    g0, p0, _ = gpu_schedule(rm, group=8)
+    g0, p0, _ = gpu_schedule(rm)
     g, p, _ = gpu_schedule(rm, group=group)
     np.testing.assert_array_equal(g, g0)
     np.testing.assert_array_equal(p, p0)

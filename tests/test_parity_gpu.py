@@ -80,13 +80,13 @@ def test_high_degree_rows_span_chunks():
     2048-entry chunks of the tiled Improve; plus a long path hanging off it."""
     n = 6000
     rng = np.random.default_rng(11)
-    hub_u = np.zeros(4999, dtype=np.int32)
-    hub_v = np.arange(1, 5000, dtype=np.int32)
-    hub_c = rng.uniform(1.0, 2.0, 4999)
+    hub_u = np.r_[0, np.ones(4998)].astype(np.int32)      # vertex 1 is the hub
+    hub_v = np.r_[1, np.arange(2, 5000)].astype(np.int32)
+    hub_c = np.r_[0.5, rng.uniform(1.0, 2.0, 4998)]
     path_u = np.arange(4999, n - 1, dtype=np.int32)
     path_v = path_u + 1
     path_c = rng.uniform(0.1, 0.2, len(path_u))
-    extra_u = rng.integers(1, 5000, 3000).astype(np.int32)
+    extra_u = rng.integers(2, 5000, 3000).astype(np.int32)
     extra_v = rng.integers(5000, n, 3000).astype(np.int32)
     extra_c = rng.uniform(0.5, 3.0, 3000)
     u = np.r_[hub_u, path_u, extra_u]

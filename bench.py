@@ -176,19 +176,25 @@ def run_ours(args) -> None:
     G = P.Graph(rm.n, rm.m, 0, rm.cost.dtype, device=local, stream=stream.cuda_stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
 
+    extra = {"wave_levels": 0, "jump_evaluates": 0, "dense_sweeps": 0, "switches": 0}
+
     def step(device_inputs=True):
         G.reset()
         relax = 0
         iters = 0
+        for k in extra:
+            extra[k] = 0
         for v0, v1, e0, e1 in rm.blocks():
             if device_inputs:
                 G.insert_batch(v1 - v0, dev_u[e0:e1], dev_v[e0:e1], dev_c[e0:e1])
             else:
                 G.insert_batch(v1 - v0, host_u[e0:e1], host_v[e0:e1], host_c[e0:e1])
-            st = G.exploit(group=args.group, dense_fraction=args.dense_fraction,
+            st = G.exploit(group=args.group, tile=args.tile, dense_fraction=args.dense_fraction,
                            evaluate=args.evaluate, wave_levels=args.wave_levels)
             relax += st["relaxations"]
             iters += st["iterations"]
+            for k in extra:
+                extra[k] += st[k]
         return relax, iters
 
     def barrier():
@@ -298,6 +304,9 @@ def run_ours(args) -> None:
                    "blocks_per_step": n_blocks, "block_size": rm.block,
                    "evaluate": args.evaluate,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
+                   "per_step": dict(extra),
+                   "improve_kernel": f"tiled ({args.tile or 'default'} vertices per tile)"
+                   if args.group == 0 else f"{args.group} threads per vertex",
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
                          % (2 * rm.m * entry_bytes / 1e9)},
@@ -412,6 +421,7 @@ def main():
     ap.add_argument("--block", type=int, default=None, help="override the block size S")
     ap.add_argument("--trial", type=int, default=0)
     ap.add_argument("--group", type=int, default=0)
+    ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--dense-fraction", type=float, default=0.0)
     ap.add_argument("--evaluate", choices=("auto", "wave", "jump"), default="auto")
     ap.add_argument("--wave-levels", type=int, default=0)

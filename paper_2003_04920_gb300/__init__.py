@@ -47,8 +47,9 @@ class pirrt_config(ctypes.Structure):
 
 class pirrt_exploit_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int32),
-                ("group", ctypes.c_int32), ("evaluate", ctypes.c_int32),
-                ("wave_levels", ctypes.c_int32), ("dense_fraction", ctypes.c_double)]
+                ("group", ctypes.c_int32), ("tile", ctypes.c_int32), ("evaluate", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("dense_fraction", ctypes.c_double)]
 
 
 class pirrt_exploit_stats(ctypes.Structure):
@@ -216,11 +217,11 @@ class Graph:
         self._check("pirrt_graph_set_policy",
                     self._lib.pirrt_graph_set_policy(self._h, pp, int(n), dev))
 
-    def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0,
+    def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                 dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
                 check: bool = True) -> dict:
-        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group),
-                                  EVALUATE_MODES[evaluate], int(wave_levels),
+        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
+                                  EVALUATE_MODES[evaluate], int(wave_levels), 0,
                                   float(dense_fraction))
         st = pirrt_exploit_stats()
         rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))

@@ -363,41 +363,50 @@ struct CostBits<double> {
     static constexpr unsigned long long kMax = 0xffffffffffffffffull;
 };
 
-template <typename CT>
-__global__ void __launch_bounds__(kThreads, 3)
+template <typename CT, int THREADS, int TILE_V, int PER>
+__global__ void __launch_bounds__(THREADS)
 improve_tile_kernel(ImproveArgs<CT> a) {
+    static_assert(TILE_V <= THREADS && TILE_V % 16 == 0 && TILE_V <= 128, "tile shape");
     using WB = typename CostBits<CT>::T;
+    constexpr int CHUNK = THREADS * PER;
+    constexpr int NW = (TILE_V + 31) / 32;
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-    __shared__ int32_t s_v[kTileV];
-    __shared__ long long s_base[kTileV];
-    __shared__ int32_t s_seg[kTileV + 1];
-    __shared__ unsigned long long s_cv[kTileV];  // chunk minimum: value bits
-    __shared__ int32_t s_cid[kTileV];            //   id
-    __shared__ WB s_cw[kTileV];                  //   cost bits
-    __shared__ unsigned long long s_bv[kTileV];  // tile minimum so far
-    __shared__ int32_t s_bid[kTileV];
-    __shared__ WB s_bw[kTileV];
-    __shared__ int32_t s_wsum[2];
+    __shared__ int32_t s_v[TILE_V];
+    __shared__ long long s_base[TILE_V];
+    __shared__ int32_t s_seg[TILE_V + 1];
+    __shared__ unsigned long long s_cv[TILE_V];  // chunk minimum: value bits
+    __shared__ int32_t s_cid[TILE_V];            //   id
+    __shared__ WB s_cw[TILE_V];                  //   cost bits
+    __shared__ unsigned long long s_bv[TILE_V];  // tile minimum so far
+    __shared__ int32_t s_bid[TILE_V];
+    __shared__ WB s_bw[TILE_V];
+    __shared__ int32_t s_wsum[NW];
 
-    const int tid = threadIdx.x;
+    const int tid = threadIdx.x, lane = tid & 31;
     const bool dense = a.ctr->dense != 0u;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
-    const int64_t n_tiles = (count + kTileV - 1) / kTileV;
+    const int64_t n_tiles = (count + TILE_V - 1) / TILE_V;
     unsigned long long relax = 0, improved = 0;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t t0 = tile * kTileV;
-        const int nv = (count - t0) < (int64_t)kTileV ? (int)(count - t0) : kTileV;
-        // 1. vertices of the tile, their row extents, exclusive scan of degrees
+        const int64_t t0 = tile * TILE_V;
+        const int nv = (count - t0) < (int64_t)TILE_V ? (int)(count - t0) : TILE_V;
+        // 1. vertices of the tile, row extents, current-parent candidate,
+        //    exclusive scan of the degrees
         int deg = 0;
-        if (tid < kTileV) {
-            int32_t v = -1;
+        int32_t v = -1, pv = -1;
+        CT pcv = CT(0);
+        double gp = CUDART_INF;
+        if (tid < TILE_V) {
             if (tid < nv) {
                 v = dense ? (int32_t)(t0 + tid) : __ldg(&a.active[t0 + tid]);
                 if (v != a.root) {
                     const long long b = a.row_off[v];
                     deg = (int)(a.row_off[v + 1] - b);
                     s_base[tid] = b;
+                    pv = a.p[v];
+                    pcv = a.pc[v];
+                    if (pv >= 0) gp = a.g[pv];
                 } else {
                     v = -1;
                 }
@@ -410,33 +419,37 @@ improve_tile_kernel(ImproveArgs<CT> a) {
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if ((tid & 31) >= off) incl += y;
+                if (lane >= off) incl += y;
             }
-            if ((tid & 31) == 31) s_wsum[tid >> 5] = incl;
-            s_seg[tid + 1] = incl;  // fixed up below for the second warp
+            if (lane == 31 || tid == TILE_V - 1) s_wsum[tid >> 5] = incl;
+            s_seg[tid + 1] = incl;
         }
         if (tid == 0) s_seg[0] = 0;
         __syncthreads();
-        if (tid >= 32 && tid < kTileV) s_seg[tid + 1] += s_wsum[0];
+        if (NW > 1 && tid >= 32 && tid < TILE_V) {
+            int add = 0;
+            for (int w = 0; w < (tid >> 5); ++w) add += s_wsum[w];
+            s_seg[tid + 1] += add;
+        }
         __syncthreads();
-        const int total = s_seg[kTileV];
+        const int total = s_seg[TILE_V];
 
         // 2. stream the concatenated rows
-        for (int c0 = 0; c0 < total; c0 += kChunk) {
-            if (tid < kTileV) {
+        for (int c0 = 0; c0 < total; c0 += CHUNK) {
+            if (tid < TILE_V) {
                 s_cv[tid] = kInfBits + 1ull;
                 s_cid[tid] = INT_MAX;
                 s_cw[tid] = CostBits<CT>::kMax;
             }
             __syncthreads();
-            Entry<CT> en[kPerThread];
-            int kk[kPerThread];
+            Entry<CT> en[PER];
+            int kk[PER];
 #pragma unroll
-            for (int i = 0; i < kPerThread; ++i) {
-                const int pos = c0 + tid + i * kThreads;
+            for (int i = 0; i < PER; ++i) {
+                const int pos = c0 + tid + i * THREADS;
                 kk[i] = -1;
                 if (pos < total) {
-                    int lo = 0, hi = kTileV;  // last k with s_seg[k] <= pos
+                    int lo = 0, hi = TILE_V;  // last k with s_seg[k] <= pos
                     while (hi - lo > 1) {
                         const int mid = (lo + hi) >> 1;
                         if (s_seg[mid] <= pos) lo = mid; else hi = mid;
@@ -445,9 +458,9 @@ improve_tile_kernel(ImproveArgs<CT> a) {
                     en[i] = ld_stream(&a.adj[s_base[lo] + (pos - s_seg[lo])]);
                 }
             }
-            unsigned long long vb[kPerThread];
+            unsigned long long vb[PER];
 #pragma unroll
-            for (int i = 0; i < kPerThread; ++i) {
+            for (int i = 0; i < PER; ++i) {
                 if (kk[i] >= 0) {
                     const double val = __ldg(&a.g[en[i].col]) + (double)en[i].w;
                     vb[i] = (unsigned long long)__double_as_longlong(val);
@@ -456,15 +469,15 @@ improve_tile_kernel(ImproveArgs<CT> a) {
             }
             __syncthreads();
 #pragma unroll
-            for (int i = 0; i < kPerThread; ++i)
+            for (int i = 0; i < PER; ++i)
                 if (kk[i] >= 0 && vb[i] == s_cv[kk[i]]) atomicMin(&s_cid[kk[i]], en[i].col);
             __syncthreads();
 #pragma unroll
-            for (int i = 0; i < kPerThread; ++i)
+            for (int i = 0; i < PER; ++i)
                 if (kk[i] >= 0 && vb[i] == s_cv[kk[i]] && en[i].col == s_cid[kk[i]])
                     atomicMin(&s_cw[kk[i]], CostBits<CT>::of(en[i].w));
             __syncthreads();
-            if (tid < kTileV) {  // merge the chunk into the tile minimum
+            if (tid < TILE_V) {  // merge the chunk into the tile minimum
                 const unsigned long long cv = s_cv[tid], bv = s_bv[tid];
                 const int32_t cid = s_cid[tid], bid = s_bid[tid];
                 const WB cw = s_cw[tid], bw = s_bw[tid];
@@ -477,26 +490,22 @@ improve_tile_kernel(ImproveArgs<CT> a) {
             __syncthreads();
         }
 
-        // 3. switch where the best candidate beats the current parent
-        if (tid < nv) {
-            const int32_t v = s_v[tid];
-            if (v >= 0) {
-                const int32_t pv = a.p[v];
-                const double cur = pv >= 0 ? a.g[pv] + (double)a.pc[v] : CUDART_INF;
-                if (s_bv[tid] <= kInfBits) {
-                    const double best = __longlong_as_double((long long)s_bv[tid]);
-                    if (best < cur) {
-                        a.p[v] = s_bid[tid];
-                        a.pc[v] = CostBits<CT>::back(s_bw[tid]);
-                        const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
-                        a.switched[slot] = v;
-                        atomicMax(&a.ctr->dj_bits,
-                                  (unsigned long long)__double_as_longlong(cur - best));
-                    }
+        // 3. switch where the best candidate beats the current parent,
+        //    g(p) + c computed by the same expression as every candidate
+        if (tid < nv && v >= 0) {
+            const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
+            if (s_bv[tid] <= kInfBits) {
+                const double best = __longlong_as_double((long long)s_bv[tid]);
+                if (best < cur) {
+                    a.p[v] = s_bid[tid];
+                    a.pc[v] = CostBits<CT>::back(s_bw[tid]);
+                    const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
+                    a.switched[slot] = v;
+                    atomicMax(&a.ctr->dj_bits, (unsigned long long)__double_as_longlong(cur - best));
                 }
-                relax += (unsigned long long)(s_seg[tid + 1] - s_seg[tid]);
-                improved += 1;
             }
+            relax += (unsigned long long)deg;
+            improved += 1;
         }
         __syncthreads();
     }
@@ -505,7 +514,7 @@ improve_tile_kernel(ImproveArgs<CT> a) {
         relax += __shfl_down_sync(0xffffffffu, relax, off);
         improved += __shfl_down_sync(0xffffffffu, improved, off);
     }
-    if ((tid & 31) == 0 && (relax || improved)) {
+    if (lane == 0 && (relax || improved)) {
         atomicAdd(&a.ctr->relax, relax);
         atomicAdd(&a.ctr->improved, improved);
     }
@@ -700,16 +709,27 @@ struct WaveArgs {
 // stale parent value and recomputed when the upper wave reaches it; the last
 // write of every vertex comes one level after its parent's last change, so
 // the result does not depend on scheduling.
+//
+// Each level is split evenly over the CTAs.  A CTA takes up to kWaveThreads
+// vertices at a time, one per thread, then streams the concatenated rows of
+// the changed ones with every thread (the loads of a whole tile in flight at
+// once), locating each entry's row by binary search over the tile's prefix
+// sums in shared memory.
+constexpr int kWaveThreads = 512;
+constexpr int kWaveUnroll = 4;
+
 template <typename CT>
-__global__ void __launch_bounds__(kThreads)
+__global__ void __launch_bounds__(kWaveThreads)
 wave_evaluate_kernel(WaveArgs<CT> a) {
+    __shared__ int32_t s_u[kWaveThreads];
+    __shared__ long long s_base[kWaveThreads];
+    __shared__ int32_t s_seg[kWaveThreads + 1];
+    __shared__ int32_t s_wsum[kWaveThreads / 32];
     DevCounters *c = a.ctr;
     const unsigned n_sw = c->n_switched;
     if (n_sw == 0u) return;
     const unsigned nblocks = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
-    const int64_t warp_id = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5);
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     unsigned long long recomputed = 0, changed_total = 0;
     unsigned t = 0;
     for (;; ++t) {
@@ -717,49 +737,96 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
             t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
         if (count == 0) break;
         if (t >= a.max_levels) {
-            if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_incomplete = 1u;
+            if (blockIdx.x == 0 && tid == 0) c->wave_incomplete = 1u;
             break;
         }
         const int32_t *in = t == 0 ? a.switched : (((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0]);
         int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
         unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
-        if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_cnt[(t + 2) % 3] = 0u;
+        if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
         const unsigned wtag = a.wave_epoch + t;  // stamp of level t + 1
         const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
-        for (int64_t j = warp_id; j < count; j += warps) {
-            const int32_t u = __ldcg(&in[j]);
-            int changed = 0;
-            if (lane == 0) {
+        const int64_t per = (count + nblocks - 1) / nblocks;
+        const int64_t lo = (int64_t)blockIdx.x * per;
+        const int64_t hi = lo + per < count ? lo + per : count;
+        for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
+            const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
+            int deg = 0;
+            int32_t u = -1;
+            if (tid < nv) {
+                u = __ldcg(&in[s0 + tid]);
                 const int32_t pu = __ldcg(&a.p[u]);
                 const double gn = __ldcg(&a.g[pu]) + (double)a.pc[u];
                 const double go = __ldcg(&a.g[u]);
+                ++recomputed;
                 if (__double_as_longlong(gn) != __double_as_longlong(go)) {
                     __stcg(&a.g[u], gn);
-                    changed = 1;
+                    ++changed_total;
+                    const long long b = a.row_off[u];
+                    deg = (int)(a.row_off[u + 1] - b);
+                    s_base[tid] = b;
                 }
             }
-            changed = __shfl_sync(0xffffffffu, changed, 0);
-            if (lane == 0) {
-                ++recomputed;
-                changed_total += (unsigned long long)changed;
+            s_u[tid] = u;
+            // block exclusive scan of the changed rows' lengths
+            int incl = deg;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
             }
-            if (!changed) continue;
-            const int64_t b = a.row_off[u], e = a.row_off[u + 1];
-            for (int64_t i0 = b; i0 < e; i0 += 32) {
-                const int64_t i = i0 + lane;
-                bool child = false, mark = false;
-                int32_t w = 0;
-                if (i < e) {
-                    w = ld_stream(&a.adj[i]).col;
-                    child = __ldcg(&a.p[w]) == u && atomicExch(&a.wstamp[w], wtag) != wtag;
-                    mark = marking && w != a.root && __ldcg(&a.stamp[w]) != a.epoch &&
-                           atomicExch(&a.stamp[w], a.epoch) != a.epoch;
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                int w = lane < kWaveThreads / 32 ? s_wsum[lane] : 0;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, w, off);
+                    if (lane >= off) w += y;
                 }
-                warp_append(child, w, out, out_cnt);
-                warp_append(mark, w, a.next, &c->n_next);
+                if (lane < kWaveThreads / 32) s_wsum[lane] = w;
             }
+            __syncthreads();
+            s_seg[tid + 1] = incl + (warp > 0 ? s_wsum[warp - 1] : 0);
+            if (tid == 0) s_seg[0] = 0;
+            __syncthreads();
+            const int total = s_seg[kWaveThreads];
+            for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
+                int32_t w[kWaveUnroll], owner[kWaveUnroll];
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    const int pos = p0 + tid + j * kWaveThreads;
+                    owner[j] = -1;
+                    w[j] = 0;
+                    if (pos < total) {
+                        int l = 0, h = kWaveThreads;  // last k with s_seg[k] <= pos
+                        while (h - l > 1) {
+                            const int mid = (l + h) >> 1;
+                            if (s_seg[mid] <= pos) l = mid; else h = mid;
+                        }
+                        owner[j] = s_u[l];
+                        w[j] = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]).col;
+                    }
+                }
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    bool child = false, mark = false;
+                    if (owner[j] >= 0) {
+                        child = __ldcg(&a.p[w[j]]) == owner[j] &&
+                                atomicExch(&a.wstamp[w[j]], wtag) != wtag;
+                        mark = marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != a.epoch &&
+                               atomicExch(&a.stamp[w[j]], a.epoch) != a.epoch;
+                    }
+                    warp_append(child, w[j], out, out_cnt);
+                    warp_append(mark, w[j], a.next, &c->n_next);
+                }
+            }
+            __syncthreads();  // s_u / s_base / s_seg are rewritten by the next tile
         }
         // changed-vertex count decides between a list and a dense sweep next
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1)
+            changed_total += __shfl_down_sync(0xffffffffu, changed_total, off);
         if (lane == 0 && changed_total) {
             const unsigned total = atomicAdd(&c->n_dg, (unsigned)changed_total) +
                                    (unsigned)changed_total;
@@ -768,9 +835,10 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
         changed_total = 0;
         if (!grid_barrier(c, nblocks)) return;
     }
-    // lane 0 of each warp counted every vertex the warp processed
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) recomputed += __shfl_down_sync(0xffffffffu, recomputed, off);
     if (lane == 0 && recomputed) atomicAdd(&c->evaluated, recomputed);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->wave_levels = t;
+    if (blockIdx.x == 0 && tid == 0) c->wave_levels = t;
 }
 
 // Clear the per-iteration fields (not the current list or the dense flag).

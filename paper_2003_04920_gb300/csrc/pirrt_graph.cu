@@ -123,17 +123,29 @@ int group_for(int requested) {
     return 0;
 }
 
-template <typename CT>
-pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a) {
+template <typename CT, int TH, int TV, int PER>
+pirrt_status launch_improve_tile_v(pirrt_graph *G, const ImproveArgs<CT> &a) {
     static int occ = -1;
     if (occ < 0) {
         int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tile_kernel<CT>, kThreads, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tile_kernel<CT, TH, TV, PER>,
+                                                         TH, 0));
         occ = nb > 0 ? nb : 1;
     }
-    improve_tile_kernel<CT><<<G->num_sms * occ, kThreads, 0, G->stream>>>(a);
+    improve_tile_kernel<CT, TH, TV, PER><<<G->num_sms * occ, TH, 0, G->stream>>>(a);
     CKL();
     return PIRRT_OK;
+}
+
+// Tiled Improve shapes (vertices per tile -> threads, entries per thread).
+template <typename CT>
+pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
+    switch (tile) {
+        case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
+        case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
+        case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
+        default: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
+    }
 }
 
 template <typename CT, int GS>
@@ -150,7 +162,7 @@ pirrt_status launch_improve_g(pirrt_graph *G, const ImproveArgs<CT> &a) {
 }
 
 template <typename CT>
-pirrt_status launch_improve(pirrt_graph *G, int gs) {
+pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
     ImproveArgs<CT> a;
     a.row_off = G->row_off[G->cur];
     a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
@@ -163,7 +175,7 @@ pirrt_status launch_improve(pirrt_graph *G, int gs) {
     a.n = G->n;
     a.root = G->cfg.root;
     switch (gs) {
-        case 0: return launch_improve_tile<CT>(G, a);
+        case 0: return launch_improve_tile<CT>(G, a, tile);
         case 4: return launch_improve_g<CT, 4>(G, a);
         case 8: return launch_improve_g<CT, 8>(G, a);
         case 16: return launch_improve_g<CT, 16>(G, a);
@@ -217,7 +229,7 @@ pirrt_status launch_wave(pirrt_graph *G, unsigned dense_limit, unsigned max_leve
     a.max_levels = max_levels;
     void *args[] = {&a};
     CK(cudaLaunchCooperativeKernel((const void *)wave_evaluate_kernel<CT>, dim3(G->wave_blocks),
-                                   dim3(kThreads), args, 0, G->stream));
+                                   dim3(kWaveThreads), args, 0, G->stream));
     return PIRRT_OK;
 }
 
@@ -318,7 +330,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     pirrt_exploit_opts o{};
     if (opts) o = *opts;
     if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
-        o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP)
+        o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
+        (o.tile != 0 && o.tile != 16 && o.tile != 32 && o.tile != 64 && o.tile != 128))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = group_for(o.group);
@@ -344,7 +357,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     for (int64_t it = 0; it < max_iters; ++it) {
         // Improve, then Evaluate (+ frontier marking), then one counter read
         if (prof) CK(cudaEventRecord(G->pev[0], G->stream));
-        if ((rc = launch_improve<CT>(G, gs))) return rc;
+        if ((rc = launch_improve<CT>(G, gs, o.tile))) return rc;
         if (prof) CK(cudaEventRecord(G->pev[1], G->stream));
         bool jumped = false;
         if (mode == PIRRT_EVAL_JUMP) {
@@ -620,14 +633,14 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     if (occ < 1) return bail(PIRRT_ERR_CUDA);
     G->eval_blocks = G->num_sms * occ;
     int wocc = 0, wocc64 = 0;
-    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, wave_evaluate_kernel<float>, kThreads,
-                                                      0) != cudaSuccess ||
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc, wave_evaluate_kernel<float>,
+                                                      kWaveThreads, 0) != cudaSuccess ||
         cudaOccupancyMaxActiveBlocksPerMultiprocessor(&wocc64, wave_evaluate_kernel<double>,
-                                                      kThreads, 0) != cudaSuccess)
+                                                      kWaveThreads, 0) != cudaSuccess)
         return bail(PIRRT_ERR_CUDA);
     wocc = std::min(wocc, wocc64);
     if (wocc < 1) return bail(PIRRT_ERR_CUDA);
-    G->wave_blocks = G->num_sms * std::min(wocc, 4);
+    G->wave_blocks = G->num_sms * std::min(wocc, 2);
     pirrt_status rc = pirrt_graph_reset(G);
     if (rc) return bail(rc);
     *out = G;

@@ -152,13 +152,14 @@ def test_c2_as_specified_small_reachable_set():
 
 # ------------------------------------------------------ invariances ---
 
-@pytest.mark.parametrize("group", [4, 8, 16, 32])
-def test_improve_kernels_agree(c3_small, group):
-    """The tiled Improve (default) and the G-threads-per-vertex kernels take
-    the same lexicographic argmin, so whole schedules agree bit for bit."""
+@pytest.mark.parametrize("group,tile", [(4, 0), (8, 0), (16, 0), (32, 0), (0, 16), (0, 32),
+                                        (0, 64), (0, 128)])
+def test_improve_kernels_agree(c3_small, group, tile):
+    """Every tiled Improve shape and the G-threads-per-vertex kernels take the
+    same lexicographic argmin, so whole schedules agree bit for bit."""
     rm = c3_small
     g0, p0, _ = gpu_schedule(rm)
-    g, p, _ = gpu_schedule(rm, group=group)
+    g, p, _ = gpu_schedule(rm, group=group, tile=tile)
     np.testing.assert_array_equal(g, g0)
     np.testing.assert_array_equal(p, p0)
 

@@ -366,7 +366,8 @@ struct CostBits<double> {
 template <typename CT, int THREADS, int TILE_V, int PER>
 __global__ void __launch_bounds__(THREADS)
 improve_tile_kernel(ImproveArgs<CT> a) {
-    static_assert(TILE_V <= THREADS && TILE_V % 16 == 0 && TILE_V <= 128, "tile shape");
+    static_assert(TILE_V % 16 == 0 && TILE_V <= 128 && THREADS % 32 == 0, "tile shape");
+    static_assert(((TILE_V + 31) / 32) * 32 <= THREADS, "the scan needs whole warps");
     using WB = typename CostBits<CT>::T;
     constexpr int CHUNK = THREADS * PER;
     constexpr int NW = (TILE_V + 31) / 32;
@@ -397,32 +398,35 @@ improve_tile_kernel(ImproveArgs<CT> a) {
         int32_t v = -1, pv = -1;
         CT pcv = CT(0);
         double gp = CUDART_INF;
-        if (tid < TILE_V) {
-            if (tid < nv) {
-                v = dense ? (int32_t)(t0 + tid) : __ldg(&a.active[t0 + tid]);
-                if (v != a.root) {
-                    const long long b = a.row_off[v];
-                    deg = (int)(a.row_off[v + 1] - b);
-                    s_base[tid] = b;
-                    pv = a.p[v];
-                    pcv = a.pc[v];
-                    if (pv >= 0) gp = a.g[pv];
-                } else {
-                    v = -1;
-                }
+        if (tid < nv) {
+            v = dense ? (int32_t)(t0 + tid) : __ldg(&a.active[t0 + tid]);
+            if (v != a.root) {
+                const long long b = a.row_off[v];
+                deg = (int)(a.row_off[v + 1] - b);
+                s_base[tid] = b;
+                pv = a.p[v];
+                pcv = a.pc[v];
+                if (pv >= 0) gp = a.g[pv];
+            } else {
+                v = -1;
             }
+        }
+        if (tid < TILE_V) {
             s_v[tid] = v;
             s_bv[tid] = kInfBits + 1ull;  // above +inf: "no candidate yet"
             s_bid[tid] = INT_MAX;
             s_bw[tid] = CostBits<CT>::kMax;
+        }
+        // whole warps take part in the shuffle scan (deg = 0 past the tile)
+        if (tid < NW * 32) {
             int incl = deg;
 #pragma unroll
             for (int off = 1; off < 32; off <<= 1) {
                 const int y = __shfl_up_sync(0xffffffffu, incl, off);
                 if (lane >= off) incl += y;
             }
-            if (lane == 31 || tid == TILE_V - 1) s_wsum[tid >> 5] = incl;
-            s_seg[tid + 1] = incl;
+            if (lane == 31) s_wsum[tid >> 5] = incl;
+            if (tid < TILE_V) s_seg[tid + 1] = incl;
         }
         if (tid == 0) s_seg[0] = 0;
         __syncthreads();

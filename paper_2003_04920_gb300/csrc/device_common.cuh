@@ -95,6 +95,43 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t *l
     if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
 }
 
+// Block-wide reservation in two lists at once: thread i wants na[i] slots of
+// list A and nb[i] of list B.  One atomicAdd per list per block; returns this
+// thread's first slot in each.  Every thread of the block must call it;
+// s_scan needs THREADS / 32 + 2 entries.
+template <int THREADS>
+__device__ __forceinline__ void block_reserve2(unsigned na, unsigned nb, unsigned *ctr_a,
+                                               unsigned *ctr_b, unsigned long long *s_scan,
+                                               unsigned &base_a, unsigned &base_b) {
+    constexpr int NW = THREADS / 32;
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long x = ((unsigned long long)nb << 32) | na;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const unsigned long long t = s_scan[w];
+            s_scan[w] = run;
+            run += t;
+        }
+        const unsigned ta = (unsigned)(run & 0xffffffffull), tb = (unsigned)(run >> 32);
+        s_scan[NW] = ta ? atomicAdd(ctr_a, ta) : 0u;
+        s_scan[NW + 1] = tb ? atomicAdd(ctr_b, tb) : 0u;
+    }
+    __syncthreads();
+    const unsigned long long ex = s_scan[warp] + incl - x;
+    base_a = (unsigned)s_scan[NW] + (unsigned)(ex & 0xffffffffull);
+    base_b = (unsigned)s_scan[NW + 1] + (unsigned)(ex >> 32);
+    __syncthreads();
+}
+
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
 // wait is bounded: on timeout the block raises kStatusTimeout and the
 // caller returns.  Returns false on timeout.

@@ -174,8 +174,12 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
             pa = a != root && atomicExch(&stamp[a], epoch) != epoch;
             pb = b != root && atomicExch(&stamp[b], epoch) != epoch;
         }
-        warp_append(pa, a, active, &ctr->n_active);
-        warp_append(pb, b, active, &ctr->n_active);
+        __shared__ unsigned long long s_scan[kThreads / 32 + 2];
+        unsigned ba, bb;
+        block_reserve2<kThreads>(pa ? 1u : 0u, pb ? 1u : 0u, &ctr->n_active, &ctr->n_active,
+                                 s_scan, ba, bb);
+        if (pa) active[ba] = a;
+        if (pb) active[bb] = b;
     }
 }
 
@@ -496,20 +500,30 @@ improve_tile_kernel(ImproveArgs<CT> a) {
 
         // 3. switch where the best candidate beats the current parent,
         //    g(p) + c computed by the same expression as every candidate
-        if (tid < nv && v >= 0) {
-            const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
-            if (s_bv[tid] <= kInfBits) {
-                const double best = __longlong_as_double((long long)s_bv[tid]);
-                if (best < cur) {
-                    a.p[v] = s_bid[tid];
-                    a.pc[v] = CostBits<CT>::back(s_bw[tid]);
-                    const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
-                    a.switched[slot] = v;
-                    atomicMax(&a.ctr->dj_bits, (unsigned long long)__double_as_longlong(cur - best));
+        if (tid < NW * 32) {  // whole warps: the appends below are warp-collective
+            bool sw = false;
+            unsigned long long dj = 0ull;
+            if (tid < nv && v >= 0) {
+                const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
+                if (s_bv[tid] <= kInfBits) {
+                    const double best = __longlong_as_double((long long)s_bv[tid]);
+                    if (best < cur) {
+                        a.p[v] = s_bid[tid];
+                        a.pc[v] = CostBits<CT>::back(s_bw[tid]);
+                        sw = true;
+                        dj = (unsigned long long)__double_as_longlong(cur - best);
+                    }
                 }
+                relax += (unsigned long long)deg;
+                improved += 1;
             }
-            relax += (unsigned long long)deg;
-            improved += 1;
+            warp_append(sw, v, a.switched, &a.ctr->n_switched);
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
+                dj = o > dj ? o : dj;
+            }
+            if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
         }
         __syncthreads();
     }
@@ -729,6 +743,7 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
     __shared__ long long s_base[kWaveThreads];
     __shared__ int32_t s_seg[kWaveThreads + 1];
     __shared__ int32_t s_wsum[kWaveThreads / 32];
+    __shared__ unsigned long long s_scan[kWaveThreads / 32 + 2];
     DevCounters *c = a.ctr;
     const unsigned n_sw = c->n_switched;
     if (n_sw == 0u) return;
@@ -812,17 +827,25 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
                         w[j] = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]).col;
                     }
                 }
+                unsigned childm = 0, markm = 0;
 #pragma unroll
                 for (int j = 0; j < kWaveUnroll; ++j) {
-                    bool child = false, mark = false;
                     if (owner[j] >= 0) {
-                        child = __ldcg(&a.p[w[j]]) == owner[j] &&
-                                atomicExch(&a.wstamp[w[j]], wtag) != wtag;
-                        mark = marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != a.epoch &&
-                               atomicExch(&a.stamp[w[j]], a.epoch) != a.epoch;
+                        if (__ldcg(&a.p[w[j]]) == owner[j] &&
+                            atomicExch(&a.wstamp[w[j]], wtag) != wtag)
+                            childm |= 1u << j;
+                        if (marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != a.epoch &&
+                            atomicExch(&a.stamp[w[j]], a.epoch) != a.epoch)
+                            markm |= 1u << j;
                     }
-                    warp_append(child, w[j], out, out_cnt);
-                    warp_append(mark, w[j], a.next, &c->n_next);
+                }
+                unsigned bc, bm;
+                block_reserve2<kWaveThreads>(__popc(childm), __popc(markm), out_cnt, &c->n_next,
+                                             s_scan, bc, bm);
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    if (childm & (1u << j)) out[bc++] = w[j];
+                    if (markm & (1u << j)) a.next[bm++] = w[j];
                 }
             }
             __syncthreads();  // s_u / s_base / s_seg are rewritten by the next tile

@@ -225,6 +225,8 @@ def run_ours(args) -> None:
             relaxes.append(r)
             iters_all.append(it)
     prof = G.get_profile()
+    if args.trace:
+        np.save(args.trace, G.get_trace())
     G.set_profiling(False)
     barrier()
     clocks = clk.summary()
@@ -427,6 +429,7 @@ def main():
     ap.add_argument("--wave-levels", type=int, default=0)
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--trace", default=None, help="save the per-iteration trace (.npy)")
     args = ap.parse_args()
     if args.impl == "reference":
         run_reference(args)

@@ -201,6 +201,24 @@ pirrt_status pirrt_graph_set_profiling(pirrt_graph *g, int enable);
 /* Copy the profile accumulated since the last pirrt_graph_set_profiling. */
 pirrt_status pirrt_graph_get_profile(const pirrt_graph *g, pirrt_profile *out);
 
+/* One Replan iteration as seen while profiling is enabled (tracing). */
+typedef struct {
+    int32_t iteration;        /* index within its exploit call */
+    int32_t dense;            /* 1 if Improve swept every vertex */
+    int64_t improve_vertices; /* vertices Improve processed */
+    int64_t improve_entries;  /* CSR entries Improve scanned */
+    int32_t switches;         /* parents switched */
+    int32_t changed;          /* vertices whose g changed in Evaluate */
+    int32_t wave_levels;      /* top-down Evaluate levels (0 for pointer jumping) */
+    int32_t next_frontier;    /* size of the next Improve list (0 if the next sweep is dense) */
+    float improve_ms, evaluate_ms, mark_ms, iteration_ms;  /* CUDA-event times */
+} pirrt_trace_record;
+
+/* Copy up to cap trace records (oldest first) recorded since the last
+ * pirrt_graph_set_profiling; returns how many exist (may exceed cap), or -1
+ * for a NULL handle. */
+int64_t pirrt_graph_get_trace(const pirrt_graph *g, pirrt_trace_record *out, int64_t cap);
+
 /* Current vertex count, or -1 for a NULL handle. */
 int64_t pirrt_graph_num_vertices(const pirrt_graph *g);
 

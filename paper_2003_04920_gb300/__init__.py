@@ -79,6 +79,15 @@ class pirrt_profile(ctypes.Structure):
         return {name: getattr(self, name) for name, _ in self._fields_}
 
 
+class pirrt_trace_record(ctypes.Structure):
+    _fields_ = [("iteration", ctypes.c_int32), ("dense", ctypes.c_int32),
+                ("improve_vertices", ctypes.c_int64), ("improve_entries", ctypes.c_int64),
+                ("switches", ctypes.c_int32), ("changed", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("next_frontier", ctypes.c_int32),
+                ("improve_ms", ctypes.c_float), ("evaluate_ms", ctypes.c_float),
+                ("mark_ms", ctypes.c_float), ("iteration_ms", ctypes.c_float)]
+
+
 _lib = None
 
 
@@ -107,6 +116,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_get_adjacency": (st, [vp, vp, vp, vp, i32]),
         "pirrt_graph_set_profiling": (st, [vp, i32]),
         "pirrt_graph_get_profile": (st, [vp, ctypes.POINTER(pirrt_profile)]),
+        "pirrt_graph_get_trace": (i64, [vp, ctypes.POINTER(pirrt_trace_record), i64]),
         "pirrt_graph_num_vertices": (i64, [vp]),
         "pirrt_graph_num_entries": (i64, [vp]),
         "pirrt_graph_last_error": (ctypes.c_char_p, [vp]),
@@ -240,6 +250,16 @@ class Graph:
         self._check("pirrt_graph_get_profile",
                     self._lib.pirrt_graph_get_profile(self._h, ctypes.byref(pr)))
         return pr.as_dict()
+
+    def get_trace(self) -> np.ndarray:
+        """Per-iteration trace recorded while profiling (structured array)."""
+        n = int(self._lib.pirrt_graph_get_trace(self._h, None, 0))
+        buf = (pirrt_trace_record * max(n, 1))()
+        self._lib.pirrt_graph_get_trace(self._h, buf, n)
+        names = [f for f, _ in pirrt_trace_record._fields_]
+        arr = np.ctypeslib.as_array(buf)[:n]
+        return np.array([tuple(r) for r in arr.tolist()], dtype=[(nm, arr.dtype[nm]) for nm in names]) \
+            if n else np.zeros(0, dtype=arr.dtype)
 
     def get_costs(self, out=None) -> np.ndarray:
         n = self.n

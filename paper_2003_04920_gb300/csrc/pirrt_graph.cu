@@ -13,6 +13,7 @@
 #include <cstring>
 #include <new>
 #include <string>
+#include <vector>
 
 #include "graph_kernels.cuh"
 #include "pirrt.h"
@@ -55,6 +56,8 @@ struct pirrt_graph {
     int wave_blocks = 0;
     int profiling = 0;
     pirrt_profile prof{};
+    std::vector<pirrt_trace_record> trace;
+    cudaEvent_t it_start = nullptr;
     cudaEvent_t pev[8] = {};          // improve, evaluate, mark, insert: (start, end) pairs
     std::string last_error;
 };
@@ -141,10 +144,10 @@ pirrt_status launch_improve_tile_v(pirrt_graph *G, const ImproveArgs<CT> &a) {
 template <typename CT>
 pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
     switch (tile) {
-        case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
         case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
+        case 64: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
         case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
-        default: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
+        default: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);  // measured best on GB300
     }
 }
 
@@ -402,6 +405,25 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 }
             }
         }
+        if (prof) {
+            pirrt_trace_record tr{};
+            tr.iteration = (int32_t)it;
+            tr.dense = h->dense ? 1 : 0;
+            tr.improve_vertices = (int64_t)(h->improved - prev_improved);
+            tr.improve_entries = (int64_t)(h->relax - prev_relax);
+            tr.switches = (int32_t)h->n_switched;
+            tr.changed = (int32_t)h->n_dg;
+            tr.wave_levels = mode != PIRRT_EVAL_JUMP ? (int32_t)h->wave_levels : 0;
+            tr.next_frontier = h->dense_next ? 0 : (int32_t)h->n_next;
+            tr.improve_ms = t_imp;
+            tr.evaluate_ms = t_eval;
+            tr.mark_ms = jumped ? t_mark : 0.f;
+            float t_it = 0.f;
+            if (it > 0) CK(cudaEventElapsedTime(&t_it, G->it_start, G->pev[0]));
+            tr.iteration_ms = t_it;  // previous iteration start to this one's start
+            if (G->trace.size() < (1u << 22)) G->trace.push_back(tr);
+            CK(cudaEventRecord(G->it_start, G->stream));
+        }
         s.iterations += 1;
         s.switches += h->n_switched;
         s.jump_rounds += (int32_t)h->rounds;
@@ -518,6 +540,7 @@ void free_all(pirrt_graph *G) {
     if (G->ev1) cudaEventDestroy(G->ev1);
     for (cudaEvent_t e : G->pev)
         if (e) cudaEventDestroy(e);
+    if (G->it_start) cudaEventDestroy(G->it_start);
 }
 
 }  // namespace
@@ -621,6 +644,7 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
         return bail(PIRRT_ERR_CUDA);
     for (cudaEvent_t &e : G->pev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(PIRRT_ERR_CUDA);
+    if (cudaEventCreate(&G->it_start) != cudaSuccess) return bail(PIRRT_ERR_CUDA);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, evaluate_kernel<float>, kThreads, 0) !=
         cudaSuccess)
@@ -764,7 +788,15 @@ pirrt_status pirrt_graph_set_profiling(pirrt_graph *G, int enable) {
     if (!G) return PIRRT_ERR_INVALID_ARG;
     G->profiling = enable ? 1 : 0;
     G->prof = pirrt_profile{};
+    G->trace.clear();
     return PIRRT_OK;
+}
+
+int64_t pirrt_graph_get_trace(const pirrt_graph *G, pirrt_trace_record *out, int64_t cap) {
+    if (!G) return -1;
+    const int64_t n = (int64_t)G->trace.size();
+    if (out && cap > 0) std::memcpy(out, G->trace.data(), sizeof(pirrt_trace_record) * (size_t)std::min(n, cap));
+    return n;
 }
 
 pirrt_status pirrt_graph_get_profile(const pirrt_graph *G, pirrt_profile *out) {

@@ -7,6 +7,7 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <cmath>
 #include <cstdarg>
 #include <cstdint>
 #include <cstdio>
@@ -47,6 +48,8 @@ struct pirrt_graph {
     int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
     unsigned *wstamp = nullptr;           // wave child dedup
     unsigned wave_epoch = 1;
+    int deep_hint = 0;                    // AUTO: recent exploits met waves past the cap
+    int exploits = 0;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned mirror
     void *stage = nullptr;            // device staging for host-side inputs
@@ -341,11 +344,24 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
     const unsigned dense_limit = (unsigned)std::min<double>(4.0e9, frac * (double)G->n);
     const int mode = o.evaluate;
-    // a wave deeper than the cap hands over to pointer jumping (AUTO); a WAVE
-    // run is only capped at |V| + 2 levels, beyond which the tree has a cycle
+    // A wave deeper than the cap hands over to pointer jumping (AUTO); a WAVE
+    // run is only capped at |V| + 2 levels, beyond which the tree has a cycle.
+    // The default cap balances a wave (~levels x one grid step) against one
+    // pointer-jumping Evaluate (~log2(depth) sweeps over every vertex), whose
+    // cost grows with |V|.
     const unsigned cap_any = (unsigned)std::min<int64_t>(G->n + 2, 0x7fffffff);
+    unsigned auto_cap = 24u;
+    if (G->n > 1000000) {
+        const double extra = 16.0 * std::log2((double)G->n / 1.0e6);
+        auto_cap = (unsigned)std::min(128.0, 24.0 + extra);
+    }
     const unsigned max_levels = mode == PIRRT_EVAL_WAVE ? cap_any
-                                : (o.wave_levels > 0 ? (unsigned)o.wave_levels : 192u);
+                                : (o.wave_levels > 0 ? (unsigned)o.wave_levels : auto_cap);
+    // AUTO: after an exploit whose waves ran past the cap, start with pointer
+    // jumping, and probe with waves again every eighth exploit
+    bool jump_first = mode == PIRRT_EVAL_AUTO && G->deep_hint && (G->exploits % 8) != 0;
+    bool saw_deep = false;
+    G->exploits += 1;
 
     CK(cudaEventRecord(G->ev0, G->stream));
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
@@ -363,7 +379,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         if ((rc = launch_improve<CT>(G, gs, o.tile))) return rc;
         if (prof) CK(cudaEventRecord(G->pev[1], G->stream));
         bool jumped = false;
-        if (mode == PIRRT_EVAL_JUMP) {
+        if (mode == PIRRT_EVAL_JUMP || jump_first) {
             if ((rc = launch_evaluate<CT>(G, 0))) return rc;
             if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
             if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
@@ -384,10 +400,12 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
             CK(cudaEventElapsedTime(&t_eval, G->pev[1], G->pev[2]));
             CK(cudaEventElapsedTime(&t_mark, G->pev[2], G->pev[3]));
         }
-        if (mode != PIRRT_EVAL_JUMP) {
+        if (mode != PIRRT_EVAL_JUMP && !jumped) {
             G->wave_epoch += h->wave_levels + 1u;
             s.wave_levels += (int32_t)h->wave_levels;
             if (h->wave_incomplete) {
+                saw_deep = true;
+                if (mode == PIRRT_EVAL_AUTO) jump_first = true;
                 // finish this Evaluate by pointer jumping from p and pc
                 if (prof) CK(cudaEventRecord(G->pev[4], G->stream));
                 pre_jump_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
@@ -413,7 +431,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
             tr.improve_entries = (int64_t)(h->relax - prev_relax);
             tr.switches = (int32_t)h->n_switched;
             tr.changed = (int32_t)h->n_dg;
-            tr.wave_levels = mode != PIRRT_EVAL_JUMP ? (int32_t)h->wave_levels : 0;
+            tr.wave_levels = (int32_t)h->wave_levels;
             tr.next_frontier = h->dense_next ? 0 : (int32_t)h->n_next;
             tr.improve_ms = t_imp;
             tr.evaluate_ms = t_eval;
@@ -441,7 +459,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
             P.evaluate_launches += 1;
             P.evaluate_vertices += (int64_t)(h->evaluated - prev_eval);
             P.evaluate_ms += t_eval;
-            if (mode == PIRRT_EVAL_JUMP) {
+            if (jumped) {
                 for (int r = 1; r <= kMaxJumpRounds + 1; ++r) P.evaluate_visits += h->wl_count[r];
                 P.evaluate_visits += G->n;  // round 0 touches every vertex
             }
@@ -469,6 +487,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
             break;
         }
     }
+    if (mode == PIRRT_EVAL_AUTO && (saw_deep || !jump_first)) G->deep_hint = saw_deep ? 1 : 0;
     CK(cudaEventRecord(G->ev1, G->stream));
     if (rc == PIRRT_OK) {
         rc = pull_counters(G);
@@ -686,6 +705,8 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     G->la = 0;
     G->epoch = 1;
     G->wave_epoch = 1;
+    G->deep_hint = 0;
+    G->exploits = 0;
     G->last_error.clear();
     return PIRRT_OK;
 }

@@ -333,19 +333,15 @@ improve_kernel(ImproveArgs<CT> a) {
     }
 }
 
-// Tiled Improve: a CTA takes a tile of kTileV vertices (a slice of the active
+// Tiled Improve: a CTA takes a tile of TILE_V vertices (a slice of the active
 // list, or of 0..n-1 in a dense sweep), lays their rows end to end and
-// streams the concatenation kChunk entries at a time, eight independent
-// entry loads per thread followed by eight independent g gathers, so the
+// streams the concatenation THREADS * PER entries at a time, PER independent
+// entry loads per thread followed by PER independent g gathers, so the
 // memory system sees whole tiles in flight instead of one row per group.
 // The lexicographic argmin of (g(u) + c, u, c) per vertex is taken in shared
 // memory in three phases (min value, then min id among those, then min cost
 // among those -- parallel edges), each an atomicMin on order-preserving bits
 // of non-negative numbers.  Chunks of one tile are merged in order.
-constexpr int kTileV = 64;
-constexpr int kPerThread = 8;
-constexpr int kChunk = kThreads * kPerThread;
-
 template <typename CT>
 struct CostBits;
 template <>

@@ -1,0 +1,333 @@
+// Improve (Alg. 2; Sec. IV-B) with the CSR stream decoupled from the
+// reduction: a producer warp stages each tile's rows into a ring of shared
+// memory buffers with bulk asynchronous copies (cp.async.bulk, completing on
+// an mbarrier), while consumer warps gather g for the staged entries and take
+// the lexicographic argmin of (g(u) + c(u, v), u, c) per vertex.  Several
+// tiles are in flight per CTA, so HBM streams while the gathers and the
+// shared-memory reduction of earlier tiles proceed.
+#pragma once
+
+#include "graph_kernels.cuh"
+
+namespace pirrt {
+
+namespace tma {
+
+constexpr int kTV = 32;                 // vertices per tile (one producer lane each)
+constexpr int kStages = 4;                 // ring depth
+constexpr int kStageBytes = 16384;         // staged CSR bytes per tile
+constexpr int kConsumerWarps = 8;
+constexpr int kConsumers = kConsumerWarps * 32;
+constexpr int kThreads = kConsumers + 32;  // + one producer warp
+constexpr int kPer = 8;                    // entries per consumer thread per pass
+constexpr unsigned long long kWaitNs = 2000000000ull;  // give up a wait after 2 s
+
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ unsigned smem_addr(const void *p) {
+    return (unsigned)__cvta_generic_to_shared(p);
+}
+
+__device__ __forceinline__ void mbar_init(unsigned long long *bar, unsigned count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(smem_addr(bar)), "r"(count));
+}
+
+__device__ __forceinline__ void mbar_arrive_expect_tx(unsigned long long *bar, unsigned bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(smem_addr(bar)),
+                 "r"(bytes)
+                 : "memory");
+}
+
+__device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
+    asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
+}
+
+// Bounded wait for the phase with the given parity; false after kWaitNs.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+    const unsigned a = smem_addr(bar);
+    const unsigned long long t0 = global_ns();
+    for (;;) {
+        unsigned done;
+        asm volatile(
+            "{\n\t.reg .pred p;\n\t"
+            "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+            "selp.u32 %0, 1, 0, p;\n\t}"
+            : "=r"(done)
+            : "r"(a), "r"(parity)
+            : "memory");
+        if (done) return true;
+        if (global_ns() - t0 > kWaitNs) return false;
+    }
+}
+
+// One bulk copy global -> shared, completion counted on `bar` (bytes, both
+// addresses and the size multiples of 16).
+__device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
+                                          unsigned long long *bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
+            "r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        : "memory");
+}
+
+__device__ __forceinline__ void consumer_sync() {
+    asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
+}
+
+template <typename CT>
+struct alignas(128) Stage {
+    static constexpr int kCap = kStageBytes / (int)sizeof(Entry<CT>);
+    Entry<CT> buf[kCap];
+    int32_t v[kTV];        // vertex, -1 if none
+    int32_t seg[kTV + 1];  // exclusive prefix of row lengths
+    int32_t start[kTV];    // index in buf of the row's first entry
+    long long gbase[kTV];  // row_off[v] (used when the tile overflows)
+    int32_t overflow;         // rows did not fit: read them from global memory
+};
+
+template <typename CT>
+struct alignas(128) Smem {
+    Stage<CT> st[kStages];
+    unsigned long long full[kStages], empty[kStages];
+    unsigned long long cv[kTV];
+    int32_t cid[kTV];
+    typename CostBits<CT>::T cw[kTV];
+    int32_t abort;    // consumers: a wait ran out (written and read by consumers only)
+};
+
+}  // namespace tma
+
+template <typename CT>
+__global__ void __launch_bounds__(tma::kThreads)
+improve_tma_kernel(ImproveArgs<CT> a) {
+    using namespace tma;
+    using WB = typename CostBits<CT>::T;
+    constexpr int ES = (int)sizeof(Entry<CT>);
+    constexpr int kCap = Stage<CT>::kCap;
+    constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+    extern __shared__ __align__(128) unsigned char smem_raw[];
+    Smem<CT> &S = *reinterpret_cast<Smem<CT> *>(smem_raw);
+
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool dense = a.ctr->dense != 0u;
+    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
+    const int64_t n_tiles = (count + kTV - 1) / kTV;
+
+    if (tid == 0) {
+        for (int s = 0; s < kStages; ++s) {
+            mbar_init(&S.full[s], 1);
+            mbar_init(&S.empty[s], 1);
+        }
+        S.abort = 0;
+        asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+    }
+    __syncthreads();
+    // From here on the producer warp and the consumer warps never meet at a
+    // CTA-wide barrier; consumers synchronise among themselves (named barrier
+    // 1) and with the producer through the full / empty mbarriers only.
+
+    if (warp == kConsumerWarps) {
+        // ------------------------------------------------------------ producer
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const int s = it % kStages;
+            const unsigned ph = (unsigned)(it / kStages) & 1u;
+            bool ok = true;
+            if (lane == 0) ok = mbar_wait(&S.empty[s], ph ^ 1u);
+            ok = __shfl_sync(0xffffffffu, ok ? 1 : 0, 0) != 0;
+            if (!ok) {
+                if (lane == 0) atomicOr(&a.ctr->status, kStatusTimeout);
+                break;  // the consumers' own waits run out in turn
+            }
+            Stage<CT> &st = S.st[s];
+            const int64_t t0 = tile * kTV;
+            int32_t v = -1;
+            long long b = 0;
+            int deg = 0;
+            if (t0 + lane < count) {
+                v = dense ? (int32_t)(t0 + lane) : __ldg(&a.active[t0 + lane]);
+                if (v == a.root) {
+                    v = -1;
+                } else {
+                    b = a.row_off[v];
+                    deg = (int)(a.row_off[v + 1] - b);
+                }
+            }
+            // 16-byte aligned source and destination for each row: the copy
+            // starts at the row start rounded down to 16 bytes (skipping at
+            // most one 8-byte entry) and is rounded up to 16 bytes, so it may
+            // read one entry past the row (the CSR buffers are padded)
+            const long long byte0 = b * ES;
+            const int skip = deg > 0 ? (int)((byte0 & 15) / ES) : 0;
+            const int alloc = deg > 0 ? ((skip + deg) * ES + 15) / 16 * (16 / ES) : 0;
+            int incl = deg, ainc = alloc;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                const int z = __shfl_up_sync(0xffffffffu, ainc, off);
+                if (lane >= off) {
+                    incl += y;
+                    ainc += z;
+                }
+            }
+            const int aex = ainc - alloc;
+            const int atotal = __shfl_sync(0xffffffffu, ainc, 31);
+            const bool ovf = atotal > kCap;
+            st.v[lane] = v;
+            st.seg[lane + 1] = incl;
+            if (lane == 0) st.seg[0] = 0;
+            st.start[lane] = aex + skip;
+            st.gbase[lane] = b;
+            if (lane == 0) st.overflow = ovf ? 1 : 0;
+            __syncwarp();
+            if (lane == 0) mbar_arrive_expect_tx(&S.full[s], ovf ? 0u : (unsigned)(atotal * ES));
+            __syncwarp();
+            if (!ovf && deg > 0) {
+                const char *src = reinterpret_cast<const char *>(a.adj) + (byte0 - skip * ES);
+                bulk_copy(&st.buf[aex], src, (unsigned)(alloc * ES), &S.full[s]);
+            }
+        }
+        // before leaving, see the copies of the last stages land (also when
+        // the consumers have given up), so no bulk copy outlives the CTA
+        if (lane == 0) {
+            const int last = it < kStages ? it : kStages;
+            for (int j = 1; j <= last; ++j) {
+                const int k = it - j;
+                mbar_wait(&S.full[k % kStages], (unsigned)(k / kStages) & 1u);
+            }
+        }
+        __syncwarp();
+    } else {
+        // ----------------------------------------------------------- consumers
+        unsigned long long relax = 0, improved = 0;
+        int it = 0;
+        for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
+            const int s = it % kStages;
+            const unsigned ph = (unsigned)(it / kStages) & 1u;
+            // every consumer thread waits (acquiring the staged bytes); a
+            // timeout anywhere is agreed on before anyone leaves the loop
+            if (!mbar_wait(&S.full[s], ph)) S.abort = 1;
+            consumer_sync();
+            if (S.abort) {
+                if (tid == 0) atomicOr(&a.ctr->status, kStatusTimeout);
+                break;
+            }
+            Stage<CT> &st = S.st[s];
+            const int total = st.seg[kTV];
+            const bool ovf = st.overflow != 0;
+            // current parent's candidate, loaded while the entries are scanned
+            int32_t v = -1, pv = -1, mydeg = 0;
+            CT pcv = CT(0);
+            double gp = CUDART_INF;
+            if (tid < kTV) {
+                v = st.v[tid];
+                mydeg = st.seg[tid + 1] - st.seg[tid];
+                if (v >= 0) {
+                    pv = a.p[v];
+                    pcv = a.pc[v];
+                    if (pv >= 0) gp = a.g[pv];
+                }
+                S.cv[tid] = kInfBits + 1ull;  // above +inf: "no candidate yet"
+                S.cid[tid] = INT_MAX;
+                S.cw[tid] = CostBits<CT>::kMax;
+            }
+            consumer_sync();
+            // Tile minimum over passes of kConsumers * kPer entries, each in
+            // three atomicMin phases.  A pass that lowers the value clears the
+            // id (and cost); one that lowers the id clears the cost, so the
+            // slots always describe the current (value, id) minimum.
+            for (int p0 = 0; p0 < total; p0 += kConsumers * kPer) {
+                Entry<CT> en[kPer];
+                int kk[kPer];
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    const int pos = p0 + tid + i * kConsumers;
+                    kk[i] = -1;
+                    if (pos < total) {
+                        int lo = 0, hi = kTV;  // last k with seg[k] <= pos
+                        while (hi - lo > 1) {
+                            const int mid = (lo + hi) >> 1;
+                            if (st.seg[mid] <= pos) lo = mid; else hi = mid;
+                        }
+                        kk[i] = lo;
+                        const int off = pos - st.seg[lo];
+                        en[i] = ovf ? ld_stream(&a.adj[st.gbase[lo] + off]) : st.buf[st.start[lo] + off];
+                    }
+                }
+                unsigned long long vb[kPer];
+#pragma unroll
+                for (int i = 0; i < kPer; ++i) {
+                    if (kk[i] >= 0) {
+                        const double val = __ldg(&a.g[en[i].col]) + (double)en[i].w;
+                        vb[i] = (unsigned long long)__double_as_longlong(val);
+                        const unsigned long long old = atomicMin(&S.cv[kk[i]], vb[i]);
+                        if (vb[i] < old) {
+                            atomicExch(&S.cid[kk[i]], INT_MAX);
+                            atomicExch(&S.cw[kk[i]], CostBits<CT>::kMax);
+                        }
+                    }
+                }
+                consumer_sync();
+#pragma unroll
+                for (int i = 0; i < kPer; ++i)
+                    if (kk[i] >= 0 && vb[i] == S.cv[kk[i]]) {
+                        const int32_t old = atomicMin(&S.cid[kk[i]], en[i].col);
+                        if (en[i].col < old) atomicExch(&S.cw[kk[i]], CostBits<CT>::kMax);
+                    }
+                consumer_sync();
+#pragma unroll
+                for (int i = 0; i < kPer; ++i)
+                    if (kk[i] >= 0 && vb[i] == S.cv[kk[i]] && en[i].col == S.cid[kk[i]])
+                        atomicMin(&S.cw[kk[i]], CostBits<CT>::of(en[i].w));
+                consumer_sync();
+            }
+            // the stage's buffer may be refilled now
+            if (tid == 0) mbar_arrive(&S.empty[s]);
+            // decision by the first consumer warp (whole warp: collective appends)
+            if (warp == 0) {
+                bool sw = false;
+                unsigned long long dj = 0ull;
+                if (v >= 0) {
+                    const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
+                    if (S.cv[tid] <= kInfBits) {
+                        const double best = __longlong_as_double((long long)S.cv[tid]);
+                        if (best < cur) {
+                            a.p[v] = S.cid[tid];
+                            a.pc[v] = CostBits<CT>::back(S.cw[tid]);
+                            sw = true;
+                            dj = (unsigned long long)__double_as_longlong(cur - best);
+                        }
+                    }
+                    relax += (unsigned long long)mydeg;
+                    improved += 1;
+                }
+                warp_append(sw, v, a.switched, &a.ctr->n_switched);
+#pragma unroll
+                for (int off = 16; off > 0; off >>= 1) {
+                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
+                    dj = o > dj ? o : dj;
+                }
+                if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
+            }
+            consumer_sync();  // cv / cid / cw are reset by the next tile
+        }
+        if (warp == 0) {
+#pragma unroll
+            for (int off = 16; off > 0; off >>= 1) {
+                relax += __shfl_down_sync(0xffffffffu, relax, off);
+                improved += __shfl_down_sync(0xffffffffu, improved, off);
+            }
+            if (lane == 0 && (relax || improved)) {
+                atomicAdd(&a.ctr->relax, relax);
+                atomicAdd(&a.ctr->improved, improved);
+            }
+        }
+    }
+}
+
+}  // namespace pirrt

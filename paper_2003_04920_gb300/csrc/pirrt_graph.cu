@@ -17,6 +17,7 @@
 #include <vector>
 
 #include "graph_kernels.cuh"
+#include "improve_tma.cuh"
 #include "pirrt.h"
 
 using namespace pirrt;
@@ -143,14 +144,33 @@ pirrt_status launch_improve_tile_v(pirrt_graph *G, const ImproveArgs<CT> &a) {
     return PIRRT_OK;
 }
 
-// Tiled Improve shapes (vertices per tile -> threads, entries per thread).
+template <typename CT>
+pirrt_status launch_improve_tma(pirrt_graph *G, const ImproveArgs<CT> &a) {
+    static int occ = -1;
+    const size_t smem = sizeof(tma::Smem<CT>);
+    if (occ < 0) {
+        CK(cudaFuncSetAttribute(improve_tma_kernel<CT>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                (int)smem));
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tma_kernel<CT>, tma::kThreads,
+                                                         smem));
+        occ = nb > 0 ? nb : 1;
+    }
+    improve_tma_kernel<CT><<<G->num_sms * occ, tma::kThreads, smem, G->stream>>>(a);
+    CKL();
+    return PIRRT_OK;
+}
+
+// Tiled Improve shapes (vertices per tile -> threads, entries per thread);
+// 0 = the staged (bulk-copy pipelined) kernel.
 template <typename CT>
 pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
     switch (tile) {
+        case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
         case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
         case 64: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
         case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
-        default: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);  // measured best on GB300
+        default: return launch_improve_tma<CT>(G, a);
     }
 }
 
@@ -635,8 +655,9 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     } while (0)
     ALLOC(G->row_off[0], sizeof(int64_t) * (nv + 1));
     ALLOC(G->row_off[1], sizeof(int64_t) * (nv + 1));
-    ALLOC(G->adj[0], G->entry_bytes * ne);
-    ALLOC(G->adj[1], G->entry_bytes * ne);
+    // +16 entries: a staged row copy is rounded up to 16 bytes past the row
+    ALLOC(G->adj[0], G->entry_bytes * (ne + 16));
+    ALLOC(G->adj[1], G->entry_bytes * (ne + 16));
     ALLOC(G->g, sizeof(double) * nv);
     ALLOC(G->p, sizeof(int32_t) * nv);
     ALLOC(G->pc, G->cost_bytes * nv);

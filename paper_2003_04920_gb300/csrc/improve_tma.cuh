@@ -2,9 +2,9 @@
 // reduction: a producer warp stages each tile's rows into a ring of shared
 // memory buffers with bulk asynchronous copies (cp.async.bulk, completing on
 // an mbarrier), while consumer warps gather g for the staged entries and take
-// the lexicographic argmin of (g(u) + c(u, v), u, c) per vertex.  Several
-// tiles are in flight per CTA, so HBM streams while the gathers and the
-// shared-memory reduction of earlier tiles proceed.
+// the lexicographic argmin of (g(u) + c(u, v), u, c) per vertex, 8 lanes per
+// vertex, in registers.  Several tiles are in flight per CTA, so HBM streams
+// while the gathers and reductions of earlier tiles proceed.
 #pragma once
 
 #include "graph_kernels.cuh"
@@ -19,7 +19,6 @@ constexpr int kStageBytes = 16384;         // staged CSR bytes per tile
 constexpr int kConsumerWarps = 8;
 constexpr int kConsumers = kConsumerWarps * 32;
 constexpr int kThreads = kConsumers + 32;  // + one producer warp
-constexpr int kPer = 8;                    // entries per consumer thread per pass
 constexpr unsigned long long kWaitNs = 2000000000ull;  // give up a wait after 2 s
 
 __device__ __forceinline__ unsigned long long global_ns() {
@@ -94,9 +93,6 @@ template <typename CT>
 struct alignas(128) Smem {
     Stage<CT> st[kStages];
     unsigned long long full[kStages], empty[kStages];
-    unsigned long long cv[kTV];
-    int32_t cid[kTV];
-    typename CostBits<CT>::T cw[kTV];
     int32_t abort;    // consumers: a wait ran out (written and read by consumers only)
 };
 
@@ -109,6 +105,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
     using WB = typename CostBits<CT>::T;
     constexpr int ES = (int)sizeof(Entry<CT>);
     constexpr int kCap = Stage<CT>::kCap;
+    static_assert(kCap % 2 == 0, "stage capacity");
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
     extern __shared__ __align__(128) unsigned char smem_raw[];
     Smem<CT> &S = *reinterpret_cast<Smem<CT> *>(smem_raw);
@@ -204,6 +201,15 @@ improve_tma_kernel(ImproveArgs<CT> a) {
         __syncwarp();
     } else {
         // ----------------------------------------------------------- consumers
+        // kConsumers / kTV = 8 lanes per vertex of the tile: each lane scans
+        // every 8th staged entry of its vertex's row, keeping the
+        // lexicographic minimum of (value bits, id, cost bits) in registers
+        // (integer compares on order-preserving bits), then three xor-shuffle
+        // steps reduce the 8 lanes.  No shared-memory atomics.
+        constexpr int GL = kConsumers / kTV;
+        static_assert(GL == 8, "8 lanes per vertex");
+        const int k = tid / GL, gl = tid % GL;
+        const unsigned gmask = 0xffu << (lane & ~(GL - 1));
         unsigned long long relax = 0, improved = 0;
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
@@ -218,114 +224,94 @@ improve_tma_kernel(ImproveArgs<CT> a) {
                 break;
             }
             Stage<CT> &st = S.st[s];
-            const int total = st.seg[kTV];
             const bool ovf = st.overflow != 0;
-            // current parent's candidate, loaded while the entries are scanned
-            int32_t v = -1, pv = -1, mydeg = 0;
+            const int32_t v = st.v[k];
+            const int deg = st.seg[k + 1] - st.seg[k];
+            const int sidx = st.start[k];
+            const long long gbase = st.gbase[k];
+            int32_t pv = -1;
             CT pcv = CT(0);
             double gp = CUDART_INF;
-            if (tid < kTV) {
-                v = st.v[tid];
-                mydeg = st.seg[tid + 1] - st.seg[tid];
-                if (v >= 0) {
-                    pv = a.p[v];
-                    pcv = a.pc[v];
-                    if (pv >= 0) gp = a.g[pv];
-                }
-                S.cv[tid] = kInfBits + 1ull;  // above +inf: "no candidate yet"
-                S.cid[tid] = INT_MAX;
-                S.cw[tid] = CostBits<CT>::kMax;
+            if (gl == 0 && v >= 0) {  // current parent's candidate, in flight meanwhile
+                pv = a.p[v];
+                pcv = a.pc[v];
+                if (pv >= 0) gp = a.g[pv];
             }
+            unsigned long long bv = kInfBits + 1ull;  // above +inf: "no candidate yet"
+            int32_t bid = INT_MAX;
+            WB bw = CostBits<CT>::kMax;
+            for (int j0 = gl; j0 < deg; j0 += GL * 4) {
+                Entry<CT> en[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    const int j = j0 + q * GL;
+                    if (j < deg) en[q] = ovf ? ld_stream(&a.adj[gbase + j]) : st.buf[sidx + j];
+                }
+                double gv[4];
+#pragma unroll
+                for (int q = 0; q < 4; ++q)
+                    if (j0 + q * GL < deg) gv[q] = __ldg(&a.g[en[q].col]);
+#pragma unroll
+                for (int q = 0; q < 4; ++q) {
+                    if (j0 + q * GL < deg) {
+                        const unsigned long long vb =
+                            (unsigned long long)__double_as_longlong(gv[q] + (double)en[q].w);
+                        const WB wb = CostBits<CT>::of(en[q].w);
+                        if (vb < bv || (vb == bv && (en[q].col < bid || (en[q].col == bid && wb < bw)))) {
+                            bv = vb;
+                            bid = en[q].col;
+                            bw = wb;
+                        }
+                    }
+                }
+            }
+            // the staged bytes are no longer needed: release the stage
             consumer_sync();
-            // Tile minimum over passes of kConsumers * kPer entries, each in
-            // three atomicMin phases.  A pass that lowers the value clears the
-            // id (and cost); one that lowers the id clears the cost, so the
-            // slots always describe the current (value, id) minimum.
-            for (int p0 = 0; p0 < total; p0 += kConsumers * kPer) {
-                Entry<CT> en[kPer];
-                int kk[kPer];
-#pragma unroll
-                for (int i = 0; i < kPer; ++i) {
-                    const int pos = p0 + tid + i * kConsumers;
-                    kk[i] = -1;
-                    if (pos < total) {
-                        int lo = 0, hi = kTV;  // last k with seg[k] <= pos
-                        while (hi - lo > 1) {
-                            const int mid = (lo + hi) >> 1;
-                            if (st.seg[mid] <= pos) lo = mid; else hi = mid;
-                        }
-                        kk[i] = lo;
-                        const int off = pos - st.seg[lo];
-                        en[i] = ovf ? ld_stream(&a.adj[st.gbase[lo] + off]) : st.buf[st.start[lo] + off];
-                    }
-                }
-                unsigned long long vb[kPer];
-#pragma unroll
-                for (int i = 0; i < kPer; ++i) {
-                    if (kk[i] >= 0) {
-                        const double val = __ldg(&a.g[en[i].col]) + (double)en[i].w;
-                        vb[i] = (unsigned long long)__double_as_longlong(val);
-                        const unsigned long long old = atomicMin(&S.cv[kk[i]], vb[i]);
-                        if (vb[i] < old) {
-                            atomicExch(&S.cid[kk[i]], INT_MAX);
-                            atomicExch(&S.cw[kk[i]], CostBits<CT>::kMax);
-                        }
-                    }
-                }
-                consumer_sync();
-#pragma unroll
-                for (int i = 0; i < kPer; ++i)
-                    if (kk[i] >= 0 && vb[i] == S.cv[kk[i]]) {
-                        const int32_t old = atomicMin(&S.cid[kk[i]], en[i].col);
-                        if (en[i].col < old) atomicExch(&S.cw[kk[i]], CostBits<CT>::kMax);
-                    }
-                consumer_sync();
-#pragma unroll
-                for (int i = 0; i < kPer; ++i)
-                    if (kk[i] >= 0 && vb[i] == S.cv[kk[i]] && en[i].col == S.cid[kk[i]])
-                        atomicMin(&S.cw[kk[i]], CostBits<CT>::of(en[i].w));
-                consumer_sync();
-            }
-            // the stage's buffer may be refilled now
             if (tid == 0) mbar_arrive(&S.empty[s]);
-            // decision by the first consumer warp (whole warp: collective appends)
-            if (warp == 0) {
-                bool sw = false;
-                unsigned long long dj = 0ull;
-                if (v >= 0) {
-                    const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
-                    if (S.cv[tid] <= kInfBits) {
-                        const double best = __longlong_as_double((long long)S.cv[tid]);
-                        if (best < cur) {
-                            a.p[v] = S.cid[tid];
-                            a.pc[v] = CostBits<CT>::back(S.cw[tid]);
-                            sw = true;
-                            dj = (unsigned long long)__double_as_longlong(cur - best);
-                        }
-                    }
-                    relax += (unsigned long long)mydeg;
-                    improved += 1;
-                }
-                warp_append(sw, v, a.switched, &a.ctr->n_switched);
 #pragma unroll
-                for (int off = 16; off > 0; off >>= 1) {
-                    const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
-                    dj = o > dj ? o : dj;
+            for (int off = GL / 2; off > 0; off >>= 1) {
+                const unsigned long long ov = __shfl_xor_sync(gmask, bv, off, GL);
+                const int32_t oi = __shfl_xor_sync(gmask, bid, off, GL);
+                const WB ow = __shfl_xor_sync(gmask, bw, off, GL);
+                if (ov < bv || (ov == bv && (oi < bid || (oi == bid && ow < bw)))) {
+                    bv = ov;
+                    bid = oi;
+                    bw = ow;
                 }
-                if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
             }
-            consumer_sync();  // cv / cid / cw are reset by the next tile
-        }
-        if (warp == 0) {
+            // decision by each group's first lane; appends are warp-collective
+            bool sw = false;
+            unsigned long long dj = 0ull;
+            if (gl == 0 && v >= 0) {
+                const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
+                if (bv <= kInfBits) {
+                    const double best = __longlong_as_double((long long)bv);
+                    if (best < cur) {
+                        a.p[v] = bid;
+                        a.pc[v] = CostBits<CT>::back(bw);
+                        sw = true;
+                        dj = (unsigned long long)__double_as_longlong(cur - best);
+                    }
+                }
+                relax += (unsigned long long)deg;
+                improved += 1;
+            }
+            warp_append(sw, v, a.switched, &a.ctr->n_switched);
 #pragma unroll
             for (int off = 16; off > 0; off >>= 1) {
-                relax += __shfl_down_sync(0xffffffffu, relax, off);
-                improved += __shfl_down_sync(0xffffffffu, improved, off);
+                const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
+                dj = o > dj ? o : dj;
             }
-            if (lane == 0 && (relax || improved)) {
-                atomicAdd(&a.ctr->relax, relax);
-                atomicAdd(&a.ctr->improved, improved);
-            }
+            if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
+        }
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            relax += __shfl_down_sync(0xffffffffu, relax, off);
+            improved += __shfl_down_sync(0xffffffffu, improved, off);
+        }
+        if (lane == 0 && (relax || improved)) {
+            atomicAdd(&a.ctr->relax, relax);
+            atomicAdd(&a.ctr->improved, improved);
         }
     }
 }

@@ -56,6 +56,33 @@ __device__ __forceinline__ Entry<double> ld_stream(const Entry<double> *p) {
     return e;
 }
 
+// L2 eviction priorities.  g is gathered once per CSR entry from anywhere in
+// the array, so it should stay resident in L2 (evict_last) while the CSR,
+// read once per sweep, passes through (evict_first).
+__device__ __forceinline__ unsigned long long policy_evict_last() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_last.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+__device__ __forceinline__ unsigned long long policy_evict_first() {
+    unsigned long long pol;
+    asm volatile("createpolicy.fractional.L2::evict_first.b64 %0, 1.0;" : "=l"(pol));
+    return pol;
+}
+// Read-only load of g(u) that keeps its line in L2.
+__device__ __forceinline__ double ld_g(const double *p, unsigned long long pol) {
+    double v;
+    asm volatile("ld.global.nc.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+// Coherent (L2) load of g(u) that keeps its line in L2 (for data written in
+// the same kernel by other CTAs).
+__device__ __forceinline__ double ld_g_cg(const double *p, unsigned long long pol) {
+    double v;
+    asm volatile("ld.global.cg.L2::cache_hint.f64 %0, [%1], %2;" : "=d"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 // Device counters of one graph.  The host copies the block back once per
 // Replan iteration.
 struct DevCounters {

@@ -246,6 +246,7 @@ improve_kernel(ImproveArgs<CT> a) {
     const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
     const bool dense = a.ctr->dense != 0u;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
+    const unsigned long long gpol = policy_evict_last();
 
     unsigned long long relax = 0, improved = 0;
     for (int64_t item = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G; item < count;
@@ -267,7 +268,7 @@ improve_kernel(ImproveArgs<CT> a) {
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k) {
                 const int64_t i = i0 + (int64_t)k * G;
-                gv[k] = (i < e) ? __ldg(&a.g[en[k].col]) : CUDART_INF;
+                gv[k] = (i < e) ? ld_g(&a.g[en[k].col], gpol) : CUDART_INF;
             }
 #pragma unroll
             for (int k = 0; k < kUnroll; ++k) {
@@ -387,6 +388,7 @@ improve_tile_kernel(ImproveArgs<CT> a) {
     const bool dense = a.ctr->dense != 0u;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const int64_t n_tiles = (count + TILE_V - 1) / TILE_V;
+    const unsigned long long gpol = policy_evict_last();
     unsigned long long relax = 0, improved = 0;
 
     for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
@@ -466,7 +468,7 @@ improve_tile_kernel(ImproveArgs<CT> a) {
 #pragma unroll
             for (int i = 0; i < PER; ++i) {
                 if (kk[i] >= 0) {
-                    const double val = __ldg(&a.g[en[i].col]) + (double)en[i].w;
+                    const double val = ld_g(&a.g[en[i].col], gpol) + (double)en[i].w;
                     vb[i] = (unsigned long long)__double_as_longlong(val);
                     atomicMin(&s_cv[kk[i]], vb[i]);
                 }
@@ -745,6 +747,7 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
     if (n_sw == 0u) return;
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const unsigned long long gpol = policy_evict_last();
     unsigned long long recomputed = 0, changed_total = 0;
     unsigned t = 0;
     for (;; ++t) {
@@ -771,8 +774,8 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
             if (tid < nv) {
                 u = __ldcg(&in[s0 + tid]);
                 const int32_t pu = __ldcg(&a.p[u]);
-                const double gn = __ldcg(&a.g[pu]) + (double)a.pc[u];
-                const double go = __ldcg(&a.g[u]);
+                const double gn = ld_g_cg(&a.g[pu], gpol) + (double)a.pc[u];
+                const double go = ld_g_cg(&a.g[u], gpol);
                 ++recomputed;
                 if (__double_as_longlong(gn) != __double_as_longlong(go)) {
                     __stcg(&a.g[u], gn);

@@ -66,11 +66,11 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
 // One bulk copy global -> shared, completion counted on `bar` (bytes, both
 // addresses and the size multiples of 16).
 __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned bytes,
-                                          unsigned long long *bar) {
+                                          unsigned long long *bar, unsigned long long pol) {
     asm volatile(
-        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];" ::
-            "r"(smem_addr(dst)),
-        "l"(src), "r"(bytes), "r"(smem_addr(bar))
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes.L2::cache_hint"
+        " [%0], [%1], %2, [%3], %4;" ::"r"(smem_addr(dst)),
+        "l"(src), "r"(bytes), "r"(smem_addr(bar)), "l"(pol)
         : "memory");
 }
 
@@ -130,6 +130,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
 
     if (warp == kConsumerWarps) {
         // ------------------------------------------------------------ producer
+        const unsigned long long stream_pol = policy_evict_first();
         int it = 0;
         for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x, ++it) {
             const int s = it % kStages;
@@ -186,7 +187,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
             __syncwarp();
             if (!ovf && deg > 0) {
                 const char *src = reinterpret_cast<const char *>(a.adj) + (byte0 - skip * ES);
-                bulk_copy(&st.buf[aex], src, (unsigned)(alloc * ES), &S.full[s]);
+                bulk_copy(&st.buf[aex], src, (unsigned)(alloc * ES), &S.full[s], stream_pol);
             }
         }
         // before leaving, see the copies of the last stages land (also when
@@ -209,6 +210,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
         constexpr int GL = kConsumers / kTV;
         static_assert(GL == 8, "8 lanes per vertex");
         const int k = tid / GL, gl = tid % GL;
+        const unsigned long long gpol = policy_evict_last();
         const unsigned gmask = 0xffu << (lane & ~(GL - 1));
         unsigned long long relax = 0, improved = 0;
         int it = 0;
@@ -250,7 +252,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
                 double gv[4];
 #pragma unroll
                 for (int q = 0; q < 4; ++q)
-                    if (j0 + q * GL < deg) gv[q] = __ldg(&a.g[en[q].col]);
+                    if (j0 + q * GL < deg) gv[q] = ld_g(&a.g[en[q].col], gpol);
 #pragma unroll
                 for (int q = 0; q < 4; ++q) {
                     if (j0 + q * GL < deg) {

@@ -83,6 +83,27 @@ __device__ __forceinline__ double ld_g_cg(const double *p, unsigned long long po
     return v;
 }
 
+// FP32 shadow of g used to screen Improve candidates (GB300 runs FP64 at a
+// small fraction of its FP32 rate).  +inf stays +inf; a finite g above 2^100
+// is stored as -1, which sends every row reading it down the exact FP64 path.
+__device__ __forceinline__ float g32_of(double g) {
+    if (g <= 1.2676506002282294e30) return __double2float_rn(g);  // g >= 0, up to 2^100
+    return isinf(g) ? __int_as_float(0x7f800000) : -1.0f;
+}
+
+// Exact widening of a positive finite float to double with integer
+// operations (no FP64 pipe); subnormals take the conversion instruction.
+__device__ __forceinline__ double widen(float w) {
+    const unsigned b = __float_as_uint(w);
+    const unsigned e = (b >> 23) & 0xffu;
+    if (e == 0u || e == 0xffu) return (double)w;
+    const unsigned long long d = ((unsigned long long)(b >> 31) << 63) |
+                                 ((unsigned long long)(e + 896u) << 52) |
+                                 ((unsigned long long)(b & 0x7fffffu) << 29);
+    return __longlong_as_double((long long)d);
+}
+__device__ __forceinline__ double widen(double w) { return w; }
+
 // Device counters of one graph.  The host copies the block back once per
 // Replan iteration.
 struct DevCounters {

@@ -188,7 +188,8 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__restrict__ g,
-                     int32_t *__restrict__ p, CT *__restrict__ pc, unsigned *__restrict__ stamp,
+                     float *__restrict__ g32, int32_t *__restrict__ p, CT *__restrict__ pc,
+                     unsigned *__restrict__ stamp,
                      unsigned epoch, int32_t *__restrict__ active, DevCounters *ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = n_old + (int64_t)blockIdx.x * blockDim.x; base < n_after; base += stride) {
@@ -196,6 +197,7 @@ insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__res
         bool pred = false;
         if (v < n_after) {
             g[v] = (v == root) ? 0.0 : CUDART_INF;
+            g32[v] = (v == root) ? 0.0f : __int_as_float(0x7f800000);
             p[v] = -1;
             pc[v] = CT(0);
             pred = v != root && atomicExch(&stamp[v], epoch) != epoch;
@@ -221,6 +223,7 @@ struct ImproveArgs {
     const int64_t *row_off;
     const Entry<CT> *adj;
     const double *g;
+    const float *g32;
     int32_t *p;
     CT *pc;
     const int32_t *active;
@@ -546,6 +549,7 @@ struct EvaluateArgs {
     const int32_t *p;
     const CT *pc;
     double *g;
+    float *g32;
     int32_t *anc[2];  // current ancestor of each unfinished vertex
     double *acc[2];   // sum of policy-edge costs from the vertex up to anc
     int32_t *done;    // round in which the vertex's g became final
@@ -620,6 +624,7 @@ evaluate_kernel(EvaluateArgs<CT> a) {
                     const double old = __ldcg(&a.g[w]);
                     changed = __double_as_longlong(gw) != __double_as_longlong(old);
                     a.g[w] = gw;
+                    a.g32[w] = g32_of(gw);
                     a.done[w] = r;
                     ++finished;
                 } else {
@@ -701,6 +706,7 @@ struct WaveArgs {
     const int32_t *p;
     const CT *pc;
     double *g;
+    float *g32;
     const int32_t *switched;  // level 0: vertices whose parent changed
     int32_t *lvl[2];          // vertices to recompute at levels t (mod 2)
     unsigned *wstamp;         // dedups a child listed twice (parallel edges)
@@ -779,6 +785,7 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
                 ++recomputed;
                 if (__double_as_longlong(gn) != __double_as_longlong(go)) {
                     __stcg(&a.g[u], gn);
+                    __stcg(&a.g32[u], g32_of(gn));
                     ++changed_total;
                     const long long b = a.row_off[u];
                     deg = (int)(a.row_off[u + 1] - b);
@@ -958,12 +965,13 @@ template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 policy_commit_kernel(int64_t n, int32_t root, const int32_t *__restrict__ p_in,
                      const CT *__restrict__ pc_in, int32_t *__restrict__ p, CT *__restrict__ pc,
-                     double *__restrict__ g) {
+                     double *__restrict__ g, float *__restrict__ g32) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
         p[v] = p_in[v];
         pc[v] = pc_in[v];
         g[v] = (v == root) ? 0.0 : CUDART_INF;
+        g32[v] = (v == root) ? 0.0f : __int_as_float(0x7f800000);
     }
 }
 

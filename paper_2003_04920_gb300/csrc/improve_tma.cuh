@@ -74,6 +74,12 @@ __device__ __forceinline__ void bulk_copy(void *dst, const void *src, unsigned b
         : "memory");
 }
 
+__device__ __forceinline__ float ld_g32(const float *p, unsigned long long pol) {
+    float v;
+    asm volatile("ld.global.nc.L2::cache_hint.f32 %0, [%1], %2;" : "=f"(v) : "l"(p), "l"(pol));
+    return v;
+}
+
 __device__ __forceinline__ void consumer_sync() {
     asm volatile("bar.sync 1, %0;" ::"n"(kConsumers) : "memory");
 }
@@ -242,29 +248,87 @@ improve_tma_kernel(ImproveArgs<CT> a) {
             unsigned long long bv = kInfBits + 1ull;  // above +inf: "no candidate yet"
             int32_t bid = INT_MAX;
             WB bw = CostBits<CT>::kMax;
-            for (int j0 = gl; j0 < deg; j0 += GL * 4) {
-                Entry<CT> en[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const int j = j0 + q * GL;
-                    if (j < deg) en[q] = ovf ? ld_stream(&a.adj[gbase + j]) : st.buf[sidx + j];
+            // candidate j of this lane's share of the row
+            auto entry = [&](int j) -> Entry<CT> {
+                return ovf ? ld_stream(&a.adj[gbase + j]) : st.buf[sidx + j];
+            };
+            auto exact = [&](const Entry<CT> &e, double gu) {
+                const unsigned long long vb =
+                    (unsigned long long)__double_as_longlong(gu + widen(e.w));
+                const WB wb = CostBits<CT>::of(e.w);
+                if (vb < bv || (vb == bv && (e.col < bid || (e.col == bid && wb < bw)))) {
+                    bv = vb;
+                    bid = e.col;
+                    bw = wb;
                 }
-                double gv[4];
+            };
+            bool screen = false;
+            float tau = 0.f;
+            if constexpr (sizeof(CT) == 4) {
+                // Screening in FP32.  With g32 = fl32(g) and a = fl32(g32 + c),
+                // |a - fl64(g + c)| <= 2^-22 a, so the exact lexicographic
+                // minimum, and every candidate tying its value, satisfy
+                // a <= A* (1 + 2^-22) / (1 - 2^-22) with A* = min a; tau
+                // below is larger still.  Rows reading a g32 of -1 (g above
+                // 2^100) or overflowing to +inf take the exact path.
+                float amin = __int_as_float(0x7f800000);
+                int exact_row = 0;
+                for (int j0 = gl; j0 < deg; j0 += GL * 4) {
+                    Entry<CT> en[4];
+                    float g32u[4];
 #pragma unroll
-                for (int q = 0; q < 4; ++q)
-                    if (j0 + q * GL < deg) gv[q] = ld_g(&a.g[en[q].col], gpol);
+                    for (int q = 0; q < 4; ++q)
+                        if (j0 + q * GL < deg) en[q] = entry(j0 + q * GL);
 #pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    if (j0 + q * GL < deg) {
-                        const unsigned long long vb =
-                            (unsigned long long)__double_as_longlong(gv[q] + (double)en[q].w);
-                        const WB wb = CostBits<CT>::of(en[q].w);
-                        if (vb < bv || (vb == bv && (en[q].col < bid || (en[q].col == bid && wb < bw)))) {
-                            bv = vb;
-                            bid = en[q].col;
-                            bw = wb;
+                    for (int q = 0; q < 4; ++q)
+                        if (j0 + q * GL < deg) g32u[q] = ld_g32(&a.g32[en[q].col], gpol);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        if (j0 + q * GL < deg) {
+                            const float av = g32u[q] + (float)en[q].w;
+                            exact_row |= (g32u[q] < 0.f) | (isinf(av) & !isinf(g32u[q]));
+                            amin = fminf(amin, av);
                         }
                     }
+                }
+#pragma unroll
+                for (int off = GL / 2; off > 0; off >>= 1) {
+                    amin = fminf(amin, __shfl_xor_sync(gmask, amin, off, GL));
+                    exact_row |= __shfl_xor_sync(gmask, exact_row, off, GL);
+                }
+                if (!exact_row) {
+                    screen = true;
+                    tau = amin * (1.0f + 0x1p-20f) + 0x1p-125f;  // +inf when nothing is reachable
+                }
+            }
+            // (a screened row whose every candidate is unreachable has tau = +inf)
+            if (!(screen && isinf(tau))) {
+                for (int j0 = gl; j0 < deg; j0 += GL * 4) {
+                    Entry<CT> en[4];
+                    bool keep[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q) {
+                        keep[q] = false;
+                        if (j0 + q * GL < deg) {
+                            en[q] = entry(j0 + q * GL);
+                            keep[q] = true;
+                        }
+                    }
+                    if constexpr (sizeof(CT) == 4) {
+                        if (screen) {
+#pragma unroll
+                            for (int q = 0; q < 4; ++q)
+                                if (keep[q])
+                                    keep[q] = ld_g32(&a.g32[en[q].col], gpol) + (float)en[q].w <= tau;
+                        }
+                    }
+                    double gv[4];
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (keep[q]) gv[q] = ld_g(&a.g[en[q].col], gpol);
+#pragma unroll
+                    for (int q = 0; q < 4; ++q)
+                        if (keep[q]) exact(en[q], gv[q]);
                 }
             }
             // the staged bytes are no longer needed: release the stage
@@ -285,7 +349,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
             bool sw = false;
             unsigned long long dj = 0ull;
             if (gl == 0 && v >= 0) {
-                const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
+                const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
                 if (bv <= kInfBits) {
                     const double best = __longlong_as_double((long long)bv);
                     if (best < cur) {

@@ -33,6 +33,7 @@ struct pirrt_graph {
     int64_t *row_off[2] = {nullptr, nullptr};
     void *adj[2] = {nullptr, nullptr};
     double *g = nullptr;
+    float *g32 = nullptr;  // FP32 shadow of g for candidate screening
     int32_t *p = nullptr;
     void *pc = nullptr;
     int32_t *deg = nullptr;
@@ -193,6 +194,7 @@ pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
     a.row_off = G->row_off[G->cur];
     a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
     a.g = G->g;
+    a.g32 = G->g32;
     a.p = G->p;
     a.pc = static_cast<CT *>(G->pc);
     a.active = G->list[G->la];
@@ -215,6 +217,7 @@ pirrt_status launch_evaluate(pirrt_graph *G, int force) {
     a.p = G->p;
     a.pc = static_cast<const CT *>(G->pc);
     a.g = G->g;
+    a.g32 = G->g32;
     a.anc[0] = G->anc[0];
     a.anc[1] = G->anc[1];
     a.acc[0] = G->acc[0];
@@ -241,6 +244,7 @@ pirrt_status launch_wave(pirrt_graph *G, unsigned dense_limit, unsigned max_leve
     a.p = G->p;
     a.pc = static_cast<const CT *>(G->pc);
     a.g = G->g;
+    a.g32 = G->g32;
     a.switched = G->switched;
     a.lvl[0] = G->wl[0];
     a.lvl[1] = G->wl[1];
@@ -330,7 +334,8 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
     // 4. seed the new vertices
     if (n_new > 0) {
         insert_init_vertices<CT><<<grid_for(n_new, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_old, n_after, G->cfg.root, G->g, G->p, static_cast<CT *>(G->pc), G->stamp, G->epoch,
+            n_old, n_after, G->cfg.root, G->g, G->g32, G->p, static_cast<CT *>(G->pc), G->stamp,
+            G->epoch,
             G->list[G->la], G->ctr);
         CKL();
     }
@@ -550,7 +555,7 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
                     "set_policy: parent out of range, root with a parent, or a parent edge not in G");
     }
     policy_commit_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
-        G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g);
+        G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g, G->g32);
     CKL();
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
     CKL();
@@ -568,7 +573,7 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
 }
 
 void free_all(pirrt_graph *G) {
-    void *bufs[] = {G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->p, G->pc,
+    void *bufs[] = {G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
                     G->wl[1], G->wstamp, G->ctr, G->stage};
@@ -659,6 +664,7 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->adj[0], G->entry_bytes * (ne + 16));
     ALLOC(G->adj[1], G->entry_bytes * (ne + 16));
     ALLOC(G->g, sizeof(double) * nv);
+    ALLOC(G->g32, sizeof(float) * nv);
     ALLOC(G->p, sizeof(int32_t) * nv);
     ALLOC(G->pc, G->cost_bytes * nv);
     ALLOC(G->deg, sizeof(int32_t) * (nv + 1));

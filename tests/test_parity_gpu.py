@@ -405,3 +405,16 @@ def test_c3_wave_and_jump_identical_parents(c3_small):
     A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
     mask, _ = A.unambiguous(d)
     np.testing.assert_array_equal(pw[mask], pj[mask])
+
+
+@pytest.mark.parametrize("scale", [1e-39, 1e29, 1e36])
+def test_extreme_cost_scales(scale):
+    """Costs in the FP32 subnormal range, and costs whose path sums exceed
+    2^100 (the Improve kernel's FP32 screen then defers to exact FP64)."""
+    rm = W.random_graph(700, 3000, 12000, cost_dtype=np.float64, cmin=1.0, cmax=4.0)
+    c = (rm.cost * scale).astype(np.float32)
+    rmd = W.Roadmap(rm.name, rm.points, rm.u, rm.v, c, rm.edge_start, rm.n)
+    g_ref, p_ref, _ = _o1(rmd)
+    g, p, _ = gpu_schedule(rmd)
+    assert_parity(rmd, g, p, g_ref, p_ref)
+

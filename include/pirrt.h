@@ -73,10 +73,11 @@ typedef struct {
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
     int32_t group;          /* Improve kernel: 0 = tiled (a CTA streams the concatenated rows
                                of 64 vertices), or 4, 8, 16, 32 threads per vertex */
-    int32_t tile;           /* Improve kernel when group = 0: 0 = staged (a producer warp
+    int32_t tile;           /* Improve kernel when group = 0: 0 = one thread per vertex with
+                               FP32 screening (FP32 costs); 1 = staged (a producer warp
                                bulk-copies 32-row tiles into a 4-stage shared-memory ring
-                               for 8 consumer warps); 16, 32, 64 or 128 = vertices per
-                               CTA tile of the unstaged tiled kernel */
+                               for 8 consumer warps); 16, 32, 64 or 128 = vertices per CTA
+                               tile of the unstaged tiled kernel */
     int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
     int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
                                pointer jumping; 0 = tuned */

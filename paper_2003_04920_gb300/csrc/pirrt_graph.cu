@@ -18,6 +18,7 @@
 
 #include "graph_kernels.cuh"
 #include "improve_tma.cuh"
+#include "improve_tpv.cuh"
 #include "pirrt.h"
 
 using namespace pirrt;
@@ -162,16 +163,34 @@ pirrt_status launch_improve_tma(pirrt_graph *G, const ImproveArgs<CT> &a) {
     return PIRRT_OK;
 }
 
+template <typename CT>
+pirrt_status launch_improve_tpv(pirrt_graph *G, const ImproveArgs<CT> &a) {
+    if constexpr (sizeof(CT) != 4) {
+        return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
+    } else {
+        static int occ = -1;
+        if (occ < 0) {
+            int nb = 0;
+            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tpv_kernel, kTpvThreads, 0));
+            occ = nb > 0 ? nb : 1;
+        }
+        improve_tpv_kernel<<<G->num_sms * occ, kTpvThreads, 0, G->stream>>>(a);
+        CKL();
+        return PIRRT_OK;
+    }
+}
+
 // Tiled Improve shapes (vertices per tile -> threads, entries per thread);
-// 0 = the staged (bulk-copy pipelined) kernel.
+// 1 = the staged (bulk-copy pipelined) kernel; 0 = one thread per vertex.
 template <typename CT>
 pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
     switch (tile) {
+        case 1: return launch_improve_tma<CT>(G, a);
         case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
         case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
         case 64: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
         case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
-        default: return launch_improve_tma<CT>(G, a);
+        default: return launch_improve_tpv<CT>(G, a);
     }
 }
 
@@ -362,7 +381,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     if (opts) o = *opts;
     if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
-        (o.tile != 0 && o.tile != 16 && o.tile != 32 && o.tile != 64 && o.tile != 128))
+        (o.tile != 0 && o.tile != 1 && o.tile != 16 && o.tile != 32 && o.tile != 64 && o.tile != 128))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = group_for(o.group);

@@ -307,8 +307,11 @@ def run_ours(args) -> None:
                    "evaluate": args.evaluate,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": dict(extra),
-                   "improve_kernel": f"tiled ({args.tile or 'default'} vertices per tile)"
-                   if args.group == 0 else f"{args.group} threads per vertex",
+                   "improve_kernel": {0: "lane groups, FP32 screening", 1: "staged bulk copies",
+                                      2: "thread per vertex, FP32 screening",
+                                      3: "lane groups, exact FP64"}.get(
+                       args.tile, f"tiled, {args.tile} vertices per CTA"),
+                   "improve_lanes_per_vertex": args.group or 8,
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
                          % (2 * rm.m * entry_bytes / 1e9)},

@@ -71,13 +71,14 @@ typedef struct {
     double eps;             /* Replan stops once Delta g <= eps (Alg. 2); 0 = until no
                                parent switches */
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
-    int32_t group;          /* Improve kernel: 0 = tiled (a CTA streams the concatenated rows
-                               of 64 vertices), or 4, 8, 16, 32 threads per vertex */
-    int32_t tile;           /* Improve kernel when group = 0: 0 = one thread per vertex with
-                               FP32 screening (FP32 costs); 1 = staged (a producer warp
-                               bulk-copies 32-row tiles into a 4-stage shared-memory ring
-                               for 8 consumer warps); 16, 32, 64 or 128 = vertices per CTA
-                               tile of the unstaged tiled kernel */
+    int32_t group;          /* lanes per vertex of the lane-group Improve kernels: 4, 8, 16
+                               or 32; 0 = 8 */
+    int32_t tile;           /* Improve kernel: 0 = lane groups with FP32 screening (FP64
+                               costs: exact lane groups); 1 = staged (a producer warp bulk-
+                               copies 32-row tiles into a 4-stage shared-memory ring for 8
+                               consumer warps); 2 = one thread per vertex with FP32
+                               screening; 3 = lane groups, exact FP64 for every candidate;
+                               16, 32, 64, 128 = vertices per CTA tile of the tiled kernel */
     int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
     int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
                                pointer jumping; 0 = tuned */

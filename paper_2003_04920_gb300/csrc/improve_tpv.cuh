@@ -142,3 +142,160 @@ improve_tpv_kernel(ImproveArgs<float> a) {
 }
 
 }  // namespace pirrt
+
+namespace pirrt {
+
+// Improve with G lanes per vertex and FP32 screening (FP32 costs).  Each
+// lane scans every G-th entry of the row, four entries and four FP32 gathers
+// in flight, tracking (minimum, entry of the minimum, second minimum) of the
+// FP32 screen; G-lane shuffles merge them.  The exact FP64 sum is formed for
+// the FP32 argmin alone, unless another candidate lies within the screening
+// margin, in which case the group rescans the row exactly.  No shared memory,
+// no CTA barriers, no FP64 arithmetic per entry.
+template <int G>
+__global__ void __launch_bounds__(256)
+improve_screen_kernel(ImproveArgs<float> a) {
+    constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
+    constexpr int kU = 4;
+    const unsigned long long gpol = policy_evict_last();
+    const int lane = threadIdx.x & 31, gl = threadIdx.x & (G - 1);
+    const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    const int gpb = 256 / G;
+    const int64_t gstride = (int64_t)gridDim.x * gpb;
+    const bool dense = a.ctr->dense != 0u;
+    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
+    const float kInf = __int_as_float(0x7f800000);
+    unsigned long long relax = 0, improved = 0;
+    // whole warps iterate together so the appends below are warp-collective
+    const int64_t first = (int64_t)blockIdx.x * gpb + (threadIdx.x >> 5) * (32 / G);
+    const int64_t warp_span = 32 / G;
+    for (int64_t wbase = first; wbase < count; wbase += gstride) {
+        const int64_t item = wbase + (lane / G);
+        int32_t v = -1;
+        if (item < count) {
+            v = dense ? (int32_t)item : __ldg(&a.active[item]);
+            if (v == a.root) v = -1;
+        }
+        bool sw = false;
+        unsigned long long dj = 0ull;
+        if (v >= 0) {  // uniform within the group
+            const int64_t b = a.row_off[v], e = a.row_off[v + 1];
+            int32_t pv = -1;
+            float pcv = 0.f;
+            double gp = CUDART_INF;
+            if (gl == 0) {
+                pv = a.p[v];
+                pcv = a.pc[v];
+                if (pv >= 0) gp = a.g[pv];
+            }
+            float m1 = kInf, m2 = kInf;
+            int64_t i1 = -1;
+            int exact_row = 0;
+            for (int64_t i0 = b + gl; i0 < e; i0 += (int64_t)G * kU) {
+                Entry<float> en[kU];
+#pragma unroll
+                for (int q = 0; q < kU; ++q)
+                    if (i0 + q * G < e) en[q] = ld_stream(&a.adj[i0 + q * G]);
+                float gu[kU];
+#pragma unroll
+                for (int q = 0; q < kU; ++q)
+                    if (i0 + q * G < e) gu[q] = ld_g32f(&a.g32[en[q].col], gpol);
+#pragma unroll
+                for (int q = 0; q < kU; ++q) {
+                    if (i0 + q * G < e) {
+                        const float av = gu[q] + en[q].w;
+                        exact_row |= (gu[q] < 0.f) | (isinf(av) & !isinf(gu[q]));
+                        if (av < m1) {
+                            m2 = m1;
+                            m1 = av;
+                            i1 = i0 + q * G;
+                        } else if (av < m2) {
+                            m2 = av;
+                        }
+                    }
+                }
+            }
+#pragma unroll
+            for (int off = G / 2; off > 0; off >>= 1) {
+                const float om1 = __shfl_xor_sync(gmask, m1, off, G);
+                const float om2 = __shfl_xor_sync(gmask, m2, off, G);
+                const int64_t oi1 = __shfl_xor_sync(gmask, i1, off, G);
+                exact_row |= __shfl_xor_sync(gmask, exact_row, off, G);
+                const float lo = fminf(m1, om1), hi = fmaxf(m1, om1);
+                if (om1 < m1 || (om1 == m1 && oi1 >= 0 && (i1 < 0 || oi1 < i1))) i1 = oi1;
+                m2 = fminf(hi, fminf(m2, om2));
+                m1 = lo;
+            }
+            // exact FP64 lexicographic minimum over the candidates in play
+            unsigned long long bv = kInfBits + 1ull;
+            int32_t bid = INT_MAX;
+            unsigned bw = 0xffffffffu;
+            const float tau = m1 * (1.0f + 0x1p-20f) + 0x1p-125f;
+            const bool rescan = exact_row || (m2 <= tau && !isinf(m1));
+            if (rescan) {
+                for (int64_t i = b + gl; i < e; i += G) {
+                    const Entry<float> en = a.adj[i];
+                    if (exact_row || ld_g32f(&a.g32[en.col], gpol) + en.w <= tau) {
+                        const unsigned long long vb = (unsigned long long)__double_as_longlong(
+                            ld_g(&a.g[en.col], gpol) + widen(en.w));
+                        const unsigned wb = __float_as_uint(en.w);
+                        if (vb < bv || (vb == bv && (en.col < bid || (en.col == bid && wb < bw)))) {
+                            bv = vb;
+                            bid = en.col;
+                            bw = wb;
+                        }
+                    }
+                }
+#pragma unroll
+                for (int off = G / 2; off > 0; off >>= 1) {
+                    const unsigned long long ov = __shfl_xor_sync(gmask, bv, off, G);
+                    const int32_t oi = __shfl_xor_sync(gmask, bid, off, G);
+                    const unsigned ow = __shfl_xor_sync(gmask, bw, off, G);
+                    if (ov < bv || (ov == bv && (oi < bid || (oi == bid && ow < bw)))) {
+                        bv = ov;
+                        bid = oi;
+                        bw = ow;
+                    }
+                }
+            } else if (gl == 0 && i1 >= 0 && !isinf(m1)) {
+                const Entry<float> en = a.adj[i1];
+                bv = (unsigned long long)__double_as_longlong(ld_g(&a.g[en.col], gpol) + widen(en.w));
+                bid = en.col;
+                bw = __float_as_uint(en.w);
+            }
+            if (gl == 0) {
+                const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
+                if (bv <= kInfBits) {
+                    const double best = __longlong_as_double((long long)bv);
+                    if (best < cur) {
+                        a.p[v] = bid;
+                        a.pc[v] = __uint_as_float(bw);
+                        sw = true;
+                        dj = (unsigned long long)__double_as_longlong(cur - best);
+                    }
+                }
+                relax += (unsigned long long)(e - b);
+                improved += 1;
+            }
+        }
+        warp_append(sw, v, a.switched, &a.ctr->n_switched);
+#pragma unroll
+        for (int off = 16; off > 0; off >>= 1) {
+            const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
+            dj = o > dj ? o : dj;
+        }
+        if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
+        (void)warp_span;
+    }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        relax += __shfl_down_sync(0xffffffffu, relax, off);
+        improved += __shfl_down_sync(0xffffffffu, improved, off);
+    }
+    if (lane == 0 && (relax || improved)) {
+        atomicAdd(&a.ctr->relax, relax);
+        atomicAdd(&a.ctr->improved, improved);
+    }
+}
+
+}  // namespace pirrt

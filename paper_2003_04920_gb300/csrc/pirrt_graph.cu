@@ -126,11 +126,6 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
     return PIRRT_OK;
 }
 
-// 0 = the tiled kernel; 4, 8, 16, 32 = G threads per vertex.
-int group_for(int requested) {
-    if (requested == 4 || requested == 8 || requested == 16 || requested == 32) return requested;
-    return 0;
-}
 
 template <typename CT, int TH, int TV, int PER>
 pirrt_status launch_improve_tile_v(pirrt_graph *G, const ImproveArgs<CT> &a) {
@@ -181,16 +176,17 @@ pirrt_status launch_improve_tpv(pirrt_graph *G, const ImproveArgs<CT> &a) {
 }
 
 // Tiled Improve shapes (vertices per tile -> threads, entries per thread);
-// 1 = the staged (bulk-copy pipelined) kernel; 0 = one thread per vertex.
+// 1 = the staged (bulk-copy pipelined) kernel; 2 = one thread per vertex.
 template <typename CT>
 pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
     switch (tile) {
         case 1: return launch_improve_tma<CT>(G, a);
+        case 2: return launch_improve_tpv<CT>(G, a);
         case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
         case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
         case 64: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
         case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
-        default: return launch_improve_tpv<CT>(G, a);
+        default: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
     }
 }
 
@@ -207,6 +203,26 @@ pirrt_status launch_improve_g(pirrt_graph *G, const ImproveArgs<CT> &a) {
     return PIRRT_OK;
 }
 
+template <int GS>
+pirrt_status launch_improve_screen(pirrt_graph *G, const ImproveArgs<float> &a) {
+    static int occ = -1;
+    if (occ < 0) {
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_screen_kernel<GS>, 256, 0));
+        occ = nb > 0 ? nb : 1;
+    }
+    improve_screen_kernel<GS><<<G->num_sms * occ, 256, 0, G->stream>>>(a);
+    CKL();
+    return PIRRT_OK;
+}
+
+// Improve kernel selection (pirrt_exploit_opts.tile / .group):
+//   tile 0  G lanes per vertex (group, default 8) with FP32 screening; FP64
+//           costs use the exact G-lane kernel
+//   tile 1  staged: producer warp bulk-copies rows into a shared-memory ring
+//   tile 2  one thread per vertex with FP32 screening
+//   tile 3  G lanes per vertex, exact FP64 for every candidate
+//   16..128 vertices per CTA tile of the unstaged tiled kernel
 template <typename CT>
 pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
     ImproveArgs<CT> a;
@@ -221,13 +237,27 @@ pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
     a.ctr = G->ctr;
     a.n = G->n;
     a.root = G->cfg.root;
-    switch (gs) {
-        case 0: return launch_improve_tile<CT>(G, a, tile);
-        case 4: return launch_improve_g<CT, 4>(G, a);
-        case 8: return launch_improve_g<CT, 8>(G, a);
-        case 16: return launch_improve_g<CT, 16>(G, a);
-        default: return launch_improve_g<CT, 32>(G, a);
+    const int g = gs ? gs : 8;
+    if (tile == 0) {
+        if constexpr (sizeof(CT) == 4) {
+            switch (g) {
+                case 4: return launch_improve_screen<4>(G, a);
+                case 16: return launch_improve_screen<16>(G, a);
+                case 32: return launch_improve_screen<32>(G, a);
+                default: return launch_improve_screen<8>(G, a);
+            }
+        }
+        tile = 3;
     }
+    if (tile == 3) {
+        switch (g) {
+            case 4: return launch_improve_g<CT, 4>(G, a);
+            case 16: return launch_improve_g<CT, 16>(G, a);
+            case 32: return launch_improve_g<CT, 32>(G, a);
+            default: return launch_improve_g<CT, 8>(G, a);
+        }
+    }
+    return launch_improve_tile<CT>(G, a, tile);
 }
 
 template <typename CT>
@@ -381,10 +411,12 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     if (opts) o = *opts;
     if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
-        (o.tile != 0 && o.tile != 1 && o.tile != 16 && o.tile != 32 && o.tile != 64 && o.tile != 128))
+        !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3 || o.tile == 16 ||
+          o.tile == 32 || o.tile == 64 || o.tile == 128) ||
+        !(o.group == 0 || o.group == 4 || o.group == 8 || o.group == 16 || o.group == 32))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
-    const int gs = group_for(o.group);
+    const int gs = o.group;
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
     const unsigned dense_limit = (unsigned)std::min<double>(4.0e9, frac * (double)G->n);
     const int mode = o.evaluate;

@@ -143,6 +143,40 @@ __device__ __forceinline__ void warp_append(bool pred, int32_t value, int32_t *l
     if (pred) list[base + __popc(ballot & ((1u << lane) - 1u))] = value;
 }
 
+// Warp-private staging of list appends in shared memory: items collect in a
+// per-warp buffer (ballot offsets, no atomics) and reach the global list in
+// batches, one atomicAdd per flush.  All 32 lanes must call push / flush
+// together; `count` is warp-uniform.
+template <int CAP>
+struct WarpStage {
+    int32_t *buf;    // CAP slots in shared memory, private to the warp
+    unsigned count;  // items staged
+
+    __device__ __forceinline__ void flush(int32_t *list, unsigned *counter) {
+        const unsigned lane = threadIdx.x & 31u;
+        if (count == 0u) return;
+        unsigned base = 0;
+        if (lane == 0) base = atomicAdd(counter, count);
+        base = __shfl_sync(0xffffffffu, base, 0);
+        __syncwarp();
+        for (unsigned i = lane; i < count; i += 32u) list[base + i] = buf[i];
+        __syncwarp();
+        count = 0u;
+    }
+
+    __device__ __forceinline__ void push(bool pred, int32_t value, int32_t *list,
+                                         unsigned *counter) {
+        const unsigned lane = threadIdx.x & 31u;
+        const unsigned ballot = __ballot_sync(0xffffffffu, pred);
+        const unsigned n = (unsigned)__popc(ballot);
+        if (n == 0u) return;
+        if (count + n > (unsigned)CAP) flush(list, counter);
+        if (pred) buf[count + __popc(ballot & ((1u << lane) - 1u))] = value;
+        count += n;
+        __syncwarp();
+    }
+};
+
 // Block-wide reservation in two lists at once: thread i wants na[i] slots of
 // list A and nb[i] of list B.  One atomicAdd per list per block; returns this
 // thread's first slot in each.  Every thread of the block must call it;

@@ -152,20 +152,23 @@ namespace pirrt {
 // the FP32 argmin alone, unless another candidate lies within the screening
 // margin, in which case the group rescans the row exactly.  No shared memory,
 // no CTA barriers, no FP64 arithmetic per entry.
-template <int G>
+template <int G, int kU>
 __global__ void __launch_bounds__(256)
 improve_screen_kernel(ImproveArgs<float> a) {
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-    constexpr int kU = 4;
+    constexpr int kStageCap = 128;
+    __shared__ int32_t s_sw[256 / 32][kStageCap];
+    WarpStage<kStageCap> swq{s_sw[threadIdx.x >> 5], 0u};
     const unsigned long long gpol = policy_evict_last();
     const int lane = threadIdx.x & 31, gl = threadIdx.x & (G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
+    (void)gmask;
     const int gpb = 256 / G;
     const int64_t gstride = (int64_t)gridDim.x * gpb;
     const bool dense = a.ctr->dense != 0u;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const float kInf = __int_as_float(0x7f800000);
-    unsigned long long relax = 0, improved = 0;
+    unsigned long long relax = 0, improved = 0, djmax = 0;
     // whole warps iterate together so the appends below are warp-collective
     const int64_t first = (int64_t)blockIdx.x * gpb + (threadIdx.x >> 5) * (32 / G);
     const int64_t warp_span = 32 / G;
@@ -278,15 +281,17 @@ improve_screen_kernel(ImproveArgs<float> a) {
                 improved += 1;
             }
         }
-        warp_append(sw, v, a.switched, &a.ctr->n_switched);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
-            dj = o > dj ? o : dj;
-        }
-        if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
+        swq.push(sw, v, a.switched, &a.ctr->n_switched);
+        djmax = dj > djmax ? dj : djmax;
         (void)warp_span;
     }
+    swq.flush(a.switched, &a.ctr->n_switched);
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_xor_sync(0xffffffffu, djmax, off);
+        djmax = o > djmax ? o : djmax;
+    }
+    if (lane == 0 && djmax) atomicMax(&a.ctr->dj_bits, djmax);
 #pragma unroll
     for (int off = 16; off > 0; off >>= 1) {
         relax += __shfl_down_sync(0xffffffffu, relax, off);

@@ -203,15 +203,15 @@ pirrt_status launch_improve_g(pirrt_graph *G, const ImproveArgs<CT> &a) {
     return PIRRT_OK;
 }
 
-template <int GS>
+template <int GS, int U>
 pirrt_status launch_improve_screen(pirrt_graph *G, const ImproveArgs<float> &a) {
     static int occ = -1;
     if (occ < 0) {
         int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_screen_kernel<GS>, 256, 0));
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_screen_kernel<GS, U>, 256, 0));
         occ = nb > 0 ? nb : 1;
     }
-    improve_screen_kernel<GS><<<G->num_sms * occ, 256, 0, G->stream>>>(a);
+    improve_screen_kernel<GS, U><<<G->num_sms * occ, 256, 0, G->stream>>>(a);
     CKL();
     return PIRRT_OK;
 }
@@ -240,11 +240,14 @@ pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
     const int g = gs ? gs : 8;
     if (tile == 0) {
         if constexpr (sizeof(CT) == 4) {
-            switch (g) {
-                case 4: return launch_improve_screen<4>(G, a);
-                case 16: return launch_improve_screen<16>(G, a);
-                case 32: return launch_improve_screen<32>(G, a);
-                default: return launch_improve_screen<8>(G, a);
+            switch (gs) {
+                case 1: return launch_improve_screen<1, 8>(G, a);
+                case 2: return launch_improve_screen<2, 8>(G, a);
+                case 8: return launch_improve_screen<8, 4>(G, a);
+                case 16: return launch_improve_screen<16, 4>(G, a);
+                case 32: return launch_improve_screen<32, 4>(G, a);
+                case 5: return launch_improve_screen<4, 8>(G, a);  // 4 lanes, 8 in flight
+                default: return launch_improve_screen<4, 4>(G, a);
             }
         }
         tile = 3;
@@ -413,7 +416,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
         !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3 || o.tile == 16 ||
           o.tile == 32 || o.tile == 64 || o.tile == 128) ||
-        !(o.group == 0 || o.group == 4 || o.group == 8 || o.group == 16 || o.group == 32))
+        !(o.group >= 0 && o.group <= 32))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = o.group;

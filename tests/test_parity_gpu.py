@@ -152,8 +152,9 @@ def test_c2_as_specified_small_reachable_set():
 
 # ------------------------------------------------------ invariances ---
 
-@pytest.mark.parametrize("group,tile", [(4, 0), (16, 0), (32, 0), (0, 1), (0, 2), (4, 3),
-                                        (8, 3), (32, 3), (0, 16), (0, 32), (0, 64), (0, 128)])
+@pytest.mark.parametrize("group,tile", [(1, 0), (2, 0), (5, 0), (8, 0), (16, 0), (32, 0),
+                                        (0, 1), (0, 2), (4, 3), (8, 3), (32, 3), (0, 16),
+                                        (0, 32), (0, 64), (0, 128)])
 def test_improve_kernels_agree(c3_small, group, tile):
     """Every tiled Improve shape and the G-threads-per-vertex kernels take the
     same lexicographic argmin, so whole schedules agree bit for bit."""

@@ -169,20 +169,35 @@ improve_screen_kernel(ImproveArgs<float> a) {
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const float kInf = __int_as_float(0x7f800000);
     unsigned long long relax = 0, improved = 0, djmax = 0;
-    // whole warps iterate together so the appends below are warp-collective
+    // whole warps iterate together so the appends below are warp-collective.
+    // The next iteration's vertex and row extent are loaded one iteration
+    // ahead, and within a row the next batch of entries is requested before
+    // the current batch's FP32 gathers are consumed.
     const int64_t first = (int64_t)blockIdx.x * gpb + (threadIdx.x >> 5) * (32 / G);
     const int64_t warp_span = 32 / G;
-    for (int64_t wbase = first; wbase < count; wbase += gstride) {
-        const int64_t item = wbase + (lane / G);
-        int32_t v = -1;
+    auto fetch = [&](int64_t wb, int32_t &v, int64_t &b, int64_t &e) {
+        const int64_t item = wb + (lane / G);
+        v = -1;
+        b = e = 0;
         if (item < count) {
             v = dense ? (int32_t)item : __ldg(&a.active[item]);
             if (v == a.root) v = -1;
+            else {
+                b = a.row_off[v];
+                e = a.row_off[v + 1];
+            }
         }
+    };
+    int32_t nv_;
+    int64_t nb_, ne_;
+    fetch(first, nv_, nb_, ne_);
+    for (int64_t wbase = first; wbase < count; wbase += gstride) {
+        const int32_t v = nv_;
+        const int64_t b = nb_, e = ne_;
+        if (wbase + gstride < count) fetch(wbase + gstride, nv_, nb_, ne_);
         bool sw = false;
         unsigned long long dj = 0ull;
         if (v >= 0) {  // uniform within the group
-            const int64_t b = a.row_off[v], e = a.row_off[v + 1];
             int32_t pv = -1;
             float pcv = 0.f;
             double gp = CUDART_INF;
@@ -194,15 +209,21 @@ improve_screen_kernel(ImproveArgs<float> a) {
             float m1 = kInf, m2 = kInf;
             int64_t i1 = -1;
             int exact_row = 0;
-            for (int64_t i0 = b + gl; i0 < e; i0 += (int64_t)G * kU) {
-                Entry<float> en[kU];
+            Entry<float> en[kU];
+            int64_t i0 = b + gl;
 #pragma unroll
-                for (int q = 0; q < kU; ++q)
-                    if (i0 + q * G < e) en[q] = ld_stream(&a.adj[i0 + q * G]);
+            for (int q = 0; q < kU; ++q)
+                if (i0 + q * G < e) en[q] = ld_stream(&a.adj[i0 + q * G]);
+            for (; i0 < e; i0 += (int64_t)G * kU) {
                 float gu[kU];
 #pragma unroll
                 for (int q = 0; q < kU; ++q)
                     if (i0 + q * G < e) gu[q] = ld_g32f(&a.g32[en[q].col], gpol);
+                Entry<float> nx[kU];
+                const int64_t i1n = i0 + (int64_t)G * kU;
+#pragma unroll
+                for (int q = 0; q < kU; ++q)
+                    if (i1n + q * G < e) nx[q] = ld_stream(&a.adj[i1n + q * G]);
 #pragma unroll
                 for (int q = 0; q < kU; ++q) {
                     if (i0 + q * G < e) {
@@ -217,6 +238,8 @@ improve_screen_kernel(ImproveArgs<float> a) {
                         }
                     }
                 }
+#pragma unroll
+                for (int q = 0; q < kU; ++q) en[q] = nx[q];
             }
 #pragma unroll
             for (int off = G / 2; off > 0; off >>= 1) {

@@ -732,32 +732,28 @@ struct WaveArgs {
 // write of every vertex comes one level after its parent's last change, so
 // the result does not depend on scheduling.
 //
-// Each level is processed by lane groups: kWaveG lanes per frontier vertex,
-// warps iterating together over the level so that the appends to the next
-// level and to the next Improve list can be staged per warp in shared memory
-// (one global atomic per kWaveStage items).  There is no CTA barrier inside
-// a level; a grid barrier separates levels.
+// Each level is split evenly over the CTAs.  A CTA takes up to kWaveThreads
+// vertices at a time, one per thread, then streams the concatenated rows of
+// the changed ones with every thread (the loads of a whole tile in flight at
+// once), locating each entry's row by binary search over the tile's prefix
+// sums in shared memory.
 constexpr int kWaveThreads = 512;
-constexpr int kWaveG = 4;
-constexpr int kWaveStage = 128;
+constexpr int kWaveUnroll = 4;
 
 template <typename CT>
 __global__ void __launch_bounds__(kWaveThreads)
 wave_evaluate_kernel(WaveArgs<CT> a) {
-    __shared__ int32_t s_child[kWaveThreads / 32][kWaveStage];
-    __shared__ int32_t s_mark[kWaveThreads / 32][kWaveStage];
+    __shared__ int32_t s_u[kWaveThreads];
+    __shared__ long long s_base[kWaveThreads];
+    __shared__ int32_t s_seg[kWaveThreads + 1];
+    __shared__ int32_t s_wsum[kWaveThreads / 32];
+    __shared__ unsigned long long s_scan[kWaveThreads / 32 + 2];
     DevCounters *c = a.ctr;
     const unsigned n_sw = c->n_switched;
     if (n_sw == 0u) return;
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int gl = lane & (kWaveG - 1);
-    const unsigned gmask = ((1u << kWaveG) - 1u) << (lane & ~(kWaveG - 1));
-    constexpr int kPerWarp = 32 / kWaveG;
     const unsigned long long gpol = policy_evict_last();
-    WarpStage<kWaveStage> cq{s_child[warp], 0u}, mq{s_mark[warp], 0u};
-    const int64_t n_warps = (int64_t)gridDim.x * (kWaveThreads / 32);
-    const int64_t warp_id = (int64_t)blockIdx.x * (kWaveThreads / 32) + warp;
     unsigned long long recomputed = 0, changed_total = 0;
     unsigned t = 0;
     for (;; ++t) {
@@ -774,64 +770,92 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
         if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
         const unsigned wtag = a.wave_epoch + t;  // stamp of level t + 1
         const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
-        for (int64_t wb = warp_id * kPerWarp; wb < count; wb += n_warps * kPerWarp) {
-            const int64_t j = wb + lane / kWaveG;
+        const int64_t per = (count + nblocks - 1) / nblocks;
+        const int64_t lo = (int64_t)blockIdx.x * per;
+        const int64_t hi = lo + per < count ? lo + per : count;
+        for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
+            const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
+            int deg = 0;
             int32_t u = -1;
-            int changed = 0;
-            long long b = 0, e = 0;
-            if (j < count) {
-                u = __ldcg(&in[j]);
-                if (gl == 0) {
-                    const int32_t pu = __ldcg(&a.p[u]);
-                    const double gn = ld_g_cg(&a.g[pu], gpol) + widen(a.pc[u]);
-                    const double go = ld_g_cg(&a.g[u], gpol);
-                    ++recomputed;
-                    if (__double_as_longlong(gn) != __double_as_longlong(go)) {
-                        __stcg(&a.g[u], gn);
-                        __stcg(&a.g32[u], g32_of(gn));
-                        changed = 1;
-                        ++changed_total;
+            if (tid < nv) {
+                u = __ldcg(&in[s0 + tid]);
+                const int32_t pu = __ldcg(&a.p[u]);
+                const double gn = ld_g_cg(&a.g[pu], gpol) + (double)a.pc[u];
+                const double go = ld_g_cg(&a.g[u], gpol);
+                ++recomputed;
+                if (__double_as_longlong(gn) != __double_as_longlong(go)) {
+                    __stcg(&a.g[u], gn);
+                    __stcg(&a.g32[u], g32_of(gn));
+                    ++changed_total;
+                    const long long b = a.row_off[u];
+                    deg = (int)(a.row_off[u + 1] - b);
+                    s_base[tid] = b;
+                }
+            }
+            s_u[tid] = u;
+            // block exclusive scan of the changed rows' lengths
+            int incl = deg;
+#pragma unroll
+            for (int off = 1; off < 32; off <<= 1) {
+                const int y = __shfl_up_sync(0xffffffffu, incl, off);
+                if (lane >= off) incl += y;
+            }
+            if (lane == 31) s_wsum[warp] = incl;
+            __syncthreads();
+            if (warp == 0) {
+                int w = lane < kWaveThreads / 32 ? s_wsum[lane] : 0;
+#pragma unroll
+                for (int off = 1; off < 32; off <<= 1) {
+                    const int y = __shfl_up_sync(0xffffffffu, w, off);
+                    if (lane >= off) w += y;
+                }
+                if (lane < kWaveThreads / 32) s_wsum[lane] = w;
+            }
+            __syncthreads();
+            s_seg[tid + 1] = incl + (warp > 0 ? s_wsum[warp - 1] : 0);
+            if (tid == 0) s_seg[0] = 0;
+            __syncthreads();
+            const int total = s_seg[kWaveThreads];
+            for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
+                int32_t w[kWaveUnroll], owner[kWaveUnroll];
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    const int pos = p0 + tid + j * kWaveThreads;
+                    owner[j] = -1;
+                    w[j] = 0;
+                    if (pos < total) {
+                        int l = 0, h = kWaveThreads;  // last k with s_seg[k] <= pos
+                        while (h - l > 1) {
+                            const int mid = (l + h) >> 1;
+                            if (s_seg[mid] <= pos) l = mid; else h = mid;
+                        }
+                        owner[j] = s_u[l];
+                        w[j] = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]).col;
                     }
                 }
-                changed = __shfl_sync(gmask, changed, lane & ~(kWaveG - 1));
-                if (changed) {
-                    b = a.row_off[u];
-                    e = a.row_off[u + 1];
+                unsigned childm = 0, markm = 0;
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    if (owner[j] >= 0) {
+                        if (__ldcg(&a.p[w[j]]) == owner[j] &&
+                            atomicExch(&a.wstamp[w[j]], wtag) != wtag)
+                            childm |= 1u << j;
+                        if (marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != a.epoch &&
+                            atomicExch(&a.stamp[w[j]], a.epoch) != a.epoch)
+                            markm |= 1u << j;
+                    }
+                }
+                unsigned bc, bm;
+                block_reserve2<kWaveThreads>(__popc(childm), __popc(markm), out_cnt, &c->n_next,
+                                             s_scan, bc, bm);
+#pragma unroll
+                for (int j = 0; j < kWaveUnroll; ++j) {
+                    if (childm & (1u << j)) out[bc++] = w[j];
+                    if (markm & (1u << j)) a.next[bm++] = w[j];
                 }
             }
-            // warp-uniform scan over the longest changed row of the warp
-            int len = (int)(e - b);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) len = max(len, __shfl_xor_sync(0xffffffffu, len, off));
-            for (int k0 = 0; k0 < len; k0 += kWaveG * 4) {
-                int32_t w[4];
-                bool ok[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const long long i = b + k0 + gl + q * kWaveG;
-                    ok[q] = i < e;
-                    w[q] = ok[q] ? ld_stream(&a.adj[i]).col : 0;
-                }
-                int32_t pw[4];
-                unsigned sw[4];
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    pw[q] = ok[q] ? __ldcg(&a.p[w[q]]) : -1;
-                    sw[q] = (ok[q] && marking) ? __ldcg(&a.stamp[w[q]]) : a.epoch;
-                }
-#pragma unroll
-                for (int q = 0; q < 4; ++q) {
-                    const bool child =
-                        ok[q] && pw[q] == u && atomicExch(&a.wstamp[w[q]], wtag) != wtag;
-                    const bool mark = ok[q] && marking && w[q] != a.root && sw[q] != a.epoch &&
-                                      atomicExch(&a.stamp[w[q]], a.epoch) != a.epoch;
-                    cq.push(child, w[q], out, out_cnt);
-                    mq.push(mark, w[q], a.next, &c->n_next);
-                }
-            }
+            __syncthreads();  // s_u / s_base / s_seg are rewritten by the next tile
         }
-        cq.flush(out, out_cnt);
-        mq.flush(a.next, &c->n_next);
         // changed-vertex count decides between a list and a dense sweep next
 #pragma unroll
         for (int off = 16; off > 0; off >>= 1)

@@ -224,6 +224,31 @@ typedef struct {
  * for a NULL handle. */
 int64_t pirrt_graph_get_trace(const pirrt_graph *g, pirrt_trace_record *out, int64_t cap);
 
+/* Evaluate that allocates nothing.  The paper has no counterpart: this is a
+ * service for callers that cannot call cudaMalloc when they need g -- a
+ * real-time planning loop that fixes all of its memory at start-up, or code
+ * recording into a CUDA stream capture, where allocation calls are refused.
+ * It computes g(v) = g(parent(v)) + parent_cost[v] from the root by the same
+ * pointer-jumping kernel as the graph handle, FP64 throughout:
+ *   n            vertex count, at most 262,144 (PIRRT_ERR_CAPACITY beyond)
+ *   root         vertex with g = 0
+ *   parent       device int32[n]: parent id, -1 for the root / unreached
+ *   parent_cost  device double[n]: cost of the edge (parent[v], v)
+ *   g_out        device double[n], written: +inf where the chain does not
+ *                reach the root
+ *   stream       cudaStream_t (NULL = legacy default stream)
+ * The caller owns all four arrays.  Scratch lives in one file-scope device
+ * array of about 11.5 MB that every GPU loading the library holds until the
+ * process exits.  The first call on a device (with that device current)
+ * resolves the array's device address and the launch shape; make that first
+ * call before any stream capture.  Every call shares the array and clears
+ * what it needs, so calls that overlap on the GPU (other streams, other host
+ * threads) race: serialise them.  Synchronises the stream to read the
+ * status.  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_CAPACITY, PIRRT_ERR_BAD_TREE
+ * (a cycle), PIRRT_ERR_DEVICE_TIMEOUT, PIRRT_ERR_CUDA. */
+pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const int32_t *parent,
+                                    const double *parent_cost, double *g_out, void *stream);
+
 /* Current vertex count, or -1 for a NULL handle. */
 int64_t pirrt_graph_num_vertices(const pirrt_graph *g);
 

@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_num_entries": (i64, [vp]),
         "pirrt_graph_last_error": (ctypes.c_char_p, [vp]),
         "pirrt_status_string": (ctypes.c_char_p, [st]),
+        "pirrt_evaluate_noalloc": (st, [i64, ctypes.c_int32, vp, vp, vp, vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -307,3 +308,16 @@ def run_schedule(graph: Graph, roadmap, block: int | None = None, on_device_inpu
             graph.insert_batch(v1 - v0, roadmap.u[e0:e1], roadmap.v[e0:e1], roadmap.cost[e0:e1])
         stats.append(graph.exploit(**exploit_kw))
     return stats
+
+
+def pirrt_evaluate_noalloc(parent, parent_cost, g_out, root: int = 0, stream=None) -> int:
+    """Evaluate g from device tensors without any allocation by the library
+    (scratch in a static device array, at most 262,144 vertices).  Returns
+    the pirrt_status code."""
+    lib = load_library()
+    n = int(parent.numel())
+    if stream is None:
+        stream = _current_stream_ptr(parent.device.index or 0)
+    return int(lib.pirrt_evaluate_noalloc(n, int(root), parent.data_ptr(), parent_cost.data_ptr(),
+                                          g_out.data_ptr(), stream))
+

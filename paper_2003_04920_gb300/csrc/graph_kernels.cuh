@@ -74,7 +74,7 @@ __device__ __forceinline__ long long block_exclusive_scan(long long x, long long
     return warp_base + incl - x;
 }
 
-__global__ void __launch_bounds__(kThreads)
+static __global__ void __launch_bounds__(kThreads)
 scan_tile_reduce(const int32_t *__restrict__ deg, int64_t len, long long *__restrict__ tile_sums) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     long long s = 0;
@@ -87,7 +87,7 @@ scan_tile_reduce(const int32_t *__restrict__ deg, int64_t len, long long *__rest
 }
 
 // Second pass: exclusive scan of the tile sums in one block.
-__global__ void __launch_bounds__(kThreads)
+static __global__ void __launch_bounds__(kThreads)
 scan_tile_sums(long long *__restrict__ tile_sums, int64_t n_tiles) {
     __shared__ long long carry;
     if (threadIdx.x == 0) carry = 0;
@@ -106,7 +106,7 @@ scan_tile_sums(long long *__restrict__ tile_sums, int64_t n_tiles) {
 
 // Third pass: new_off[v] = old_off[min(v, n_old)] + (entries added to rows < v).
 // len = n_after + 1 and deg[n_after] = 0, so new_off[n_after] is the new total.
-__global__ void __launch_bounds__(kThreads)
+static __global__ void __launch_bounds__(kThreads)
 scan_tile_apply(const int32_t *__restrict__ deg, int64_t len,
                 const long long *__restrict__ tile_sums, const int64_t *__restrict__ old_off,
                 int64_t n_old, int64_t *__restrict__ new_off) {
@@ -892,7 +892,7 @@ __device__ __forceinline__ void clear_iteration(DevCounters *c) {
 
 // Before pointer jumping takes over from an unfinished wave: its changed
 // list starts empty (the wave counted changes without listing them).
-__global__ void pre_jump_kernel(DevCounters *c) {
+static __global__ void pre_jump_kernel(DevCounters *c) {
     c->n_dg = 0u;
     c->rounds = 0u;
     c->bar_count = 0u;
@@ -900,7 +900,7 @@ __global__ void pre_jump_kernel(DevCounters *c) {
 }
 
 // Between iterations: the list built by mark becomes the current list.
-__global__ void advance_kernel(DevCounters *c) {
+static __global__ void advance_kernel(DevCounters *c) {
     c->n_active = c->dense_next ? 0u : c->n_next;
     c->dense = c->dense_next;
     c->dense_next = 0u;
@@ -909,7 +909,7 @@ __global__ void advance_kernel(DevCounters *c) {
 
 // Before an exploit or a forced Evaluate: clear the per-iteration fields and
 // the whole-exploit totals.
-__global__ void begin_exploit_kernel(DevCounters *c) {
+static __global__ void begin_exploit_kernel(DevCounters *c) {
     clear_iteration(c);
     c->relax = 0ull;
     c->improved = 0ull;

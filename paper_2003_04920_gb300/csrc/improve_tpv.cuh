@@ -32,7 +32,7 @@ __device__ __forceinline__ Entry<float> ld_entry_hint(const Entry<float> *p, uns
 }
 
 // FP32 costs only (the FP64-cost path uses the tiled kernels).
-__global__ void __launch_bounds__(kTpvThreads)
+static __global__ void __launch_bounds__(kTpvThreads)
 improve_tpv_kernel(ImproveArgs<float> a) {
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
     const unsigned long long gpol = policy_evict_last();

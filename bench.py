@@ -308,10 +308,8 @@ def run_ours(args) -> None:
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": dict(extra),
                    "improve_kernel": {0: "lane groups, FP32 screening", 1: "staged bulk copies",
-                                      2: "thread per vertex, FP32 screening",
-                                      3: "lane groups, exact FP64"}.get(
-                       args.tile, f"tiled, {args.tile} vertices per CTA"),
-                   "improve_lanes_per_vertex": args.group or 8,
+                                      3: "lane groups, exact FP64"}[args.tile],
+                   "improve_lanes_per_vertex": args.group or (4 if args.tile == 0 else 8),
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
                          % (2 * rm.m * entry_bytes / 1e9)},

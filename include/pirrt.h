@@ -71,18 +71,20 @@ typedef struct {
     double eps;             /* Replan stops once Delta g <= eps (Alg. 2); 0 = until no
                                parent switches */
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
-    int32_t group;          /* lanes per vertex of the lane-group Improve kernels: 4, 8, 16
-                               or 32; 0 = 8 */
+    int32_t group;          /* lanes per vertex of the lane-group Improve kernels: 2 (screened
+                               only), 4, 8, 16 or 32; 0 = tuned (4 screened, 8 exact) */
     int32_t tile;           /* Improve kernel: 0 = lane groups with FP32 screening (FP64
                                costs: exact lane groups); 1 = staged (a producer warp bulk-
                                copies 32-row tiles into a 4-stage shared-memory ring for 8
-                               consumer warps); 2 = one thread per vertex with FP32
-                               screening; 3 = lane groups, exact FP64 for every candidate;
-                               16, 32, 64, 128 = vertices per CTA tile of the tiled kernel */
+                               consumer warps); 3 = lane groups, exact FP64 for every
+                               candidate */
     int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
     int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
                                pointer jumping; 0 = tuned */
-    int32_t reserved;
+    int32_t host_loop;      /* 1 = drive the Replan loop from the host, one counter read per
+                               iteration; 0 = one CUDA-graph launch for the whole loop (a WHILE
+                               node repeats Improve / Evaluate on the device).  Profiling
+                               always uses the host loop. */
     double dense_fraction;  /* changed vertices, as a fraction of |V|, above which the next
                                Improve sweeps every vertex instead of a list; 0 = tuned */
 } pirrt_exploit_opts;
@@ -111,7 +113,7 @@ typedef struct {
     int32_t wave_levels;    /* top-down Evaluate levels, summed over Evaluate calls */
     int32_t jump_evaluates; /* Evaluate calls done (or finished) by pointer jumping */
     float ms_exploit;       /* device time of the call, CUDA events on the graph's stream */
-    float reserved;
+    int32_t graph_launch;   /* 1 if the loop ran as one CUDA-graph launch */
 } pirrt_exploit_stats;
 
 typedef struct pirrt_graph pirrt_graph;   /* opaque, library-owned */

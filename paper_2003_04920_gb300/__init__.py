@@ -48,7 +48,7 @@ class pirrt_config(ctypes.Structure):
 class pirrt_exploit_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("group", ctypes.c_int32), ("tile", ctypes.c_int32), ("evaluate", ctypes.c_int32),
-                ("wave_levels", ctypes.c_int32), ("reserved", ctypes.c_int32),
+                ("wave_levels", ctypes.c_int32), ("host_loop", ctypes.c_int32),
                 ("dense_fraction", ctypes.c_double)]
 
 
@@ -58,10 +58,10 @@ class pirrt_exploit_stats(ctypes.Structure):
                 ("switches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("jump_rounds", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("jump_evaluates", ctypes.c_int32),
-                ("ms_exploit", ctypes.c_float), ("reserved", ctypes.c_float)]
+                ("ms_exploit", ctypes.c_float), ("graph_launch", ctypes.c_int32)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_ if name != "reserved"}
+        return {name: getattr(self, name) for name, _ in self._fields_}
 
 
 class pirrt_profile(ctypes.Structure):
@@ -230,9 +230,9 @@ class Graph:
 
     def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                 dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
-                check: bool = True) -> dict:
+                host_loop: bool = False, check: bool = True) -> dict:
         opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
-                                  EVALUATE_MODES[evaluate], int(wave_levels), 0,
+                                  EVALUATE_MODES[evaluate], int(wave_levels), int(bool(host_loop)),
                                   float(dense_fraction))
         st = pirrt_exploit_stats()
         rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))

@@ -125,9 +125,27 @@ struct DevCounters {
     unsigned wave_cnt[3];         // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
     unsigned wave_levels;         // levels run by the last top-down Evaluate
     unsigned wave_incomplete;     // the top-down Evaluate stopped at its level cap
-    unsigned pad[3];
+    // Iteration state kept on the device so that one captured loop body (and
+    // the host loop alike) serves every iteration:
+    unsigned la;                  // which of the two lists Improve reads
+    unsigned epoch;               // stamp value of the current Improve list
+    unsigned wave_epoch;          // stamp of level 1 of the next top-down Evaluate
+    unsigned iter;                // Improve rounds run in this exploit
+    unsigned max_iters;           // cap on Improve rounds
+    unsigned cont;                // the loop continues (set by advance)
+    unsigned converged;           // the last advance saw a stable policy
+    unsigned jumped;              // this iteration's Evaluate ran pointer jumping
+    unsigned long long eps_bits;  // Delta g threshold (bits of a double >= 0)
+    // last completed iteration (read by the host after advance)
+    unsigned last_switched, last_dg, last_levels, last_next, last_dense, last_rounds, last_jumped;
+    // whole-exploit totals
+    unsigned cum_wave_levels, cum_dense, cum_jump_rounds, cum_jump_evals;
+    unsigned pad[1];
     unsigned wl_count[kMaxJumpRounds + 2];  // Evaluate work-list sizes per round
 };
+
+// Parent marker of a root vertex (g = 0, never re-parented).  Reported as -1.
+constexpr int32_t kRootMark = -2;
 
 // Append `value` to `list` for every lane with `pred`, one atomic per warp.
 // Every lane of the warp must call this (warp-uniform control flow).

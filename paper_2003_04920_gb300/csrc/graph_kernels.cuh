@@ -152,7 +152,10 @@ __global__ void __launch_bounds__(kThreads)
 insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
                const CT *__restrict__ cost, const int64_t *__restrict__ new_off,
                int32_t *__restrict__ deg, Entry<CT> *__restrict__ adj, unsigned *__restrict__ stamp,
-               unsigned epoch, int32_t root, int32_t *__restrict__ active, DevCounters *ctr) {
+               int32_t root, int32_t *__restrict__ list0, int32_t *__restrict__ list1,
+               DevCounters *ctr) {
+    const unsigned epoch = ctr->epoch;
+    int32_t *active = (ctr->la & 1u) ? list1 : list0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = (int64_t)blockIdx.x * blockDim.x; base < n_edges; base += stride) {
         const int64_t e = base + threadIdx.x;
@@ -189,8 +192,10 @@ template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__restrict__ g,
                      float *__restrict__ g32, int32_t *__restrict__ p, CT *__restrict__ pc,
-                     unsigned *__restrict__ stamp,
-                     unsigned epoch, int32_t *__restrict__ active, DevCounters *ctr) {
+                     unsigned *__restrict__ stamp, int32_t *__restrict__ list0,
+                     int32_t *__restrict__ list1, DevCounters *ctr) {
+    const unsigned epoch = ctr->epoch;
+    int32_t *active = (ctr->la & 1u) ? list1 : list0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = n_old + (int64_t)blockIdx.x * blockDim.x; base < n_after; base += stride) {
         const int64_t v = base + threadIdx.x;
@@ -198,7 +203,7 @@ insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__res
         if (v < n_after) {
             g[v] = (v == root) ? 0.0 : CUDART_INF;
             g32[v] = (v == root) ? 0.0f : __int_as_float(0x7f800000);
-            p[v] = -1;
+            p[v] = (v == root) ? kRootMark : -1;
             pc[v] = CT(0);
             pred = v != root && atomicExch(&stamp[v], epoch) != epoch;
         }
@@ -226,8 +231,8 @@ struct ImproveArgs {
     const float *g32;
     int32_t *p;
     CT *pc;
-    const int32_t *active;
-    int32_t *switched;  // list of vertices whose parent changed
+    const int32_t *list[2];  // Improve reads list[la & 1] (la in the counter block)
+    int32_t *switched;       // list of vertices whose parent changed
     DevCounters *ctr;
     int64_t n;
     int32_t root;
@@ -240,7 +245,9 @@ struct ImproveArgs {
 // by the same expression g(p) + c, and switches only on a strict decrease.
 template <typename CT, int G>
 __global__ void __launch_bounds__(kThreads)
-improve_kernel(ImproveArgs<CT> a) {
+improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
+    const ImproveArgs<CT> a = *ap;
+    const int32_t *active = a.list[a.ctr->la & 1u];
     constexpr int kUnroll = 4;
     const int lane_g = threadIdx.x & (G - 1);
     const unsigned group_mask =
@@ -254,7 +261,7 @@ improve_kernel(ImproveArgs<CT> a) {
     unsigned long long relax = 0, improved = 0;
     for (int64_t item = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G; item < count;
          item += gstride) {
-        const int32_t v = dense ? (int32_t)item : a.active[item];
+        const int32_t v = dense ? (int32_t)item : active[item];
         if (v == a.root) continue;  // uniform within the group
         const int64_t b = a.row_off[v], e = a.row_off[v + 1];
         double best = CUDART_INF;
@@ -297,7 +304,7 @@ improve_kernel(ImproveArgs<CT> a) {
                 bw = ow;
             }
         }
-        if (lane_g == 0) {
+        if (lane_g == 0 && a.p[v] != kRootMark) {
             const int32_t pv = a.p[v];
             const double cur = pv >= 0 ? a.g[pv] + (double)a.pc[v] : CUDART_INF;
             if (best < cur) {
@@ -337,15 +344,6 @@ improve_kernel(ImproveArgs<CT> a) {
     }
 }
 
-// Tiled Improve: a CTA takes a tile of TILE_V vertices (a slice of the active
-// list, or of 0..n-1 in a dense sweep), lays their rows end to end and
-// streams the concatenation THREADS * PER entries at a time, PER independent
-// entry loads per thread followed by PER independent g gathers, so the
-// memory system sees whole tiles in flight instead of one row per group.
-// The lexicographic argmin of (g(u) + c, u, c) per vertex is taken in shared
-// memory in three phases (min value, then min id among those, then min cost
-// among those -- parallel edges), each an atomicMin on order-preserving bits
-// of non-negative numbers.  Chunks of one tile are merged in order.
 template <typename CT>
 struct CostBits;
 template <>
@@ -367,178 +365,6 @@ struct CostBits<double> {
     static constexpr unsigned long long kMax = 0xffffffffffffffffull;
 };
 
-template <typename CT, int THREADS, int TILE_V, int PER>
-__global__ void __launch_bounds__(THREADS)
-improve_tile_kernel(ImproveArgs<CT> a) {
-    static_assert(TILE_V % 16 == 0 && TILE_V <= 128 && THREADS % 32 == 0, "tile shape");
-    static_assert(((TILE_V + 31) / 32) * 32 <= THREADS, "the scan needs whole warps");
-    using WB = typename CostBits<CT>::T;
-    constexpr int CHUNK = THREADS * PER;
-    constexpr int NW = (TILE_V + 31) / 32;
-    constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-    __shared__ int32_t s_v[TILE_V];
-    __shared__ long long s_base[TILE_V];
-    __shared__ int32_t s_seg[TILE_V + 1];
-    __shared__ unsigned long long s_cv[TILE_V];  // chunk minimum: value bits
-    __shared__ int32_t s_cid[TILE_V];            //   id
-    __shared__ WB s_cw[TILE_V];                  //   cost bits
-    __shared__ unsigned long long s_bv[TILE_V];  // tile minimum so far
-    __shared__ int32_t s_bid[TILE_V];
-    __shared__ WB s_bw[TILE_V];
-    __shared__ int32_t s_wsum[NW];
-
-    const int tid = threadIdx.x, lane = tid & 31;
-    const bool dense = a.ctr->dense != 0u;
-    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
-    const int64_t n_tiles = (count + TILE_V - 1) / TILE_V;
-    const unsigned long long gpol = policy_evict_last();
-    unsigned long long relax = 0, improved = 0;
-
-    for (int64_t tile = blockIdx.x; tile < n_tiles; tile += gridDim.x) {
-        const int64_t t0 = tile * TILE_V;
-        const int nv = (count - t0) < (int64_t)TILE_V ? (int)(count - t0) : TILE_V;
-        // 1. vertices of the tile, row extents, current-parent candidate,
-        //    exclusive scan of the degrees
-        int deg = 0;
-        int32_t v = -1, pv = -1;
-        CT pcv = CT(0);
-        double gp = CUDART_INF;
-        if (tid < nv) {
-            v = dense ? (int32_t)(t0 + tid) : __ldg(&a.active[t0 + tid]);
-            if (v != a.root) {
-                const long long b = a.row_off[v];
-                deg = (int)(a.row_off[v + 1] - b);
-                s_base[tid] = b;
-                pv = a.p[v];
-                pcv = a.pc[v];
-                if (pv >= 0) gp = a.g[pv];
-            } else {
-                v = -1;
-            }
-        }
-        if (tid < TILE_V) {
-            s_v[tid] = v;
-            s_bv[tid] = kInfBits + 1ull;  // above +inf: "no candidate yet"
-            s_bid[tid] = INT_MAX;
-            s_bw[tid] = CostBits<CT>::kMax;
-        }
-        // whole warps take part in the shuffle scan (deg = 0 past the tile)
-        if (tid < NW * 32) {
-            int incl = deg;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
-            }
-            if (lane == 31) s_wsum[tid >> 5] = incl;
-            if (tid < TILE_V) s_seg[tid + 1] = incl;
-        }
-        if (tid == 0) s_seg[0] = 0;
-        __syncthreads();
-        if (NW > 1 && tid >= 32 && tid < TILE_V) {
-            int add = 0;
-            for (int w = 0; w < (tid >> 5); ++w) add += s_wsum[w];
-            s_seg[tid + 1] += add;
-        }
-        __syncthreads();
-        const int total = s_seg[TILE_V];
-
-        // 2. stream the concatenated rows
-        for (int c0 = 0; c0 < total; c0 += CHUNK) {
-            if (tid < TILE_V) {
-                s_cv[tid] = kInfBits + 1ull;
-                s_cid[tid] = INT_MAX;
-                s_cw[tid] = CostBits<CT>::kMax;
-            }
-            __syncthreads();
-            Entry<CT> en[PER];
-            int kk[PER];
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                const int pos = c0 + tid + i * THREADS;
-                kk[i] = -1;
-                if (pos < total) {
-                    int lo = 0, hi = TILE_V;  // last k with s_seg[k] <= pos
-                    while (hi - lo > 1) {
-                        const int mid = (lo + hi) >> 1;
-                        if (s_seg[mid] <= pos) lo = mid; else hi = mid;
-                    }
-                    kk[i] = lo;
-                    en[i] = ld_stream(&a.adj[s_base[lo] + (pos - s_seg[lo])]);
-                }
-            }
-            unsigned long long vb[PER];
-#pragma unroll
-            for (int i = 0; i < PER; ++i) {
-                if (kk[i] >= 0) {
-                    const double val = ld_g(&a.g[en[i].col], gpol) + (double)en[i].w;
-                    vb[i] = (unsigned long long)__double_as_longlong(val);
-                    atomicMin(&s_cv[kk[i]], vb[i]);
-                }
-            }
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < PER; ++i)
-                if (kk[i] >= 0 && vb[i] == s_cv[kk[i]]) atomicMin(&s_cid[kk[i]], en[i].col);
-            __syncthreads();
-#pragma unroll
-            for (int i = 0; i < PER; ++i)
-                if (kk[i] >= 0 && vb[i] == s_cv[kk[i]] && en[i].col == s_cid[kk[i]])
-                    atomicMin(&s_cw[kk[i]], CostBits<CT>::of(en[i].w));
-            __syncthreads();
-            if (tid < TILE_V) {  // merge the chunk into the tile minimum
-                const unsigned long long cv = s_cv[tid], bv = s_bv[tid];
-                const int32_t cid = s_cid[tid], bid = s_bid[tid];
-                const WB cw = s_cw[tid], bw = s_bw[tid];
-                if (cv < bv || (cv == bv && (cid < bid || (cid == bid && cw < bw)))) {
-                    s_bv[tid] = cv;
-                    s_bid[tid] = cid;
-                    s_bw[tid] = cw;
-                }
-            }
-            __syncthreads();
-        }
-
-        // 3. switch where the best candidate beats the current parent,
-        //    g(p) + c computed by the same expression as every candidate
-        if (tid < NW * 32) {  // whole warps: the appends below are warp-collective
-            bool sw = false;
-            unsigned long long dj = 0ull;
-            if (tid < nv && v >= 0) {
-                const double cur = pv >= 0 ? gp + (double)pcv : CUDART_INF;
-                if (s_bv[tid] <= kInfBits) {
-                    const double best = __longlong_as_double((long long)s_bv[tid]);
-                    if (best < cur) {
-                        a.p[v] = s_bid[tid];
-                        a.pc[v] = CostBits<CT>::back(s_bw[tid]);
-                        sw = true;
-                        dj = (unsigned long long)__double_as_longlong(cur - best);
-                    }
-                }
-                relax += (unsigned long long)deg;
-                improved += 1;
-            }
-            warp_append(sw, v, a.switched, &a.ctr->n_switched);
-#pragma unroll
-            for (int off = 16; off > 0; off >>= 1) {
-                const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
-                dj = o > dj ? o : dj;
-            }
-            if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
-        }
-        __syncthreads();
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        relax += __shfl_down_sync(0xffffffffu, relax, off);
-        improved += __shfl_down_sync(0xffffffffu, improved, off);
-    }
-    if (lane == 0 && (relax || improved)) {
-        atomicAdd(&a.ctr->relax, relax);
-        atomicAdd(&a.ctr->improved, improved);
-    }
-}
-
 // ---------------------------------------------------------------------------
 // Evaluate (Alg. 2; Sec. IV-C) -- g(v) = g(p(v)) + c(p(v), v) from the root,
 // by pointer jumping over the parent tree in FP64.
@@ -558,7 +384,8 @@ struct EvaluateArgs {
     DevCounters *ctr;
     int64_t n;
     int32_t root;
-    int32_t force;    // run even if Improve switched nothing
+    int32_t force;    // run even if Improve switched nothing (set_policy)
+    int32_t role;     // 0: the iteration's Evaluate; 1: finish a wave that hit its level cap
 };
 
 // Rounds are separated by a grid barrier.  Round 0 links every vertex to its
@@ -568,9 +395,12 @@ struct EvaluateArgs {
 // written before round r, so the sums, hence g, do not depend on scheduling.
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
-evaluate_kernel(EvaluateArgs<CT> a) {
+evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
+    const EvaluateArgs<CT> a = *ap;
     DevCounters *c = a.ctr;
     if (!a.force && c->n_switched == 0u) return;
+    if (a.role == 1 && c->wave_incomplete == 0u) return;
+    if (blockIdx.x == 0 && threadIdx.x == 0) c->jumped = 1u;
     const unsigned nblocks = gridDim.x;
     const int lane = threadIdx.x & 31;
     const int64_t wstride = (int64_t)gridDim.x * kThreads;
@@ -584,7 +414,7 @@ evaluate_kernel(EvaluateArgs<CT> a) {
         if (v < a.n) {
             const int32_t pv = a.p[v];
             if (v == a.root || pv < 0) {
-                a.done[v] = 0;  // g(root) = 0, unreached = +inf: already in g
+                a.done[v] = 0;  // g(root) = 0 (parent kRootMark), unreached = +inf: already in g
             } else {
                 a.anc[0][v] = pv;
                 a.acc[0][v] = (double)a.pc[v];
@@ -656,17 +486,21 @@ struct MarkArgs {
     const Entry<CT> *adj;
     const int32_t *dg;
     unsigned *stamp;
-    int32_t *next;
+    int32_t *list[2];      // the next Improve list is list[(la & 1) ^ 1]
     DevCounters *ctr;
-    unsigned epoch;
     int32_t root;
     unsigned dense_limit;  // |dg| above this -> dense sweep next
+    int32_t role;          // 0: after every Evaluate; 1: only after a pointer-jumping finish
 };
 
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
-mark_frontier_kernel(MarkArgs<CT> a) {
+mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
+    const MarkArgs<CT> a = *ap;
     DevCounters *c = a.ctr;
+    if (a.role == 1 && c->wave_incomplete == 0u) return;
+    const unsigned epoch = c->epoch + 1u;
+    int32_t *next = a.list[(c->la & 1u) ^ 1u];
     const unsigned n_dg = c->n_dg;
     if (c->n_switched == 0u || n_dg == 0u) return;
     if (n_dg > a.dense_limit) {
@@ -686,9 +520,9 @@ mark_frontier_kernel(MarkArgs<CT> a) {
             int32_t u = 0;
             if (i < e) {
                 u = __ldg(&a.adj[i].col);
-                pred = u != a.root && atomicExch(&a.stamp[u], a.epoch) != a.epoch;
+                pred = u != a.root && atomicExch(&a.stamp[u], epoch) != epoch;
             }
-            warp_append(pred, u, a.next, &c->n_next);
+            warp_append(pred, u, next, &c->n_next);
         }
     }
 }
@@ -710,10 +544,8 @@ struct WaveArgs {
     const int32_t *switched;  // level 0: vertices whose parent changed
     int32_t *lvl[2];          // vertices to recompute at levels t (mod 2)
     unsigned *wstamp;         // dedups a child listed twice (parallel edges)
-    unsigned wave_epoch;      // wstamp value of level 1 (level t uses + t - 1)
     unsigned *stamp;          // Improve-list stamps
-    unsigned epoch;           // stamp value of the list being built
-    int32_t *next;            // next Improve list
+    int32_t *list[2];         // the next Improve list is list[(la & 1) ^ 1]
     DevCounters *ctr;
     int32_t root;
     unsigned dense_limit;     // |changed| above this -> dense sweep next, stop marking
@@ -742,7 +574,8 @@ constexpr int kWaveUnroll = 4;
 
 template <typename CT>
 __global__ void __launch_bounds__(kWaveThreads)
-wave_evaluate_kernel(WaveArgs<CT> a) {
+wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
+    const WaveArgs<CT> a = *ap;
     __shared__ int32_t s_u[kWaveThreads];
     __shared__ long long s_base[kWaveThreads];
     __shared__ int32_t s_seg[kWaveThreads + 1];
@@ -751,6 +584,9 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
     DevCounters *c = a.ctr;
     const unsigned n_sw = c->n_switched;
     if (n_sw == 0u) return;
+    const unsigned epoch = c->epoch + 1u;         // stamp of the list being built
+    const unsigned wave_epoch = c->wave_epoch;    // wstamp of level 1 (level t uses + t - 1)
+    int32_t *next = a.list[(c->la & 1u) ^ 1u];
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long gpol = policy_evict_last();
@@ -768,7 +604,7 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
         int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
         unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
         if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
-        const unsigned wtag = a.wave_epoch + t;  // stamp of level t + 1
+        const unsigned wtag = wave_epoch + t;  // stamp of level t + 1
         const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
         const int64_t per = (count + nblocks - 1) / nblocks;
         const int64_t lo = (int64_t)blockIdx.x * per;
@@ -840,8 +676,8 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
                         if (__ldcg(&a.p[w[j]]) == owner[j] &&
                             atomicExch(&a.wstamp[w[j]], wtag) != wtag)
                             childm |= 1u << j;
-                        if (marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != a.epoch &&
-                            atomicExch(&a.stamp[w[j]], a.epoch) != a.epoch)
+                        if (marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != epoch &&
+                            atomicExch(&a.stamp[w[j]], epoch) != epoch)
                             markm |= 1u << j;
                     }
                 }
@@ -851,7 +687,7 @@ wave_evaluate_kernel(WaveArgs<CT> a) {
 #pragma unroll
                 for (int j = 0; j < kWaveUnroll; ++j) {
                     if (childm & (1u << j)) out[bc++] = w[j];
-                    if (markm & (1u << j)) a.next[bm++] = w[j];
+                    if (markm & (1u << j)) next[bm++] = w[j];
                 }
             }
             __syncthreads();  // s_u / s_base / s_seg are rewritten by the next tile
@@ -881,6 +717,7 @@ __device__ __forceinline__ void clear_iteration(DevCounters *c) {
     c->wave_cnt[2] = 0u;
     c->wave_levels = 0u;
     c->wave_incomplete = 0u;
+    c->jumped = 0u;
     c->n_next = 0u;
     c->n_switched = 0u;
     c->dj_bits = 0ull;
@@ -890,32 +727,94 @@ __device__ __forceinline__ void clear_iteration(DevCounters *c) {
     for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
 }
 
-// Before pointer jumping takes over from an unfinished wave: its changed
-// list starts empty (the wave counted changes without listing them).
+// Before pointer jumping finishes a wave that hit its level cap: its changed
+// list starts empty (the wave counted changes without listing them).  A no-op
+// unless the wave stopped early.
 static __global__ void pre_jump_kernel(DevCounters *c) {
+    if (c->wave_incomplete == 0u) return;
     c->n_dg = 0u;
     c->rounds = 0u;
     c->bar_count = 0u;
     for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
 }
 
-// Between iterations: the list built by mark becomes the current list.
-static __global__ void advance_kernel(DevCounters *c) {
+// End of one Replan iteration (Alg. 2): record it, decide whether the loop
+// goes on (Improve switched a parent with Delta g > eps, no error, under the
+// iteration cap), and make the list built by this iteration's Evaluate the
+// current one.  In a captured loop the decision drives the WHILE node.
+static __global__ void advance_kernel(DevCounters *c, cudaGraphConditionalHandle cond,
+                                      int use_cond) {
+    const unsigned sw = c->n_switched;
+    double dj = 0.0, eps = 0.0;
+    dj = __longlong_as_double((long long)c->dj_bits);
+    eps = __longlong_as_double((long long)c->eps_bits);
+    c->last_switched = sw;
+    c->last_dg = c->n_dg;
+    c->last_levels = c->wave_levels;
+    c->last_next = c->dense_next ? 0u : c->n_next;
+    c->last_dense = c->dense;
+    c->last_rounds = c->rounds;
+    c->last_jumped = c->jumped;
+    c->switches += sw;
+    c->cum_wave_levels += c->wave_levels;
+    c->cum_jump_rounds += c->rounds;
+    c->cum_dense += c->dense ? 1u : 0u;
+    c->cum_jump_evals += (c->jumped && sw) ? 1u : 0u;
+    c->wave_epoch += c->wave_levels + 1u;
+    c->iter += 1u;
+    const bool stable = sw == 0u || dj <= eps;
+    const bool stop = stable || c->status != 0u || c->iter >= c->max_iters;
+    c->converged = (stable && c->status == 0u) ? 1u : 0u;
+    c->cont = stop ? 0u : 1u;
+    c->la ^= 1u;
+    c->epoch += 1u;
     c->n_active = c->dense_next ? 0u : c->n_next;
     c->dense = c->dense_next;
     c->dense_next = 0u;
     clear_iteration(c);
+    if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
 
 // Before an exploit or a forced Evaluate: clear the per-iteration fields and
 // the whole-exploit totals.
-static __global__ void begin_exploit_kernel(DevCounters *c) {
+static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
+                                            unsigned long long eps_bits) {
     clear_iteration(c);
     c->relax = 0ull;
     c->improved = 0ull;
     c->evaluated = 0ull;
     c->switches = 0ull;
     c->dense_next = 0u;
+    c->iter = 0u;
+    c->max_iters = max_iters;
+    c->eps_bits = eps_bits;
+    c->cont = 1u;
+    c->converged = 0u;
+    c->cum_wave_levels = 0u;
+    c->cum_dense = 0u;
+    c->cum_jump_rounds = 0u;
+    c->cum_jump_evals = 0u;
+}
+
+// Parents as reported through the ABI: the root marker becomes -1.
+static __global__ void export_parents_kernel(int64_t n, const int32_t *__restrict__ p,
+                                             int32_t *__restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        out[v] = p[v] < 0 ? -1 : p[v];
+}
+
+// Make each listed vertex a root: g = 0, parent marker kRootMark.
+static __global__ void set_roots_kernel(int64_t k, const int32_t *__restrict__ roots,
+                                        double *__restrict__ g, float *__restrict__ g32,
+                                        int32_t *__restrict__ p) {
+    for (int64_t i = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; i < k;
+         i += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t r = roots[i];
+        g[r] = 0.0;
+        g32[r] = 0.0f;
+        p[r] = kRootMark;
+    }
 }
 
 // ---------------------------------------------------------------------------
@@ -932,7 +831,7 @@ policy_lookup_kernel(int64_t n, int32_t root, const int32_t *__restrict__ parent
         const int32_t q = parent[v];
         if (v == root) {
             if (q != -1) atomicOr(&c->status, kStatusBadInput);
-            p_out[v] = -1;
+            p_out[v] = kRootMark;
             pc_out[v] = CT(0);
             continue;
         }

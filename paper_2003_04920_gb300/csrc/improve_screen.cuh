@@ -1,18 +1,13 @@
-// Improve (Alg. 2; Sec. IV-B) with one thread per vertex, as the paper's GPU
-// kernel assigns them, rebuilt for GB300: warps are fully independent (no
-// CTA barriers), each lane keeps eight CSR entries and eight FP32 gathers in
-// flight, and candidates are screened in FP32 with a running (minimum,
-// argmin, second minimum) so that the exact FP64 sum g(u) + c(u, v) is
-// formed only for the FP32 argmin -- or for every candidate within the
-// screening margin when a near tie leaves more than one in play.
+// Improve (Alg. 2; Sec. IV-B) for FP32 edge costs with candidates screened
+// in FP32 (GB300 issues FP64 at a small fraction of its FP32 rate): the
+// exact FP64 sum g(u) + c(u, v) is formed only for the FP32 argmin, or for
+// every candidate within the screening margin when a near tie leaves more
+// than one in play, so parents and g are those of the FP64 rule.
 #pragma once
 
 #include "graph_kernels.cuh"
 
 namespace pirrt {
-
-constexpr int kTpvThreads = 128;
-constexpr int kTpvUnroll = 8;
 
 __device__ __forceinline__ float ld_g32f(const float *p, unsigned long long pol) {
     float v;
@@ -20,130 +15,7 @@ __device__ __forceinline__ float ld_g32f(const float *p, unsigned long long pol)
     return v;
 }
 
-__device__ __forceinline__ Entry<float> ld_entry_hint(const Entry<float> *p, unsigned long long pol) {
-    int2 r;
-    asm volatile("ld.global.nc.L1::no_allocate.L2::cache_hint.v2.s32 {%0, %1}, [%2], %3;"
-                 : "=r"(r.x), "=r"(r.y)
-                 : "l"(p), "l"(pol));
-    Entry<float> e;
-    e.col = r.x;
-    e.w = __int_as_float(r.y);
-    return e;
-}
 
-// FP32 costs only (the FP64-cost path uses the tiled kernels).
-static __global__ void __launch_bounds__(kTpvThreads)
-improve_tpv_kernel(ImproveArgs<float> a) {
-    constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
-    const unsigned long long gpol = policy_evict_last();
-    const unsigned long long spol = policy_evict_first();
-    const int lane = threadIdx.x & 31;
-    const bool dense = a.ctr->dense != 0u;
-    const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
-    const int64_t stride = (int64_t)gridDim.x * kTpvThreads;
-    unsigned long long relax = 0, improved = 0;
-
-    for (int64_t base = (int64_t)blockIdx.x * kTpvThreads; base < count; base += stride) {
-        const int64_t item = base + threadIdx.x;
-        int32_t v = -1;
-        if (item < count) {
-            v = dense ? (int32_t)item : __ldg(&a.active[item]);
-            if (v == a.root) v = -1;
-        }
-        bool sw = false;
-        unsigned long long dj = 0ull;
-        if (v >= 0) {
-            const int64_t b = a.row_off[v], e = a.row_off[v + 1];
-            const int32_t pv = a.p[v];
-            const float pcv = a.pc[v];
-            const double gp = pv >= 0 ? a.g[pv] : CUDART_INF;
-            // pass 1: FP32 screen with (m1, i1, m2)
-            float m1 = __int_as_float(0x7f800000), m2 = m1;
-            int64_t i1 = -1;
-            int exact_row = 0;
-            for (int64_t i0 = b; i0 < e; i0 += kTpvUnroll) {
-                Entry<float> en[kTpvUnroll];
-#pragma unroll
-                for (int q = 0; q < kTpvUnroll; ++q)
-                    if (i0 + q < e) en[q] = ld_entry_hint(&a.adj[i0 + q], spol);
-                float gu[kTpvUnroll];
-#pragma unroll
-                for (int q = 0; q < kTpvUnroll; ++q)
-                    if (i0 + q < e) gu[q] = ld_g32f(&a.g32[en[q].col], gpol);
-#pragma unroll
-                for (int q = 0; q < kTpvUnroll; ++q) {
-                    if (i0 + q < e) {
-                        const float av = gu[q] + en[q].w;
-                        exact_row |= (gu[q] < 0.f) | (isinf(av) & !isinf(gu[q]));
-                        if (av < m1) {
-                            m2 = m1;
-                            m1 = av;
-                            i1 = i0 + q;
-                        } else if (av < m2) {
-                            m2 = av;
-                        }
-                    }
-                }
-            }
-            // exact FP64 lexicographic minimum over the candidates in play
-            unsigned long long bv = kInfBits + 1ull;
-            int32_t bid = INT_MAX;
-            unsigned bw = 0xffffffffu;
-            auto take = [&](const Entry<float> &en) {
-                const unsigned long long vb = (unsigned long long)__double_as_longlong(
-                    ld_g(&a.g[en.col], gpol) + widen(en.w));
-                const unsigned wb = __float_as_uint(en.w);
-                if (vb < bv || (vb == bv && (en.col < bid || (en.col == bid && wb < bw)))) {
-                    bv = vb;
-                    bid = en.col;
-                    bw = wb;
-                }
-            };
-            // same bound as the staged kernel: |fl32 screen - fl64 sum| <= 2^-22 of it
-            const float tau = m1 * (1.0f + 0x1p-20f) + 0x1p-125f;
-            if (exact_row || (m2 <= tau && !isinf(m1))) {
-                for (int64_t i = b; i < e; ++i) {
-                    const Entry<float> en = a.adj[i];
-                    if (exact_row || ld_g32f(&a.g32[en.col], gpol) + en.w <= tau) take(en);
-                }
-            } else if (i1 >= 0 && !isinf(m1)) {
-                take(a.adj[i1]);
-            }
-            const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
-            if (bv <= kInfBits) {
-                const double best = __longlong_as_double((long long)bv);
-                if (best < cur) {
-                    a.p[v] = bid;
-                    a.pc[v] = __uint_as_float(bw);
-                    sw = true;
-                    dj = (unsigned long long)__double_as_longlong(cur - best);
-                }
-            }
-            relax += (unsigned long long)(e - b);
-            improved += 1;
-        }
-        warp_append(sw, v, a.switched, &a.ctr->n_switched);
-#pragma unroll
-        for (int off = 16; off > 0; off >>= 1) {
-            const unsigned long long o = __shfl_xor_sync(0xffffffffu, dj, off);
-            dj = o > dj ? o : dj;
-        }
-        if (lane == 0 && dj) atomicMax(&a.ctr->dj_bits, dj);
-    }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        relax += __shfl_down_sync(0xffffffffu, relax, off);
-        improved += __shfl_down_sync(0xffffffffu, improved, off);
-    }
-    if (lane == 0 && (relax || improved)) {
-        atomicAdd(&a.ctr->relax, relax);
-        atomicAdd(&a.ctr->improved, improved);
-    }
-}
-
-}  // namespace pirrt
-
-namespace pirrt {
 
 // Improve with G lanes per vertex and FP32 screening (FP32 costs).  Each
 // lane scans every G-th entry of the row, four entries and four FP32 gathers
@@ -154,7 +26,9 @@ namespace pirrt {
 // no CTA barriers, no FP64 arithmetic per entry.
 template <int G, int kU>
 __global__ void __launch_bounds__(256)
-improve_screen_kernel(ImproveArgs<float> a) {
+improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
+    const ImproveArgs<float> a = *ap;
+    const int32_t *active = a.list[a.ctr->la & 1u];
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
     constexpr int kStageCap = 128;
     __shared__ int32_t s_sw[256 / 32][kStageCap];
@@ -180,7 +54,7 @@ improve_screen_kernel(ImproveArgs<float> a) {
         v = -1;
         b = e = 0;
         if (item < count) {
-            v = dense ? (int32_t)item : __ldg(&a.active[item]);
+            v = dense ? (int32_t)item : __ldg(&active[item]);
             if (v == a.root) v = -1;
             else {
                 b = a.row_off[v];
@@ -289,7 +163,7 @@ improve_screen_kernel(ImproveArgs<float> a) {
                 bid = en.col;
                 bw = __float_as_uint(en.w);
             }
-            if (gl == 0) {
+            if (gl == 0 && pv != kRootMark) {
                 const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
                 if (bv <= kInfBits) {
                     const double best = __longlong_as_double((long long)bv);

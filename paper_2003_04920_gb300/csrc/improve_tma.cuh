@@ -106,7 +106,9 @@ struct alignas(128) Smem {
 
 template <typename CT>
 __global__ void __launch_bounds__(tma::kThreads)
-improve_tma_kernel(ImproveArgs<CT> a) {
+improve_tma_kernel(const ImproveArgs<CT> *__restrict__ ap) {
+    const ImproveArgs<CT> a = *ap;
+    const int32_t *active = a.list[a.ctr->la & 1u];
     using namespace tma;
     using WB = typename CostBits<CT>::T;
     constexpr int ES = (int)sizeof(Entry<CT>);
@@ -154,7 +156,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
             long long b = 0;
             int deg = 0;
             if (t0 + lane < count) {
-                v = dense ? (int32_t)(t0 + lane) : __ldg(&a.active[t0 + lane]);
+                v = dense ? (int32_t)(t0 + lane) : __ldg(&active[t0 + lane]);
                 if (v == a.root) {
                     v = -1;
                 } else {
@@ -348,7 +350,7 @@ improve_tma_kernel(ImproveArgs<CT> a) {
             // decision by each group's first lane; appends are warp-collective
             bool sw = false;
             unsigned long long dj = 0ull;
-            if (gl == 0 && v >= 0) {
+            if (gl == 0 && v >= 0 && pv != kRootMark) {
                 const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
                 if (bv <= kInfBits) {
                     const double best = __longlong_as_double((long long)bv);

@@ -1,9 +1,12 @@
 // Host runtime and C ABI of the single-graph PI-RRT# exploitation path.
 //
 // All graph state (CSR, g, parents, work lists) stays resident on the
-// device; the host only sequences kernels on the caller's stream and reads
-// one small counter block per Replan iteration to test convergence (Alg. 2:
-// stop when Improve switched no parent).
+// device.  A Replan (Alg. 2: Improve, then Evaluate, until no parent
+// switches) runs as one CUDA-graph launch whose WHILE node repeats the loop
+// body on the device -- Improve, Evaluate, and an advance kernel that tests
+// convergence and sets the loop condition -- so the host waits once per
+// exploit.  With profiling enabled the same kernels run from a host loop
+// that reads the counter block after every iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -12,20 +15,28 @@
 #include <cstdint>
 #include <cstdio>
 #include <cstring>
+#include <map>
 #include <new>
 #include <string>
 #include <vector>
 
 #include "graph_kernels.cuh"
+#include "improve_screen.cuh"
 #include "improve_tma.cuh"
-#include "improve_tpv.cuh"
 #include "pirrt.h"
 
 using namespace pirrt;
 
+namespace {
+// Offsets of the kernel argument structs in the device argument block.
+constexpr size_t kArgImprove = 0, kArgEval = 512, kArgEvalFallback = 1024, kArgWave = 1536,
+                 kArgMark = 2048, kArgMarkFallback = 2560, kArgEvalForce = 3072, kArgBytes = 4096;
+}  // namespace
+
 struct pirrt_graph {
     pirrt_config cfg{};
     cudaStream_t stream = nullptr;
+    cudaStream_t capture = nullptr;  // private stream for recording loop bodies
     int num_sms = 0;
     int64_t cap_n = 0, cap_e = 0;  // vertices, directed CSR entries
     int64_t n = 0, m = 0;
@@ -40,9 +51,7 @@ struct pirrt_graph {
     int32_t *deg = nullptr;
     long long *tile_sums = nullptr;
     unsigned *stamp = nullptr;
-    unsigned epoch = 1;            // stamp value of the current Improve list
     int32_t *list[2] = {nullptr, nullptr};
-    int la = 0;                    // current Improve list
     int32_t *switched = nullptr;
     int32_t *dg = nullptr;
     int32_t *anc[2] = {nullptr, nullptr};
@@ -50,11 +59,23 @@ struct pirrt_graph {
     int32_t *done = nullptr;
     int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
     unsigned *wstamp = nullptr;           // wave child dedup
-    unsigned wave_epoch = 1;
+    int32_t *pexport = nullptr;           // parents as reported (root marker -> -1)
     int deep_hint = 0;                    // AUTO: recent exploits met waves past the cap
     int exploits = 0;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned mirror
+    unsigned char *dargs = nullptr;   // device copies of the kernel argument structs
+    unsigned char *hargs = nullptr;   // pinned host staging of the same
+    struct ArgsKey {
+        int64_t n = -1;
+        int cur = -1;
+        unsigned dense_limit = 0, max_levels = 0;
+        bool operator==(const ArgsKey &o) const {
+            return n == o.n && cur == o.cur && dense_limit == o.dense_limit &&
+                   max_levels == o.max_levels;
+        }
+    } args_key;
+    std::map<unsigned long long, cudaGraphExec_t> loops;  // captured Replan loops
     void *stage = nullptr;            // device staging for host-side inputs
     size_t stage_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
@@ -126,23 +147,115 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
     return PIRRT_OK;
 }
 
-
-template <typename CT, int TH, int TV, int PER>
-pirrt_status launch_improve_tile_v(pirrt_graph *G, const ImproveArgs<CT> &a) {
-    static int occ = -1;
-    if (occ < 0) {
-        int nb = 0;
-        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tile_kernel<CT, TH, TV, PER>,
-                                                         TH, 0));
-        occ = nb > 0 ? nb : 1;
+// Write every kernel argument struct of the exploit path into the device
+// argument block (stream-ordered; skipped when nothing changed).
+template <typename CT>
+pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels) {
+    pirrt_graph::ArgsKey key;
+    key.n = G->n;
+    key.cur = G->cur;
+    key.dense_limit = dense_limit;
+    key.max_levels = max_levels;
+    if (key == G->args_key) return PIRRT_OK;
+    std::memset(G->hargs, 0, kArgBytes);
+    const Entry<CT> *adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
+    auto *ia = reinterpret_cast<ImproveArgs<CT> *>(G->hargs + kArgImprove);
+    ia->row_off = G->row_off[G->cur];
+    ia->adj = adj;
+    ia->g = G->g;
+    ia->g32 = G->g32;
+    ia->p = G->p;
+    ia->pc = static_cast<CT *>(G->pc);
+    ia->list[0] = G->list[0];
+    ia->list[1] = G->list[1];
+    ia->switched = G->switched;
+    ia->ctr = G->ctr;
+    ia->n = G->n;
+    ia->root = G->cfg.root;
+    for (size_t off : {kArgEval, kArgEvalFallback, kArgEvalForce}) {
+        auto *ea = reinterpret_cast<EvaluateArgs<CT> *>(G->hargs + off);
+        ea->p = G->p;
+        ea->pc = static_cast<const CT *>(G->pc);
+        ea->g = G->g;
+        ea->g32 = G->g32;
+        ea->anc[0] = G->anc[0];
+        ea->anc[1] = G->anc[1];
+        ea->acc[0] = G->acc[0];
+        ea->acc[1] = G->acc[1];
+        ea->done = G->done;
+        ea->wl[0] = G->wl[0];
+        ea->wl[1] = G->wl[1];
+        ea->dg = G->dg;
+        ea->ctr = G->ctr;
+        ea->n = G->n;
+        ea->root = G->cfg.root;
+        ea->force = off == kArgEvalForce ? 1 : 0;
+        ea->role = off == kArgEvalFallback ? 1 : 0;
     }
-    improve_tile_kernel<CT, TH, TV, PER><<<G->num_sms * occ, TH, 0, G->stream>>>(a);
-    CKL();
+    auto *wa = reinterpret_cast<WaveArgs<CT> *>(G->hargs + kArgWave);
+    wa->row_off = G->row_off[G->cur];
+    wa->adj = adj;
+    wa->p = G->p;
+    wa->pc = static_cast<const CT *>(G->pc);
+    wa->g = G->g;
+    wa->g32 = G->g32;
+    wa->switched = G->switched;
+    wa->lvl[0] = G->wl[0];
+    wa->lvl[1] = G->wl[1];
+    wa->wstamp = G->wstamp;
+    wa->stamp = G->stamp;
+    wa->list[0] = G->list[0];
+    wa->list[1] = G->list[1];
+    wa->ctr = G->ctr;
+    wa->root = G->cfg.root;
+    wa->dense_limit = dense_limit;
+    wa->max_levels = max_levels;
+    for (size_t off : {kArgMark, kArgMarkFallback}) {
+        auto *ma = reinterpret_cast<MarkArgs<CT> *>(G->hargs + off);
+        ma->row_off = G->row_off[G->cur];
+        ma->adj = adj;
+        ma->dg = G->dg;
+        ma->stamp = G->stamp;
+        ma->list[0] = G->list[0];
+        ma->list[1] = G->list[1];
+        ma->ctr = G->ctr;
+        ma->root = G->cfg.root;
+        ma->dense_limit = dense_limit;
+        ma->role = off == kArgMarkFallback ? 1 : 0;
+    }
+    CK(cudaMemcpyAsync(G->dargs, G->hargs, kArgBytes, cudaMemcpyHostToDevice, G->stream));
+    // the pinned staging is rewritten only after this copy has been consumed
+    CK(cudaStreamSynchronize(G->stream));
+    G->args_key = key;
+    return PIRRT_OK;
+}
+
+template <typename A>
+const A *dev_arg(pirrt_graph *G, size_t off) {
+    return reinterpret_cast<const A *>(G->dargs + off);
+}
+
+// Cooperative launch (all CTAs co-resident for the grid barrier); works on a
+// capturing stream as well.
+template <typename A>
+pirrt_status launch_coop(pirrt_graph *G, cudaStream_t st, void (*kernel)(const A *), int blocks,
+                         int threads, const A *arg) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(blocks);
+    cfg.blockDim = dim3(threads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, kernel, arg));
     return PIRRT_OK;
 }
 
 template <typename CT>
-pirrt_status launch_improve_tma(pirrt_graph *G, const ImproveArgs<CT> &a) {
+pirrt_status launch_improve_tma(pirrt_graph *G, cudaStream_t st) {
     static int occ = -1;
     const size_t smem = sizeof(tma::Smem<CT>);
     if (occ < 0) {
@@ -153,182 +266,154 @@ pirrt_status launch_improve_tma(pirrt_graph *G, const ImproveArgs<CT> &a) {
                                                          smem));
         occ = nb > 0 ? nb : 1;
     }
-    improve_tma_kernel<CT><<<G->num_sms * occ, tma::kThreads, smem, G->stream>>>(a);
+    improve_tma_kernel<CT><<<G->num_sms * occ, tma::kThreads, smem, st>>>(
+        dev_arg<ImproveArgs<CT>>(G, kArgImprove));
     CKL();
     return PIRRT_OK;
 }
 
-template <typename CT>
-pirrt_status launch_improve_tpv(pirrt_graph *G, const ImproveArgs<CT> &a) {
-    if constexpr (sizeof(CT) != 4) {
-        return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
-    } else {
-        static int occ = -1;
-        if (occ < 0) {
-            int nb = 0;
-            CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_tpv_kernel, kTpvThreads, 0));
-            occ = nb > 0 ? nb : 1;
-        }
-        improve_tpv_kernel<<<G->num_sms * occ, kTpvThreads, 0, G->stream>>>(a);
-        CKL();
-        return PIRRT_OK;
-    }
-}
-
-// Tiled Improve shapes (vertices per tile -> threads, entries per thread);
-// 1 = the staged (bulk-copy pipelined) kernel; 2 = one thread per vertex.
-template <typename CT>
-pirrt_status launch_improve_tile(pirrt_graph *G, const ImproveArgs<CT> &a, int tile) {
-    switch (tile) {
-        case 1: return launch_improve_tma<CT>(G, a);
-        case 2: return launch_improve_tpv<CT>(G, a);
-        case 16: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
-        case 32: return launch_improve_tile_v<CT, 128, 32, 8>(G, a);
-        case 64: return launch_improve_tile_v<CT, 256, 64, 8>(G, a);
-        case 128: return launch_improve_tile_v<CT, 256, 128, 8>(G, a);
-        default: return launch_improve_tile_v<CT, 64, 16, 8>(G, a);
-    }
-}
-
 template <typename CT, int GS>
-pirrt_status launch_improve_g(pirrt_graph *G, const ImproveArgs<CT> &a) {
+pirrt_status launch_improve_g(pirrt_graph *G, cudaStream_t st) {
     static int occ = -1;
     if (occ < 0) {
         int nb = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_kernel<CT, GS>, kThreads, 0));
         occ = nb > 0 ? nb : 1;
     }
-    improve_kernel<CT, GS><<<G->num_sms * occ, kThreads, 0, G->stream>>>(a);
+    improve_kernel<CT, GS><<<G->num_sms * occ, kThreads, 0, st>>>(
+        dev_arg<ImproveArgs<CT>>(G, kArgImprove));
     CKL();
     return PIRRT_OK;
 }
 
 template <int GS, int U>
-pirrt_status launch_improve_screen(pirrt_graph *G, const ImproveArgs<float> &a) {
+pirrt_status launch_improve_screen(pirrt_graph *G, cudaStream_t st) {
     static int occ = -1;
     if (occ < 0) {
         int nb = 0;
         CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_screen_kernel<GS, U>, 256, 0));
         occ = nb > 0 ? nb : 1;
     }
-    improve_screen_kernel<GS, U><<<G->num_sms * occ, 256, 0, G->stream>>>(a);
+    improve_screen_kernel<GS, U><<<G->num_sms * occ, 256, 0, st>>>(
+        dev_arg<ImproveArgs<float>>(G, kArgImprove));
     CKL();
     return PIRRT_OK;
 }
 
 // Improve kernel selection (pirrt_exploit_opts.tile / .group):
-//   tile 0  G lanes per vertex (group, default 8) with FP32 screening; FP64
+//   tile 0  G lanes per vertex (group, default 4) with FP32 screening; FP64
 //           costs use the exact G-lane kernel
 //   tile 1  staged: producer warp bulk-copies rows into a shared-memory ring
-//   tile 2  one thread per vertex with FP32 screening
-//   tile 3  G lanes per vertex, exact FP64 for every candidate
-//   16..128 vertices per CTA tile of the unstaged tiled kernel
+//   tile 3  G lanes per vertex (default 8), exact FP64 for every candidate
 template <typename CT>
-pirrt_status launch_improve(pirrt_graph *G, int gs, int tile) {
-    ImproveArgs<CT> a;
-    a.row_off = G->row_off[G->cur];
-    a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
-    a.g = G->g;
-    a.g32 = G->g32;
-    a.p = G->p;
-    a.pc = static_cast<CT *>(G->pc);
-    a.active = G->list[G->la];
-    a.switched = G->switched;
-    a.ctr = G->ctr;
-    a.n = G->n;
-    a.root = G->cfg.root;
-    const int g = gs ? gs : 8;
+pirrt_status launch_improve(pirrt_graph *G, cudaStream_t st, int gs, int tile) {
     if (tile == 0) {
         if constexpr (sizeof(CT) == 4) {
             switch (gs) {
-                case 1: return launch_improve_screen<1, 8>(G, a);
-                case 2: return launch_improve_screen<2, 8>(G, a);
-                case 8: return launch_improve_screen<8, 4>(G, a);
-                case 16: return launch_improve_screen<16, 4>(G, a);
-                case 32: return launch_improve_screen<32, 4>(G, a);
-                case 5: return launch_improve_screen<4, 8>(G, a);  // 4 lanes, 8 in flight
-                default: return launch_improve_screen<4, 4>(G, a);
+                case 2: return launch_improve_screen<2, 8>(G, st);
+                case 8: return launch_improve_screen<8, 4>(G, st);
+                case 16: return launch_improve_screen<16, 4>(G, st);
+                case 32: return launch_improve_screen<32, 4>(G, st);
+                default: return launch_improve_screen<4, 4>(G, st);
             }
         }
         tile = 3;
     }
-    if (tile == 3) {
-        switch (g) {
-            case 4: return launch_improve_g<CT, 4>(G, a);
-            case 16: return launch_improve_g<CT, 16>(G, a);
-            case 32: return launch_improve_g<CT, 32>(G, a);
-            default: return launch_improve_g<CT, 8>(G, a);
-        }
+    if (tile == 1) return launch_improve_tma<CT>(G, st);
+    switch (gs) {
+        case 4: return launch_improve_g<CT, 4>(G, st);
+        case 16: return launch_improve_g<CT, 16>(G, st);
+        case 32: return launch_improve_g<CT, 32>(G, st);
+        default: return launch_improve_g<CT, 8>(G, st);
     }
-    return launch_improve_tile<CT>(G, a, tile);
 }
 
 template <typename CT>
-pirrt_status launch_evaluate(pirrt_graph *G, int force) {
-    EvaluateArgs<CT> a;
-    a.p = G->p;
-    a.pc = static_cast<const CT *>(G->pc);
-    a.g = G->g;
-    a.g32 = G->g32;
-    a.anc[0] = G->anc[0];
-    a.anc[1] = G->anc[1];
-    a.acc[0] = G->acc[0];
-    a.acc[1] = G->acc[1];
-    a.done = G->done;
-    a.wl[0] = G->wl[0];
-    a.wl[1] = G->wl[1];
-    a.dg = G->dg;
-    a.ctr = G->ctr;
-    a.n = G->n;
-    a.root = G->cfg.root;
-    a.force = force;
-    void *args[] = {&a};
-    CK(cudaLaunchCooperativeKernel((const void *)evaluate_kernel<CT>, dim3(G->eval_blocks),
-                                   dim3(kThreads), args, 0, G->stream));
-    return PIRRT_OK;
+pirrt_status launch_evaluate(pirrt_graph *G, cudaStream_t st, size_t off) {
+    return launch_coop<EvaluateArgs<CT>>(G, st, evaluate_kernel<CT>, G->eval_blocks, kThreads,
+                                         dev_arg<EvaluateArgs<CT>>(G, off));
 }
 
 template <typename CT>
-pirrt_status launch_wave(pirrt_graph *G, unsigned dense_limit, unsigned max_levels) {
-    WaveArgs<CT> a;
-    a.row_off = G->row_off[G->cur];
-    a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
-    a.p = G->p;
-    a.pc = static_cast<const CT *>(G->pc);
-    a.g = G->g;
-    a.g32 = G->g32;
-    a.switched = G->switched;
-    a.lvl[0] = G->wl[0];
-    a.lvl[1] = G->wl[1];
-    a.wstamp = G->wstamp;
-    a.wave_epoch = G->wave_epoch;
-    a.stamp = G->stamp;
-    a.epoch = G->epoch + 1u;
-    a.next = G->list[G->la ^ 1];
-    a.ctr = G->ctr;
-    a.root = G->cfg.root;
-    a.dense_limit = dense_limit;
-    a.max_levels = max_levels;
-    void *args[] = {&a};
-    CK(cudaLaunchCooperativeKernel((const void *)wave_evaluate_kernel<CT>, dim3(G->wave_blocks),
-                                   dim3(kWaveThreads), args, 0, G->stream));
-    return PIRRT_OK;
+pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st) {
+    return launch_coop<WaveArgs<CT>>(G, st, wave_evaluate_kernel<CT>, G->wave_blocks, kWaveThreads,
+                                     dev_arg<WaveArgs<CT>>(G, kArgWave));
 }
 
 template <typename CT>
-pirrt_status launch_mark(pirrt_graph *G, unsigned dense_limit) {
-    MarkArgs<CT> a;
-    a.row_off = G->row_off[G->cur];
-    a.adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
-    a.dg = G->dg;
-    a.stamp = G->stamp;
-    a.next = G->list[G->la ^ 1];
-    a.ctr = G->ctr;
-    a.epoch = G->epoch + 1u;
-    a.root = G->cfg.root;
-    a.dense_limit = dense_limit;
-    mark_frontier_kernel<CT><<<G->num_sms * 8, kThreads, 0, G->stream>>>(a);
+pirrt_status launch_mark(pirrt_graph *G, cudaStream_t st, size_t off) {
+    mark_frontier_kernel<CT><<<G->num_sms * 8, kThreads, 0, st>>>(dev_arg<MarkArgs<CT>>(G, off));
     CKL();
+    return PIRRT_OK;
+}
+
+// One Replan iteration after Improve: the Evaluate strategy, then advance.
+// JUMP: pointer jumping + marking.  WAVE / AUTO: the top-down wave, then a
+// pointer-jumping finish and its marking, both no-ops unless the wave hit its
+// level cap.
+template <typename CT>
+pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile, bool jump,
+                              cudaGraphConditionalHandle cond, int use_cond) {
+    pirrt_status rc;
+    if ((rc = launch_improve<CT>(G, st, gs, tile))) return rc;
+    if (jump) {
+        if ((rc = launch_evaluate<CT>(G, st, kArgEval))) return rc;
+        if ((rc = launch_mark<CT>(G, st, kArgMark))) return rc;
+    } else {
+        if ((rc = launch_wave<CT>(G, st))) return rc;
+        pre_jump_kernel<<<1, 1, 0, st>>>(G->ctr);
+        CKL();
+        if ((rc = launch_evaluate<CT>(G, st, kArgEvalFallback))) return rc;
+        if ((rc = launch_mark<CT>(G, st, kArgMarkFallback))) return rc;
+    }
+    advance_kernel<<<1, 1, 0, st>>>(G->ctr, cond, use_cond);
+    CKL();
+    return PIRRT_OK;
+}
+
+// The Replan loop as a CUDA graph: a WHILE conditional node whose body is one
+// iteration; advance_kernel sets the condition.  Cached per kernel choice.
+template <typename CT>
+pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, cudaGraphExec_t *out) {
+    const unsigned long long key = ((unsigned long long)gs << 8) | ((unsigned long long)tile << 1) |
+                                   (jump ? 1ull : 0ull) | ((unsigned long long)sizeof(CT) << 24);
+    auto it = G->loops.find(key);
+    if (it != G->loops.end()) {
+        *out = it->second;
+        return PIRRT_OK;
+    }
+    cudaGraph_t graph = nullptr;
+    CK(cudaGraphCreate(&graph, 0));
+    cudaGraphConditionalHandle cond;
+    CK(cudaGraphConditionalHandleCreate(&cond, graph, 1u, cudaGraphCondAssignDefault));
+    cudaGraphNodeParams cp{};
+    cp.type = cudaGraphNodeTypeConditional;
+    cp.conditional.handle = cond;
+    cp.conditional.type = cudaGraphCondTypeWhile;
+    cp.conditional.size = 1;
+    cudaGraphNode_t node;
+    CK(cudaGraphAddNode(&node, graph, nullptr, nullptr, 0, &cp));
+    cudaGraph_t body = cp.conditional.phGraph_out[0];
+    CK(cudaStreamBeginCaptureToGraph(G->capture, body, nullptr, nullptr, 0,
+                                     cudaStreamCaptureModeRelaxed));
+    pirrt_status rc = launch_iteration<CT>(G, G->capture, gs, tile, jump, cond, 1);
+    cudaGraph_t captured = nullptr;
+    const cudaError_t ec = cudaStreamEndCapture(G->capture, &captured);
+    if (rc) {
+        cudaGraphDestroy(graph);
+        return rc;
+    }
+    if (ec != cudaSuccess) {
+        cudaGraphDestroy(graph);
+        return fail(G, PIRRT_ERR_CUDA, "capturing the Replan loop: %s", cudaGetErrorString(ec));
+    }
+    cudaGraphExec_t exec = nullptr;
+    const cudaError_t ei = cudaGraphInstantiate(&exec, graph, 0);
+    cudaGraphDestroy(graph);
+    if (ei != cudaSuccess)
+        return fail(G, PIRRT_ERR_CUDA, "instantiating the Replan loop: %s", cudaGetErrorString(ei));
+    G->loops[key] = exec;
+    *out = exec;
     return PIRRT_OK;
 }
 
@@ -379,16 +464,15 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
     }
     if (n_edges > 0) {
         insert_scatter<CT><<<grid_for(n_edges, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_edges, src, dst, cost, G->row_off[nxt], G->deg, new_adj, G->stamp, G->epoch,
-            G->cfg.root, G->list[G->la], G->ctr);
+            n_edges, src, dst, cost, G->row_off[nxt], G->deg, new_adj, G->stamp, G->cfg.root,
+            G->list[0], G->list[1], G->ctr);
         CKL();
     }
     // 4. seed the new vertices
     if (n_new > 0) {
         insert_init_vertices<CT><<<grid_for(n_new, kThreads, max_blocks), kThreads, 0, G->stream>>>(
             n_old, n_after, G->cfg.root, G->g, G->g32, G->p, static_cast<CT *>(G->pc), G->stamp,
-            G->epoch,
-            G->list[G->la], G->ctr);
+            G->list[0], G->list[1], G->ctr);
         CKL();
     }
     G->prof.launches += 3 + (n_edges > 0 ? 2 : 0) + (n_old > 0 && G->m > 0 ? 1 : 0) + (n_new > 0 ? 1 : 0);
@@ -414,12 +498,12 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     if (opts) o = *opts;
     if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
-        !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3 || o.tile == 16 ||
-          o.tile == 32 || o.tile == 64 || o.tile == 128) ||
-        !(o.group >= 0 && o.group <= 32))
+        !(o.tile == 0 || o.tile == 1 || o.tile == 3) ||
+        !(o.group == 0 || o.group == 2 || o.group == 4 || o.group == 8 || o.group == 16 ||
+          o.group == 32))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
-    const int gs = o.group;
+    const int gs = o.group, tile = o.tile;
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
     const unsigned dense_limit = (unsigned)std::min<double>(4.0e9, frac * (double)G->n);
     const int mode = o.evaluate;
@@ -436,154 +520,138 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     }
     const unsigned max_levels = mode == PIRRT_EVAL_WAVE ? cap_any
                                 : (o.wave_levels > 0 ? (unsigned)o.wave_levels : auto_cap);
-    // AUTO: after an exploit whose waves ran past the cap, start with pointer
-    // jumping, and probe with waves again every eighth exploit
-    bool jump_first = mode == PIRRT_EVAL_AUTO && G->deep_hint && (G->exploits % 8) != 0;
-    bool saw_deep = false;
+    // AUTO: after an exploit whose waves ran past the cap, use pointer
+    // jumping; probe with waves again every eighth exploit
+    bool jump = mode == PIRRT_EVAL_JUMP ||
+                (mode == PIRRT_EVAL_AUTO && G->deep_hint && (G->exploits % 8) != 0);
     G->exploits += 1;
+    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels);
+    if (rc) return rc;
+    const bool prof = G->profiling != 0;
+    const bool use_graph = !prof && o.host_loop == 0;
+    double eps = o.eps;
+    unsigned long long eps_bits;
+    std::memcpy(&eps_bits, &eps, sizeof(eps_bits));
 
     CK(cudaEventRecord(G->ev0, G->stream));
-    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
+    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(
+        G->ctr, (unsigned)std::min<int64_t>(max_iters, 0xffffffffll), eps_bits);
     CKL();
-    G->prof.launches += 1;
-    pirrt_exploit_stats s{};
-    pirrt_status rc = PIRRT_OK;
-    bool converged = false;
-    unsigned long long prev_relax = 0, prev_improved = 0, prev_eval = 0;
-    const bool prof = G->profiling != 0;
     pirrt_profile &P = G->prof;
-    for (int64_t it = 0; it < max_iters; ++it) {
-        // Improve, then Evaluate (+ frontier marking), then one counter read
-        if (prof) CK(cudaEventRecord(G->pev[0], G->stream));
-        if ((rc = launch_improve<CT>(G, gs, o.tile))) return rc;
-        if (prof) CK(cudaEventRecord(G->pev[1], G->stream));
-        bool jumped = false;
-        if (mode == PIRRT_EVAL_JUMP || jump_first) {
-            if ((rc = launch_evaluate<CT>(G, 0))) return rc;
-            if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
-            if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
-            P.launches += 2;
-            jumped = true;
+    P.launches += 1;
+    pirrt_exploit_stats s{};
+    bool graph_ran = false;
+    if (use_graph) {
+        cudaGraphExec_t exec = nullptr;
+        rc = get_loop<CT>(G, gs, tile, jump, &exec);
+        if (rc == PIRRT_OK) {
+            CK(cudaGraphLaunch(exec, G->stream));
+            graph_ran = true;
         } else {
-            if ((rc = launch_wave<CT>(G, dense_limit, max_levels))) return rc;
-            if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
-            P.launches += 1;
+            G->last_error.clear();  // fall back to the host loop
         }
-        if (prof) CK(cudaEventRecord(G->pev[3], G->stream));
-        if ((rc = pull_counters(G))) return rc;
-        P.launches += 1;
-        const DevCounters *h = G->ctr_host;
-        float t_imp = 0.f, t_eval = 0.f, t_mark = 0.f;
-        if (prof) {
-            CK(cudaEventElapsedTime(&t_imp, G->pev[0], G->pev[1]));
-            CK(cudaEventElapsedTime(&t_eval, G->pev[1], G->pev[2]));
-            CK(cudaEventElapsedTime(&t_mark, G->pev[2], G->pev[3]));
-        }
-        if (mode != PIRRT_EVAL_JUMP && !jumped) {
-            G->wave_epoch += h->wave_levels + 1u;
-            s.wave_levels += (int32_t)h->wave_levels;
-            if (h->wave_incomplete) {
-                saw_deep = true;
-                if (mode == PIRRT_EVAL_AUTO) jump_first = true;
-                // finish this Evaluate by pointer jumping from p and pc
-                if (prof) CK(cudaEventRecord(G->pev[4], G->stream));
+    }
+    if (!graph_ran) {
+        unsigned long long prev_relax = 0, prev_improved = 0, prev_eval = 0;
+        for (int64_t it = 0; it < max_iters; ++it) {
+            if (prof) CK(cudaEventRecord(G->pev[0], G->stream));
+            if ((rc = launch_improve<CT>(G, G->stream, gs, tile))) return rc;
+            if (prof) CK(cudaEventRecord(G->pev[1], G->stream));
+            if (jump) {
+                if ((rc = launch_evaluate<CT>(G, G->stream, kArgEval))) return rc;
+                if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
+                if ((rc = launch_mark<CT>(G, G->stream, kArgMark))) return rc;
+            } else {
+                if ((rc = launch_wave<CT>(G, G->stream))) return rc;
+                if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
                 pre_jump_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
                 CKL();
-                if ((rc = launch_evaluate<CT>(G, 0))) return rc;
-                if ((rc = launch_mark<CT>(G, dense_limit))) return rc;
-                if (prof) CK(cudaEventRecord(G->pev[5], G->stream));
-                if ((rc = pull_counters(G))) return rc;
-                P.launches += 3;
-                jumped = true;
-                if (prof) {
-                    float t = 0.f;
-                    CK(cudaEventElapsedTime(&t, G->pev[4], G->pev[5]));
-                    t_eval += t;
+                if ((rc = launch_evaluate<CT>(G, G->stream, kArgEvalFallback))) return rc;
+                if ((rc = launch_mark<CT>(G, G->stream, kArgMarkFallback))) return rc;
+            }
+            if (prof) CK(cudaEventRecord(G->pev[3], G->stream));
+            advance_kernel<<<1, 1, 0, G->stream>>>(G->ctr, cudaGraphConditionalHandle{}, 0);
+            CKL();
+            if ((rc = pull_counters(G))) return rc;
+            P.launches += jump ? 4 : 6;
+            const DevCounters *h = G->ctr_host;
+            float t_imp = 0.f, t_eval = 0.f, t_mark = 0.f;
+            if (prof) {
+                CK(cudaEventElapsedTime(&t_imp, G->pev[0], G->pev[1]));
+                CK(cudaEventElapsedTime(&t_eval, G->pev[1], G->pev[2]));
+                CK(cudaEventElapsedTime(&t_mark, G->pev[2], G->pev[3]));
+                if (!jump) {  // the pointer-jumping finish counts as Evaluate
+                    t_eval += t_mark;
+                    t_mark = 0.f;
+                }
+                pirrt_trace_record tr{};
+                tr.iteration = (int32_t)it;
+                tr.dense = h->last_dense ? 1 : 0;
+                tr.improve_vertices = (int64_t)(h->improved - prev_improved);
+                tr.improve_entries = (int64_t)(h->relax - prev_relax);
+                tr.switches = (int32_t)h->last_switched;
+                tr.changed = (int32_t)h->last_dg;
+                tr.wave_levels = (int32_t)h->last_levels;
+                tr.next_frontier = (int32_t)h->last_next;
+                tr.improve_ms = t_imp;
+                tr.evaluate_ms = t_eval;
+                tr.mark_ms = t_mark;
+                float t_it = 0.f;
+                if (it > 0) CK(cudaEventElapsedTime(&t_it, G->it_start, G->pev[0]));
+                tr.iteration_ms = t_it;
+                if (G->trace.size() < (1u << 22)) G->trace.push_back(tr);
+                CK(cudaEventRecord(G->it_start, G->stream));
+            }
+            P.improve_launches += 1;
+            P.improve_entries += (int64_t)(h->relax - prev_relax);
+            P.improve_vertices += (int64_t)(h->improved - prev_improved);
+            if (h->last_dense) P.improve_dense_vertices += (int64_t)(h->improved - prev_improved);
+            P.improve_switches += h->last_switched;
+            P.improve_ms += t_imp;
+            if (h->last_switched) {
+                P.evaluate_launches += 1;
+                P.evaluate_vertices += (int64_t)(h->evaluated - prev_eval);
+                P.evaluate_ms += t_eval;
+                if (jump && h->last_dg && h->last_dg <= dense_limit) {
+                    P.mark_launches += 1;
+                    P.mark_vertices += h->last_dg;
+                    P.mark_ms += t_mark;
                 }
             }
-        }
-        if (prof) {
-            pirrt_trace_record tr{};
-            tr.iteration = (int32_t)it;
-            tr.dense = h->dense ? 1 : 0;
-            tr.improve_vertices = (int64_t)(h->improved - prev_improved);
-            tr.improve_entries = (int64_t)(h->relax - prev_relax);
-            tr.switches = (int32_t)h->n_switched;
-            tr.changed = (int32_t)h->n_dg;
-            tr.wave_levels = (int32_t)h->wave_levels;
-            tr.next_frontier = h->dense_next ? 0 : (int32_t)h->n_next;
-            tr.improve_ms = t_imp;
-            tr.evaluate_ms = t_eval;
-            tr.mark_ms = jumped ? t_mark : 0.f;
-            float t_it = 0.f;
-            if (it > 0) CK(cudaEventElapsedTime(&t_it, G->it_start, G->pev[0]));
-            tr.iteration_ms = t_it;  // previous iteration start to this one's start
-            if (G->trace.size() < (1u << 22)) G->trace.push_back(tr);
-            CK(cudaEventRecord(G->it_start, G->stream));
-        }
-        s.iterations += 1;
-        s.switches += h->n_switched;
-        s.jump_rounds += (int32_t)h->rounds;
-        if (jumped && h->n_switched) s.jump_evaluates += 1;
-        if (h->dense) s.dense_sweeps += 1;
-        P.improve_launches += 1;
-        P.improve_entries += (int64_t)(h->relax - prev_relax);
-        P.improve_vertices += (int64_t)(h->improved - prev_improved);
-        if (h->dense) P.improve_dense_vertices += (int64_t)(h->improved - prev_improved);
-        P.improve_switches += h->n_switched;
-        P.improve_ms += t_imp;
-        prev_relax = h->relax;
-        prev_improved = h->improved;
-        if (h->n_switched) {
-            P.evaluate_launches += 1;
-            P.evaluate_vertices += (int64_t)(h->evaluated - prev_eval);
-            P.evaluate_ms += t_eval;
-            if (jumped) {
-                for (int r = 1; r <= kMaxJumpRounds + 1; ++r) P.evaluate_visits += h->wl_count[r];
-                P.evaluate_visits += G->n;  // round 0 touches every vertex
-            }
-            if (jumped && h->n_dg && h->n_dg <= dense_limit) {
-                P.mark_launches += 1;
-                P.mark_vertices += h->n_dg;
-                P.mark_ms += t_mark;
-            }
-        }
-        prev_eval = h->evaluated;
-        if ((rc = status_from_bits(G, h->status))) break;
-        // Alg. 2: stop once Delta g <= eps; with eps = 0 that is "no switch".
-        // (The Evaluate of this iteration has already run, so g always
-        // matches the returned policy.)
-        double dj = 0.0;
-        std::memcpy(&dj, &h->dj_bits, sizeof(dj));
-        const bool stop = h->n_switched == 0u || dj <= o.eps;
-        advance_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
-        CKL();
-        P.launches += 1;
-        G->la ^= 1;
-        G->epoch += 1u;
-        if (stop) {
-            converged = true;
-            break;
+            prev_relax = h->relax;
+            prev_improved = h->improved;
+            prev_eval = h->evaluated;
+            if (h->status) break;
+            // AUTO: a wave that ran past its cap -> pointer jumping from now on
+            if (mode == PIRRT_EVAL_AUTO && !jump && h->last_jumped) jump = true;
+            if (!h->cont) break;
         }
     }
-    if (mode == PIRRT_EVAL_AUTO && (saw_deep || !jump_first)) G->deep_hint = saw_deep ? 1 : 0;
     CK(cudaEventRecord(G->ev1, G->stream));
-    if (rc == PIRRT_OK) {
-        rc = pull_counters(G);
-        if (rc) return rc;
-    }
-    CK(cudaEventSynchronize(G->ev1));
+    if ((rc = pull_counters(G))) return rc;
     float ms = 0.f;
     CK(cudaEventElapsedTime(&ms, G->ev0, G->ev1));
     const DevCounters &h = *G->ctr_host;
-    s.converged = converged ? 1 : 0;
+    if (mode == PIRRT_EVAL_AUTO) {
+        const bool saw_deep = h.cum_jump_evals > 0;
+        if (saw_deep || !jump || (G->exploits % 8) == 1) G->deep_hint = saw_deep ? 1 : 0;
+    }
+    if (graph_ran) P.launches += (int64_t)h.iter * (jump ? 4 : 6);
+    s.iterations = (int32_t)h.iter;
+    s.converged = h.converged ? 1 : 0;
     s.relaxations = (int64_t)h.relax;
     s.improved = (int64_t)h.improved;
     s.evaluated = (int64_t)h.evaluated;
+    s.switches = (int64_t)h.switches;
+    s.jump_rounds = (int32_t)h.cum_jump_rounds;
+    s.dense_sweeps = (int32_t)h.cum_dense;
+    s.wave_levels = (int32_t)h.cum_wave_levels;
+    s.jump_evaluates = (int32_t)h.cum_jump_evals;
     s.ms_exploit = ms;
+    s.graph_launch = graph_ran ? 1 : 0;
     if (st) *st = s;
-    if (rc) return rc;
-    if (!converged)
+    if ((rc = status_from_bits(G, h.status))) return rc;
+    if (!h.converged)
         return fail(G, PIRRT_ERR_NOT_CONVERGED, "exploit: %lld Improve rounds without convergence",
                     (long long)max_iters);
     return PIRRT_OK;
@@ -611,14 +679,15 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     policy_commit_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
         G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g, G->g32);
     CKL();
-    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
-    CKL();
-    pirrt_status rc = launch_evaluate<CT>(G, 1);
+    pirrt_status rc = write_args<CT>(G, 0u, 1u);
     if (rc) return rc;
+    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr, 1u, 0ull);
+    CKL();
+    if ((rc = launch_evaluate<CT>(G, G->stream, kArgEvalForce))) return rc;
     if ((rc = pull_counters(G))) return rc;
     if ((rc = status_from_bits(G, G->ctr_host->status))) return rc;
     // the next Improve sweeps every vertex; the seeded list is moot
-    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
+    begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr, 1u, 0ull);
     CKL();
     const unsigned one = 1u;
     CK(cudaMemcpyAsync(&G->ctr->dense, &one, sizeof(unsigned), cudaMemcpyHostToDevice, G->stream));
@@ -627,7 +696,12 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
 }
 
 void free_all(pirrt_graph *G) {
-    void *bufs[] = {G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
+    for (auto &kv : G->loops)
+        if (kv.second) cudaGraphExecDestroy(kv.second);
+    G->loops.clear();
+    if (G->capture) cudaStreamDestroy(G->capture);
+    if (G->hargs) cudaFreeHost(G->hargs);
+    void *bufs[] = {G->dargs, G->pexport, G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
                     G->wl[1], G->wstamp, G->ctr, G->stage};
@@ -737,7 +811,12 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->wl[1], sizeof(int32_t) * nv);
     ALLOC(G->wstamp, sizeof(unsigned) * nv);
     ALLOC(G->ctr, sizeof(DevCounters));
+    ALLOC(G->dargs, kArgBytes);
+    ALLOC(G->pexport, sizeof(int32_t) * nv);
 #undef ALLOC
+    if (cudaMallocHost((void **)&G->hargs, kArgBytes) != cudaSuccess) return bail(PIRRT_ERR_OOM);
+    if (cudaStreamCreateWithFlags(&G->capture, cudaStreamNonBlocking) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
     if (cudaMallocHost((void **)&G->ctr_host, sizeof(DevCounters)) != cudaSuccess)
         return bail(PIRRT_ERR_OOM);
     if (cudaEventCreate(&G->ev0) != cudaSuccess || cudaEventCreate(&G->ev1) != cudaSuccess)
@@ -779,13 +858,16 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemsetAsync(G->stamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->ctr, 0, sizeof(DevCounters), G->stream));
+    // stamps start at 0, so the first list uses stamp value 1
+    const unsigned one = 1u;
+    CK(cudaMemcpyAsync(&G->ctr->epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice, G->stream));
+    CK(cudaMemcpyAsync(&G->ctr->wave_epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice,
+                       G->stream));
     CK(cudaStreamSynchronize(G->stream));
     G->n = 0;
     G->m = 0;
     G->cur = 0;
-    G->la = 0;
-    G->epoch = 1;
-    G->wave_epoch = 1;
+    G->args_key = pirrt_graph::ArgsKey{};
     G->deep_hint = 0;
     G->exploits = 0;
     G->last_error.clear();
@@ -879,9 +961,15 @@ pirrt_status pirrt_graph_get_parents(const pirrt_graph *Gc, int32_t *p_out, int6
         return fail(G, PIRRT_ERR_INVALID_ARG, "get_parents: n = %lld but the graph has %lld vertices",
                     (long long)n, (long long)G->n);
     CK(cudaSetDevice(G->cfg.device));
-    if (n > 0)
-        CK(cudaMemcpyAsync(p_out, G->p, sizeof(int32_t) * (size_t)n,
-                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, G->stream));
+    if (n > 0) {
+        int32_t *dst = on_device ? p_out : G->pexport;
+        export_parents_kernel<<<grid_for(n, kThreads, G->num_sms * 8), kThreads, 0, G->stream>>>(
+            n, G->p, dst);
+        CKL();
+        if (!on_device)
+            CK(cudaMemcpyAsync(p_out, G->pexport, sizeof(int32_t) * (size_t)n,
+                               cudaMemcpyDeviceToHost, G->stream));
+    }
     CK(cudaStreamSynchronize(G->stream));
     return PIRRT_OK;
 }

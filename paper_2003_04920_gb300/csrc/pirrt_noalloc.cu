@@ -31,7 +31,8 @@ constexpr size_t round256(size_t b) { return (b + 255) & ~size_t(255); }
 constexpr size_t kN = (size_t)kMaxNoAllocVertices;
 constexpr size_t kScratchBytes = 2 * round256(4 * kN) + 2 * round256(8 * kN) + round256(4 * kN) +
                                  2 * round256(4 * kN) + round256(4 * kN) + round256(4 * kN) +
-                                 round256(sizeof(DevCounters));
+                                 round256(sizeof(DevCounters)) +
+                                 round256(sizeof(EvaluateArgs<double>));
 
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -109,17 +110,25 @@ extern "C" pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const in
     a.dg = reinterpret_cast<int32_t *>(take(4 * N));
     a.g32 = reinterpret_cast<float *>(take(4 * N));
     DevCounters *ctr = reinterpret_cast<DevCounters *>(take(sizeof(DevCounters)));
+    // the kernel reads its arguments from device memory: they live in the array too
+    EvaluateArgs<double> *dargs =
+        reinterpret_cast<EvaluateArgs<double> *>(take(sizeof(EvaluateArgs<double>)));
     if ((size_t)(base - s.scratch) != kScratchBytes) return PIRRT_ERR_CUDA;  // layout mismatch
     a.ctr = ctr;
     a.n = n;
     a.root = root;
     a.force = 1;
+    a.role = 0;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
     const int pb = (int)((n + kThreads - 1) / kThreads);
     noalloc_prepare<<<pb < 1024 ? pb : 1024, kThreads, 0, st>>>(n, root, g_out, ctr);
     if (cudaGetLastError() != cudaSuccess) return PIRRT_ERR_CUDA;
-    void *args[] = {&a};
+    // pageable source: the call returns once `a` has been read
+    if (cudaMemcpyAsync(dargs, &a, sizeof(a), cudaMemcpyHostToDevice, st) != cudaSuccess)
+        return PIRRT_ERR_CUDA;
+    const EvaluateArgs<double> *argp = dargs;
+    void *args[] = {&argp};
     if (cudaLaunchCooperativeKernel((const void *)evaluate_kernel<double>, dim3(s.blocks),
                                     dim3(kThreads), args, 0, st) != cudaSuccess)
         return PIRRT_ERR_CUDA;

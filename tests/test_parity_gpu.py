@@ -152,9 +152,8 @@ def test_c2_as_specified_small_reachable_set():
 
 # ------------------------------------------------------ invariances ---
 
-@pytest.mark.parametrize("group,tile", [(1, 0), (2, 0), (5, 0), (8, 0), (16, 0), (32, 0),
-                                        (0, 1), (0, 2), (4, 3), (8, 3), (32, 3), (0, 16),
-                                        (0, 32), (0, 64), (0, 128)])
+@pytest.mark.parametrize("group,tile", [(2, 0), (8, 0), (16, 0), (32, 0), (0, 1), (4, 3),
+                                        (8, 3), (32, 3)])
 def test_improve_kernels_agree(c3_small, group, tile):
     """Every tiled Improve shape and the G-threads-per-vertex kernels take the
     same lexicographic argmin, so whole schedules agree bit for bit."""
@@ -418,4 +417,30 @@ def test_extreme_cost_scales(scale):
     g_ref, p_ref, _ = _o1(rmd)
     g, p, _ = gpu_schedule(rmd)
     assert_parity(rmd, g, p, g_ref, p_ref)
+
+
+@pytest.mark.parametrize("evaluate", ["auto", "wave", "jump"])
+def test_graph_launch_matches_host_loop(c2_small, evaluate):
+    """The Replan loop captured as one CUDA graph (WHILE node) and the host-driven
+    loop run the same kernels and reach the same policy, bit for bit."""
+    rm = c2_small
+    g0, p0, st0 = gpu_schedule(rm, evaluate=evaluate, host_loop=True)
+    g1, p1, st1 = gpu_schedule(rm, evaluate=evaluate)
+    assert all(s["graph_launch"] == 0 for s in st0)
+    assert all(s["graph_launch"] == 1 for s in st1)
+    assert [s["iterations"] for s in st0] == [s["iterations"] for s in st1]
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+
+
+def test_graph_launch_max_iters_then_resume():
+    gd = golden_io.load("path5.txt")
+    with P.Graph(5, 4, 0, np.float64) as D:
+        D.insert_batch(5, gd["u"], gd["v"], gd["c"])
+        st = D.exploit(max_iters=2, check=False)
+        assert st["graph_launch"] == 1 and st["iterations"] == 2
+        assert st["status"] == P.PIRRT_ERR_NOT_CONVERGED
+        st = D.exploit()
+        assert st["converged"] == 1
+        np.testing.assert_array_equal(D.get_costs(), gd["g"])
 

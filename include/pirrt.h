@@ -251,6 +251,63 @@ int64_t pirrt_graph_get_trace(const pirrt_graph *g, pirrt_trace_record *out, int
 pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const int32_t *parent,
                                     const double *parent_cost, double *g_out, void *stream);
 
+/* ------------------------------------------------------------------------
+ * Batched form: many independent planning graphs exploited together.
+ *
+ * The batch is one device graph made of the disjoint union of its members:
+ * member b owns the vertex ids [base_b, base_b + max_vertices[b]) and its
+ * own root.  Policy iteration on the union is policy iteration on every
+ * member at once (no edge joins two members), so every member reaches
+ * exactly the policy of its own Replan, bit for bit; the whole batch runs in
+ * one CUDA-graph launch per exploit.  Inserts are staged per member and
+ * merged into the device CSR in one pass at the next exploit (Sec. IV-A:
+ * one CSR rebuild per Replan).
+ * ------------------------------------------------------------------------ */
+typedef struct pirrt_batch pirrt_batch;   /* opaque, library-owned */
+
+/* n_graphs members; max_vertices[b] and max_edges[b] are member b's
+ * capacities, roots[b] its x_init (a member-local id).  Every member starts
+ * with its full vertex capacity present and isolated (g = +inf) except its
+ * root (g = 0).  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_OOM, PIRRT_ERR_CUDA. */
+pirrt_status pirrt_batch_create(int32_t n_graphs, const int64_t *max_vertices,
+                                const int64_t *max_edges, const int32_t *roots,
+                                int32_t cost_dtype, int32_t device, void *stream,
+                                pirrt_batch **out);
+
+void pirrt_batch_destroy(pirrt_batch *b);
+
+/* Stage n_edges undirected edges of member `graph` in member-local ids (each
+ * in [0, max_vertices[graph])); they join the device CSR at the next
+ * exploit.  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_CAPACITY,
+ * PIRRT_ERR_BAD_INPUT (an id out of range; nothing is staged). */
+pirrt_status pirrt_batch_insert(pirrt_batch *b, int32_t graph, int64_t n_edges,
+                                const int32_t *src, const int32_t *dst, const void *cost,
+                                int on_device);
+
+/* Merge the staged edges, then Replan every member to convergence (see
+ * pirrt_graph_exploit; the options and totals refer to the whole batch). */
+pirrt_status pirrt_batch_exploit(pirrt_batch *b, const pirrt_exploit_opts *opts,
+                                 pirrt_exploit_stats *stats);
+
+/* Autotuner: merge the staged edges, then time pirrt_batch_exploit for each
+ * of n candidate option sets from the same starting state (the device state
+ * is restored after each trial) and return the fastest in *best (its index
+ * in *best_index, its time in *best_ms).  The batch is left as it was
+ * before the call. */
+pirrt_status pirrt_batch_autotune(pirrt_batch *b, const pirrt_exploit_opts *candidates,
+                                  int32_t n, pirrt_exploit_opts *best, int32_t *best_index,
+                                  float *best_ms);
+
+/* Member `graph`'s g / parents (member-local ids, -1 for the root and for
+ * unreached vertices) for its first n vertices (n <= max_vertices[graph]). */
+pirrt_status pirrt_batch_get_costs(const pirrt_batch *b, int32_t graph, double *g_out, int64_t n,
+                                   int on_device);
+pirrt_status pirrt_batch_get_parents(const pirrt_batch *b, int32_t graph, int32_t *p_out,
+                                     int64_t n, int on_device);
+
+/* The union graph (for profiling and tracing calls). */
+pirrt_graph *pirrt_batch_graph(pirrt_batch *b);
+
 /* Current vertex count, or -1 for a NULL handle. */
 int64_t pirrt_graph_num_vertices(const pirrt_graph *g);
 

@@ -122,6 +122,18 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_last_error": (ctypes.c_char_p, [vp]),
         "pirrt_status_string": (ctypes.c_char_p, [st]),
         "pirrt_evaluate_noalloc": (st, [i64, ctypes.c_int32, vp, vp, vp, vp]),
+        "pirrt_batch_create": (st, [ctypes.c_int32, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp,
+                                    ctypes.POINTER(vp)]),
+        "pirrt_batch_destroy": (None, [vp]),
+        "pirrt_batch_insert": (st, [vp, ctypes.c_int32, i64, vp, vp, vp, i32]),
+        "pirrt_batch_exploit": (st, [vp, ctypes.POINTER(pirrt_exploit_opts),
+                                     ctypes.POINTER(pirrt_exploit_stats)]),
+        "pirrt_batch_autotune": (st, [vp, ctypes.POINTER(pirrt_exploit_opts), ctypes.c_int32,
+                                      ctypes.POINTER(pirrt_exploit_opts),
+                                      ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "pirrt_batch_get_costs": (st, [vp, ctypes.c_int32, vp, i64, i32]),
+        "pirrt_batch_get_parents": (st, [vp, ctypes.c_int32, vp, i64, i32]),
+        "pirrt_batch_graph": (vp, [vp]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -320,4 +332,118 @@ def pirrt_evaluate_noalloc(parent, parent_cost, g_out, root: int = 0, stream=Non
         stream = _current_stream_ptr(parent.device.index or 0)
     return int(lib.pirrt_evaluate_noalloc(n, int(root), parent.data_ptr(), parent_cost.data_ptr(),
                                           g_out.data_ptr(), stream))
+
+
+def exploit_opts(eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
+                 dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
+                 host_loop: bool = False) -> pirrt_exploit_opts:
+    return pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
+                              EVALUATE_MODES[evaluate], int(wave_levels), int(bool(host_loop)),
+                              float(dense_fraction))
+
+
+class Batch:
+    """Many independent planning graphs exploited together (wraps a
+    ``pirrt_batch*``): the disjoint union of the members in one device graph,
+    one CUDA-graph launch per exploit."""
+
+    def __init__(self, max_vertices, max_edges, roots=None, cost_dtype=np.float32,
+                 device: int = 0, stream=None):
+        self._lib = load_library()
+        mv = np.ascontiguousarray(max_vertices, dtype=np.int64)
+        me = np.ascontiguousarray(max_edges, dtype=np.int64)
+        rt = np.ascontiguousarray(np.zeros(len(mv)) if roots is None else roots, dtype=np.int32)
+        self.cost_dtype = np.dtype(cost_dtype)
+        if stream is None:
+            stream = _current_stream_ptr(device)
+        h = ctypes.c_void_p()
+        rc = self._lib.pirrt_batch_create(len(mv), mv.ctypes.data, me.ctypes.data, rt.ctypes.data,
+                                          PIRRT_COST_F32 if self.cost_dtype == np.float32
+                                          else PIRRT_COST_F64, int(device), stream,
+                                          ctypes.byref(h))
+        if rc:
+            raise PirrtError("pirrt_batch_create", rc)
+        self._h = h
+        self.n_graphs = len(mv)
+        self.max_vertices = mv
+
+    def _graph_handle(self):
+        return self._lib.pirrt_batch_graph(self._h)
+
+    def _check(self, call: str, rc: int):
+        if rc:
+            detail = self._lib.pirrt_graph_last_error(self._graph_handle()).decode()
+            raise PirrtError(call, rc, detail)
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pirrt_batch_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def __enter__(self):
+        return self
+
+    def __exit__(self, *exc):
+        self.close()
+
+    def insert(self, graph: int, src, dst, cost):
+        ps, ds, ks = _buf(src, np.int32)
+        pd, dd, kd = _buf(dst, np.int32)
+        pc, dc, kc = _buf(cost, self.cost_dtype)
+        if not (ds == dd == dc):
+            raise ValueError("src, dst and cost must all be host or all be device buffers")
+        n_edges = len(ks) if ds == 0 else ks.numel()
+        self._check("pirrt_batch_insert",
+                    self._lib.pirrt_batch_insert(self._h, int(graph), int(n_edges), ps, pd, pc, ds))
+
+    def exploit(self, check: bool = True, **kw) -> dict:
+        opts = exploit_opts(**kw)
+        st = pirrt_exploit_stats()
+        rc = self._lib.pirrt_batch_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))
+        out = st.as_dict()
+        out["status"] = int(rc)
+        if check:
+            self._check("pirrt_batch_exploit", rc)
+        return out
+
+    def autotune(self, candidates: list[dict]):
+        """Time every candidate option set from the current state (restored
+        after each trial); returns (best options dict, index, ms)."""
+        arr = (pirrt_exploit_opts * len(candidates))(*[exploit_opts(**c) for c in candidates])
+        best = pirrt_exploit_opts()
+        idx = ctypes.c_int32(-1)
+        ms = ctypes.c_float(0)
+        self._check("pirrt_batch_autotune",
+                    self._lib.pirrt_batch_autotune(self._h, arr, len(candidates), ctypes.byref(best),
+                                                   ctypes.byref(idx), ctypes.byref(ms)))
+        return candidates[idx.value], idx.value, ms.value
+
+    def get_costs(self, graph: int, n: int, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(n, dtype=np.float64)
+        p, dev, keep = _buf(out, np.float64)
+        self._check("pirrt_batch_get_costs",
+                    self._lib.pirrt_batch_get_costs(self._h, int(graph), p, int(n), dev))
+        return out
+
+    def get_parents(self, graph: int, n: int, out=None) -> np.ndarray:
+        if out is None:
+            out = np.empty(n, dtype=np.int32)
+        p, dev, keep = _buf(out, np.int32)
+        self._check("pirrt_batch_get_parents",
+                    self._lib.pirrt_batch_get_parents(self._h, int(graph), p, int(n), dev))
+        return out
+
+    def set_profiling(self, enable: bool = True):
+        self._check("pirrt_graph_set_profiling",
+                    self._lib.pirrt_graph_set_profiling(self._graph_handle(), 1 if enable else 0))
+
+    def get_profile(self) -> dict:
+        pr = pirrt_profile()
+        self._check("pirrt_graph_get_profile",
+                    self._lib.pirrt_graph_get_profile(self._graph_handle(), ctypes.byref(pr)))
+        return pr.as_dict()
 

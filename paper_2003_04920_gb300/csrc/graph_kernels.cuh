@@ -804,6 +804,42 @@ static __global__ void export_parents_kernel(int64_t n, const int32_t *__restric
         out[v] = p[v] < 0 ? -1 : p[v];
 }
 
+// Batched form: translate one graph's local edge ids into the union graph
+// (id + base), rejecting ids outside [0, limit).  Writes into the pending
+// edge buffer at `out`.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+batch_translate_kernel(int64_t n_edges, const int32_t *__restrict__ src,
+                       const int32_t *__restrict__ dst, const CT *__restrict__ cost, int64_t base,
+                       int64_t limit, int32_t *__restrict__ out_src, int32_t *__restrict__ out_dst,
+                       CT *__restrict__ out_cost, DevCounters *ctr) {
+    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_edges;
+         e += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t a = src[e], b = dst[e];
+        if (a < 0 || b < 0 || a >= limit || b >= limit) {
+            atomicOr(&ctr->status, kStatusBadInput);
+            out_src[e] = 0;
+            out_dst[e] = 0;  // rejected by the union validation as a self loop
+            out_cost[e] = CT(0);
+            continue;
+        }
+        out_src[e] = (int32_t)(a + base);
+        out_dst[e] = (int32_t)(b + base);
+        out_cost[e] = cost[e];
+    }
+}
+
+// Batched form: parents of one graph in its own ids (root marker -> -1).
+static __global__ void export_parents_local_kernel(int64_t n, int64_t base,
+                                                   const int32_t *__restrict__ p,
+                                                   int32_t *__restrict__ out) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        const int32_t q = p[base + v];
+        out[v] = q < 0 ? -1 : (int32_t)(q - base);
+    }
+}
+
 // Make each listed vertex a root: g = 0, parent marker kRootMark.
 static __global__ void set_roots_kernel(int64_t k, const int32_t *__restrict__ roots,
                                         double *__restrict__ g, float *__restrict__ g32,

@@ -715,6 +715,88 @@ void free_all(pirrt_graph *G) {
     if (G->it_start) cudaEventDestroy(G->it_start);
 }
 
+// Snapshot of the mutable exploit state, for the autotuner's repeated trials.
+struct StateSnapshot {
+    void *buf = nullptr;
+    size_t bytes = 0;
+};
+
+pirrt_status snapshot_io(pirrt_graph *G, StateSnapshot &S, bool save) {
+    const size_t n = (size_t)G->n;
+    const size_t parts[] = {8 * n, 4 * n, 4 * n, G->cost_bytes * n, 4 * n, 4 * n, 4 * n,
+                            sizeof(DevCounters)};
+    void *dev[] = {G->g, G->g32, G->p, G->pc, G->stamp, G->list[0], G->list[1], G->ctr};
+    size_t total = 0;
+    for (size_t b : parts) total += (b + 255) & ~size_t(255);
+    if (save && S.bytes < total) {
+        if (S.buf) CK(cudaFree(S.buf));
+        S.buf = nullptr;
+        CK(cudaMalloc(&S.buf, total));
+        S.bytes = total;
+    }
+    char *q = static_cast<char *>(S.buf);
+    for (int i = 0; i < 8; ++i) {
+        if (parts[i]) {
+            if (save)
+                CK(cudaMemcpyAsync(q, dev[i], parts[i], cudaMemcpyDeviceToDevice, G->stream));
+            else
+                CK(cudaMemcpyAsync(dev[i], q, parts[i], cudaMemcpyDeviceToDevice, G->stream));
+        }
+        q += (parts[i] + 255) & ~size_t(255);
+    }
+    return PIRRT_OK;
+}
+
+}  // namespace
+
+struct pirrt_batch {
+    pirrt_graph *G = nullptr;
+    int32_t n_graphs = 0;
+    std::vector<int64_t> base, cap_v, cap_e, staged_e;
+    int32_t *pend_src = nullptr, *pend_dst = nullptr;
+    void *pend_cost = nullptr;
+    int64_t pend_n = 0, pend_cap = 0;
+};
+
+namespace {
+
+pirrt_status batch_flush(pirrt_batch *B) {
+    pirrt_graph *G = B->G;
+    if (B->pend_n == 0) return PIRRT_OK;
+    pirrt_status rc;
+    if (G->cfg.cost_dtype == PIRRT_COST_F32)
+        rc = insert_impl<float>(G, 0, B->pend_n, B->pend_src, B->pend_dst,
+                                static_cast<const float *>(B->pend_cost));
+    else
+        rc = insert_impl<double>(G, 0, B->pend_n, B->pend_src, B->pend_dst,
+                                 static_cast<const double *>(B->pend_cost));
+    if (rc == PIRRT_OK) B->pend_n = 0;
+    return rc;
+}
+
+template <typename CT>
+pirrt_status batch_translate(pirrt_batch *B, int32_t graph, int64_t n_edges, const int32_t *src,
+                             const int32_t *dst, const CT *cost) {
+    pirrt_graph *G = B->G;
+    CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
+    batch_translate_kernel<CT><<<grid_for(n_edges, kThreads, G->num_sms * 32), kThreads, 0,
+                                 G->stream>>>(
+        n_edges, src, dst, cost, B->base[graph], B->cap_v[graph], B->pend_src + B->pend_n,
+        B->pend_dst + B->pend_n, static_cast<CT *>(B->pend_cost) + B->pend_n, G->ctr);
+    CKL();
+    CK(cudaMemcpyAsync(&G->ctr_host->status, &G->ctr->status, sizeof(unsigned),
+                       cudaMemcpyDeviceToHost, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    if (G->ctr_host->status) {
+        CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
+        return fail(G, PIRRT_ERR_BAD_INPUT, "batch_insert: an id outside [0, %lld) of graph %d",
+                    (long long)B->cap_v[graph], graph);
+    }
+    B->pend_n += n_edges;
+    B->staged_e[graph] += n_edges;
+    return PIRRT_OK;
+}
+
 }  // namespace
 
 extern "C" {
@@ -1015,6 +1097,214 @@ pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *Gc, int64_t *row_off, 
             CK(cudaMemcpy2DAsync(cost, G->cost_bytes, base + off, G->entry_bytes, G->cost_bytes,
                                  (size_t)G->m, kind, G->stream));
         }
+    }
+    CK(cudaStreamSynchronize(G->stream));
+    return PIRRT_OK;
+}
+
+
+pirrt_status pirrt_batch_create(int32_t n_graphs, const int64_t *max_vertices,
+                                const int64_t *max_edges, const int32_t *roots,
+                                int32_t cost_dtype, int32_t device, void *stream,
+                                pirrt_batch **out) {
+    if (!out) return PIRRT_ERR_INVALID_ARG;
+    *out = nullptr;
+    if (n_graphs <= 0 || !max_vertices || !max_edges || !roots) return PIRRT_ERR_INVALID_ARG;
+    int64_t tv = 0, te = 0;
+    for (int32_t b = 0; b < n_graphs; ++b) {
+        if (max_vertices[b] <= 0 || max_edges[b] < 0 || roots[b] < 0 || roots[b] >= max_vertices[b])
+            return PIRRT_ERR_INVALID_ARG;
+        tv += max_vertices[b];
+        te += max_edges[b];
+    }
+    if (tv > INT32_MAX - 1) return PIRRT_ERR_CAPACITY;
+    pirrt_batch *B = new (std::nothrow) pirrt_batch();
+    if (!B) return PIRRT_ERR_OOM;
+    B->n_graphs = n_graphs;
+    B->base.resize(n_graphs);
+    B->cap_v.assign(max_vertices, max_vertices + n_graphs);
+    B->cap_e.assign(max_edges, max_edges + n_graphs);
+    B->staged_e.assign(n_graphs, 0);
+    int64_t acc_v = 0;
+    for (int32_t b = 0; b < n_graphs; ++b) {
+        B->base[b] = acc_v;
+        acc_v += max_vertices[b];
+    }
+    pirrt_config cfg{};
+    cfg.max_vertices = tv;
+    cfg.max_edges = te;
+    cfg.root = roots[0];
+    cfg.cost_dtype = cost_dtype;
+    cfg.device = device;
+    cfg.stream = stream;
+    pirrt_status rc = pirrt_graph_create(&cfg, &B->G);
+    if (rc) {
+        delete B;
+        return rc;
+    }
+    pirrt_graph *G = B->G;
+    auto bail = [&](pirrt_status r) {
+        if (B->pend_src) cudaFree(B->pend_src);
+        if (B->pend_dst) cudaFree(B->pend_dst);
+        if (B->pend_cost) cudaFree(B->pend_cost);
+        pirrt_graph_destroy(B->G);
+        delete B;
+        return r;
+    };
+    // every member's vertices exist from the start, isolated; roots get g = 0
+    if ((rc = pirrt_graph_insert_batch(G, tv, 0, nullptr, nullptr, nullptr, 1))) return bail(rc);
+    std::vector<int32_t> groots(n_graphs);
+    for (int32_t b = 0; b < n_graphs; ++b) groots[b] = (int32_t)(B->base[b] + roots[b]);
+    const size_t pe = (size_t)std::max<int64_t>(te, 1);
+    if (cudaMalloc((void **)&B->pend_src, 4 * pe) != cudaSuccess ||
+        cudaMalloc((void **)&B->pend_dst, 4 * pe) != cudaSuccess ||
+        cudaMalloc(&B->pend_cost, G->cost_bytes * pe) != cudaSuccess)
+        return bail(PIRRT_ERR_OOM);
+    B->pend_cap = te;
+    if ((rc = ensure_stage(G, 4 * (size_t)n_graphs))) return bail(rc);
+    if (cudaMemcpyAsync(G->stage, groots.data(), 4 * (size_t)n_graphs, cudaMemcpyHostToDevice,
+                        G->stream) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
+    set_roots_kernel<<<grid_for(n_graphs, kThreads, 1024), kThreads, 0, G->stream>>>(
+        n_graphs, static_cast<const int32_t *>(G->stage), G->g, G->g32, G->p);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(G->stream) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
+    *out = B;
+    return PIRRT_OK;
+}
+
+void pirrt_batch_destroy(pirrt_batch *B) {
+    if (!B) return;
+    if (B->G) {
+        cudaSetDevice(B->G->cfg.device);
+        cudaStreamSynchronize(B->G->stream);
+    }
+    if (B->pend_src) cudaFree(B->pend_src);
+    if (B->pend_dst) cudaFree(B->pend_dst);
+    if (B->pend_cost) cudaFree(B->pend_cost);
+    pirrt_graph_destroy(B->G);
+    delete B;
+}
+
+pirrt_graph *pirrt_batch_graph(pirrt_batch *B) { return B ? B->G : nullptr; }
+
+pirrt_status pirrt_batch_insert(pirrt_batch *B, int32_t graph, int64_t n_edges, const int32_t *src,
+                                const int32_t *dst, const void *cost, int on_device) {
+    if (!B || graph < 0 || graph >= B->n_graphs || n_edges < 0 ||
+        (n_edges > 0 && (!src || !dst || !cost)))
+        return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    if (B->staged_e[graph] + n_edges > B->cap_e[graph])
+        return fail(G, PIRRT_ERR_CAPACITY, "batch_insert: graph %d would exceed %lld edges", graph,
+                    (long long)B->cap_e[graph]);
+    if (n_edges == 0) return PIRRT_OK;
+    CK(cudaSetDevice(G->cfg.device));
+    const int32_t *s = src, *d = dst;
+    const void *c = cost;
+    if (!on_device) {
+        const size_t ib = sizeof(int32_t) * (size_t)n_edges;
+        const size_t cb = G->cost_bytes * (size_t)n_edges;
+        const size_t a16 = (ib + 15) & ~size_t(15);
+        pirrt_status rc = ensure_stage(G, 2 * a16 + cb);
+        if (rc) return rc;
+        char *base = static_cast<char *>(G->stage);
+        CK(cudaMemcpyAsync(base, src, ib, cudaMemcpyHostToDevice, G->stream));
+        CK(cudaMemcpyAsync(base + a16, dst, ib, cudaMemcpyHostToDevice, G->stream));
+        CK(cudaMemcpyAsync(base + 2 * a16, cost, cb, cudaMemcpyHostToDevice, G->stream));
+        s = reinterpret_cast<const int32_t *>(base);
+        d = reinterpret_cast<const int32_t *>(base + a16);
+        c = base + 2 * a16;
+    }
+    if (G->cfg.cost_dtype == PIRRT_COST_F32)
+        return batch_translate<float>(B, graph, n_edges, s, d, static_cast<const float *>(c));
+    return batch_translate<double>(B, graph, n_edges, s, d, static_cast<const double *>(c));
+}
+
+pirrt_status pirrt_batch_exploit(pirrt_batch *B, const pirrt_exploit_opts *opts,
+                                 pirrt_exploit_stats *stats) {
+    if (!B) return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    CK(cudaSetDevice(G->cfg.device));
+    pirrt_status rc = batch_flush(B);
+    if (rc) return rc;
+    return pirrt_graph_exploit(G, opts, stats);
+}
+
+pirrt_status pirrt_batch_autotune(pirrt_batch *B, const pirrt_exploit_opts *cand, int32_t n,
+                                  pirrt_exploit_opts *best, int32_t *best_index, float *best_ms) {
+    if (!B || !cand || n <= 0 || !best) return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    CK(cudaSetDevice(G->cfg.device));
+    pirrt_status rc = batch_flush(B);
+    if (rc) return rc;
+    StateSnapshot snap;
+    if ((rc = snapshot_io(G, snap, true))) return rc;
+    const int deep0 = G->deep_hint, expl0 = G->exploits;
+    unsigned wave_epoch_max = 0;
+    float tbest = 0.f;
+    int ibest = -1;
+    for (int32_t i = 0; i < n && rc == PIRRT_OK; ++i) {
+        if (i > 0 && (rc = snapshot_io(G, snap, false))) break;
+        if (i > 0) {  // wave stamps written by earlier trials stay below this value
+            CK(cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
+                               cudaMemcpyHostToDevice, G->stream));
+        }
+        G->deep_hint = deep0;
+        G->exploits = expl0;
+        pirrt_exploit_stats st{};
+        rc = pirrt_graph_exploit(G, &cand[i], &st);
+        if (rc == PIRRT_OK) {
+            wave_epoch_max = std::max(wave_epoch_max, G->ctr_host->wave_epoch + 1u);
+            if (ibest < 0 || st.ms_exploit < tbest) {
+                tbest = st.ms_exploit;
+                ibest = i;
+            }
+        }
+    }
+    pirrt_status rc2 = snapshot_io(G, snap, false);
+    if (rc2 == PIRRT_OK && wave_epoch_max)
+        rc2 = cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
+                              cudaMemcpyHostToDevice, G->stream) == cudaSuccess ? PIRRT_OK
+                                                                                 : PIRRT_ERR_CUDA;
+    cudaStreamSynchronize(G->stream);
+    G->deep_hint = deep0;
+    G->exploits = expl0;
+    if (snap.buf) cudaFree(snap.buf);
+    if (rc) return rc;
+    if (rc2) return rc2;
+    *best = cand[ibest];
+    if (best_index) *best_index = ibest;
+    if (best_ms) *best_ms = tbest;
+    return PIRRT_OK;
+}
+
+pirrt_status pirrt_batch_get_costs(const pirrt_batch *B, int32_t graph, double *g_out, int64_t n,
+                                   int on_device) {
+    if (!B || graph < 0 || graph >= B->n_graphs || n < 0 || n > B->cap_v[graph] || (n > 0 && !g_out))
+        return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    CK(cudaSetDevice(G->cfg.device));
+    if (n > 0)
+        CK(cudaMemcpyAsync(g_out, G->g + B->base[graph], sizeof(double) * (size_t)n,
+                           on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    return PIRRT_OK;
+}
+
+pirrt_status pirrt_batch_get_parents(const pirrt_batch *B, int32_t graph, int32_t *p_out, int64_t n,
+                                     int on_device) {
+    if (!B || graph < 0 || graph >= B->n_graphs || n < 0 || n > B->cap_v[graph] || (n > 0 && !p_out))
+        return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    CK(cudaSetDevice(G->cfg.device));
+    if (n > 0) {
+        int32_t *dst = on_device ? p_out : G->pexport;
+        export_parents_local_kernel<<<grid_for(n, kThreads, G->num_sms * 8), kThreads, 0,
+                                      G->stream>>>(n, B->base[graph], G->p, dst);
+        CKL();
+        if (!on_device)
+            CK(cudaMemcpyAsync(p_out, G->pexport, sizeof(int32_t) * (size_t)n,
+                               cudaMemcpyDeviceToHost, G->stream));
     }
     CK(cudaStreamSynchronize(G->stream));
     return PIRRT_OK;

@@ -84,7 +84,7 @@ def test_autotune_restores_state_and_picks_a_candidate(members):
 
 def test_batch_incremental_inserts_and_errors():
     rms = [W.random_graph(900 + i, 40 + 10 * i, 120) for i in range(5)]
-    with P.Batch([rm.n for rm in rms], [rm.m for rm in rms], cost_dtype=np.float64) as B:
+    with P.Batch([rm.n for rm in rms], [rm.m + 8 for rm in rms], cost_dtype=np.float64) as B:
         # first half of every member, exploit, then the rest
         for i, rm in enumerate(rms):
             h = rm.m // 2

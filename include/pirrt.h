@@ -276,6 +276,10 @@ pirrt_status pirrt_batch_create(int32_t n_graphs, const int64_t *max_vertices,
 
 void pirrt_batch_destroy(pirrt_batch *b);
 
+/* Back to the state right after create (every member isolated, roots at
+ * g = 0, nothing staged), keeping the allocations. */
+pirrt_status pirrt_batch_reset(pirrt_batch *b);
+
 /* Stage n_edges undirected edges of member `graph` in member-local ids (each
  * in [0, max_vertices[graph])); they join the device CSR at the next
  * exploit.  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_CAPACITY,

@@ -125,6 +125,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_batch_create": (st, [ctypes.c_int32, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp,
                                     ctypes.POINTER(vp)]),
         "pirrt_batch_destroy": (None, [vp]),
+        "pirrt_batch_reset": (st, [vp]),
         "pirrt_batch_insert": (st, [vp, ctypes.c_int32, i64, vp, vp, vp, i32]),
         "pirrt_batch_exploit": (st, [vp, ctypes.POINTER(pirrt_exploit_opts),
                                      ctypes.POINTER(pirrt_exploit_stats)]),
@@ -388,6 +389,9 @@ class Batch:
 
     def __exit__(self, *exc):
         self.close()
+
+    def reset(self):
+        self._check("pirrt_batch_reset", self._lib.pirrt_batch_reset(self._h))
 
     def insert(self, graph: int, src, dst, cost):
         ps, ds, ks = _buf(src, np.int32)

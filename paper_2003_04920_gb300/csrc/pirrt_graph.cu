@@ -753,6 +753,7 @@ struct pirrt_batch {
     pirrt_graph *G = nullptr;
     int32_t n_graphs = 0;
     std::vector<int64_t> base, cap_v, cap_e, staged_e;
+    std::vector<int32_t> groots;  // roots in union ids
     int32_t *pend_src = nullptr, *pend_dst = nullptr;
     void *pend_cost = nullptr;
     int64_t pend_n = 0, pend_cap = 0;
@@ -1151,25 +1152,37 @@ pirrt_status pirrt_batch_create(int32_t n_graphs, const int64_t *max_vertices,
         delete B;
         return r;
     };
-    // every member's vertices exist from the start, isolated; roots get g = 0
-    if ((rc = pirrt_graph_insert_batch(G, tv, 0, nullptr, nullptr, nullptr, 1))) return bail(rc);
-    std::vector<int32_t> groots(n_graphs);
-    for (int32_t b = 0; b < n_graphs; ++b) groots[b] = (int32_t)(B->base[b] + roots[b]);
+    B->groots.resize(n_graphs);
+    for (int32_t b = 0; b < n_graphs; ++b) B->groots[b] = (int32_t)(B->base[b] + roots[b]);
     const size_t pe = (size_t)std::max<int64_t>(te, 1);
     if (cudaMalloc((void **)&B->pend_src, 4 * pe) != cudaSuccess ||
         cudaMalloc((void **)&B->pend_dst, 4 * pe) != cudaSuccess ||
         cudaMalloc(&B->pend_cost, G->cost_bytes * pe) != cudaSuccess)
         return bail(PIRRT_ERR_OOM);
     B->pend_cap = te;
-    if ((rc = ensure_stage(G, 4 * (size_t)n_graphs))) return bail(rc);
-    if (cudaMemcpyAsync(G->stage, groots.data(), 4 * (size_t)n_graphs, cudaMemcpyHostToDevice,
-                        G->stream) != cudaSuccess)
-        return bail(PIRRT_ERR_CUDA);
-    set_roots_kernel<<<grid_for(n_graphs, kThreads, 1024), kThreads, 0, G->stream>>>(
-        n_graphs, static_cast<const int32_t *>(G->stage), G->g, G->g32, G->p);
-    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(G->stream) != cudaSuccess)
-        return bail(PIRRT_ERR_CUDA);
+    if ((rc = pirrt_batch_reset(B))) return bail(rc);
     *out = B;
+    return PIRRT_OK;
+}
+
+pirrt_status pirrt_batch_reset(pirrt_batch *B) {
+    if (!B) return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    pirrt_status rc = pirrt_graph_reset(G);
+    if (rc) return rc;
+    // every member's vertices exist from the start, isolated; roots get g = 0
+    int64_t tv = 0;
+    for (int64_t c : B->cap_v) tv += c;
+    if ((rc = pirrt_graph_insert_batch(G, tv, 0, nullptr, nullptr, nullptr, 1))) return rc;
+    const size_t k = B->groots.size();
+    if ((rc = ensure_stage(G, 4 * k))) return rc;
+    CK(cudaMemcpyAsync(G->stage, B->groots.data(), 4 * k, cudaMemcpyHostToDevice, G->stream));
+    set_roots_kernel<<<grid_for((int64_t)k, kThreads, 1024), kThreads, 0, G->stream>>>(
+        (int64_t)k, static_cast<const int32_t *>(G->stage), G->g, G->g32, G->p);
+    CKL();
+    CK(cudaStreamSynchronize(G->stream));
+    B->pend_n = 0;
+    std::fill(B->staged_e.begin(), B->staged_e.end(), 0);
     return PIRRT_OK;
 }
 

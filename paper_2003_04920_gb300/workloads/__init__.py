@@ -291,8 +291,15 @@ def roadmap_c3(trial: int = 0, n: int = 4_000_000, block: int = 50_000) -> Roadm
     return roadmap_nd_knn("c3", 3 * 1000 + trial, n, 6, 64, 0.3, 0.8, 30, block)
 
 
+def _batch_member(args):
+    i, n, d, s = args
+    if d == 2:
+        return roadmap_2d_knn(f"b{i}", s, n, 20, 0.02, 0.08, n)
+    return roadmap_nd_knn(f"b{i}", s, n, d, 64, 0.3, 0.8, knn_k(n), n)
+
+
 def roadmap_batch(n_graphs: int = 512, trial: int = 0, n_min: int = 1_000,
-                  n_max: int = 200_000, dims=(2, 3, 4, 6, 7)) -> list[Roadmap]:
+                  n_max: int = 200_000, dims=(2, 3, 4, 6, 7), workers: int = 1) -> list[Roadmap]:
     """Independent roadmaps: N_g log-uniform in [n_min, n_max], dimension
     uniform in ``dims``, k = ceil(2e ln N_g), each with its own obstacles.
     2-D scenes use 20 circles r ~ U[0.02, 0.08] in the unit square with an
@@ -302,15 +309,14 @@ def roadmap_batch(n_graphs: int = 512, trial: int = 0, n_min: int = 1_000,
     sizes = np.exp(rng.uniform(math.log(n_min), math.log(n_max), n_graphs)).round().astype(int)
     dim_pick = rng.choice(np.asarray(dims), n_graphs)
     seeds = rng.integers(0, 2**31 - 1, n_graphs)
-    out = []
-    for i in range(n_graphs):
-        n, d, s = int(sizes[i]), int(dim_pick[i]), int(seeds[i])
-        if d == 2:
-            rm = roadmap_2d_knn(f"b{i}", s, n, 20, 0.02, 0.08, n)
-        else:
-            rm = roadmap_nd_knn(f"b{i}", s, n, d, 64, 0.3, 0.8, knn_k(n), n)
-        out.append(rm)
-    return out
+    jobs = [(i, int(sizes[i]), int(dim_pick[i]), int(seeds[i])) for i in range(n_graphs)]
+    if workers > 1:
+        import concurrent.futures as cf
+        import multiprocessing as mp
+        build_roadgen()
+        with cf.ProcessPoolExecutor(max_workers=workers, mp_context=mp.get_context("spawn")) as ex:
+            return list(ex.map(_batch_member, jobs, chunksize=4))
+    return [_batch_member(j) for j in jobs]
 
 
 def bfs_tree_parents(rm: Roadmap, root: int = 0) -> np.ndarray:
@@ -389,4 +395,36 @@ def cached(name: str, fn, **kw) -> Roadmap:
              dim=sc.dim, lo=sc.lo, hi=sc.hi, centers=sc.centers, radii=sc.radii)
     os.replace(tmp, path)
     return rm
+
+
+def cached_batch(n_graphs: int = 512, trial: int = 0, n_min: int = 1_000, n_max: int = 200_000,
+                 workers: int = 1) -> list[Roadmap]:
+    """roadmap_batch memoised on disk as one archive (members concatenated)."""
+    import json
+    import tempfile
+    root = os.environ.get("PIRRT_CACHE", os.path.join(tempfile.gettempdir(), "pirrt_cache"))
+    os.makedirs(root, exist_ok=True)
+    path = os.path.join(root, f"batch-{n_graphs}-{trial}-{n_min}-{n_max}.npz")
+    if os.path.exists(path):
+        d = np.load(path, allow_pickle=False)
+        out = []
+        nv, ne = d["nv"], d["ne"]
+        ov, oe = np.r_[0, np.cumsum(nv)], np.r_[0, np.cumsum(ne)]
+        metas = json.loads(str(d["metas"]))
+        for i in range(len(nv)):
+            u = d["u"][oe[i]:oe[i + 1]]
+            v = d["v"][oe[i]:oe[i + 1]]
+            n = int(nv[i])
+            out.append(Roadmap(f"b{i}", np.zeros((n, 1)), u, v, d["cost"][oe[i]:oe[i + 1]],
+                               np.searchsorted(v, np.arange(n + 1)).astype(np.int64), n, None,
+                               metas[i]))
+        return out
+    rms = roadmap_batch(n_graphs, trial, n_min, n_max, workers=workers)
+    tmp = f"{path}.{os.getpid()}.tmp.npz"
+    np.savez(tmp, nv=np.array([r.n for r in rms]), ne=np.array([r.m for r in rms]),
+             u=np.concatenate([r.u for r in rms]), v=np.concatenate([r.v for r in rms]),
+             cost=np.concatenate([r.cost for r in rms]),
+             metas=json.dumps([r.meta for r in rms], default=str))
+    os.replace(tmp, path)
+    return rms
 

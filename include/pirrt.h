@@ -312,6 +312,76 @@ pirrt_status pirrt_batch_get_parents(const pirrt_batch *b, int32_t graph, int32_
 /* The union graph (for profiling and tracing calls). */
 pirrt_graph *pirrt_batch_graph(pirrt_batch *b);
 
+/* ------------------------------------------------------------------------
+ * Learned sampling proposal (an addition on top of the method; the paper
+ * samples uniformly).  A 3-layer MLP maps a scene's 64 x 64 occupancy grid
+ * (4096 values in {0, 1}) and 8-D Gaussian noise to a sample position in
+ * [0, 1]^2:
+ *   a1 = W1g grid + W1n z + b1, h1 = relu(a1); a2 = W2 h1 + b2, h2 = relu(a2);
+ *   y = sigmoid(W3 h2 + b3).
+ * BF16 weights and layer inputs on the tensor cores with FP32 accumulation,
+ * FP32 master weights trained by Adam.  Training is implicit maximum-
+ * likelihood estimation: for each target sample, K noise draws go through the
+ * network and only the draw nearest the target is pulled towards it.
+ * Parameters are packed FP32 in the order W1g [256 x 4096], W1n [256 x 8],
+ * b1 [256], W2 [256 x 256], b2 [256], W3 [2 x 256], b3 [2].
+ * All array arguments are device pointers; noise is supplied by the caller.
+ * ------------------------------------------------------------------------ */
+typedef struct pirrt_proposal pirrt_proposal;
+
+/* Number of packed parameters (1,117,186). */
+int64_t pirrt_proposal_num_params(void);
+
+/* Working space for up to max_scenes scenes and max_rows sample rows per call;
+ * He-uniform initial weights from `seed`. */
+pirrt_status pirrt_proposal_create(int32_t max_scenes, int32_t max_rows, uint64_t seed,
+                                   int32_t device, void *stream, pirrt_proposal **out);
+void pirrt_proposal_destroy(pirrt_proposal *p);
+
+/* Replace / read the FP32 master weights (n = num_params); set clears the
+ * Adam state and the accumulated gradient. */
+pirrt_status pirrt_proposal_set_weights(pirrt_proposal *p, const float *w, int64_t n);
+pirrt_status pirrt_proposal_get_weights(const pirrt_proposal *p, float *w, int64_t n);
+
+/* Samples: out_xy[r] = network(grids[scene[r]], noise[r]) for r < rows.
+ * grids: [n_scenes x 4096] FP32 0/1; scene: int32[rows]; noise: [rows x 8];
+ * out_xy: [rows x 2]. */
+pirrt_status pirrt_proposal_forward(pirrt_proposal *p, int32_t n_scenes, const float *grids,
+                                    int32_t rows, const int32_t *scene, const float *noise,
+                                    float *out_xy);
+
+/* IMLE draw selection: rows t*K .. t*K+K-1 (scene draw_scene[row], noise
+ * noise[row]) belong to target t; pick[t] = the draw whose output is nearest
+ * targets[t] (lowest index on ties). */
+pirrt_status pirrt_proposal_imle_select(pirrt_proposal *p, int32_t n_scenes, const float *grids,
+                                        int32_t n_targets, const int32_t *draw_scene,
+                                        const float *targets, int32_t K, const float *noise,
+                                        int32_t *pick);
+
+/* Accumulate the gradient of mean_r |y_r - targets_r|^2 over `rows` rows into
+ * the internal gradient; *loss_out (host, may be NULL) gets the loss. */
+pirrt_status pirrt_proposal_backward(pirrt_proposal *p, int32_t n_scenes, const float *grids,
+                                     int32_t rows, const int32_t *scene, const float *noise,
+                                     const float *targets, float *loss_out);
+
+/* Read / clear the accumulated gradient (n = num_params). */
+pirrt_status pirrt_proposal_get_grads(const pirrt_proposal *p, float *g, int64_t n);
+pirrt_status pirrt_proposal_zero_grads(pirrt_proposal *p);
+
+/* One Adam step on the accumulated gradient, which is then cleared. */
+pirrt_status pirrt_proposal_adam(pirrt_proposal *p, float lr, float beta1, float beta2, float eps);
+
+/* One IMLE training step: K draws per target (noise: [n_targets * K x 8],
+ * target t owns rows t*K .. t*K+K-1, all in scene target_scene[t]), the
+ * nearest draw of each target is pulled towards it (squared error, mean over
+ * targets), then Adam (beta1 0.9, beta2 0.999, eps 1e-8) with rate lr.
+ * *loss_out (host, may be NULL) gets the loss before the step.
+ * n_targets * K must not exceed max_rows. */
+pirrt_status pirrt_proposal_train_step(pirrt_proposal *p, int32_t n_scenes, const float *grids,
+                                       int32_t n_targets, const int32_t *target_scene,
+                                       const float *targets, int32_t K, const float *noise,
+                                       float lr, float *loss_out);
+
 /* Current vertex count, or -1 for a NULL handle. */
 int64_t pirrt_graph_num_vertices(const pirrt_graph *g);
 

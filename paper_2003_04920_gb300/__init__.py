@@ -135,6 +135,24 @@ def load_library(path: str = LIB_PATH):
         "pirrt_batch_get_costs": (st, [vp, ctypes.c_int32, vp, i64, i32]),
         "pirrt_batch_get_parents": (st, [vp, ctypes.c_int32, vp, i64, i32]),
         "pirrt_batch_graph": (vp, [vp]),
+        "pirrt_proposal_num_params": (i64, []),
+        "pirrt_proposal_create": (st, [ctypes.c_int32, ctypes.c_int32, ctypes.c_uint64,
+                                       ctypes.c_int32, vp, ctypes.POINTER(vp)]),
+        "pirrt_proposal_destroy": (None, [vp]),
+        "pirrt_proposal_set_weights": (st, [vp, vp, i64]),
+        "pirrt_proposal_get_weights": (st, [vp, vp, i64]),
+        "pirrt_proposal_forward": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp]),
+        "pirrt_proposal_imle_select": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp,
+                                            ctypes.c_int32, vp, vp]),
+        "pirrt_proposal_backward": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp,
+                                         ctypes.POINTER(ctypes.c_float)]),
+        "pirrt_proposal_get_grads": (st, [vp, vp, i64]),
+        "pirrt_proposal_zero_grads": (st, [vp]),
+        "pirrt_proposal_train_step": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp,
+                                           ctypes.c_int32, vp, ctypes.c_float,
+                                           ctypes.POINTER(ctypes.c_float)]),
+        "pirrt_proposal_adam": (st, [vp, ctypes.c_float, ctypes.c_float, ctypes.c_float,
+                                     ctypes.c_float]),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)
@@ -451,3 +469,104 @@ class Batch:
                     self._lib.pirrt_graph_get_profile(self._graph_handle(), ctypes.byref(pr)))
         return pr.as_dict()
 
+
+class Proposal:
+    """Learned sampling proposal (wraps a ``pirrt_proposal*``).  Arrays are
+    PyTorch CUDA tensors: grids [S, 4096] float32 in {0, 1}, scene int32 [R],
+    noise float32 [R, 8], targets float32 [R, 2]."""
+
+    def __init__(self, max_scenes: int, max_rows: int, seed: int = 0, device: int = 0,
+                 stream=None):
+        self._lib = load_library()
+        if stream is None:
+            stream = _current_stream_ptr(device)
+        h = ctypes.c_void_p()
+        rc = self._lib.pirrt_proposal_create(int(max_scenes), int(max_rows), int(seed),
+                                             int(device), stream, ctypes.byref(h))
+        if rc:
+            raise PirrtError("pirrt_proposal_create", rc)
+        self._h = h
+        self.n_params = int(self._lib.pirrt_proposal_num_params())
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.pirrt_proposal_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        self.close()
+
+    def _check(self, call, rc):
+        if rc:
+            raise PirrtError(call, rc)
+
+    @staticmethod
+    def _dev(x):
+        assert x.is_cuda and x.is_contiguous()
+        return x.data_ptr()
+
+    def get_weights(self):
+        import torch
+        w = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        self._check("pirrt_proposal_get_weights",
+                    self._lib.pirrt_proposal_get_weights(self._h, w.data_ptr(), self.n_params))
+        return w
+
+    def set_weights(self, w):
+        self._check("pirrt_proposal_set_weights",
+                    self._lib.pirrt_proposal_set_weights(self._h, self._dev(w), self.n_params))
+
+    def get_grads(self):
+        import torch
+        g = torch.empty(self.n_params, dtype=torch.float32, device="cuda")
+        self._check("pirrt_proposal_get_grads",
+                    self._lib.pirrt_proposal_get_grads(self._h, g.data_ptr(), self.n_params))
+        return g
+
+    def zero_grads(self):
+        self._check("pirrt_proposal_zero_grads", self._lib.pirrt_proposal_zero_grads(self._h))
+
+    def forward(self, grids, scene, noise):
+        import torch
+        out = torch.empty((scene.numel(), 2), dtype=torch.float32, device="cuda")
+        self._check("pirrt_proposal_forward",
+                    self._lib.pirrt_proposal_forward(self._h, grids.shape[0], self._dev(grids),
+                                                     scene.numel(), self._dev(scene),
+                                                     self._dev(noise), out.data_ptr()))
+        return out
+
+    def imle_select(self, grids, draw_scene, targets, K: int, noise):
+        import torch
+        pick = torch.empty(targets.shape[0], dtype=torch.int32, device="cuda")
+        self._check("pirrt_proposal_imle_select",
+                    self._lib.pirrt_proposal_imle_select(self._h, grids.shape[0], self._dev(grids),
+                                                         targets.shape[0], self._dev(draw_scene),
+                                                         self._dev(targets), int(K),
+                                                         self._dev(noise), pick.data_ptr()))
+        return pick
+
+    def backward(self, grids, scene, noise, targets) -> float:
+        loss = ctypes.c_float(0)
+        self._check("pirrt_proposal_backward",
+                    self._lib.pirrt_proposal_backward(self._h, grids.shape[0], self._dev(grids),
+                                                      scene.numel(), self._dev(scene),
+                                                      self._dev(noise), self._dev(targets),
+                                                      ctypes.byref(loss)))
+        return float(loss.value)
+
+    def adam(self, lr: float, beta1: float = 0.9, beta2: float = 0.999, eps: float = 1e-8):
+        self._check("pirrt_proposal_adam",
+                    self._lib.pirrt_proposal_adam(self._h, float(lr), float(beta1), float(beta2),
+                                                  float(eps)))
+
+    def train_step(self, grids, target_scene, targets, K: int, noise, lr: float) -> float:
+        """One IMLE step in the library: K draws per target, the nearest is
+        pulled to it, then Adam.  Returns the loss before the step."""
+        loss = ctypes.c_float(0)
+        self._check("pirrt_proposal_train_step",
+                    self._lib.pirrt_proposal_train_step(self._h, grids.shape[0], self._dev(grids),
+                                                        targets.shape[0], self._dev(target_scene),
+                                                        self._dev(targets), int(K),
+                                                        self._dev(noise), float(lr),
+                                                        ctypes.byref(loss)))
+        return float(loss.value)

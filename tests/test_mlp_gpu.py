@@ -1,0 +1,112 @@
+"""The proposal's CUDA forward / backward / IMLE / Adam kernels against the
+CPU oracle (oracle/mlp.py, FP64 with BF16 rounding where the kernels round).
+
+Tolerances: the GPU accumulates in FP32 (4096-term and 256-term sums) where
+the oracle uses FP64, and a changed FP32 value occasionally rounds to the
+neighbouring BF16 value (relative step 2^-8) in an intermediate activation,
+so outputs are compared to 2e-3 absolute and gradients to 5e-3 of each
+tensor's norm."""
+import numpy as np
+import pytest
+
+import paper_2003_04920_gb300 as P
+from oracle import mlp as M
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load_library()
+    return t
+
+
+def _data(torch, seed=0, S=5, R=300):
+    rng = np.random.default_rng(seed)
+    grids = (rng.random((S, M.GRID)) < 0.25).astype(np.float32)
+    scene = rng.integers(0, S, R).astype(np.int32)
+    z = rng.normal(size=(R, M.NOISE)).astype(np.float32)
+    target = rng.random((R, 2)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    return (grids, scene, z, target), (dev(grids), dev(scene), dev(z), dev(target))
+
+
+def test_forward_matches_oracle(torch):
+    (g, s, z, t), (gd, sd, zd, td) = _data(torch)
+    prop = P.Proposal(8, 1024, seed=3)
+    params = M.unpack(prop.get_weights().cpu().numpy().astype(np.float64))
+    y = prop.forward(gd, sd, zd).cpu().numpy()
+    ref = M.forward(params, g, s, z.astype(np.float64), rounded=True)["y"]
+    assert np.max(np.abs(y - ref)) < 2e-3
+    prop.close()
+
+
+def test_backward_matches_oracle(torch):
+    (g, s, z, t), (gd, sd, zd, td) = _data(torch, seed=1)
+    prop = P.Proposal(8, 1024, seed=4)
+    params = M.unpack(prop.get_weights().cpu().numpy().astype(np.float64))
+    prop.zero_grads()
+    loss = prop.backward(gd, sd, zd, td)
+    grads = M.unpack(prop.get_grads().cpu().numpy().astype(np.float64))
+    L, ref = M.backward(params, g, s, z.astype(np.float64), t.astype(np.float64), rounded=True)
+    assert abs(loss - L) <= 1e-4 * max(1.0, L)
+    for name, _ in M.SHAPES:
+        err = np.linalg.norm(grads[name] - ref[name]) / max(np.linalg.norm(ref[name]), 1e-30)
+        assert err < 5e-3, (name, err)
+
+
+def test_imle_select_matches_oracle(torch):
+    (g, s, z, t), _ = _data(torch, seed=2, R=64)
+    K = 16
+    rng = np.random.default_rng(7)
+    zk = rng.normal(size=(64 * K, M.NOISE)).astype(np.float32)
+    draw_scene = np.repeat(s, K).astype(np.int32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prop = P.Proposal(8, 64 * K, seed=5)
+    pick = prop.imle_select(dev(g), dev(draw_scene), dev(t), K, dev(zk)).cpu().numpy()
+    y = prop.forward(dev(g), dev(draw_scene), dev(zk)).cpu().numpy()
+    np.testing.assert_array_equal(pick, M.imle_pick(y.astype(np.float64), t.astype(np.float64), K))
+    params = M.unpack(prop.get_weights().cpu().numpy().astype(np.float64))
+    yref = M.forward(params, g, draw_scene, zk.astype(np.float64), rounded=True)["y"]
+    d = np.sum((yref.reshape(64, K, 2) - t[:, None, :]) ** 2, axis=2)
+    srt = np.sort(d, axis=1)
+    clear = (srt[:, 1] - srt[:, 0]) > 1e-3
+    np.testing.assert_array_equal(pick[clear], np.argmin(d, axis=1)[clear])
+    prop.close()
+
+
+def test_adam_step_matches_definition(torch):
+    (g, s, z, t), (gd, sd, zd, td) = _data(torch, seed=3)
+    prop = P.Proposal(8, 1024, seed=6)
+    w0 = prop.get_weights().cpu().numpy().astype(np.float64)
+    prop.zero_grads()
+    prop.backward(gd, sd, zd, td)
+    grad = prop.get_grads().cpu().numpy().astype(np.float64)
+    prop.adam(1e-3)
+    w1 = prop.get_weights().cpu().numpy().astype(np.float64)
+    want, _, _ = M.adam(w0, np.zeros_like(w0), np.zeros_like(w0), grad, 1, 1e-3)
+    np.testing.assert_allclose(w1, want, rtol=1e-5, atol=1e-6)
+    assert np.all(prop.get_grads().cpu().numpy() == 0)  # the step clears the gradient
+    prop.close()
+
+
+def test_imle_training_reduces_loss(torch):
+    """Targets cluster around a scene-dependent point; IMLE training pulls the
+    nearest draws onto them."""
+    rng = np.random.default_rng(11)
+    S, T, K = 6, 128, 8
+    grids = (rng.random((S, M.GRID)) < 0.2).astype(np.float32)
+    centers = rng.uniform(0.2, 0.8, (S, 2)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prop = P.Proposal(S, T * K, seed=8)
+    losses = []
+    for it in range(150):
+        sc = rng.integers(0, S, T).astype(np.int32)
+        tg = (centers[sc] + rng.normal(0, 0.03, (T, 2))).astype(np.float32)
+        nz = rng.normal(size=(T * K, M.NOISE)).astype(np.float32)
+        losses.append(prop.train_step(dev(grids), dev(sc), dev(tg), K, dev(nz), 3e-3))
+    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
+    prop.close()

@@ -350,6 +350,17 @@ pirrt_status pirrt_proposal_forward(pirrt_proposal *p, int32_t n_scenes, const f
                                     int32_t rows, const int32_t *scene, const float *noise,
                                     float *out_xy);
 
+/* Sampling distribution of the planner with the proposal: row r is the
+ * network's output for (grids[scene[r]], noise[r]) when coin[r] <
+ * learned_fraction, else uniform_xy[r] (a 50/50 mixture at 0.5).  The caller
+ * draws noise [rows x 8] ~ N(0, I), uniform_xy [rows x 2] ~ U[0,1]^2 and
+ * coin [rows] ~ U[0,1); out_xy: [rows x 2].  Samples inside obstacles are
+ * the caller's to reject, as for uniform sampling. */
+pirrt_status pirrt_proposal_sample(pirrt_proposal *p, int32_t n_scenes, const float *grids,
+                                   int32_t rows, const int32_t *scene, const float *noise,
+                                   const float *uniform_xy, const float *coin,
+                                   float learned_fraction, float *out_xy);
+
 /* IMLE draw selection: rows t*K .. t*K+K-1 (scene draw_scene[row], noise
  * noise[row]) belong to target t; pick[t] = the draw whose output is nearest
  * targets[t] (lowest index on ties). */

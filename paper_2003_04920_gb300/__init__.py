@@ -142,6 +142,8 @@ def load_library(path: str = LIB_PATH):
         "pirrt_proposal_set_weights": (st, [vp, vp, i64]),
         "pirrt_proposal_get_weights": (st, [vp, vp, i64]),
         "pirrt_proposal_forward": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp]),
+        "pirrt_proposal_sample": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp, vp,
+                                       ctypes.c_float, vp]),
         "pirrt_proposal_imle_select": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp,
                                             ctypes.c_int32, vp, vp]),
         "pirrt_proposal_backward": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp, vp,
@@ -533,6 +535,19 @@ class Proposal:
                     self._lib.pirrt_proposal_forward(self._h, grids.shape[0], self._dev(grids),
                                                      scene.numel(), self._dev(scene),
                                                      self._dev(noise), out.data_ptr()))
+        return out
+
+    def sample(self, grids, scene, noise, uniform_xy, coin, learned_fraction: float = 0.5):
+        """Mixture of the network's samples and the caller's uniform ones:
+        row r is learned when coin[r] < learned_fraction."""
+        import torch
+        out = torch.empty((scene.numel(), 2), dtype=torch.float32, device="cuda")
+        self._check("pirrt_proposal_sample",
+                    self._lib.pirrt_proposal_sample(self._h, grids.shape[0], self._dev(grids),
+                                                    scene.numel(), self._dev(scene),
+                                                    self._dev(noise), self._dev(uniform_xy),
+                                                    self._dev(coin), float(learned_fraction),
+                                                    out.data_ptr()))
         return out
 
     def imle_select(self, grids, draw_scene, targets, K: int, noise):

@@ -216,6 +216,19 @@ __global__ void imle_select(int n_targets, int K, const float *__restrict__ y,
     }
 }
 
+// 50/50 (or any fraction) mixture with uniform samples: row r keeps the
+// network's output when coin[r] < learned_fraction, else the caller's uniform
+// sample.  The random numbers are inputs, so the mixture is reproducible.
+__global__ void mix_samples(int rows, const float *__restrict__ y, const float *__restrict__ uni,
+                            const float *__restrict__ coin, float learned_fraction,
+                            float *__restrict__ out) {
+    for (int r = blockIdx.x * blockDim.x + threadIdx.x; r < rows; r += gridDim.x * blockDim.x) {
+        const bool learned = coin[r] < learned_fraction;
+        out[2 * r] = learned ? y[2 * r] : uni[2 * r];
+        out[2 * r + 1] = learned ? y[2 * r + 1] : uni[2 * r + 1];
+    }
+}
+
 // draw_scene[t*K + k] = target_scene[t]
 __global__ void repeat_scene(int n_targets, int K, const int32_t *__restrict__ scene,
                              int32_t *__restrict__ out) {

@@ -262,6 +262,24 @@ pirrt_status pirrt_proposal_forward(pirrt_proposal *P, int32_t n_scenes, const f
     return PIRRT_OK;
 }
 
+pirrt_status pirrt_proposal_sample(pirrt_proposal *P, int32_t n_scenes, const float *grids,
+                                   int32_t rows, const int32_t *scene, const float *noise,
+                                   const float *uniform_xy, const float *coin,
+                                   float learned_fraction, float *out_xy) {
+    if (!P || !grids || !scene || !noise || !uniform_xy || !coin || !out_xy ||
+        !(learned_fraction >= 0.f && learned_fraction <= 1.f))
+        return PIRRT_ERR_INVALID_ARG;
+    PCK(cudaSetDevice(P->device));
+    pirrt_status rc = scene_features(P, n_scenes, grids);
+    if (rc) return rc;
+    if ((rc = forward_rows(P, rows, scene, noise))) return rc;
+    mix_samples<<<blocks_for(rows), 256, 0, P->stream>>>(rows, P->y, uniform_xy, coin,
+                                                          learned_fraction, out_xy);
+    PCK(cudaGetLastError());
+    PCK(cudaStreamSynchronize(P->stream));
+    return PIRRT_OK;
+}
+
 pirrt_status pirrt_proposal_imle_select(pirrt_proposal *P, int32_t n_scenes, const float *grids,
                                         int32_t n_targets, const int32_t *draw_scene,
                                         const float *targets, int32_t K, const float *noise,

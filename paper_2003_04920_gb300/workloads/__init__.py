@@ -291,6 +291,47 @@ def roadmap_c3(trial: int = 0, n: int = 4_000_000, block: int = 50_000) -> Roadm
     return roadmap_nd_knn("c3", 3 * 1000 + trial, n, 6, 64, 0.3, 0.8, 30, block)
 
 
+C5_X_INIT = (0.05, 0.05)
+C5_X_GOAL = (0.95, 0.95)
+
+
+def c5_scene(seed: int) -> Scene:
+    """Learned-proposal scene: 200 circles, r ~ U[0.01, 0.04], in the unit
+    square; an obstacle covering x_init = (0.05, 0.05) or x_goal = (0.95, 0.95)
+    is redrawn."""
+    rng = np.random.default_rng(5 * 1000 + int(seed))
+    return _draw_scene(rng, 2, 0.0, 1.0, 200, 0.01, 0.04,
+                       [np.array(C5_X_INIT), np.array(C5_X_GOAL)])
+
+
+def occupancy_grid(scene: Scene, res: int = 64) -> np.ndarray:
+    """res x res occupancy of a 2-D scene, row-major (row = y cell, column =
+    x cell): 1 where the cell centre lies inside an obstacle, else 0."""
+    c = (np.arange(res) + 0.5) / res
+    xx, yy = np.meshgrid(c, c)
+    pts = np.stack([xx.ravel(), yy.ravel()], axis=1) * (scene.hi - scene.lo) + scene.lo
+    return scene.inside(pts).astype(np.float32)
+
+
+def free_uniform(rng: np.random.Generator, scene: Scene, count: int) -> np.ndarray:
+    """``count`` uniform samples of the free space (rejection sampling)."""
+    return _free_samples(rng, scene, count)
+
+
+def roadmap_from_points(name: str, pts: np.ndarray, scene: Scene, k: int | None = None,
+                        cost_dtype=np.float32, exact_segment: bool = True,
+                        n_check: int = 16) -> Roadmap:
+    """Roadmap over given free points (vertex i = pts[i]): symmetrised k-NN,
+    k = ceil(2e ln N) unless given, collision-checked edges, Euclidean costs,
+    one block holding every vertex."""
+    pts = np.ascontiguousarray(pts, dtype=np.float64)
+    n = len(pts)
+    kk = knn_k(n) if k is None else int(k)
+    u, v = _knn_edges(pts, kk)
+    return _finish(name, pts, u, v, scene, cost_dtype, n, exact_segment, n_check,
+                   dict(k=kk, n_obs=len(scene.radii)))
+
+
 def _batch_member(args):
     i, n, d, s = args
     if d == 2:

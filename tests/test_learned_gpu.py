@@ -1,0 +1,69 @@
+"""The learned-proposal workflow end to end at a small scale: planner
+solutions on the GPU (one pirrt_batch per chunk of scenes) against the
+oracle's Dijkstra, the near-path targets, IMLE training and the paired
+mixed-vs-uniform comparison."""
+import math
+
+import numpy as np
+import pytest
+
+from paper_2003_04920_gb300 import learned as L
+from paper_2003_04920_gb300 import workloads as W
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    t = pytest.importorskip("torch")
+    if not t.cuda.is_available():
+        pytest.skip("no CUDA device")
+    return t
+
+
+def test_planner_solutions_match_dijkstra(torch):
+    import oracle
+    rms = L.roadmaps([(s, ("uniform", 3000, 0)) for s in range(6)])
+    sols = L.solve(rms, max_entries=40_000)  # several chunks
+    assert len(sols) == 6
+    for rm, (g, p) in zip(rms, sols):
+        d, _ = oracle.dijkstra(rm[3], rm[0], rm[1], rm[2].astype(np.float64))
+        fin = np.isfinite(d)
+        np.testing.assert_array_equal(np.isfinite(g), fin)
+        np.testing.assert_allclose(g[fin], d[fin], rtol=1e-5)
+        if fin[L.GOAL]:
+            path = L.path_to_root(p, L.GOAL)
+            assert path[-1] == 0
+            # the path's edge lengths add up to g(x_goal)
+            pts = rm[4]
+            length = np.sum(np.linalg.norm(np.diff(pts[path], axis=0), axis=1))
+            assert math.isclose(length, g[L.GOAL], rel_tol=1e-5)
+
+
+def test_training_set_targets_lie_in_the_band(torch):
+    grids, targets, costs, kept = L.training_set(range(6), 3000, band=0.02, chunk=4)
+    assert grids.shape == (len(kept), 4096) and len(targets) == len(kept) > 0
+    for s, t in zip(kept, targets):
+        assert len(t) > 0
+        assert not W.c5_scene(s).inside(t.astype(np.float64)).any()
+    # costs are at least the straight-line distance
+    assert np.all(costs >= np.linalg.norm(L.X_GOAL - L.X_INIT) - 1e-9)
+
+
+def test_train_and_compare_small(torch):
+    from paper_2003_04920_gb300 import Proposal
+    grids, targets, costs, kept = L.training_set(range(8), 3000, chunk=8)
+    prop = Proposal(4, 4 * 16 * 8, seed=1)
+    losses, secs = L.train(prop, grids, targets, 60, scenes_per_step=4, targets_per_scene=16, K=8,
+                           lr=3e-4)
+    assert np.all(np.isfinite(losses)) and losses[-10:].mean() < losses[:10].mean()
+    ev = Proposal(1, 4096, seed=1)
+    ev.set_weights(prop.get_weights())
+    pts = L.learned_points(ev, 123, 2000, 0.5, chunk=4096)
+    assert pts.shape == (2000, 2) and not W.c5_scene(123).inside(pts).any()
+    res = L.compare(ev, [100, 101, 102], [2000], pool_=None)
+    cu, cl = res[2000]
+    assert cu.shape == cl.shape == (3,)
+    summ = L.summarize(res)[2000]
+    assert summ["scenes"] == 3
+    prop.close(); ev.close()

@@ -95,7 +95,9 @@ def test_adam_step_matches_definition(torch):
 
 def test_imle_training_reduces_loss(torch):
     """Targets cluster around a scene-dependent point; IMLE training pulls the
-    nearest draws onto them."""
+    nearest draws onto them.  The learning rate is one at which the exact FP64
+    network trained by the oracle's rule also converges on this data (at 3e-3
+    it saturates the sigmoid, on the CPU as well)."""
     rng = np.random.default_rng(11)
     S, T, K = 6, 128, 8
     grids = (rng.random((S, M.GRID)) < 0.2).astype(np.float32)
@@ -107,6 +109,49 @@ def test_imle_training_reduces_loss(torch):
         sc = rng.integers(0, S, T).astype(np.int32)
         tg = (centers[sc] + rng.normal(0, 0.03, (T, 2))).astype(np.float32)
         nz = rng.normal(size=(T * K, M.NOISE)).astype(np.float32)
-        losses.append(prop.train_step(dev(grids), dev(sc), dev(tg), K, dev(nz), 3e-3))
-    assert np.mean(losses[-10:]) < 0.5 * np.mean(losses[:10])
+        losses.append(prop.train_step(dev(grids), dev(sc), dev(tg), K, dev(nz), 3e-4))
+    assert np.mean(losses[-10:]) < 0.1 * np.mean(losses[:10])
+    prop.close()
+
+
+def test_train_step_is_the_composition_of_its_parts(torch):
+    """train_step == forward of K draws, nearest-draw pick, backward on the
+    picked noise, Adam: run both ways from the same initial weights."""
+    rng = np.random.default_rng(12)
+    S, T, K = 4, 96, 6
+    grids = (rng.random((S, M.GRID)) < 0.3).astype(np.float32)
+    sc = rng.integers(0, S, T).astype(np.int32)
+    tg = rng.uniform(0.1, 0.9, (T, 2)).astype(np.float32)
+    nz = rng.normal(size=(T * K, M.NOISE)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    a = P.Proposal(S, T * K, seed=21)
+    b = P.Proposal(S, T * K, seed=21)
+    la = a.train_step(dev(grids), dev(sc), dev(tg), K, dev(nz), 1e-3)
+    pick = b.imle_select(dev(grids), dev(np.repeat(sc, K)), dev(tg), K, dev(nz)).cpu().numpy()
+    zs = nz.reshape(T, K, -1)[np.arange(T), pick]
+    b.zero_grads()
+    lb = b.backward(dev(grids), dev(sc), dev(zs), dev(tg))
+    b.adam(1e-3)
+    assert abs(la - lb) <= 1e-6 * max(1.0, lb)
+    np.testing.assert_allclose(a.get_weights().cpu().numpy(), b.get_weights().cpu().numpy(),
+                               rtol=0, atol=1e-6)
+    a.close(); b.close()
+
+
+def test_sample_mixture(torch):
+    rng = np.random.default_rng(13)
+    S, R = 3, 500
+    grids = (rng.random((S, M.GRID)) < 0.3).astype(np.float32)
+    sc = rng.integers(0, S, R).astype(np.int32)
+    nz = rng.normal(size=(R, M.NOISE)).astype(np.float32)
+    uni = rng.random((R, 2)).astype(np.float32)
+    coin = rng.random(R).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prop = P.Proposal(S, R, seed=2)
+    y = prop.forward(dev(grids), dev(sc), dev(nz)).cpu().numpy()
+    for frac in (0.0, 0.5, 1.0):
+        out = prop.sample(dev(grids), dev(sc), dev(nz), dev(uni), dev(coin), frac).cpu().numpy()
+        learned = coin < frac
+        np.testing.assert_array_equal(out[learned], y[learned])
+        np.testing.assert_array_equal(out[~learned], uni[~learned])
     prop.close()

@@ -151,6 +151,20 @@ def evaluate_bytes(prof: dict, cost_bytes: int) -> float:
     return prof["evaluate_vertices"] * (4 + cost_bytes + 8)
 
 
+def reduce_over_ranks(elapsed: float, units: float, world: int, device) -> tuple[float, float]:
+    """Whole-job figures of a replicated run: the slowest rank's time (MAX)
+    and the units every rank processed (SUM).  A no-op for one rank."""
+    if world <= 1:
+        return elapsed, units
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([elapsed], dtype=torch.float64, device=device)
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    u = torch.tensor([units], dtype=torch.float64, device=device)
+    dist.all_reduce(u, op=dist.ReduceOp.SUM)
+    return float(t.item()), float(u.item())
+
+
 def run_ours(args) -> None:
     import torch
     import torch.distributed as dist
@@ -233,13 +247,7 @@ def run_ours(args) -> None:
 
     total_ms = float(sum(times))
     total_relax = float(sum(relaxes))
-    if world > 1:
-        t = torch.tensor([total_ms], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        total_ms = float(t.item())
-        r = torch.tensor([total_relax], dtype=torch.float64, device="cuda")
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-        total_relax = float(r.item())
+    total_ms, total_relax = reduce_over_ranks(total_ms, total_relax, world, "cuda")
     value = total_relax / (total_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
@@ -260,13 +268,7 @@ def run_ours(args) -> None:
         e2e_relax += r
     torch.cuda.synchronize()
     e2e_s = time.perf_counter() - t0
-    if world > 1:
-        t = torch.tensor([e2e_s], dtype=torch.float64, device="cuda")
-        dist.all_reduce(t, op=dist.ReduceOp.MAX)
-        e2e_s = float(t.item())
-        r = torch.tensor([float(e2e_relax)], dtype=torch.float64, device="cuda")
-        dist.all_reduce(r, op=dist.ReduceOp.SUM)
-        e2e_relax = float(r.item())
+    e2e_s, e2e_relax = reduce_over_ranks(e2e_s, float(e2e_relax), world, "cuda")
     h2d = rm.m * (4 + 4 + cost_bytes)
     d2h = rm.n * (8 + 4)
 

@@ -488,6 +488,7 @@ class Proposal:
         if rc:
             raise PirrtError("pirrt_proposal_create", rc)
         self._h = h
+        self.max_scenes, self.max_rows = int(max_scenes), int(max_rows)
         self.n_params = int(self._lib.pirrt_proposal_num_params())
 
     def close(self):

@@ -194,6 +194,7 @@ def learned_points(prop, seed: int, n: int, fraction: float = 0.5, stream: int =
     sc = W.c5_scene(seed)
     grid = torch.from_numpy(W.occupancy_grid(sc)[None]).cuda()
     rng = np.random.default_rng([int(seed), int(n), int(stream), 1])
+    chunk = min(int(chunk), prop.max_rows)
     out, have = [], 0
     scene = torch.zeros(chunk, dtype=torch.int32, device="cuda")
     while have < n - 2:

@@ -1,0 +1,87 @@
+"""Parity at the benchmark's full sizes, in the launch configuration that
+bench.py times.
+
+The whole Batched-Extension schedule (Alg. 3) of the 6-D roadmap (N =
+4,000,000, k = 30, blocks of 50,000: 80 exploitation rounds) and of the 2-D
+roadmap (N = 1,000,000, k = 76, blocks of 10,000: 100 rounds) runs from
+device-resident blocks with the default options, every exploit one CUDA-graph
+launch, exactly as in the benchmark's timed steps.  The oracle cannot replay
+policy iteration at these sizes in seconds, so the checks are what holds at
+any size and what the oracle computes directly:
+
+* the final tree against the oracle's FP64 Dijkstra on the final graph (the
+  fixpoint of every schedule is the shortest-path tree, Sec. V correctness),
+  with the parity rule of the small cases: g within 1e-5 relative, parents
+  bit-exact wherever the runner-up is more than 1e-6 relative worse;
+* the same after an intermediate block, on the graph present at that point;
+* on every entry: the Bellman inequality, g(v) = g(p(v)) + c(p(v), v), and a
+  parent tree rooted at vertex 0 with -1 exactly outside the root's component.
+"""
+import numpy as np
+import pytest
+
+import oracle as O
+import paper_2003_04920_gb300 as P
+from paper_2003_04920_gb300 import workloads as W
+from tests.gpu_util import assert_parity
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def torch():
+    torch = pytest.importorskip("torch")
+    if not torch.cuda.is_available():
+        pytest.skip("no CUDA device")
+    P.load_library()
+    return torch
+
+
+def _prefix(rm, v1, e1):
+    return W.Roadmap(rm.name, rm.points[:v1], rm.u[:e1], rm.v[:e1], rm.cost[:e1],
+                     rm.edge_start[:v1 + 1], rm.block)
+
+
+def _full_schedule(torch, rm, check_block):
+    """The benchmark's step (device inputs, graph-launched exploits); the tree
+    after block `check_block` and after the last block, with the stats."""
+    dev = [torch.from_numpy(a).cuda() for a in (rm.u, rm.v, rm.cost)]
+    stream = torch.cuda.current_stream()
+    mid = None
+    stats = []
+    with P.Graph(rm.n, rm.m, 0, rm.cost.dtype, stream=stream.cuda_stream) as G:
+        for b, (v0, v1, e0, e1) in enumerate(rm.blocks()):
+            G.insert_batch(v1 - v0, dev[0][e0:e1], dev[1][e0:e1], dev[2][e0:e1])
+            stats.append(G.exploit())
+            if b == check_block:
+                mid = (v1, e1, G.get_costs(), G.get_parents())
+        g, p = G.get_costs(), G.get_parents()
+    return mid, g, p, stats
+
+
+def _check(rm, g, p):
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    try:
+        d, _ = A.dijkstra()
+        mask = assert_parity(rm, g, p, d, csr=A)
+    finally:
+        A.close()
+    return mask
+
+
+@pytest.mark.parametrize("name,fn,kw,check_block", [
+    ("c3", W.roadmap_c3, dict(trial=0), 39),
+    ("c2-companion", W.roadmap_c2, dict(trial=0, companion=True), 49),
+])
+def test_full_size_schedule_matches_dijkstra(torch, name, fn, kw, check_block):
+    rm = W.cached(name, fn, **kw)
+    mid, g, p, stats = _full_schedule(torch, rm, check_block)
+    assert len(stats) == rm.n_blocks()
+    assert all(s["converged"] == 1 for s in stats)
+    assert all(s["graph_launch"] == 1 for s in stats)
+    v1, e1, g_mid, p_mid = mid
+    mask_mid = _check(_prefix(rm, v1, e1), g_mid, p_mid)
+    mask = _check(rm, g, p)
+    # nearly every parent is unambiguous at these sizes
+    assert mask.mean() > 0.99 and mask_mid.mean() > 0.99
+    assert np.isfinite(g).mean() > 0.5

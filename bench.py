@@ -131,24 +131,34 @@ class ClockSampler:
                 "reasons": sorted(reasons), "samples": len(rows)}
 
 
-def improve_bytes(prof: dict, n: int, entry_bytes: int, cost_bytes: int) -> float:
-    """Algorithmic (compulsory) HBM bytes of all Improve launches: every CSR
-    entry scanned (col + cost), per processed vertex its row offset, parent,
-    parent-edge cost and the parent's g, the list id in sparse sweeps, g of
-    every vertex once per dense sweep, and the parent / cost writes of each
-    switch.  Gathers of g(u) in sparse sweeps are not counted (lower bound)."""
+def improve_bytes(prof: dict, entry_bytes: int, cost_bytes: int, offers: bool) -> float:
+    """Algorithmic (compulsory) HBM bytes of all Improve launches.  Every CSR
+    entry scanned (col + cost); per vertex of a dense sweep its row offsets,
+    parent, parent-edge cost, the parent's g and its own g; per listed vertex
+    the list id, parent, parent-edge cost and the parent's g, plus its row
+    offsets (full scans) or its best offer (candidate offers, where only the
+    deciding vertices -- at least every switch -- read their row offsets);
+    the parent / cost writes and the switch-list id of each switch.  Gathers
+    of g(u) for scanned entries are not counted (a lower bound)."""
     entries = prof["improve_entries"]
     verts = prof["improve_vertices"]
     dense_v = prof["improve_dense_vertices"]
     sparse_v = verts - dense_v
-    per_vertex = 8 + 4 + cost_bytes + 8
-    return (entries * entry_bytes + verts * per_vertex + sparse_v * 4 + dense_v * 8
-            + prof["improve_switches"] * (4 + cost_bytes + 4))
+    sw = prof["improve_switches"]
+    dense = dense_v * (8 + 4 + cost_bytes + 8 + 8)
+    if offers:
+        sparse = sparse_v * (4 + 4 + cost_bytes + 8 + 8) + sw * 8
+    else:
+        sparse = sparse_v * (4 + 8 + 4 + cost_bytes + 8)
+    return entries * entry_bytes + dense + sparse + sw * (4 + cost_bytes + 4)
 
 
-def evaluate_bytes(prof: dict, cost_bytes: int) -> float:
-    """Evaluate: read p and the parent-edge cost, write g, per vertex."""
-    return prof["evaluate_vertices"] * (4 + cost_bytes + 8)
+def evaluate_bytes(prof: dict, entry_bytes: int, cost_bytes: int) -> float:
+    """Evaluate: per recomputed vertex its parent, parent-edge cost, the
+    parent's g and the g write; per candidate offer the CSR entry it comes
+    from (offer updates themselves are not counted)."""
+    return (prof["evaluate_vertices"] * (4 + cost_bytes + 8 + 8)
+            + prof.get("evaluate_offers", 0) * entry_bytes)
 
 
 def reduce_over_ranks(elapsed: float, units: float, world: int, device) -> tuple[float, float]:
@@ -288,28 +298,37 @@ def run_ours(args) -> None:
     d2h = rm.n * (8 + 4)
 
     peak, peak_src = measured_peaks()
+    offers = args.tile == 0
     kernels = {}
-    for name, ms_key, launches_key, nbytes in (
-            ("improve", "improve_ms", "improve_launches", improve_bytes(prof, rm.n, entry_bytes, cost_bytes)),
-            ("evaluate", "evaluate_ms", "evaluate_launches", evaluate_bytes(prof, cost_bytes)),
-            ("mark_frontier", "mark_ms", "mark_launches", None),
-            ("insert", "insert_ms", "insert_calls", prof["insert_new_entries"] * entry_bytes)):
+    kbytes = {"improve": improve_bytes(prof, entry_bytes, cost_bytes, offers),
+              "evaluate": evaluate_bytes(prof, entry_bytes, cost_bytes),
+              "mark_frontier": None,
+              "insert": prof["insert_new_entries"] * entry_bytes}
+    for name, ms_key, launches_key in (
+            ("improve", "improve_ms", "improve_launches"),
+            ("evaluate", "evaluate_ms", "evaluate_launches"),
+            ("mark_frontier", "mark_ms", "mark_launches"),
+            ("insert", "insert_ms", "insert_calls")):
         ms = prof[ms_key]
+        nbytes = kbytes[name]
         k = {"ms": round(ms, 3), "launches": prof[launches_key],
              "share_of_step": round(ms / prof_ms, 4) if prof_ms else None}
         if nbytes is not None and ms > 0:
             k["algorithmic_gbs"] = round(nbytes / (ms / 1e3) / 1e9, 1)
+            k["algorithmic_bytes"] = int(nbytes)
         kernels[name] = k
-    imp_bytes = improve_bytes(prof, rm.n, entry_bytes, cost_bytes)
-    launches = max(1, prof["improve_launches"])
-    imp_ms_avg = prof["improve_ms"] / launches
-    achieved = (imp_bytes / launches) / (imp_ms_avg / 1e3) / 1e9 if imp_ms_avg > 0 else 0.0
+    # the dominant kernel: the largest share of the profiled step
+    dom = max(("improve", "evaluate", "insert"), key=lambda k: kernels[k]["ms"])
+    launches = max(1, kernels[dom]["launches"])
+    dom_ms_avg = kernels[dom]["ms"] / launches
+    dom_bytes = kbytes[dom]
+    achieved = (dom_bytes / launches) / (dom_ms_avg / 1e3) / 1e9 if dom_ms_avg > 0 else 0.0
     traffic = None
-    tpath = os.path.join(ROOT, "profiles", "improve_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        if tj.get("workload") == args.workload and tj.get("kernel_hash") == kernel_hash():
+        if tj.get("workload") == args.workload and tj.get("kernel_hash") == kernel_hash(dom):
             traffic = tj.get("traffic_bytes_per_launch")
 
     line = {
@@ -324,7 +343,9 @@ def run_ours(args) -> None:
                    "evaluate": args.evaluate,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": dict(extra),
-                   "improve_kernel": {0: "lane groups, FP32 screening", 1: "staged bulk copies",
+                   "improve_kernel": {0: "candidate offers; dense sweeps by lane groups with "
+                                         "FP32 screening",
+                                      2: "lane groups, FP32 screening", 1: "staged bulk copies",
                                       3: "lane groups, exact FP64"}[args.tile],
                    "improve_lanes_per_vertex": args.group or (4 if args.tile == 0 else 8),
                    "timing": ("each exploit one CUDA-graph launch; per-kernel split and roofline "
@@ -336,13 +357,13 @@ def run_ours(args) -> None:
                    "parallelism": f"replicas x{world}",
                    "l2": "inputs larger than L2 (CSR ~%.2f GB) and L2 flushed between steps"
                          % (2 * rm.m * entry_bytes / 1e9)},
-        "roofline": {"bound": "hbm", "kernel": "improve", "achieved": round(achieved, 1),
+        "roofline": {"bound": "hbm", "kernel": dom, "achieved": round(achieved, 1),
                      "peak": peak, "unit": "GB/s", "frac": round(achieved / peak, 4),
                      "peak_source": f"{peak_src} copy bandwidth",
                      "frac_of_nominal_8tbs": round(achieved / 8000.0, 4),
                      "traffic": traffic,
-                     "bytes_per_launch": round(imp_bytes / launches, 1),
-                     "avg_launch_ms": round(imp_ms_avg, 5)},
+                     "bytes_per_launch": round(dom_bytes / launches, 1),
+                     "avg_launch_ms": round(dom_ms_avg, 5)},
         "kernels": kernels,
         "e2e": {"value": round(e2e_relax / e2e_s, 1), "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
@@ -359,10 +380,18 @@ def run_ours(args) -> None:
         dist.destroy_process_group()
 
 
-def kernel_hash() -> str:
+KERNEL_FILES = {"improve": ("improve_push.cuh", "improve_screen.cuh", "graph_kernels.cuh",
+                            "device_common.cuh"),
+                "evaluate": ("graph_kernels.cuh", "evaluate_async.cuh", "device_common.cuh"),
+                "insert": ("graph_kernels.cuh", "device_common.cuh")}
+
+
+def kernel_hash(kernel: str) -> str:
+    """Hash of the sources a kernel is built from: a stored DRAM traffic
+    figure is used only while it matches."""
     import hashlib
     h = hashlib.sha1()
-    for f in ("improve_screen.cuh", "device_common.cuh"):
+    for f in KERNEL_FILES[kernel]:
         with open(os.path.join(ROOT, "paper_2003_04920_gb300", "csrc", f), "rb") as fh:
             h.update(fh.read())
     return h.hexdigest()[:12]
@@ -474,7 +503,7 @@ def run_batch(args) -> None:
     B.set_profiling(False)
     peak, peak_src = measured_peaks()
     launches = max(1, prof["improve_launches"])
-    imp_bytes = improve_bytes(prof, sum(r.n for r in rms), 8, 4)
+    imp_bytes = improve_bytes(prof, 8, 4, best.get("tile", 0) == 0)
     imp_avg = prof["improve_ms"] / launches
     achieved = (imp_bytes / launches) / (imp_avg / 1e3) / 1e9 if imp_avg > 0 else 0.0
     line = {
@@ -553,7 +582,7 @@ def main():
     ap.add_argument("--group", type=int, default=0)
     ap.add_argument("--tile", type=int, default=0)
     ap.add_argument("--dense-fraction", type=float, default=0.0)
-    ap.add_argument("--evaluate", choices=("auto", "wave", "jump"), default="auto")
+    ap.add_argument("--evaluate", choices=("auto", "wave", "jump", "async"), default="auto")
     ap.add_argument("--wave-levels", type=int, default=0)
     ap.add_argument("--timing", choices=("graph", "profiled"), default="graph")
     ap.add_argument("--profile-steps", type=int, default=1)

@@ -73,14 +73,18 @@ typedef struct {
     int32_t max_iters;      /* cap on Improve rounds; 0 = |V| + 2 */
     int32_t group;          /* lanes per vertex of the lane-group Improve kernels: 2 (screened
                                only), 4, 8, 16 or 32; 0 = tuned (4 screened, 8 exact) */
-    int32_t tile;           /* Improve kernel: 0 = lane groups with FP32 screening (FP64
-                               costs: exact lane groups); 1 = staged (a producer warp bulk-
+    int32_t tile;           /* Improve kernel: 0 = list sweeps from candidate offers (every
+                               vertex whose g changed offers g(u) + c(u, v) to each neighbour
+                               while its row is scanned; a listed vertex reads its row only
+                               when the best offer beats its parent), dense sweeps as tile 2;
+                               2 = lane groups with FP32 screening (FP64 costs: exact lane
+                               groups) for every sweep; 1 = staged (a producer warp bulk-
                                copies 32-row tiles into a 4-stage shared-memory ring for 8
                                consumer warps); 3 = lane groups, exact FP64 for every
-                               candidate */
-    int32_t evaluate;       /* PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE or PIRRT_EVAL_JUMP */
-    int32_t wave_levels;    /* level cap of the top-down Evaluate before it hands over to
-                               pointer jumping; 0 = tuned */
+                               candidate.  All give the same parents and g. */
+    int32_t evaluate;       /* PIRRT_EVAL_AUTO, _WAVE, _JUMP or _ASYNC */
+    int32_t wave_levels;    /* AUTO: level cap of the top-down Evaluate before it hands over
+                               to pointer jumping; 0 = tuned */
     int32_t host_loop;      /* 1 = drive the Replan loop from the host, one counter read per
                                iteration; 0 = one CUDA-graph launch for the whole loop (a WHILE
                                node repeats Improve / Evaluate on the device).  Profiling
@@ -89,22 +93,28 @@ typedef struct {
                                Improve sweeps every vertex instead of a list; 0 = tuned */
 } pirrt_exploit_opts;
 
-/* Evaluate strategies.  Both compute g(v) = g(p(v)) + c(p(v), v) from the root
+/* Evaluate strategies.  All compute g(v) = g(p(v)) + c(p(v), v) from the root
  * in FP64 (Alg. 2 Evaluate):
- *   WAVE -- top-down over the policy tree, level by level, only below the
- *           vertices whose parent switched, pruning where g is unchanged; the
- *           next Improve frontier is marked in the same row scan.  Sums are
- *           taken root-to-leaf, one addition per edge, as in Alg. 2.
- *   JUMP -- pointer jumping (parent doubling) over every vertex in about
- *           log2(depth) rounds; the sums are reassociated (within a few ulp).
- *   AUTO -- WAVE, handing over to JUMP when a wave exceeds its level cap. */
-enum { PIRRT_EVAL_AUTO = 0, PIRRT_EVAL_WAVE = 1, PIRRT_EVAL_JUMP = 2 };
+ *   WAVE  -- top-down over the policy tree, level by level, only below the
+ *            vertices whose parent switched, pruning where g is unchanged; the
+ *            next Improve frontier is marked in the same row scan.  Sums are
+ *            taken root-to-leaf, one addition per edge, as in Alg. 2.  Levels
+ *            are separated by a grid-wide barrier.
+ *   JUMP  -- pointer jumping (parent doubling) over every vertex in about
+ *            log2(depth) rounds; the sums are reassociated (within a few ulp).
+ *   ASYNC -- the same walk as WAVE without level barriers: each CTA follows
+ *            subtrees on its own and g is lowered by an atomic minimum, which
+ *            no stale value can defeat because Improve never raises a
+ *            cost-to-come (Sec. V policy improvement).  Same sums, bit for bit.
+ *   AUTO  -- WAVE, handing over to JUMP when a wave exceeds its level cap. */
+enum { PIRRT_EVAL_AUTO = 0, PIRRT_EVAL_WAVE = 1, PIRRT_EVAL_JUMP = 2, PIRRT_EVAL_ASYNC = 3 };
 
 /* Filled by pirrt_graph_exploit. */
 typedef struct {
     int32_t iterations;     /* Improve rounds run (the last one switched nothing if converged) */
     int32_t converged;      /* 1 if the policy is stable */
-    int64_t relaxations;    /* adjacency entries scanned by Improve, i.e. candidates g(u)+c(u,v) */
+    int64_t relaxations;    /* candidates g(u) + c(u, v) formed: adjacency entries scanned by
+                               Improve, plus the offers made by Evaluate (tile 0) */
     int64_t improved;       /* vertices processed by Improve, summed over rounds */
     int64_t switches;       /* parent switches, summed over rounds */
     int64_t evaluated;      /* vertices whose g Evaluate recomputed, summed over rounds */
@@ -120,7 +130,7 @@ typedef struct pirrt_graph pirrt_graph;   /* opaque, library-owned */
 
 /* Allocate an empty graph (no vertices) with the given capacities on
  * cfg->device.  Device memory: about 2 x 8 B x (max_vertices + 1) row offsets,
- * 2 x (8 or 16 B) x 2 x max_edges CSR entries, and about 80 B per vertex of
+ * 2 x (8 or 16 B) x 2 x max_edges CSR entries, and about 110 B per vertex of
  * policy and work arrays.  *out is set to NULL on failure. */
 pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out);
 
@@ -200,6 +210,7 @@ typedef struct {
     int64_t improve_entries, improve_vertices, improve_dense_vertices, improve_switches;
     int64_t evaluate_vertices, evaluate_visits, mark_vertices;
     int64_t insert_new_entries, insert_copied_entries;
+    int64_t evaluate_offers;  /* candidates offered by Evaluate to the next Improve (tile 0) */
 } pirrt_profile;
 
 /* Clear the profile and turn event timing on (enable = 1) or off (0). */
@@ -219,6 +230,7 @@ typedef struct {
     int32_t wave_levels;      /* top-down Evaluate levels (0 for pointer jumping) */
     int32_t next_frontier;    /* size of the next Improve list (0 if the next sweep is dense) */
     float improve_ms, evaluate_ms, mark_ms, iteration_ms;  /* CUDA-event times */
+    int64_t offers;           /* candidates offered by this iteration's Evaluate */
 } pirrt_trace_record;
 
 /* Copy up to cap trace records (oldest first) recorded since the last

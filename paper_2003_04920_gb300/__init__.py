@@ -35,7 +35,9 @@ PIRRT_COST_F64 = 1
 PIRRT_EVAL_AUTO = 0
 PIRRT_EVAL_WAVE = 1
 PIRRT_EVAL_JUMP = 2
-EVALUATE_MODES = {"auto": PIRRT_EVAL_AUTO, "wave": PIRRT_EVAL_WAVE, "jump": PIRRT_EVAL_JUMP}
+PIRRT_EVAL_ASYNC = 3
+EVALUATE_MODES = {"auto": PIRRT_EVAL_AUTO, "wave": PIRRT_EVAL_WAVE, "jump": PIRRT_EVAL_JUMP,
+                  "async": PIRRT_EVAL_ASYNC}
 
 
 class pirrt_config(ctypes.Structure):
@@ -73,7 +75,8 @@ class pirrt_profile(ctypes.Structure):
                 ("improve_vertices", ctypes.c_int64), ("improve_dense_vertices", ctypes.c_int64),
                 ("improve_switches", ctypes.c_int64), ("evaluate_vertices", ctypes.c_int64),
                 ("evaluate_visits", ctypes.c_int64), ("mark_vertices", ctypes.c_int64),
-                ("insert_new_entries", ctypes.c_int64), ("insert_copied_entries", ctypes.c_int64)]
+                ("insert_new_entries", ctypes.c_int64), ("insert_copied_entries", ctypes.c_int64),
+                ("evaluate_offers", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -85,7 +88,8 @@ class pirrt_trace_record(ctypes.Structure):
                 ("switches", ctypes.c_int32), ("changed", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("next_frontier", ctypes.c_int32),
                 ("improve_ms", ctypes.c_float), ("evaluate_ms", ctypes.c_float),
-                ("mark_ms", ctypes.c_float), ("iteration_ms", ctypes.c_float)]
+                ("mark_ms", ctypes.c_float), ("iteration_ms", ctypes.c_float),
+                ("offers", ctypes.c_int64)]
 
 
 _lib = None

@@ -111,6 +111,7 @@ struct DevCounters {
     unsigned long long improved;  // vertices processed by Improve (whole exploit)
     unsigned long long evaluated; // vertices whose g was recomputed (whole exploit)
     unsigned long long switches;  // parent switches (whole exploit)
+    unsigned long long offers;    // candidates offered to the next Improve (whole exploit)
     unsigned long long dj_bits;   // Delta g of the current Improve (bits of a double >= 0)
     unsigned n_active;            // size of the current Improve list
     unsigned n_next;              // size of the list being built for the next Improve

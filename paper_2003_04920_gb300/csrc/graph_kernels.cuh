@@ -16,6 +16,16 @@ namespace pirrt {
 
 constexpr int kThreads = 256;
 
+// Candidate offers for the next Improve (see improve_push.cuh): cand[v] is
+// the minimum, on FP64 bits, of the values g(u) + c(u, v) offered by
+// neighbours u whose g changed; +inf bits when nothing was offered.
+constexpr unsigned long long kCandNone = 0x7ff0000000000000ull;
+
+// Offer g(u) + c(u, v) to v: an atomic minimum whose result is not used.
+__device__ __forceinline__ void offer(unsigned long long *cand, int32_t v, double val) {
+    atomicMin(cand + v, (unsigned long long)__double_as_longlong(val));
+}
+
 // ---------------------------------------------------------------------------
 // Insertion
 // ---------------------------------------------------------------------------
@@ -153,6 +163,7 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
                const CT *__restrict__ cost, const int64_t *__restrict__ new_off,
                int32_t *__restrict__ deg, Entry<CT> *__restrict__ adj, unsigned *__restrict__ stamp,
                int32_t root, int32_t *__restrict__ list0, int32_t *__restrict__ list1,
+               const double *__restrict__ g, unsigned long long *__restrict__ cand,
                DevCounters *ctr) {
     const unsigned epoch = ctr->epoch;
     int32_t *active = (ctr->la & 1u) ? list1 : list0;
@@ -174,6 +185,10 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
             eb.w = w;
             adj[sa] = ea;
             adj[sb] = eb;
+            // the new edge offers each endpoint the other's candidate
+            const double ga = g[a], gb = g[b];
+            if (b != root && ga < CUDART_INF) offer(cand, b, ga + widen(w));
+            if (a != root && gb < CUDART_INF) offer(cand, a, gb + widen(w));
             pa = a != root && atomicExch(&stamp[a], epoch) != epoch;
             pb = b != root && atomicExch(&stamp[b], epoch) != epoch;
         }
@@ -192,8 +207,8 @@ template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__restrict__ g,
                      float *__restrict__ g32, int32_t *__restrict__ p, CT *__restrict__ pc,
-                     unsigned *__restrict__ stamp, int32_t *__restrict__ list0,
-                     int32_t *__restrict__ list1, DevCounters *ctr) {
+                     unsigned long long *__restrict__ cand, unsigned *__restrict__ stamp,
+                     int32_t *__restrict__ list0, int32_t *__restrict__ list1, DevCounters *ctr) {
     const unsigned epoch = ctr->epoch;
     int32_t *active = (ctr->la & 1u) ? list1 : list0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
@@ -205,6 +220,7 @@ insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__res
             g32[v] = (v == root) ? 0.0f : __int_as_float(0x7f800000);
             p[v] = (v == root) ? kRootMark : -1;
             pc[v] = CT(0);
+            cand[v] = kCandNone;
             pred = v != root && atomicExch(&stamp[v], epoch) != epoch;
         }
         warp_append(pred, (int32_t)v, active, &ctr->n_active);
@@ -236,6 +252,9 @@ struct ImproveArgs {
     DevCounters *ctr;
     int64_t n;
     int32_t root;
+    int32_t push;            // list sweeps run from offers (improve_push_kernel); this
+                             // kernel then only runs dense sweeps
+    unsigned long long *cand;
 };
 
 // G lanes cooperate on one vertex: each lane scans every G-th entry of the
@@ -255,6 +274,7 @@ improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     const int groups_per_block = kThreads / G;
     const int64_t gstride = (int64_t)gridDim.x * groups_per_block;
     const bool dense = a.ctr->dense != 0u;
+    if (a.push && !dense) return;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const unsigned long long gpol = policy_evict_last();
 
@@ -491,6 +511,9 @@ struct MarkArgs {
     int32_t root;
     unsigned dense_limit;  // |dg| above this -> dense sweep next
     int32_t role;          // 0: after every Evaluate; 1: only after a pointer-jumping finish
+    int32_t push;          // offer g(x) + c(x, u) to every neighbour u
+    const double *g;
+    unsigned long long *cand;
 };
 
 template <typename CT>
@@ -510,21 +533,31 @@ mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
     // one warp per changed vertex; lanes stride over its row
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    unsigned long long offers = 0;
     for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n_dg;
          j += warps) {
         const int32_t x = a.dg[j];
         const int64_t b = a.row_off[x], e = a.row_off[x + 1];
+        const double gx = a.push ? a.g[x] : 0.0;
         for (int64_t i0 = b; i0 < e; i0 += 32) {
             const int64_t i = i0 + lane;
             bool pred = false;
             int32_t u = 0;
             if (i < e) {
-                u = __ldg(&a.adj[i].col);
+                const Entry<CT> en = a.adj[i];
+                u = en.col;
+                if (a.push && u != a.root) {
+                    offer(a.cand, u, gx + widen(en.w));
+                    ++offers;
+                }
                 pred = u != a.root && atomicExch(&a.stamp[u], epoch) != epoch;
             }
             warp_append(pred, u, next, &c->n_next);
         }
     }
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) offers += __shfl_down_sync(0xffffffffu, offers, off);
+    if (lane == 0 && offers) atomicAdd(&c->offers, offers);
 }
 
 // ---------------------------------------------------------------------------
@@ -550,6 +583,8 @@ struct WaveArgs {
     int32_t root;
     unsigned dense_limit;     // |changed| above this -> dense sweep next, stop marking
     unsigned max_levels;      // give up (wave_incomplete) after this many levels
+    int32_t push;             // offer g(u) + c(u, w) to every neighbour w of a changed u
+    unsigned long long *cand;
 };
 
 // A vertex u on level t takes g(u) = g(p(u)) + c(p(u), u), one FP64 addition
@@ -577,6 +612,7 @@ __global__ void __launch_bounds__(kWaveThreads)
 wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
     const WaveArgs<CT> a = *ap;
     __shared__ int32_t s_u[kWaveThreads];
+    __shared__ double s_gn[kWaveThreads];
     __shared__ long long s_base[kWaveThreads];
     __shared__ int32_t s_seg[kWaveThreads + 1];
     __shared__ int32_t s_wsum[kWaveThreads / 32];
@@ -590,7 +626,7 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const unsigned long long gpol = policy_evict_last();
-    unsigned long long recomputed = 0, changed_total = 0;
+    unsigned long long recomputed = 0, changed_total = 0, offers = 0;
     unsigned t = 0;
     for (;; ++t) {
         const int64_t count =
@@ -626,6 +662,7 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
                     const long long b = a.row_off[u];
                     deg = (int)(a.row_off[u + 1] - b);
                     s_base[tid] = b;
+                    s_gn[tid] = gn;
                 }
             }
             s_u[tid] = u;
@@ -666,7 +703,12 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
                             if (s_seg[mid] <= pos) l = mid; else h = mid;
                         }
                         owner[j] = s_u[l];
-                        w[j] = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]).col;
+                        const Entry<CT> en = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]);
+                        w[j] = en.col;
+                        if (a.push && marking && en.col != a.root) {
+                            offer(a.cand, en.col, s_gn[l] + widen(en.w));
+                            ++offers;
+                        }
                     }
                 }
                 unsigned childm = 0, markm = 0;
@@ -705,8 +747,12 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
         if (!grid_barrier(c, nblocks)) return;
     }
 #pragma unroll
-    for (int off = 16; off > 0; off >>= 1) recomputed += __shfl_down_sync(0xffffffffu, recomputed, off);
+    for (int off = 16; off > 0; off >>= 1) {
+        recomputed += __shfl_down_sync(0xffffffffu, recomputed, off);
+        offers += __shfl_down_sync(0xffffffffu, offers, off);
+    }
     if (lane == 0 && recomputed) atomicAdd(&c->evaluated, recomputed);
+    if (lane == 0 && offers) atomicAdd(&c->offers, offers);
     if (blockIdx.x == 0 && tid == 0) c->wave_levels = t;
 }
 
@@ -784,6 +830,7 @@ static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
     c->improved = 0ull;
     c->evaluated = 0ull;
     c->switches = 0ull;
+    c->offers = 0ull;
     c->dense_next = 0u;
     c->iter = 0u;
     c->max_iters = max_iters;

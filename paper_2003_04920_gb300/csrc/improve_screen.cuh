@@ -40,6 +40,7 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
     const int gpb = 256 / G;
     const int64_t gstride = (int64_t)gridDim.x * gpb;
     const bool dense = a.ctr->dense != 0u;
+    if (a.push && !dense) return;  // list sweeps run from offers
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const float kInf = __int_as_float(0x7f800000);
     unsigned long long relax = 0, improved = 0, djmax = 0;

@@ -20,7 +20,9 @@
 #include <string>
 #include <vector>
 
+#include "evaluate_async.cuh"
 #include "graph_kernels.cuh"
+#include "improve_push.cuh"
 #include "improve_screen.cuh"
 #include "improve_tma.cuh"
 #include "pirrt.h"
@@ -30,7 +32,8 @@ using namespace pirrt;
 namespace {
 // Offsets of the kernel argument structs in the device argument block.
 constexpr size_t kArgImprove = 0, kArgEval = 512, kArgEvalFallback = 1024, kArgWave = 1536,
-                 kArgMark = 2048, kArgMarkFallback = 2560, kArgEvalForce = 3072, kArgBytes = 4096;
+                 kArgMark = 2048, kArgMarkFallback = 2560, kArgEvalForce = 3072, kArgAsync = 3584,
+                 kArgBytes = 4096;
 }  // namespace
 
 struct pirrt_graph {
@@ -58,7 +61,12 @@ struct pirrt_graph {
     double *acc[2] = {nullptr, nullptr};
     int32_t *done = nullptr;
     int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
-    unsigned *wstamp = nullptr;           // wave child dedup
+    unsigned *wstamp = nullptr;           // wave child dedup; first-change stamps
+    unsigned *swstamp = nullptr;          // barrier-free Evaluate: switched-vertex stamps
+    unsigned long long *cand = nullptr;   // candidate offers for the next Improve
+    AsyncQueue *aq = nullptr;             // barrier-free Evaluate: walk state
+    AsyncItem *aring = nullptr;           // barrier-free Evaluate: spill list
+    int async_dirty = 0;                  // an exploit failed: reset the walk state first
     int32_t *pexport = nullptr;           // parents as reported (root marker -> -1)
     int deep_hint = 0;                    // AUTO: recent exploits met waves past the cap
     int exploits = 0;
@@ -70,9 +78,10 @@ struct pirrt_graph {
         int64_t n = -1;
         int cur = -1;
         unsigned dense_limit = 0, max_levels = 0;
+        int push = -1;
         bool operator==(const ArgsKey &o) const {
             return n == o.n && cur == o.cur && dense_limit == o.dense_limit &&
-                   max_levels == o.max_levels;
+                   max_levels == o.max_levels && push == o.push;
         }
     } args_key;
     std::map<unsigned long long, cudaGraphExec_t> loops;  // captured Replan loops
@@ -81,6 +90,7 @@ struct pirrt_graph {
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int eval_blocks = 0;
     int wave_blocks = 0;
+    int async_blocks = 0;
     int profiling = 0;
     pirrt_profile prof{};
     std::vector<pirrt_trace_record> trace;
@@ -150,12 +160,13 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
 // Write every kernel argument struct of the exploit path into the device
 // argument block (stream-ordered; skipped when nothing changed).
 template <typename CT>
-pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels) {
+pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels, int push) {
     pirrt_graph::ArgsKey key;
     key.n = G->n;
     key.cur = G->cur;
     key.dense_limit = dense_limit;
     key.max_levels = max_levels;
+    key.push = push;
     if (key == G->args_key) return PIRRT_OK;
     std::memset(G->hargs, 0, kArgBytes);
     const Entry<CT> *adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
@@ -172,6 +183,8 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     ia->ctr = G->ctr;
     ia->n = G->n;
     ia->root = G->cfg.root;
+    ia->push = push;
+    ia->cand = G->cand;
     for (size_t off : {kArgEval, kArgEvalFallback, kArgEvalForce}) {
         auto *ea = reinterpret_cast<EvaluateArgs<CT> *>(G->hargs + off);
         ea->p = G->p;
@@ -210,6 +223,31 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->root = G->cfg.root;
     wa->dense_limit = dense_limit;
     wa->max_levels = max_levels;
+    wa->push = push;
+    wa->cand = G->cand;
+    auto *aa = reinterpret_cast<AsyncArgs<CT> *>(G->hargs + kArgAsync);
+    aa->row_off = G->row_off[G->cur];
+    aa->adj = adj;
+    aa->p = G->p;
+    aa->pc = static_cast<const CT *>(G->pc);
+    aa->g = G->g;
+    aa->g32 = G->g32;
+    aa->switched = G->switched;
+    aa->dg = G->dg;
+    aa->wstamp = G->wstamp;
+    aa->swstamp = G->swstamp;
+    aa->stamp = G->stamp;
+    aa->list[0] = G->list[0];
+    aa->list[1] = G->list[1];
+    aa->ctr = G->ctr;
+    aa->q = G->aq;
+    aa->ring = G->aring;
+    aa->ring_cap = G->cap_n;
+    aa->root = G->cfg.root;
+    aa->dense_limit = dense_limit;
+    aa->max_levels = max_levels;
+    aa->push = push;
+    aa->cand = G->cand;
     for (size_t off : {kArgMark, kArgMarkFallback}) {
         auto *ma = reinterpret_cast<MarkArgs<CT> *>(G->hargs + off);
         ma->row_off = G->row_off[G->cur];
@@ -222,6 +260,9 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
         ma->root = G->cfg.root;
         ma->dense_limit = dense_limit;
         ma->role = off == kArgMarkFallback ? 1 : 0;
+        ma->push = push;
+        ma->g = G->g;
+        ma->cand = G->cand;
     }
     CK(cudaMemcpyAsync(G->dargs, G->hargs, kArgBytes, cudaMemcpyHostToDevice, G->stream));
     // the pinned staging is rewritten only after this copy has been consumed
@@ -300,14 +341,35 @@ pirrt_status launch_improve_screen(pirrt_graph *G, cudaStream_t st) {
     return PIRRT_OK;
 }
 
+template <typename CT>
+pirrt_status launch_improve_push(pirrt_graph *G, cudaStream_t st) {
+    static int occ = -1;
+    if (occ < 0) {
+        int nb = 0;
+        CK(cudaOccupancyMaxActiveBlocksPerMultiprocessor(&nb, improve_push_kernel<CT, 8>, 256, 0));
+        occ = nb > 0 ? nb : 1;
+    }
+    improve_push_kernel<CT, 8><<<G->num_sms * occ, 256, 0, st>>>(
+        dev_arg<ImproveArgs<CT>>(G, kArgImprove));
+    CKL();
+    return PIRRT_OK;
+}
+
 // Improve kernel selection (pirrt_exploit_opts.tile / .group):
-//   tile 0  G lanes per vertex (group, default 4) with FP32 screening; FP64
+//   tile 0  list sweeps from candidate offers (improve_push_kernel), dense
+//           sweeps by the tile-2 kernel (which returns at once otherwise)
+//   tile 2  G lanes per vertex (group, default 4) with FP32 screening; FP64
 //           costs use the exact G-lane kernel
 //   tile 1  staged: producer warp bulk-copies rows into a shared-memory ring
 //   tile 3  G lanes per vertex (default 8), exact FP64 for every candidate
 template <typename CT>
 pirrt_status launch_improve(pirrt_graph *G, cudaStream_t st, int gs, int tile) {
     if (tile == 0) {
+        pirrt_status rc = launch_improve_push<CT>(G, st);
+        if (rc) return rc;
+        tile = 2;
+    }
+    if (tile == 2) {
         if constexpr (sizeof(CT) == 4) {
             switch (gs) {
                 case 2: return launch_improve_screen<2, 8>(G, st);
@@ -340,6 +402,24 @@ pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st) {
                                      dev_arg<WaveArgs<CT>>(G, kArgWave));
 }
 
+constexpr size_t kAsyncSmem = (size_t)kAsyncLocal * (sizeof(double) + 2 * sizeof(int32_t));
+
+template <typename CT>
+pirrt_status launch_async(pirrt_graph *G, cudaStream_t st) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G->async_blocks);
+    cfg.blockDim = dim3(kAsyncThreads);
+    cfg.dynamicSmemBytes = kAsyncSmem;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, async_evaluate_kernel<CT>, dev_arg<AsyncArgs<CT>>(G, kArgAsync)));
+    return PIRRT_OK;
+}
+
 template <typename CT>
 pirrt_status launch_mark(pirrt_graph *G, cudaStream_t st, size_t off) {
     mark_frontier_kernel<CT><<<G->num_sms * 8, kThreads, 0, st>>>(dev_arg<MarkArgs<CT>>(G, off));
@@ -353,14 +433,14 @@ pirrt_status launch_mark(pirrt_graph *G, cudaStream_t st, size_t off) {
 // level cap.
 template <typename CT>
 pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile, bool jump,
-                              cudaGraphConditionalHandle cond, int use_cond) {
+                              bool async, cudaGraphConditionalHandle cond, int use_cond) {
     pirrt_status rc;
     if ((rc = launch_improve<CT>(G, st, gs, tile))) return rc;
     if (jump) {
         if ((rc = launch_evaluate<CT>(G, st, kArgEval))) return rc;
         if ((rc = launch_mark<CT>(G, st, kArgMark))) return rc;
     } else {
-        if ((rc = launch_wave<CT>(G, st))) return rc;
+        if ((rc = async ? launch_async<CT>(G, st) : launch_wave<CT>(G, st))) return rc;
         pre_jump_kernel<<<1, 1, 0, st>>>(G->ctr);
         CKL();
         if ((rc = launch_evaluate<CT>(G, st, kArgEvalFallback))) return rc;
@@ -374,9 +454,11 @@ pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile,
 // The Replan loop as a CUDA graph: a WHILE conditional node whose body is one
 // iteration; advance_kernel sets the condition.  Cached per kernel choice.
 template <typename CT>
-pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, cudaGraphExec_t *out) {
+pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, bool async,
+                      cudaGraphExec_t *out) {
     const unsigned long long key = ((unsigned long long)gs << 8) | ((unsigned long long)tile << 1) |
-                                   (jump ? 1ull : 0ull) | ((unsigned long long)sizeof(CT) << 24);
+                                   (jump ? 1ull : 0ull) | ((unsigned long long)sizeof(CT) << 24) |
+                                   (async ? 1ull << 32 : 0ull);
     auto it = G->loops.find(key);
     if (it != G->loops.end()) {
         *out = it->second;
@@ -396,7 +478,7 @@ pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, cudaGraphExec
     cudaGraph_t body = cp.conditional.phGraph_out[0];
     CK(cudaStreamBeginCaptureToGraph(G->capture, body, nullptr, nullptr, 0,
                                      cudaStreamCaptureModeRelaxed));
-    pirrt_status rc = launch_iteration<CT>(G, G->capture, gs, tile, jump, cond, 1);
+    pirrt_status rc = launch_iteration<CT>(G, G->capture, gs, tile, jump, async, cond, 1);
     cudaGraph_t captured = nullptr;
     const cudaError_t ec = cudaStreamEndCapture(G->capture, &captured);
     if (rc) {
@@ -462,17 +544,17 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
             n_old, G->row_off[G->cur], old_adj, G->row_off[nxt], new_adj);
         CKL();
     }
+    // 4. seed the new vertices (before the scatter, whose offers may reach them)
+    if (n_new > 0) {
+        insert_init_vertices<CT><<<grid_for(n_new, kThreads, max_blocks), kThreads, 0, G->stream>>>(
+            n_old, n_after, G->cfg.root, G->g, G->g32, G->p, static_cast<CT *>(G->pc), G->cand,
+            G->stamp, G->list[0], G->list[1], G->ctr);
+        CKL();
+    }
     if (n_edges > 0) {
         insert_scatter<CT><<<grid_for(n_edges, kThreads, max_blocks), kThreads, 0, G->stream>>>(
             n_edges, src, dst, cost, G->row_off[nxt], G->deg, new_adj, G->stamp, G->cfg.root,
-            G->list[0], G->list[1], G->ctr);
-        CKL();
-    }
-    // 4. seed the new vertices
-    if (n_new > 0) {
-        insert_init_vertices<CT><<<grid_for(n_new, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_old, n_after, G->cfg.root, G->g, G->g32, G->p, static_cast<CT *>(G->pc), G->stamp,
-            G->list[0], G->list[1], G->ctr);
+            G->list[0], G->list[1], G->g, G->cand, G->ctr);
         CKL();
     }
     G->prof.launches += 3 + (n_edges > 0 ? 2 : 0) + (n_old > 0 && G->m > 0 ? 1 : 0) + (n_new > 0 ? 1 : 0);
@@ -497,8 +579,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     pirrt_exploit_opts o{};
     if (opts) o = *opts;
     if (o.max_iters < 0 || o.eps < 0.0 || o.dense_fraction < 0.0 || o.dense_fraction > 1.0 ||
-        o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_JUMP ||
-        !(o.tile == 0 || o.tile == 1 || o.tile == 3) ||
+        o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_ASYNC ||
+        !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3) ||
         !(o.group == 0 || o.group == 2 || o.group == 4 || o.group == 8 || o.group == 16 ||
           o.group == 32))
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
@@ -518,14 +600,19 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         const double extra = 16.0 * std::log2((double)G->n / 1.0e6);
         auto_cap = (unsigned)std::min(128.0, 24.0 + extra);
     }
-    const unsigned max_levels = mode == PIRRT_EVAL_WAVE ? cap_any
+    // The barrier-free walk (ASYNC) is an explicit choice: on the 6-D
+    // roadmaps its per-CTA subtree walks took about twice as long per
+    // Evaluate as the level-synchronous wave, which spreads every level over
+    // the whole grid.
+    const bool async = mode == PIRRT_EVAL_ASYNC;
+    const unsigned max_levels = (mode == PIRRT_EVAL_WAVE || mode == PIRRT_EVAL_ASYNC) ? cap_any
                                 : (o.wave_levels > 0 ? (unsigned)o.wave_levels : auto_cap);
     // AUTO: after an exploit whose waves ran past the cap, use pointer
-    // jumping; probe with waves again every eighth exploit
+    // jumping; probe with a wave again every eighth exploit
     bool jump = mode == PIRRT_EVAL_JUMP ||
                 (mode == PIRRT_EVAL_AUTO && G->deep_hint && (G->exploits % 8) != 0);
     G->exploits += 1;
-    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels);
+    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0);
     if (rc) return rc;
     const bool prof = G->profiling != 0;
     const bool use_graph = !prof && o.host_loop == 0;
@@ -534,6 +621,11 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     std::memcpy(&eps_bits, &eps, sizeof(eps_bits));
 
     CK(cudaEventRecord(G->ev0, G->stream));
+    if (G->async_dirty) {  // a failed walk may have left its state behind
+        async_reset_kernel<<<1, 1, 0, G->stream>>>(G->aq);
+        CKL();
+        G->async_dirty = 0;
+    }
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(
         G->ctr, (unsigned)std::min<int64_t>(max_iters, 0xffffffffll), eps_bits);
     CKL();
@@ -543,7 +635,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     bool graph_ran = false;
     if (use_graph) {
         cudaGraphExec_t exec = nullptr;
-        rc = get_loop<CT>(G, gs, tile, jump, &exec);
+        rc = get_loop<CT>(G, gs, tile, jump, async, &exec);
         if (rc == PIRRT_OK) {
             CK(cudaGraphLaunch(exec, G->stream));
             graph_ran = true;
@@ -552,7 +644,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         }
     }
     if (!graph_ran) {
-        unsigned long long prev_relax = 0, prev_improved = 0, prev_eval = 0;
+        unsigned long long prev_relax = 0, prev_improved = 0, prev_eval = 0, prev_offers = 0;
         for (int64_t it = 0; it < max_iters; ++it) {
             if (prof) CK(cudaEventRecord(G->pev[0], G->stream));
             if ((rc = launch_improve<CT>(G, G->stream, gs, tile))) return rc;
@@ -562,7 +654,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
                 if ((rc = launch_mark<CT>(G, G->stream, kArgMark))) return rc;
             } else {
-                if ((rc = launch_wave<CT>(G, G->stream))) return rc;
+                if ((rc = async ? launch_async<CT>(G, G->stream) : launch_wave<CT>(G, G->stream)))
+                    return rc;
                 if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
                 pre_jump_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
                 CKL();
@@ -589,6 +682,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 tr.dense = h->last_dense ? 1 : 0;
                 tr.improve_vertices = (int64_t)(h->improved - prev_improved);
                 tr.improve_entries = (int64_t)(h->relax - prev_relax);
+                tr.offers = (int64_t)(h->offers - prev_offers);
                 tr.switches = (int32_t)h->last_switched;
                 tr.changed = (int32_t)h->last_dg;
                 tr.wave_levels = (int32_t)h->last_levels;
@@ -604,6 +698,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
             }
             P.improve_launches += 1;
             P.improve_entries += (int64_t)(h->relax - prev_relax);
+            P.evaluate_offers += (int64_t)(h->offers - prev_offers);
             P.improve_vertices += (int64_t)(h->improved - prev_improved);
             if (h->last_dense) P.improve_dense_vertices += (int64_t)(h->improved - prev_improved);
             P.improve_switches += h->last_switched;
@@ -619,6 +714,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 }
             }
             prev_relax = h->relax;
+            prev_offers = h->offers;
             prev_improved = h->improved;
             prev_eval = h->evaluated;
             if (h->status) break;
@@ -639,7 +735,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     if (graph_ran) P.launches += (int64_t)h.iter * (jump ? 4 : 6);
     s.iterations = (int32_t)h.iter;
     s.converged = h.converged ? 1 : 0;
-    s.relaxations = (int64_t)h.relax;
+    s.relaxations = (int64_t)(h.relax + h.offers);
     s.improved = (int64_t)h.improved;
     s.evaluated = (int64_t)h.evaluated;
     s.switches = (int64_t)h.switches;
@@ -679,7 +775,7 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     policy_commit_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
         G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g, G->g32);
     CKL();
-    pirrt_status rc = write_args<CT>(G, 0u, 1u);
+    pirrt_status rc = write_args<CT>(G, 0u, 1u, 0);
     if (rc) return rc;
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr, 1u, 0ull);
     CKL();
@@ -704,7 +800,7 @@ void free_all(pirrt_graph *G) {
     void *bufs[] = {G->dargs, G->pexport, G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
-                    G->wl[1], G->wstamp, G->ctr, G->stage};
+                    G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage};
     for (void *q : bufs)
         if (q) cudaFree(q);
     if (G->ctr_host) cudaFreeHost(G->ctr_host);
@@ -723,9 +819,9 @@ struct StateSnapshot {
 
 pirrt_status snapshot_io(pirrt_graph *G, StateSnapshot &S, bool save) {
     const size_t n = (size_t)G->n;
-    const size_t parts[] = {8 * n, 4 * n, 4 * n, G->cost_bytes * n, 4 * n, 4 * n, 4 * n,
+    const size_t parts[] = {8 * n, 4 * n, 4 * n, G->cost_bytes * n, 4 * n, 4 * n, 4 * n, 8 * n,
                             sizeof(DevCounters)};
-    void *dev[] = {G->g, G->g32, G->p, G->pc, G->stamp, G->list[0], G->list[1], G->ctr};
+    void *dev[] = {G->g, G->g32, G->p, G->pc, G->stamp, G->list[0], G->list[1], G->cand, G->ctr};
     size_t total = 0;
     for (size_t b : parts) total += (b + 255) & ~size_t(255);
     if (save && S.bytes < total) {
@@ -735,7 +831,7 @@ pirrt_status snapshot_io(pirrt_graph *G, StateSnapshot &S, bool save) {
         S.bytes = total;
     }
     char *q = static_cast<char *>(S.buf);
-    for (int i = 0; i < 8; ++i) {
+    for (int i = 0; i < 9; ++i) {
         if (parts[i]) {
             if (save)
                 CK(cudaMemcpyAsync(q, dev[i], parts[i], cudaMemcpyDeviceToDevice, G->stream));
@@ -893,6 +989,10 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->wl[0], sizeof(int32_t) * nv);
     ALLOC(G->wl[1], sizeof(int32_t) * nv);
     ALLOC(G->wstamp, sizeof(unsigned) * nv);
+    ALLOC(G->swstamp, sizeof(unsigned) * nv);
+    ALLOC(G->cand, sizeof(unsigned long long) * nv);
+    ALLOC(G->aq, sizeof(AsyncQueue));
+    ALLOC(G->aring, sizeof(AsyncItem) * nv);
     ALLOC(G->ctr, sizeof(DevCounters));
     ALLOC(G->dargs, kArgBytes);
     ALLOC(G->pexport, sizeof(int32_t) * nv);
@@ -927,6 +1027,26 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     wocc = std::min(wocc, wocc64);
     if (wocc < 1) return bail(PIRRT_ERR_CUDA);
     G->wave_blocks = G->num_sms * std::min(wocc, 2);
+    int aocc = 0, aocc64 = 0;
+    if (cudaFuncSetAttribute(async_evaluate_kernel<float>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsyncSmem) !=
+            cudaSuccess ||
+        cudaFuncSetAttribute(async_evaluate_kernel<double>,
+                             cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsyncSmem) !=
+            cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aocc, async_evaluate_kernel<float>,
+                                                      kAsyncThreads, kAsyncSmem) != cudaSuccess ||
+        cudaOccupancyMaxActiveBlocksPerMultiprocessor(&aocc64, async_evaluate_kernel<double>,
+                                                      kAsyncThreads, kAsyncSmem) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
+    aocc = std::min(aocc, aocc64);
+    if (aocc < 1) return bail(PIRRT_ERR_CUDA);
+    G->async_blocks = G->num_sms * std::min(aocc, 2);
+    // spill-list slots carry their index, so zeroed slots match none; the
+    // walk's indices grow over the graph's lifetime and are never reset
+    if (cudaMemset(G->aq, 0, sizeof(AsyncQueue)) != cudaSuccess ||
+        cudaMemset(G->aring, 0, sizeof(AsyncItem) * nv) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
     pirrt_status rc = pirrt_graph_reset(G);
     if (rc) return bail(rc);
     *out = G;
@@ -940,6 +1060,7 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemsetAsync(G->row_off[1], 0, sizeof(int64_t), G->stream));
     CK(cudaMemsetAsync(G->stamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
+    CK(cudaMemsetAsync(G->swstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->ctr, 0, sizeof(DevCounters), G->stream));
     // stamps start at 0, so the first list uses stamp value 1
     const unsigned one = 1u;
@@ -1019,8 +1140,10 @@ pirrt_status pirrt_graph_exploit(pirrt_graph *G, const pirrt_exploit_opts *opts,
         if (stats) stats->converged = 1;
         return PIRRT_OK;
     }
-    if (G->cfg.cost_dtype == PIRRT_COST_F32) return exploit_impl<float>(G, opts, stats);
-    return exploit_impl<double>(G, opts, stats);
+    const pirrt_status rc = G->cfg.cost_dtype == PIRRT_COST_F32 ? exploit_impl<float>(G, opts, stats)
+                                                                : exploit_impl<double>(G, opts, stats);
+    if (rc != PIRRT_OK) G->async_dirty = 1;
+    return rc;
 }
 
 pirrt_status pirrt_graph_get_costs(const pirrt_graph *Gc, double *g_out, int64_t n, int on_device) {

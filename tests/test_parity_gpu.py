@@ -152,16 +152,34 @@ def test_c2_as_specified_small_reachable_set():
 
 # ------------------------------------------------------ invariances ---
 
-@pytest.mark.parametrize("group,tile", [(2, 0), (8, 0), (16, 0), (32, 0), (0, 1), (4, 3),
-                                        (8, 3), (32, 3)])
+@pytest.mark.parametrize("group,tile", [(2, 0), (8, 0), (16, 0), (32, 0), (0, 1), (2, 2),
+                                        (4, 2), (8, 2), (4, 3), (8, 3), (32, 3)])
 def test_improve_kernels_agree(c3_small, group, tile):
-    """Every tiled Improve shape and the G-threads-per-vertex kernels take the
+    """Every Improve kernel -- from candidate offers (tile 0, the default),
+    full screened scans (2), staged scans (1) and exact scans (3) -- takes the
     same lexicographic argmin, so whole schedules agree bit for bit."""
     rm = c3_small
     g0, p0, _ = gpu_schedule(rm)
     g, p, _ = gpu_schedule(rm, group=group, tile=tile)
     np.testing.assert_array_equal(g, g0)
     np.testing.assert_array_equal(p, p0)
+
+
+@pytest.mark.parametrize("evaluate", ["wave", "jump", "async", "auto"])
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_offers_match_full_scans(c2_small, c3_small, evaluate, which):
+    """Improve from candidate offers (a listed vertex reads its row only when
+    the best offer beats its parent) reaches the policy of full scans bit for
+    bit, iteration for iteration, with every Evaluate form making the offers;
+    it forms far fewer candidates."""
+    rm = c2_small if which == "c2" else c3_small
+    g0, p0, s0 = gpu_schedule(rm, evaluate=evaluate, tile=2)
+    g1, p1, s1 = gpu_schedule(rm, evaluate=evaluate, tile=0)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+    assert [s["iterations"] for s in s0] == [s["iterations"] for s in s1]
+    assert [s["switches"] for s in s0] == [s["switches"] for s in s1]
+    assert sum(s["relaxations"] for s in s1) < sum(s["relaxations"] for s in s0)
 
 
 @pytest.mark.parametrize("frac", [1e-9, 0.05, 1.0])
@@ -362,28 +380,30 @@ def test_outputs_into_device_tensors(c2_small):
 
 # ------------------------------------------------- Evaluate strategies ---
 
-@pytest.mark.parametrize("mode,levels", [("wave", 0), ("jump", 0), ("auto", 0), ("auto", 1),
-                                         ("auto", 3)])
+@pytest.mark.parametrize("mode,levels", [("wave", 0), ("jump", 0), ("async", 0), ("auto", 0),
+                                         ("auto", 1), ("auto", 3)])
 def test_evaluate_strategies_agree(c2_small, mode, levels):
-    """Top-down waves, pointer jumping and a wave handing over to pointer
-    jumping after `levels` levels reach the same policy (Alg. 2 Evaluate)."""
+    """Top-down waves, pointer jumping, the barrier-free walk and a walk
+    handing over to pointer jumping past depth `levels` reach the same policy
+    (Alg. 2 Evaluate)."""
     rm = c2_small
     g_ref, p_ref, _ = O.replan_schedule(rm)
     g, p, st = gpu_schedule(rm, evaluate=mode, wave_levels=levels)
     assert_parity(rm, g, p, g_ref, p_ref)
     if mode == "jump" or (mode == "auto" and levels == 1):
         assert sum(s["jump_evaluates"] for s in st) > 0
-    if mode == "wave":
+    if mode in ("wave", "async"):
         assert sum(s["jump_evaluates"] for s in st) == 0
 
 
-def test_wave_sums_match_oracle_bitwise():
-    """The top-down Evaluate adds one edge cost per level from the root, the
+@pytest.mark.parametrize("mode", ["wave", "async"])
+def test_wave_sums_match_oracle_bitwise(mode):
+    """The top-down Evaluates add one edge cost per level from the root, the
     order of Alg. 2's breadth-first Evaluate, so with the same tree g agrees
     with the oracle to the last bit."""
     rm = W.roadmap_c1(trial=4)
     g_ref, p_ref, _ = O.replan_schedule(rm)
-    g, p, _ = gpu_schedule(rm, evaluate="wave")
+    g, p, _ = gpu_schedule(rm, evaluate=mode)
     same = p == p_ref
     assert same.mean() > 0.99
     # vertices whose whole root path agrees
@@ -407,6 +427,64 @@ def test_c3_wave_and_jump_identical_parents(c3_small):
     np.testing.assert_array_equal(pw[mask], pj[mask])
 
 
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_async_walk_equals_wave_bitwise(c2_small, c3_small, which):
+    """The barrier-free walk and the level-synchronous wave compute the same
+    sums, so whole schedules agree bit for bit, iteration for iteration.  (The
+    wave counts a vertex recomputed on two levels twice when it decides on a
+    dense next sweep, the walk once, so their Improve sweeps may differ in
+    shape, not in result.)"""
+    rm = c2_small if which == "c2" else c3_small
+    gw, pw, sw = gpu_schedule(rm, evaluate="wave")
+    ga, pa, sa = gpu_schedule(rm, evaluate="async")
+    np.testing.assert_array_equal(gw, ga)
+    np.testing.assert_array_equal(pw, pa)
+    assert [s["iterations"] for s in sw] == [s["iterations"] for s in sa]
+    assert [s["switches"] for s in sw] == [s["switches"] for s in sa]
+
+
+@pytest.mark.parametrize("mode,n", [("async", 30_000), ("wave", 2_000), ("auto", 30_000)])
+def test_long_chain_with_nested_switches(mode, n):
+    """A path whose vertices first hang off the root by long direct edges
+    (cost 10^6 + 10k), so that the second Improve re-parents every path vertex
+    at once onto its predecessor: one Evaluate then walks an n-level tree in
+    which every vertex switched.  g is the exact prefix sum (one FP64 addition
+    per level, as Alg. 2's Evaluate).  The level-synchronous wave recomputes
+    every stale vertex on every level, so it runs a shorter path; AUTO hands
+    the deep walk over to pointer jumping.  A hub joined to the root and to
+    every 7th vertex then re-parents thousands of nested vertices again."""
+    rng = np.random.default_rng(11)
+    c = rng.uniform(1.0, 2.0, n - 1)
+    ks = np.arange(2, n, dtype=np.int32)
+    u1 = np.r_[np.arange(n - 1, dtype=np.int32), np.zeros(len(ks), np.int32)].astype(np.int32)
+    v1 = np.r_[np.arange(1, n, dtype=np.int32), ks].astype(np.int32)
+    c1 = np.r_[c, 1e6 + 10.0 * ks]
+    hub = n
+    far = np.arange(7, n, 7, dtype=np.int32)
+    u2 = np.r_[np.int32(0), far].astype(np.int32)
+    v2 = np.full(len(u2), hub, dtype=np.int32)
+    c2 = np.r_[0.5, rng.uniform(0.5, 1.0, len(far))]
+    with P.Graph(n + 1, len(u1) + len(u2), 0, np.float64) as D:
+        D.insert_batch(n, u1, v1, c1)
+        st1 = D.exploit(evaluate=mode)
+        g1 = D.get_costs()
+        assert st1["switches"] >= 2 * (n - 2)
+        if mode == "auto":  # the walk passes its depth cap; pointer jumping finishes
+            assert st1["jump_evaluates"] > 0
+            np.testing.assert_allclose(g1[1:], np.cumsum(c), rtol=1e-12)
+        else:
+            assert st1["jump_evaluates"] == 0
+            np.testing.assert_array_equal(g1[1:], np.cumsum(c))
+        D.insert_batch(1, u2, v2, c2)
+        st2 = D.exploit(evaluate=mode)
+        g, p = D.get_costs(), D.get_parents()
+    assert st2["switches"] > 100
+    uu, vv, cc = np.r_[u1, u2], np.r_[v1, v2], np.r_[c1, c2]
+    rm = W.Roadmap("chain", np.zeros((n + 1, 2)), uu, vv, cc, np.zeros(n + 2, np.int64), n + 1)
+    d, _ = O.dijkstra(n + 1, uu, vv, cc)
+    assert_parity(rm, g, p, d)
+
+
 @pytest.mark.parametrize("scale", [1e-39, 1e29, 1e36])
 def test_extreme_cost_scales(scale):
     """Costs in the FP32 subnormal range, and costs whose path sums exceed
@@ -419,7 +497,7 @@ def test_extreme_cost_scales(scale):
     assert_parity(rmd, g, p, g_ref, p_ref)
 
 
-@pytest.mark.parametrize("evaluate", ["auto", "wave", "jump"])
+@pytest.mark.parametrize("evaluate", ["auto", "wave", "jump", "async"])
 def test_graph_launch_matches_host_loop(c2_small, evaluate):
     """The Replan loop captured as one CUDA graph (WHILE node) and the host-driven
     loop run the same kernels and reach the same policy, bit for bit."""

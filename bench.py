@@ -215,7 +215,8 @@ def run_ours(args) -> None:
                 G.insert_batch(v1 - v0, host_u[e0:e1], host_v[e0:e1], host_c[e0:e1])
             st = G.exploit(group=args.group, tile=args.tile, dense_fraction=args.dense_fraction,
                            evaluate=args.evaluate, wave_levels=args.wave_levels,
-                           host_loop=args.host_loop)
+                           host_loop=args.host_loop, wave_tail=args.wave_tail,
+                           wave_ctas=args.wave_ctas)
             relax += st["relaxations"]
             iters += st["iterations"]
             for k in extra:
@@ -340,7 +341,8 @@ def run_ours(args) -> None:
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][1]}",
                    "vertices": rm.n, "undirected_edges": rm.m, "csr_entries": 2 * rm.m,
                    "blocks_per_step": n_blocks, "block_size": rm.block,
-                   "evaluate": args.evaluate,
+                   "evaluate": args.evaluate, "wave_tail": args.wave_tail,
+                   "wave_ctas": args.wave_ctas,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": dict(extra),
                    "improve_kernel": {0: "candidate offers; dense sweeps by lane groups with "
@@ -584,6 +586,9 @@ def main():
     ap.add_argument("--dense-fraction", type=float, default=0.0)
     ap.add_argument("--evaluate", choices=("auto", "wave", "jump", "async"), default="auto")
     ap.add_argument("--wave-levels", type=int, default=0)
+    ap.add_argument("--wave-ctas", type=int, default=0, help="wave CTAs per SM (0 tuned)")
+    ap.add_argument("--wave-tail", type=int, default=0,
+                    help="levels of at most this many vertices walked by one CTA (0 tuned, <0 off)")
     ap.add_argument("--timing", choices=("graph", "profiled"), default="graph")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--host-loop", action="store_true",

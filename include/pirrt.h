@@ -91,6 +91,9 @@ typedef struct {
                                always uses the host loop. */
     double dense_fraction;  /* changed vertices, as a fraction of |V|, above which the next
                                Improve sweeps every vertex instead of a list; 0 = tuned */
+    int32_t wave_tail;      /* top-down Evaluate: levels of at most this many vertices are
+                               walked by one CTA without grid barriers; 0 = tuned, < 0 = off */
+    int32_t wave_ctas;      /* top-down Evaluate: CTAs per SM (1 or 2); 0 = tuned */
 } pirrt_exploit_opts;
 
 /* Evaluate strategies.  All compute g(v) = g(p(v)) + c(p(v), v) from the root
@@ -129,8 +132,12 @@ typedef struct {
 typedef struct pirrt_graph pirrt_graph;   /* opaque, library-owned */
 
 /* Allocate an empty graph (no vertices) with the given capacities on
- * cfg->device.  Device memory: about 2 x 8 B x (max_vertices + 1) row offsets,
- * 2 x (8 or 16 B) x 2 x max_edges CSR entries, and about 110 B per vertex of
+ * cfg->device.  Device memory: a CSR pool of (8 or 16 B) x (4 x max_edges +
+ * 4 x max_vertices) entries -- every row keeps room to grow in place, and a
+ * row that outgrows it moves to the end of the pool, so an insertion copies
+ * only the rows that moved; a second pool of the same size is allocated the
+ * first time the pool is used up and every row is repacked -- plus 16 B of
+ * row extent and about 130 B per vertex of
  * policy and work arrays.  *out is set to NULL on failure. */
 pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out);
 
@@ -188,7 +195,7 @@ pirrt_status pirrt_graph_get_costs(const pirrt_graph *g, double *g_out, int64_t 
 pirrt_status pirrt_graph_get_parents(const pirrt_graph *g, int32_t *p_out, int64_t n,
                                      int on_device);
 
-/* Copy the device CSR: row_off[0..n] (int64), col[0..m) (int32) and
+/* Copy the device CSR, packed: row_off[0..n] (int64), col[0..m) (int32) and
  * cost[0..m) (float or double), m = pirrt_graph_num_entries().  Entries of
  * a row are in no particular order.  Any output pointer may be NULL. */
 pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *g, int64_t *row_off, int32_t *col,
@@ -201,8 +208,8 @@ pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *g, int64_t *row_off, i
  * `improve_vertices` vertices (of which `improve_dense_vertices` in dense
  * sweeps) and switched `improve_switches` parents; Evaluate finished
  * `evaluate_vertices` vertices in `evaluate_visits` work-list visits;
- * insertion wrote `insert_new_entries` new and copied `insert_copied_entries`
- * old CSR entries. */
+ * insertion wrote `insert_new_entries` new CSR entries and moved
+ * `insert_copied_entries` old ones (rows that outgrew their room, repacks). */
 typedef struct {
     int64_t launches;             /* every kernel launch of this handle */
     int64_t improve_launches, evaluate_launches, mark_launches, insert_calls;

@@ -51,7 +51,8 @@ class pirrt_exploit_opts(ctypes.Structure):
     _fields_ = [("eps", ctypes.c_double), ("max_iters", ctypes.c_int32),
                 ("group", ctypes.c_int32), ("tile", ctypes.c_int32), ("evaluate", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("host_loop", ctypes.c_int32),
-                ("dense_fraction", ctypes.c_double)]
+                ("dense_fraction", ctypes.c_double), ("wave_tail", ctypes.c_int32),
+                ("wave_ctas", ctypes.c_int32)]
 
 
 class pirrt_exploit_stats(ctypes.Structure):
@@ -267,10 +268,10 @@ class Graph:
 
     def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                 dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
-                host_loop: bool = False, check: bool = True) -> dict:
-        opts = pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
-                                  EVALUATE_MODES[evaluate], int(wave_levels), int(bool(host_loop)),
-                                  float(dense_fraction))
+                host_loop: bool = False, wave_tail: int = 0, wave_ctas: int = 0,
+                check: bool = True) -> dict:
+        opts = exploit_opts(eps, max_iters, group, tile, dense_fraction, evaluate, wave_levels,
+                            host_loop, wave_tail, wave_ctas)
         st = pirrt_exploit_stats()
         rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))
         out = st.as_dict()
@@ -361,10 +362,11 @@ def pirrt_evaluate_noalloc(parent, parent_cost, g_out, root: int = 0, stream=Non
 
 def exploit_opts(eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                  dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
-                 host_loop: bool = False) -> pirrt_exploit_opts:
+                 host_loop: bool = False, wave_tail: int = 0,
+                 wave_ctas: int = 0) -> pirrt_exploit_opts:
     return pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
                               EVALUATE_MODES[evaluate], int(wave_levels), int(bool(host_loop)),
-                              float(dense_fraction))
+                              float(dense_fraction), int(wave_tail), int(wave_ctas))
 
 
 class Batch:

@@ -106,25 +106,31 @@ __device__ __forceinline__ double widen(double w) { return w; }
 
 // Device counters of one graph.  The host copies the block back once per
 // Replan iteration.
+// Counters that every CTA of a kernel adds to sit on 128-byte lines of
+// their own: atomics to one line are serialised by its L2 slice, and
+// unrelated counters must not queue behind each other.
 struct DevCounters {
-    unsigned long long relax;     // adjacency entries scanned by Improve (whole exploit)
-    unsigned long long improved;  // vertices processed by Improve (whole exploit)
-    unsigned long long evaluated; // vertices whose g was recomputed (whole exploit)
+    alignas(128) unsigned long long relax;  // adjacency entries scanned by Improve (whole exploit)
+    alignas(128) unsigned long long improved;  // vertices processed by Improve (whole exploit)
+    alignas(128) unsigned long long evaluated;  // vertices whose g was recomputed (whole exploit)
+    alignas(128) unsigned long long offers;  // candidates offered to the next Improve (whole exploit)
+    alignas(128) unsigned long long dj_bits;  // Delta g of the current Improve (bits of a double >= 0)
+    alignas(128) unsigned n_switched;  // switches in the current iteration
+    alignas(128) unsigned n_next;      // size of the list being built for the next Improve
+    alignas(128) unsigned n_dg;        // vertices whose g changed in the current Evaluate
+    alignas(128) unsigned wave_cnt[3];  // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
+    alignas(128) unsigned bar_count;   // grid barrier: arrivals
+    alignas(128) unsigned bar_gen;     // grid barrier: generation
+    alignas(128) unsigned wl_count[kMaxJumpRounds + 2];  // pointer-jumping work-list sizes per round
+    alignas(128) unsigned status;      // kStatus* bits
     unsigned long long switches;  // parent switches (whole exploit)
-    unsigned long long offers;    // candidates offered to the next Improve (whole exploit)
-    unsigned long long dj_bits;   // Delta g of the current Improve (bits of a double >= 0)
+    unsigned long long insert_copied;  // CSR entries moved by insertions (graph lifetime)
     unsigned n_active;            // size of the current Improve list
-    unsigned n_next;              // size of the list being built for the next Improve
-    unsigned n_switched;          // switches in the current iteration
-    unsigned n_dg;                // vertices whose g changed in the current Evaluate
     unsigned rounds;              // pointer-jumping rounds of the current Evaluate
-    unsigned status;              // kStatus* bits
     unsigned dense;               // current Improve sweeps every vertex
     unsigned dense_next;          // next Improve sweeps every vertex
-    unsigned bar_count;           // grid barrier: arrivals
-    unsigned bar_gen;             // grid barrier: generation
-    unsigned wave_cnt[3];         // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
     unsigned wave_levels;         // levels run by the last top-down Evaluate
+    unsigned wave_t;              // top-down Evaluate: level reached by a one-CTA tail walk
     unsigned wave_incomplete;     // the top-down Evaluate stopped at its level cap
     // Iteration state kept on the device so that one captured loop body (and
     // the host loop alike) serves every iteration:
@@ -141,9 +147,58 @@ struct DevCounters {
     unsigned last_switched, last_dg, last_levels, last_next, last_dense, last_rounds, last_jumped;
     // whole-exploit totals
     unsigned cum_wave_levels, cum_dense, cum_jump_rounds, cum_jump_evals;
-    unsigned pad[1];
-    unsigned wl_count[kMaxJumpRounds + 2];  // Evaluate work-list sizes per round
 };
+
+// Block-wide sum of one value per thread, added to *counter by one atomic.
+// Every thread of the block must call it; s needs blockDim.x / 32 entries.
+__device__ __forceinline__ void block_add(unsigned long long x, unsigned long long *counter,
+                                          unsigned long long *s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) x += __shfl_down_sync(0xffffffffu, x, off);
+    __syncthreads();
+    if (lane == 0) s[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t += s[w];
+        if (t) atomicAdd(counter, t);
+    }
+}
+
+// Block-wide maximum, applied to *counter by one atomic (same rules).
+__device__ __forceinline__ void block_max(unsigned long long x, unsigned long long *counter,
+                                          unsigned long long *s) {
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+#pragma unroll
+    for (int off = 16; off > 0; off >>= 1) {
+        const unsigned long long o = __shfl_down_sync(0xffffffffu, x, off);
+        x = o > x ? o : x;
+    }
+    __syncthreads();
+    if (lane == 0) s[warp] = x;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long t = 0;
+        for (int w = 0; w < (int)(blockDim.x >> 5); ++w) t = s[w] > t ? s[w] : t;
+        if (t) atomicMax(counter, t);
+    }
+}
+
+// Row extent of a vertex in the slack CSR: its entries are
+// adj[beg, beg + len); the row may grow in place up to beg + cap.
+struct __align__(16) RowExt {
+    long long beg;
+    int32_t len;
+    int32_t cap;
+};
+
+// [b, e) of row v, one 16-byte load.
+__device__ __forceinline__ void row_range(const RowExt *rows, int64_t v, int64_t &b, int64_t &e) {
+    const longlong2 r = __ldg(reinterpret_cast<const longlong2 *>(rows) + v);
+    b = r.x;
+    e = r.x + (long long)(int32_t)(unsigned)((unsigned long long)r.y & 0xffffffffull);
+}
 
 // Parent marker of a root vertex (g = 0, never re-parented).  Reported as -1.
 constexpr int32_t kRootMark = -2;
@@ -180,6 +235,28 @@ struct WarpStage {
         __syncwarp();
         for (unsigned i = lane; i < count; i += 32u) list[base + i] = buf[i];
         __syncwarp();
+        count = 0u;
+    }
+
+    // End of a kernel: every warp of the block flushes together, one
+    // atomicAdd per block.  s needs blockDim.x / 32 + 1 entries.
+    __device__ __forceinline__ void flush_block(int32_t *list, unsigned *counter, unsigned *s) {
+        const unsigned lane = threadIdx.x & 31u, warp = threadIdx.x >> 5;
+        __syncthreads();
+        if (lane == 0) s[warp] = count;
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            unsigned run = 0;
+            for (unsigned w = 0; w < (blockDim.x >> 5); ++w) {
+                const unsigned k = s[w];
+                s[w] = run;
+                run += k;
+            }
+            s[blockDim.x >> 5] = run ? atomicAdd(counter, run) : 0u;
+        }
+        __syncthreads();
+        const unsigned base = s[blockDim.x >> 5] + s[warp];
+        for (unsigned i = lane; i < count; i += 32u) list[base + i] = buf[i];
         count = 0u;
     }
 
@@ -230,6 +307,39 @@ __device__ __forceinline__ void block_reserve2(unsigned na, unsigned nb, unsigne
     const unsigned long long ex = s_scan[warp] + incl - x;
     base_a = (unsigned)s_scan[NW] + (unsigned)(ex & 0xffffffffull);
     base_b = (unsigned)s_scan[NW + 1] + (unsigned)(ex >> 32);
+    __syncthreads();
+}
+
+// block_reserve2 for any block size (s_scan: blockDim.x / 32 + 2 entries).
+__device__ __forceinline__ void block_reserve2_dyn(unsigned na, unsigned nb, unsigned *ctr_a,
+                                                   unsigned *ctr_b, unsigned long long *s_scan,
+                                                   unsigned &base_a, unsigned &base_b) {
+    const int nw = (int)(blockDim.x >> 5);
+    const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5;
+    const unsigned long long x = ((unsigned long long)nb << 32) | na;
+    unsigned long long incl = x;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) s_scan[warp] = incl;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        unsigned long long run = 0;
+        for (int w = 0; w < nw; ++w) {
+            const unsigned long long t = s_scan[w];
+            s_scan[w] = run;
+            run += t;
+        }
+        const unsigned ta = (unsigned)(run & 0xffffffffull), tb = (unsigned)(run >> 32);
+        s_scan[nw] = ta ? atomicAdd(ctr_a, ta) : 0u;
+        s_scan[nw + 1] = tb ? atomicAdd(ctr_b, tb) : 0u;
+    }
+    __syncthreads();
+    const unsigned long long ex = s_scan[warp] + incl - x;
+    base_a = (unsigned)s_scan[nw] + (unsigned)(ex & 0xffffffffull);
+    base_b = (unsigned)s_scan[nw + 1] + (unsigned)(ex >> 32);
     __syncthreads();
 }
 

@@ -56,7 +56,7 @@ struct AsyncItem {
 
 template <typename CT>
 struct AsyncArgs {
-    const int64_t *row_off;
+    const RowExt *rows;
     const Entry<CT> *adj;
     const int32_t *p;
     const CT *pc;
@@ -314,8 +314,9 @@ async_evaluate_kernel(const AsyncArgs<CT> *__restrict__ ap) {
         if (kind == 1) warp_append(first, u, a.dg, &c->n_dg);
         int deg = 0;
         if (u >= 0) {
-            const long long b = a.row_off[u];
-            deg = (int)(a.row_off[u + 1] - b);
+            int64_t b, e;
+            row_range(a.rows, u, b, e);
+            deg = (int)(e - b);
             s_base[tid] = b;
             max_depth = max(max_depth, du);
         }

@@ -114,12 +114,11 @@ scan_tile_sums(long long *__restrict__ tile_sums, int64_t n_tiles) {
     }
 }
 
-// Third pass: new_off[v] = old_off[min(v, n_old)] + (entries added to rows < v).
-// len = n_after + 1 and deg[n_after] = 0, so new_off[n_after] is the new total.
+// Third pass: new_off[v] = deg[0] + ... + deg[v - 1].  With len = n + 1 and
+// deg[n] = 0, new_off[n] is the total.
 static __global__ void __launch_bounds__(kThreads)
 scan_tile_apply(const int32_t *__restrict__ deg, int64_t len,
-                const long long *__restrict__ tile_sums, const int64_t *__restrict__ old_off,
-                int64_t n_old, int64_t *__restrict__ new_off) {
+                const long long *__restrict__ tile_sums, int64_t *__restrict__ new_off) {
     const int64_t base = (int64_t)blockIdx.x * kScanTile + (int64_t)threadIdx.x * kScanItems;
     long long v[kScanItems];
     long long s = 0;
@@ -133,24 +132,128 @@ scan_tile_apply(const int32_t *__restrict__ deg, int64_t len,
 #pragma unroll
     for (int i = 0; i < kScanItems; ++i) {
         const int64_t x = base + i;
-        if (x < len) new_off[x] = old_off[x < n_old ? x : n_old] + run;
+        if (x < len) new_off[x] = run;
         run += v[i];
     }
 }
 
-// Copy every old row to its new position (the new row keeps its old entries
-// first).  One warp per row.
+// Slack CSR.  Every row owns adj[beg, beg + cap) of a pool and fills it from
+// the front; a block's new entries go to the row tails.  A row that would
+// overflow moves to fresh space at the end of the pool with room to grow, so
+// an insertion copies only the rows that moved, not the whole graph.  When
+// the pool is used up, every row is repacked into a second pool.
+
+// Room a moving row reserves: 1.5x its new length + 4 (a few moves over a
+// row's life); a repacked row gets 1.25x + 2, so a repack always fits a pool
+// of 2 x (directed entries) + 4 x (vertices).
+__device__ __forceinline__ int32_t row_room(int32_t need, bool repack) {
+    return repack ? need + (need >> 2) + 2 : need + (need >> 1) + 4;
+}
+
+// Plan: the pool space each row must take (0: stays where it is).
+// alloc[n_after] = 0 closes the scan.
+static __global__ void __launch_bounds__(kThreads)
+insert_plan(int64_t n_old, int64_t n_after, const RowExt *__restrict__ rows,
+            const int32_t *__restrict__ deg, int32_t *__restrict__ alloc, int repack) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n_after;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        int32_t a = 0;
+        if (v < n_after) {
+            const int32_t len = v < n_old ? rows[v].len : 0;
+            const int32_t cap = v < n_old ? rows[v].cap : 0;
+            const int32_t need = len + deg[v];
+            if (repack) a = need > 0 ? row_room(need, true) : 0;
+            else if (need > cap) a = row_room(need, false);
+        }
+        alloc[v] = a;
+    }
+}
+
+// Move the rows that need space (their old entries first) to pool offset
+// base + off[v], and set every row's extent to its length after the block.
+// One warp per 32 rows: each moving row is copied by the whole warp.
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
-insert_copy_rows(int64_t n_old, const int64_t *__restrict__ old_off,
-                 const Entry<CT> *__restrict__ old_adj, const int64_t *__restrict__ new_off,
-                 Entry<CT> *__restrict__ new_adj) {
+insert_move_rows(int64_t n_old, int64_t n_after, RowExt *__restrict__ rows,
+                 const int32_t *__restrict__ deg, const int32_t *__restrict__ alloc,
+                 const int64_t *__restrict__ off, long long base,
+                 const Entry<CT> *__restrict__ src, Entry<CT> *__restrict__ dst,
+                 DevCounters *ctr, int repack) {
     const int lane = threadIdx.x & 31;
     const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
-    for (int64_t v = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); v < n_old;
-         v += warps) {
-        const int64_t b = old_off[v], e = old_off[v + 1], dst = new_off[v];
-        for (int64_t i = b + lane; i < e; i += 32) new_adj[dst + (i - b)] = ld_stream(&old_adj[i]);
+    unsigned long long copied = 0;
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         w0 < n_after; w0 += warps * 32) {
+        const int64_t v = w0 + lane;
+        long long ob = 0, nb = 0;
+        int32_t len = 0;
+        bool move = false;
+        if (v < n_after) {
+            RowExt r{0, 0, 0};
+            if (v < n_old) r = rows[v];
+            const int32_t add = deg[v];
+            const int32_t a = alloc[v];
+            len = r.len;
+            ob = r.beg;
+            RowExt nr = r;
+            nr.len = r.len + add;
+            const bool place = a > 0 || v >= n_old || repack;
+            if (place) {
+                nb = base + off[v];
+                nr.beg = nb;
+                nr.cap = a;
+                move = a > 0 && len > 0;
+            }
+            if (place || add > 0) rows[v] = nr;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, move);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const long long sb = __shfl_sync(0xffffffffu, ob, l);
+            const long long db = __shfl_sync(0xffffffffu, nb, l);
+            const int32_t n = __shfl_sync(0xffffffffu, len, l);
+            for (int32_t k = lane; k < n; k += 32) dst[db + k] = ld_stream(&src[sb + k]);
+            copied += (unsigned long long)n;
+        }
+    }
+    if (lane == 0 && copied) atomicAdd(&ctr->insert_copied, copied);
+}
+
+// Export: row lengths (len[n] = 0 closes the scan), then each row copied to
+// its compact position off[v] (one warp per 32 rows, as above).
+static __global__ void __launch_bounds__(kThreads)
+row_lengths(int64_t n, const RowExt *__restrict__ rows, int32_t *__restrict__ len) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v <= n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        len[v] = v < n ? rows[v].len : 0;
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+export_rows(int64_t n, const RowExt *__restrict__ rows, const int64_t *__restrict__ off,
+            const Entry<CT> *__restrict__ adj, Entry<CT> *__restrict__ out) {
+    const int lane = threadIdx.x & 31;
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32; w0 < n;
+         w0 += warps * 32) {
+        const int64_t v = w0 + lane;
+        long long sb = 0, db = 0;
+        int32_t len = 0;
+        if (v < n) {
+            sb = rows[v].beg;
+            len = rows[v].len;
+            db = off[v];
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, len > 0);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const long long s0 = __shfl_sync(0xffffffffu, sb, l);
+            const long long d0 = __shfl_sync(0xffffffffu, db, l);
+            const int32_t k0 = __shfl_sync(0xffffffffu, len, l);
+            for (int32_t k = lane; k < k0; k += 32) out[d0 + k] = adj[s0 + k];
+        }
     }
 }
 
@@ -160,7 +263,7 @@ insert_copy_rows(int64_t n_old, const int64_t *__restrict__ old_off,
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *__restrict__ dst,
-               const CT *__restrict__ cost, const int64_t *__restrict__ new_off,
+               const CT *__restrict__ cost, const RowExt *__restrict__ rows,
                int32_t *__restrict__ deg, Entry<CT> *__restrict__ adj, unsigned *__restrict__ stamp,
                int32_t root, int32_t *__restrict__ list0, int32_t *__restrict__ list1,
                const double *__restrict__ g, unsigned long long *__restrict__ cand,
@@ -176,8 +279,9 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
             a = src[e];
             b = dst[e];
             const CT w = cost[e];
-            const int64_t sa = new_off[a + 1] - atomicSub(&deg[a], 1);
-            const int64_t sb = new_off[b + 1] - atomicSub(&deg[b], 1);
+            // rows hold the lengths after the block: fill the tails from the end
+            const int64_t sa = rows[a].beg + rows[a].len - atomicSub(&deg[a], 1);
+            const int64_t sb = rows[b].beg + rows[b].len - atomicSub(&deg[b], 1);
             Entry<CT> ea{}, eb{};
             ea.col = b;
             ea.w = w;
@@ -241,7 +345,7 @@ __device__ __forceinline__ bool cand_less(double v1, int32_t u1, CT w1, double v
 
 template <typename CT>
 struct ImproveArgs {
-    const int64_t *row_off;
+    const RowExt *rows;
     const Entry<CT> *adj;
     const double *g;
     const float *g32;
@@ -283,7 +387,8 @@ improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
          item += gstride) {
         const int32_t v = dense ? (int32_t)item : active[item];
         if (v == a.root) continue;  // uniform within the group
-        const int64_t b = a.row_off[v], e = a.row_off[v + 1];
+        int64_t b, e;
+        row_range(a.rows, v, b, e);
         double best = CUDART_INF;
         int32_t bu = INT_MAX;
         CT bw = CT(0);
@@ -413,19 +518,17 @@ struct EvaluateArgs {
 // if a's g became final in an earlier round (g(w) = acc(w) + g(a)), or
 // jumps: acc(w) += acc(a), anc(w) = anc(a).  Every value read in round r was
 // written before round r, so the sums, hence g, do not depend on scheduling.
+// The whole pointer-jumping Evaluate, for any cooperative grid; false if a
+// grid barrier timed out.
 template <typename CT>
-__global__ void __launch_bounds__(kThreads)
-evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
-    const EvaluateArgs<CT> a = *ap;
+__device__ bool jump_evaluate(const EvaluateArgs<CT> &a) {
     DevCounters *c = a.ctr;
-    if (!a.force && c->n_switched == 0u) return;
-    if (a.role == 1 && c->wave_incomplete == 0u) return;
     if (blockIdx.x == 0 && threadIdx.x == 0) c->jumped = 1u;
     const unsigned nblocks = gridDim.x;
-    const int lane = threadIdx.x & 31;
-    const int64_t wstride = (int64_t)gridDim.x * kThreads;
-    const int64_t tid0 = (int64_t)blockIdx.x * kThreads;
+    const int64_t wstride = (int64_t)gridDim.x * blockDim.x;
+    const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x;
     unsigned long long finished = 0;
+    __shared__ unsigned long long s_scan[1024 / 32 + 2];
 
     // round 0
     for (int64_t base = tid0; base < a.n; base += wstride) {
@@ -442,9 +545,11 @@ evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
                 keep = true;
             }
         }
-        warp_append(keep, (int32_t)v, a.wl[0], &c->wl_count[1]);
+        unsigned bk, bd;
+        block_reserve2_dyn(keep ? 1u : 0u, 0u, &c->wl_count[1], &c->n_dg, s_scan, bk, bd);
+        if (keep) a.wl[0][bk] = (int32_t)v;
     }
-    if (!grid_barrier(c, nblocks)) return;
+    if (!grid_barrier(c, nblocks)) return false;
 
     int r = 1;
     for (;; ++r) {
@@ -483,15 +588,27 @@ evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
                     keep = true;
                 }
             }
-            warp_append(keep, w, wl_out, &c->wl_count[r + 1]);
-            warp_append(changed, w, a.dg, &c->n_dg);
+            unsigned bk, bd;
+            block_reserve2_dyn(keep ? 1u : 0u, changed ? 1u : 0u, &c->wl_count[r + 1], &c->n_dg,
+                               s_scan, bk, bd);
+            if (keep) wl_out[bk] = w;
+            if (changed) a.dg[bd] = w;
         }
-        if (!grid_barrier(c, nblocks)) return;
+        if (!grid_barrier(c, nblocks)) return false;
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) finished += __shfl_down_sync(0xffffffffu, finished, off);
-    if (lane == 0 && finished) atomicAdd(&c->evaluated, finished);
+    block_add(finished, &c->evaluated, s_scan);
     if (blockIdx.x == 0 && threadIdx.x == 0) c->rounds = (unsigned)(r - 1);
+    return true;
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
+    const EvaluateArgs<CT> a = *ap;
+    DevCounters *c = a.ctr;
+    if (!a.force && c->n_switched == 0u) return;
+    if (a.role == 1 && c->wave_incomplete == 0u) return;
+    jump_evaluate<CT>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -502,7 +619,7 @@ evaluate_kernel(const EvaluateArgs<CT> *__restrict__ ap) {
 
 template <typename CT>
 struct MarkArgs {
-    const int64_t *row_off;
+    const RowExt *rows;
     const Entry<CT> *adj;
     const int32_t *dg;
     unsigned *stamp;
@@ -516,29 +633,36 @@ struct MarkArgs {
     unsigned long long *cand;
 };
 
+// Frontier marking (and offers) for the changed list, any grid.  The list
+// and g may have been written earlier in the same kernel by other CTAs, so
+// they are read through L2.
 template <typename CT>
-__global__ void __launch_bounds__(kThreads)
-mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
-    const MarkArgs<CT> a = *ap;
+__device__ void mark_changed(const MarkArgs<CT> &a) {
     DevCounters *c = a.ctr;
-    if (a.role == 1 && c->wave_incomplete == 0u) return;
     const unsigned epoch = c->epoch + 1u;
-    int32_t *next = a.list[(c->la & 1u) ^ 1u];
-    const unsigned n_dg = c->n_dg;
+    int32_t *next = ((c->la & 1u) ^ 1u) ? a.list[1] : a.list[0];
+    const unsigned n_dg = *(volatile unsigned *)&c->n_dg;
     if (c->n_switched == 0u || n_dg == 0u) return;
     if (n_dg > a.dense_limit) {
         if (blockIdx.x == 0 && threadIdx.x == 0) c->dense_next = 1u;
         return;
     }
-    // one warp per changed vertex; lanes stride over its row
+    // one warp per changed vertex; lanes stride over its row; appends are
+    // staged per warp and reach the list 128 at a time
+    constexpr int kCap = 128;
+    __shared__ int32_t s_stage[1024 / 32][kCap];
+    __shared__ unsigned s_fl[1024 / 32 + 1];
+    __shared__ unsigned long long s_red[1024 / 32];
+    WarpStage<kCap> stq{s_stage[threadIdx.x >> 5], 0u};
     const int lane = threadIdx.x & 31;
-    const int64_t warps = (int64_t)gridDim.x * (kThreads / 32);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
     unsigned long long offers = 0;
-    for (int64_t j = (int64_t)blockIdx.x * (kThreads / 32) + (threadIdx.x >> 5); j < n_dg;
+    for (int64_t j = (int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5); j < n_dg;
          j += warps) {
-        const int32_t x = a.dg[j];
-        const int64_t b = a.row_off[x], e = a.row_off[x + 1];
-        const double gx = a.push ? a.g[x] : 0.0;
+        const int32_t x = __ldcg(&a.dg[j]);
+        int64_t b, e;
+        row_range(a.rows, x, b, e);
+        const double gx = a.push ? __ldcg(&a.g[x]) : 0.0;
         for (int64_t i0 = b; i0 < e; i0 += 32) {
             const int64_t i = i0 + lane;
             bool pred = false;
@@ -552,12 +676,19 @@ mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
                 }
                 pred = u != a.root && atomicExch(&a.stamp[u], epoch) != epoch;
             }
-            warp_append(pred, u, next, &c->n_next);
+            stq.push(pred, u, next, &c->n_next);
         }
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) offers += __shfl_down_sync(0xffffffffu, offers, off);
-    if (lane == 0 && offers) atomicAdd(&c->offers, offers);
+    stq.flush_block(next, &c->n_next, s_fl);
+    block_add(offers, &c->offers, s_red);
+}
+
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
+    const MarkArgs<CT> a = *ap;
+    if (a.role == 1 && a.ctr->wave_incomplete == 0u) return;
+    mark_changed<CT>(a);
 }
 
 // ---------------------------------------------------------------------------
@@ -568,15 +699,17 @@ mark_frontier_kernel(const MarkArgs<CT> *__restrict__ ap) {
 
 template <typename CT>
 struct WaveArgs {
-    const int64_t *row_off;
+    const RowExt *rows;
     const Entry<CT> *adj;
     const int32_t *p;
     const CT *pc;
     double *g;
     float *g32;
     const int32_t *switched;  // level 0: vertices whose parent changed
-    int32_t *lvl[2];          // vertices to recompute at levels t (mod 2)
-    unsigned *wstamp;         // dedups a child listed twice (parallel edges)
+    int32_t *lvl[2];          // vertices of levels t (mod 2), their g already lowered
+    double *lvg[2];           // ... and the lowered g they carry
+    int32_t *dg;              // vertices whose g changed (each once)
+    unsigned *wstamp;         // first-change stamps (tag = wave_epoch)
     unsigned *stamp;          // Improve-list stamps
     int32_t *list[2];         // the next Improve list is list[(la & 1) ^ 1]
     DevCounters *ctr;
@@ -585,175 +718,191 @@ struct WaveArgs {
     unsigned max_levels;      // give up (wave_incomplete) after this many levels
     int32_t push;             // offer g(u) + c(u, w) to every neighbour w of a changed u
     unsigned long long *cand;
+    unsigned tail_max;        // levels of at most this many vertices: one CTA, no grid barrier
+    int64_t list_cap;         // capacity of lvl[] / lvg[]
 };
 
-// A vertex u on level t takes g(u) = g(p(u)) + c(p(u), u), one FP64 addition
-// along the path exactly as Alg. 2's Evaluate walks the policy tree.  If g(u)
-// changed, u's row is scanned once: every neighbour joins the next Improve
-// list (only neighbours of changed vertices can find a better parent) and
-// every child (neighbour w with p(w) = u) joins level t + 1.  g(u) unchanged
-// means its whole subtree is unchanged, so the walk is pruned there.
+// Level 0 holds the switched vertices: each takes g(s) = g(p(s)) + c(p(s), s).
+// A vertex whose g was lowered is expanded: its row is scanned once, every
+// neighbour joins the next Improve list (only neighbours of changed vertices
+// can find a better parent) and is offered its candidate through it, and
+// every child w (p(w) = u) is lowered at once to g(u) + c(u, w) -- one FP64
+// addition per tree edge, root to leaf, as in Alg. 2's Evaluate -- and, if
+// that lowered it, joins level t + 1 carrying the value.  A vertex whose g
+// does not drop prunes its subtree.
 //
-// A switched vertex below another switched vertex is first computed from a
-// stale parent value and recomputed when the upper wave reaches it; the last
-// write of every vertex comes one level after its parent's last change, so
-// the result does not depend on scheduling.
+// Improve only switches to strictly cheaper parents, so no cost-to-come rises
+// under the new policy: every value computed for a vertex (from an ancestor
+// not yet final, when switched vertices lie below one another) is at least
+// its final value, and g is lowered by an atomic minimum on its bit pattern
+// (non-negative doubles order like unsigned integers).  A stale value can
+// never overwrite a smaller one, and each vertex is reached again one level
+// after its parent's last drop, so the result is the root-to-leaf sum
+// whatever the scheduling.  The FP32 shadow is refreshed once at the end
+// from the final g of every vertex that changed.
 //
-// Each level is split evenly over the CTAs.  A CTA takes up to kWaveThreads
-// vertices at a time, one per thread, then streams the concatenated rows of
-// the changed ones with every thread (the loads of a whole tile in flight at
-// once), locating each entry's row by binary search over the tile's prefix
-// sums in shared memory.
+// A level is split evenly over the CTAs, with a grid barrier between levels.
+// A CTA takes up to kWaveThreads vertices at a time, one per thread, then
+// streams the concatenated rows with every thread (the loads of a whole tile
+// in flight at once), locating each entry's row by binary search over the
+// tile's prefix sums in shared memory.  Levels of at most tail_max vertices
+// (the thin tails of most Evaluates) are walked by CTA 0 alone with CTA
+// barriers, while the other CTAs wait at one grid barrier.
 constexpr int kWaveThreads = 512;
 constexpr int kWaveUnroll = 4;
 
 template <typename CT>
-__global__ void __launch_bounds__(kWaveThreads)
-wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap) {
-    const WaveArgs<CT> a = *ap;
-    __shared__ int32_t s_u[kWaveThreads];
-    __shared__ double s_gn[kWaveThreads];
-    __shared__ long long s_base[kWaveThreads];
-    __shared__ int32_t s_seg[kWaveThreads + 1];
-    __shared__ int32_t s_wsum[kWaveThreads / 32];
-    __shared__ unsigned long long s_scan[kWaveThreads / 32 + 2];
+struct WaveShared {
+    int32_t u[kWaveThreads];
+    double gu[kWaveThreads];
+    long long base[kWaveThreads];
+    int32_t seg[kWaveThreads + 1];
+    unsigned long long scan[kWaveThreads / 32 + 2];
+};
+
+// Vertices [lo, hi) of level t.  Every thread of the CTA calls this.
+template <typename CT>
+__device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT> &sh, unsigned t,
+                                           int64_t lo, int64_t hi, unsigned tag, unsigned epoch,
+                                           int32_t *next, unsigned long long gpol,
+                                           unsigned long long &recomputed,
+                                           unsigned long long &offers, bool children) {
     DevCounters *c = a.ctr;
-    const unsigned n_sw = c->n_switched;
-    if (n_sw == 0u) return;
-    const unsigned epoch = c->epoch + 1u;         // stamp of the list being built
-    const unsigned wave_epoch = c->wave_epoch;    // wstamp of level 1 (level t uses + t - 1)
-    int32_t *next = a.list[(c->la & 1u) ^ 1u];
-    const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const unsigned long long gpol = policy_evict_last();
-    unsigned long long recomputed = 0, changed_total = 0, offers = 0;
-    unsigned t = 0;
-    for (;; ++t) {
-        const int64_t count =
-            t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
-        if (count == 0) break;
-        if (t >= a.max_levels) {
-            if (blockIdx.x == 0 && tid == 0) c->wave_incomplete = 1u;
-            break;
-        }
-        const int32_t *in = t == 0 ? a.switched : (((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0]);
-        int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
-        unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
-        if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
-        const unsigned wtag = wave_epoch + t;  // stamp of level t + 1
-        const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
-        const int64_t per = (count + nblocks - 1) / nblocks;
-        const int64_t lo = (int64_t)blockIdx.x * per;
-        const int64_t hi = lo + per < count ? lo + per : count;
-        for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
-            const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
-            int deg = 0;
-            int32_t u = -1;
-            if (tid < nv) {
-                u = __ldcg(&in[s0 + tid]);
-                const int32_t pu = __ldcg(&a.p[u]);
-                const double gn = ld_g_cg(&a.g[pu], gpol) + (double)a.pc[u];
-                const double go = ld_g_cg(&a.g[u], gpol);
+    const int32_t *in = ((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0];
+    const double *ing = ((t & 1u) != 0u) ? a.lvg[1] : a.lvg[0];
+    int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
+    double *outg = ((t & 1u) != 0u) ? a.lvg[0] : a.lvg[1];
+    unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
+    const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
+    const bool offering = a.push && marking;
+    for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
+        const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
+        int deg = 0;
+        int32_t u = -1;
+        double gu = 0.0;
+        bool first = false;
+        if (tid < nv) {
+            if (t == 0u) {
+                const int32_t s = __ldcg(&a.switched[s0 + tid]);
+                const int32_t ps = __ldcg(&a.p[s]);
+                const double gs = ld_g_cg(&a.g[ps], gpol) + widen(__ldcg(&a.pc[s]));
                 ++recomputed;
-                if (__double_as_longlong(gn) != __double_as_longlong(go)) {
-                    __stcg(&a.g[u], gn);
-                    __stcg(&a.g32[u], g32_of(gn));
-                    ++changed_total;
-                    const long long b = a.row_off[u];
-                    deg = (int)(a.row_off[u + 1] - b);
-                    s_base[tid] = b;
-                    s_gn[tid] = gn;
+                const unsigned long long b = (unsigned long long)__double_as_longlong(gs);
+                if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[s]), b) > b) {
+                    u = s;
+                    gu = gs;
                 }
+            } else {
+                u = __ldcg(&in[s0 + tid]);
+                gu = __ldcg(&ing[s0 + tid]);
             }
-            s_u[tid] = u;
-            // block exclusive scan of the changed rows' lengths
-            int incl = deg;
-#pragma unroll
-            for (int off = 1; off < 32; off <<= 1) {
-                const int y = __shfl_up_sync(0xffffffffu, incl, off);
-                if (lane >= off) incl += y;
+            if (u >= 0) {
+                first = atomicExch(&a.wstamp[u], tag) != tag;
+                int64_t b, e;
+                row_range(a.rows, u, b, e);
+                deg = (int)(e - b);
+                sh.base[tid] = b;
             }
-            if (lane == 31) s_wsum[warp] = incl;
-            __syncthreads();
-            if (warp == 0) {
-                int w = lane < kWaveThreads / 32 ? s_wsum[lane] : 0;
+        }
+        sh.u[tid] = u;
+        sh.gu[tid] = gu;
+        // one block scan of (first change, row length): the row offsets of
+        // the tile, and the slots of its first changes in the changed list
+        // (one atomic per tile)
+        constexpr int NW = kWaveThreads / 32;
+        const unsigned long long xv = ((unsigned long long)(first ? 1u : 0u) << 32) | (unsigned)deg;
+        unsigned long long incl = xv;
 #pragma unroll
-                for (int off = 1; off < 32; off <<= 1) {
-                    const int y = __shfl_up_sync(0xffffffffu, w, off);
-                    if (lane >= off) w += y;
-                }
-                if (lane < kWaveThreads / 32) s_wsum[lane] = w;
+        for (int off = 1; off < 32; off <<= 1) {
+            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
+            if (lane >= off) incl += y;
+        }
+        if (lane == 31) sh.scan[warp] = incl;
+        __syncthreads();
+        if (tid == 0) {
+            unsigned long long run = 0;
+            for (int w = 0; w < NW; ++w) {
+                const unsigned long long x = sh.scan[w];
+                sh.scan[w] = run;
+                run += x;
             }
-            __syncthreads();
-            s_seg[tid + 1] = incl + (warp > 0 ? s_wsum[warp - 1] : 0);
-            if (tid == 0) s_seg[0] = 0;
-            __syncthreads();
-            const int total = s_seg[kWaveThreads];
-            for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
-                int32_t w[kWaveUnroll], owner[kWaveUnroll];
+            const unsigned nf = (unsigned)(run >> 32);
+            unsigned base = 0;
+            if (nf) {
+                base = atomicAdd(&c->n_dg, nf);
+                if (base + nf > a.dense_limit) *(volatile unsigned *)&c->dense_next = 1u;
+            }
+            sh.scan[NW] = base;
+            sh.seg[kWaveThreads] = (int)(run & 0xffffffffull);
+        }
+        __syncthreads();
+        {
+            const unsigned long long ex = sh.scan[warp] + incl - xv;
+            sh.seg[tid] = (int)(ex & 0xffffffffull);
+            if (first) a.dg[(unsigned)sh.scan[NW] + (unsigned)(ex >> 32)] = u;
+        }
+        __syncthreads();
+        const int total = sh.seg[kWaveThreads];
+        for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
+            int32_t x[kWaveUnroll], own[kWaveUnroll];
+            double gx[kWaveUnroll];
 #pragma unroll
-                for (int j = 0; j < kWaveUnroll; ++j) {
-                    const int pos = p0 + tid + j * kWaveThreads;
-                    owner[j] = -1;
-                    w[j] = 0;
-                    if (pos < total) {
-                        int l = 0, h = kWaveThreads;  // last k with s_seg[k] <= pos
-                        while (h - l > 1) {
-                            const int mid = (l + h) >> 1;
-                            if (s_seg[mid] <= pos) l = mid; else h = mid;
-                        }
-                        owner[j] = s_u[l];
-                        const Entry<CT> en = ld_stream(&a.adj[s_base[l] + (pos - s_seg[l])]);
-                        w[j] = en.col;
-                        if (a.push && marking && en.col != a.root) {
-                            offer(a.cand, en.col, s_gn[l] + widen(en.w));
-                            ++offers;
-                        }
+            for (int j = 0; j < kWaveUnroll; ++j) {
+                const int pos = p0 + tid + j * kWaveThreads;
+                own[j] = -1;
+                x[j] = 0;
+                gx[j] = 0.0;
+                if (pos < total) {
+                    int l = 0, h = kWaveThreads;  // last k with seg[k] <= pos
+                    while (h - l > 1) {
+                        const int mid = (l + h) >> 1;
+                        if (sh.seg[mid] <= pos) l = mid; else h = mid;
+                    }
+                    own[j] = l;
+                    const Entry<CT> en = ld_stream(&a.adj[sh.base[l] + (pos - sh.seg[l])]);
+                    x[j] = en.col;
+                    // c(u, w) of this entry; with parallel edges the cheaper one
+                    // wins the minimum, as Improve chose it
+                    gx[j] = sh.gu[l] + widen(en.w);
+                    if (offering && en.col != a.root) {
+                        offer(a.cand, en.col, gx[j]);
+                        ++offers;
                     }
                 }
-                unsigned childm = 0, markm = 0;
+            }
+            unsigned childm = 0, markm = 0;
 #pragma unroll
-                for (int j = 0; j < kWaveUnroll; ++j) {
-                    if (owner[j] >= 0) {
-                        if (__ldcg(&a.p[w[j]]) == owner[j] &&
-                            atomicExch(&a.wstamp[w[j]], wtag) != wtag)
+            for (int j = 0; j < kWaveUnroll; ++j) {
+                if (own[j] >= 0) {
+                    if (children && __ldcg(&a.p[x[j]]) == sh.u[own[j]]) {
+                        const unsigned long long b = (unsigned long long)__double_as_longlong(gx[j]);
+                        if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[x[j]]), b) > b)
                             childm |= 1u << j;
-                        if (marking && w[j] != a.root && __ldcg(&a.stamp[w[j]]) != epoch &&
-                            atomicExch(&a.stamp[w[j]], epoch) != epoch)
-                            markm |= 1u << j;
                     }
-                }
-                unsigned bc, bm;
-                block_reserve2<kWaveThreads>(__popc(childm), __popc(markm), out_cnt, &c->n_next,
-                                             s_scan, bc, bm);
-#pragma unroll
-                for (int j = 0; j < kWaveUnroll; ++j) {
-                    if (childm & (1u << j)) out[bc++] = w[j];
-                    if (markm & (1u << j)) next[bm++] = w[j];
+                    if (marking && x[j] != a.root && __ldcg(&a.stamp[x[j]]) != epoch &&
+                        atomicExch(&a.stamp[x[j]], epoch) != epoch)
+                        markm |= 1u << j;
                 }
             }
-            __syncthreads();  // s_u / s_base / s_seg are rewritten by the next tile
-        }
-        // changed-vertex count decides between a list and a dense sweep next
+            recomputed += (unsigned long long)__popc(childm);
+            unsigned bc, bm;
+            block_reserve2<kWaveThreads>(__popc(childm), __popc(markm), out_cnt, &c->n_next,
+                                         sh.scan, bc, bm);
 #pragma unroll
-        for (int off = 16; off > 0; off >>= 1)
-            changed_total += __shfl_down_sync(0xffffffffu, changed_total, off);
-        if (lane == 0 && changed_total) {
-            const unsigned total = atomicAdd(&c->n_dg, (unsigned)changed_total) +
-                                   (unsigned)changed_total;
-            if (total > a.dense_limit) c->dense_next = 1u;
+            for (int j = 0; j < kWaveUnroll; ++j) {
+                if (childm & (1u << j)) {
+                    if (bc < a.list_cap) {  // else the level overflows: see the caller
+                        out[bc] = x[j];
+                        outg[bc] = gx[j];
+                    }
+                    ++bc;
+                }
+                if (markm & (1u << j)) next[bm++] = x[j];
+            }
         }
-        changed_total = 0;
-        if (!grid_barrier(c, nblocks)) return;
+        __syncthreads();  // u / gu / base / seg are rewritten by the next tile
     }
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        recomputed += __shfl_down_sync(0xffffffffu, recomputed, off);
-        offers += __shfl_down_sync(0xffffffffu, offers, off);
-    }
-    if (lane == 0 && recomputed) atomicAdd(&c->evaluated, recomputed);
-    if (lane == 0 && offers) atomicAdd(&c->offers, offers);
-    if (blockIdx.x == 0 && tid == 0) c->wave_levels = t;
 }
 
 // Clear the per-iteration fields (not the current list or the dense flag).
@@ -788,8 +937,12 @@ static __global__ void pre_jump_kernel(DevCounters *c) {
 // goes on (Improve switched a parent with Delta g > eps, no error, under the
 // iteration cap), and make the list built by this iteration's Evaluate the
 // current one.  In a captured loop the decision drives the WHILE node.
-static __global__ void advance_kernel(DevCounters *c, cudaGraphConditionalHandle cond,
-                                      int use_cond) {
+// Called by one thread, possibly at the end of a kernel whose other CTAs
+// wrote the counters: every access goes through L2 (volatile).
+__device__ __forceinline__ void advance_iteration(DevCounters *cc, cudaGraphConditionalHandle cond,
+                                                  int use_cond) {
+    __threadfence();
+    volatile DevCounters *c = cc;
     const unsigned sw = c->n_switched;
     double dj = 0.0, eps = 0.0;
     dj = __longlong_as_double((long long)c->dj_bits);
@@ -817,9 +970,123 @@ static __global__ void advance_kernel(DevCounters *c, cudaGraphConditionalHandle
     c->n_active = c->dense_next ? 0u : c->n_next;
     c->dense = c->dense_next;
     c->dense_next = 0u;
-    clear_iteration(c);
+    clear_iteration(cc);
+    __threadfence();
     if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }
+
+static __global__ void advance_kernel(DevCounters *c, cudaGraphConditionalHandle cond,
+                                      int use_cond) {
+    advance_iteration(c, cond, use_cond);
+}
+
+// One Replan iteration after Improve, in one launch: the top-down wave; if
+// it stopped at its level cap, pointer jumping and the frontier marking of
+// its changes; then the end of the iteration (advance_iteration), which in a
+// captured loop sets the WHILE condition.
+template <typename CT>
+__global__ void __launch_bounds__(kWaveThreads)
+wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT> *__restrict__ ep,
+                     const MarkArgs<CT> *__restrict__ mp, cudaGraphConditionalHandle cond,
+                     int use_cond) {
+    const WaveArgs<CT> a = *ap;
+    __shared__ WaveShared<CT> sh;
+    __shared__ unsigned s_t;
+    DevCounters *c = a.ctr;
+    const unsigned n_sw = c->n_switched;
+    if (n_sw == 0u) {
+        if (blockIdx.x == 0 && threadIdx.x == 0) advance_iteration(c, cond, use_cond);
+        return;
+    }
+    const unsigned epoch = c->epoch + 1u;  // stamp of the list being built
+    const unsigned tag = c->wave_epoch;    // first-change stamp of this Evaluate
+    int32_t *next = ((c->la & 1u) ^ 1u) ? a.list[1] : a.list[0];
+    const unsigned nblocks = gridDim.x;
+    const int tid = threadIdx.x;
+    const unsigned long long gpol = policy_evict_last();
+    unsigned long long recomputed = 0, offers = 0;
+    unsigned t = 0;
+    for (;;) {
+        int64_t count =
+            t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
+        if (count == 0) break;
+        if (t >= a.max_levels || count > a.list_cap) {
+            // Stop: this level's vertices were lowered but not expanded.  Scan
+            // their rows for the frontier and the offers only; pointer jumping
+            // finishes the values below them.  (Children beyond the list's
+            // capacity -- parallel edges -- were lost: the next sweep is dense.)
+            if (blockIdx.x == 0 && tid == 0) {
+                c->wave_incomplete = 1u;
+                if (count > a.list_cap) c->dense_next = 1u;
+            }
+            if (count > a.list_cap) count = a.list_cap;
+            const int64_t per = (count + nblocks - 1) / nblocks;
+            const int64_t lo = (int64_t)blockIdx.x * per;
+            const int64_t hi = lo + per < count ? lo + per : count;
+            wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, false);
+            grid_barrier(c, nblocks);
+            break;
+        }
+        if (count <= (int64_t)a.tail_max) {
+            // a thin level: CTA 0 walks on alone while the levels stay thin
+            if (blockIdx.x == 0) {
+                for (;;) {
+                    if (tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
+                    __syncthreads();
+                    wave_level<CT>(a, sh, t, 0, count, tag, epoch, next, gpol, recomputed, offers,
+                                   true);
+                    ++t;
+                    if (tid == 0) s_t = *(volatile unsigned *)&c->wave_cnt[t % 3];
+                    __syncthreads();
+                    count = (int64_t)s_t;
+                    __syncthreads();
+                    if (count == 0 || count > (int64_t)a.tail_max || count > a.list_cap ||
+                        t >= a.max_levels)
+                        break;
+                }
+                if (tid == 0) c->wave_t = t;
+            }
+            if (!grid_barrier(c, nblocks)) break;
+            t = *(volatile unsigned *)&c->wave_t;
+            continue;
+        }
+        if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
+        const int64_t per = (count + nblocks - 1) / nblocks;
+        const int64_t lo = (int64_t)blockIdx.x * per;
+        const int64_t hi = lo + per < count ? lo + per : count;
+        wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, true);
+        ++t;
+        if (!grid_barrier(c, nblocks)) break;
+    }
+    // the FP32 shadow of every changed vertex, from its final g
+    const unsigned n_dg = *(volatile unsigned *)&c->n_dg;
+    for (unsigned i = blockIdx.x * kWaveThreads + tid; i < n_dg; i += nblocks * kWaveThreads) {
+        const int32_t w = __ldcg(&a.dg[i]);
+        a.g32[w] = g32_of(__ldcg(&a.g[w]));
+    }
+    block_add(recomputed, &c->evaluated, sh.scan);
+    block_add(offers, &c->offers, sh.scan);
+    if (blockIdx.x == 0 && tid == 0) c->wave_levels = t;
+    // A grid barrier that timed out raised kStatusTimeout: skip to the end,
+    // which stops the loop.
+    bool ok = grid_barrier(c, nblocks) && *(volatile unsigned *)&c->status == 0u;
+    if (ok && *(volatile unsigned *)&c->wave_incomplete != 0u) {
+        // stopped at the level cap: pointer jumping finishes the values and
+        // its changes are marked; the wave's changed list gives way
+        if (blockIdx.x == 0 && tid == 0) {
+            c->n_dg = 0u;
+            c->rounds = 0u;
+            for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
+        }
+        ok = grid_barrier(c, nblocks);
+        if (ok) ok = jump_evaluate<CT>(*ep);
+        if (ok) ok = grid_barrier(c, nblocks);
+        if (ok) mark_changed<CT>(*mp);
+        if (ok) grid_barrier(c, nblocks);
+    }
+    if (blockIdx.x == 0 && tid == 0) advance_iteration(c, cond, use_cond);
+}
+
 
 // Before an exploit or a forced Evaluate: clear the per-iteration fields and
 // the whole-exploit totals.
@@ -907,7 +1174,7 @@ static __global__ void set_roots_kernel(int64_t k, const int32_t *__restrict__ r
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 policy_lookup_kernel(int64_t n, int32_t root, const int32_t *__restrict__ parent,
-                     const int64_t *__restrict__ row_off, const Entry<CT> *__restrict__ adj,
+                     const RowExt *__restrict__ rows, const Entry<CT> *__restrict__ adj,
                      int32_t *__restrict__ p_out, CT *__restrict__ pc_out, DevCounters *c) {
     for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
          v += (int64_t)gridDim.x * blockDim.x) {
@@ -929,7 +1196,9 @@ policy_lookup_kernel(int64_t n, int32_t root, const int32_t *__restrict__ parent
         }
         bool found = false;
         CT best = CT(0);
-        for (int64_t i = row_off[v]; i < row_off[v + 1]; ++i) {
+        int64_t rb, re;
+        row_range(rows, v, rb, re);
+        for (int64_t i = rb; i < re; ++i) {
             const Entry<CT> en = adj[i];
             if (en.col == q && (!found || en.w < best)) {
                 best = en.w;

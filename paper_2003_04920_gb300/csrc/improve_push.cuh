@@ -21,7 +21,7 @@ namespace pirrt {
 
 // One thread per listed vertex decides; G lanes per deciding vertex scan.
 template <typename CT, int G>
-__global__ void __launch_bounds__(256)
+__global__ void __launch_bounds__(256, 4)
 improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     const ImproveArgs<CT> a = *ap;
     DevCounters *c = a.ctr;
@@ -79,8 +79,7 @@ improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
             CT bw = CT(0);
             int64_t b = 0, e = 0;
             if (mine) {
-                b = a.row_off[sv];
-                e = a.row_off[sv + 1];
+                row_range(a.rows, sv, b, e);
                 for (int64_t i0 = b + gl; i0 < e; i0 += (int64_t)G * kUnroll) {
                     Entry<CT> en[kUnroll];
 #pragma unroll
@@ -134,19 +133,13 @@ improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
             swq.push(sw, sv, a.switched, &c->n_switched);
         }
     }
-    swq.flush(a.switched, &c->n_switched);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, djmax, off);
-        djmax = o > djmax ? o : djmax;
-        relax += __shfl_down_sync(0xffffffffu, relax, off);
-        improved += __shfl_down_sync(0xffffffffu, improved, off);
-    }
-    if (lane == 0) {
-        if (djmax) atomicMax(&c->dj_bits, djmax);
-        if (relax) atomicAdd(&c->relax, relax);
-        if (improved) atomicAdd(&c->improved, improved);
-    }
+    // one atomic per block and counter (thousands of warps end together)
+    __shared__ unsigned s_fl[256 / 32 + 1];
+    __shared__ unsigned long long s_red[256 / 32];
+    swq.flush_block(a.switched, &c->n_switched, s_fl);
+    block_max(djmax, &c->dj_bits, s_red);
+    block_add(relax, &c->relax, s_red);
+    block_add(improved, &c->improved, s_red);
 }
 
 }  // namespace pirrt

@@ -58,8 +58,7 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
             v = dense ? (int32_t)item : __ldg(&active[item]);
             if (v == a.root) v = -1;
             else {
-                b = a.row_off[v];
-                e = a.row_off[v + 1];
+                row_range(a.rows, v, b, e);
             }
         }
     };
@@ -183,22 +182,13 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
         djmax = dj > djmax ? dj : djmax;
         (void)warp_span;
     }
-    swq.flush(a.switched, &a.ctr->n_switched);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        const unsigned long long o = __shfl_xor_sync(0xffffffffu, djmax, off);
-        djmax = o > djmax ? o : djmax;
-    }
-    if (lane == 0 && djmax) atomicMax(&a.ctr->dj_bits, djmax);
-#pragma unroll
-    for (int off = 16; off > 0; off >>= 1) {
-        relax += __shfl_down_sync(0xffffffffu, relax, off);
-        improved += __shfl_down_sync(0xffffffffu, improved, off);
-    }
-    if (lane == 0 && (relax || improved)) {
-        atomicAdd(&a.ctr->relax, relax);
-        atomicAdd(&a.ctr->improved, improved);
-    }
+    // one atomic per block and counter (thousands of warps end together)
+    __shared__ unsigned s_fl[256 / 32 + 1];
+    __shared__ unsigned long long s_red[256 / 32];
+    swq.flush_block(a.switched, &a.ctr->n_switched, s_fl);
+    block_max(djmax, &a.ctr->dj_bits, s_red);
+    block_add(relax, &a.ctr->relax, s_red);
+    block_add(improved, &a.ctr->improved, s_red);
 }
 
 }  // namespace pirrt

@@ -91,7 +91,7 @@ struct alignas(128) Stage {
     int32_t v[kTV];        // vertex, -1 if none
     int32_t seg[kTV + 1];  // exclusive prefix of row lengths
     int32_t start[kTV];    // index in buf of the row's first entry
-    long long gbase[kTV];  // row_off[v] (used when the tile overflows)
+    long long gbase[kTV];  // first entry of row v (used when the tile overflows)
     int32_t overflow;         // rows did not fit: read them from global memory
 };
 
@@ -160,8 +160,10 @@ improve_tma_kernel(const ImproveArgs<CT> *__restrict__ ap) {
                 if (v == a.root) {
                     v = -1;
                 } else {
-                    b = a.row_off[v];
-                    deg = (int)(a.row_off[v + 1] - b);
+                    int64_t rb, re;
+                    row_range(a.rows, v, rb, re);
+                    b = rb;
+                    deg = (int)(re - rb);
                 }
             }
             // 16-byte aligned source and destination for each row: the copy

@@ -44,9 +44,15 @@ struct pirrt_graph {
     int64_t cap_n = 0, cap_e = 0;  // vertices, directed CSR entries
     int64_t n = 0, m = 0;
     size_t entry_bytes = 0, cost_bytes = 0;
-    int cur = 0;                   // live CSR buffer
-    int64_t *row_off[2] = {nullptr, nullptr};
-    void *adj[2] = {nullptr, nullptr};
+    int cur = 0;                   // live CSR pool
+    RowExt *rows = nullptr;        // row extents in the live pool
+    void *adj[2] = {nullptr, nullptr};  // pools; the second is allocated on the first repack
+    int64_t pool_cap = 0;          // entries per pool
+    int64_t pool_used = 0;         // entries taken in the live pool (rows, slack, moved-out)
+    int32_t *ralloc = nullptr;     // insertion: pool space per row
+    int64_t *roff = nullptr;       // insertion / export: exclusive scan
+    unsigned long long copied_seen = 0;
+    int64_t *hx = nullptr;         // pinned host scalars read back by insertion
     double *g = nullptr;
     float *g32 = nullptr;  // FP32 shadow of g for candidate screening
     int32_t *p = nullptr;
@@ -79,9 +85,10 @@ struct pirrt_graph {
         int cur = -1;
         unsigned dense_limit = 0, max_levels = 0;
         int push = -1;
+        unsigned tail_max = 0;
         bool operator==(const ArgsKey &o) const {
             return n == o.n && cur == o.cur && dense_limit == o.dense_limit &&
-                   max_levels == o.max_levels && push == o.push;
+                   max_levels == o.max_levels && push == o.push && tail_max == o.tail_max;
         }
     } args_key;
     std::map<unsigned long long, cudaGraphExec_t> loops;  // captured Replan loops
@@ -89,7 +96,8 @@ struct pirrt_graph {
     size_t stage_bytes = 0;
     cudaEvent_t ev0 = nullptr, ev1 = nullptr;
     int eval_blocks = 0;
-    int wave_blocks = 0;
+    int wave_blocks = 0;                  // grid of the wave for the current exploit
+    int wave_occ = 0;                     // CTAs per SM the wave can keep resident (<= 2)
     int async_blocks = 0;
     int profiling = 0;
     pirrt_profile prof{};
@@ -160,18 +168,20 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
 // Write every kernel argument struct of the exploit path into the device
 // argument block (stream-ordered; skipped when nothing changed).
 template <typename CT>
-pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels, int push) {
+pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels, int push,
+                        unsigned tail_max) {
     pirrt_graph::ArgsKey key;
     key.n = G->n;
     key.cur = G->cur;
     key.dense_limit = dense_limit;
     key.max_levels = max_levels;
     key.push = push;
+    key.tail_max = tail_max;
     if (key == G->args_key) return PIRRT_OK;
     std::memset(G->hargs, 0, kArgBytes);
     const Entry<CT> *adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
     auto *ia = reinterpret_cast<ImproveArgs<CT> *>(G->hargs + kArgImprove);
-    ia->row_off = G->row_off[G->cur];
+    ia->rows = G->rows;
     ia->adj = adj;
     ia->g = G->g;
     ia->g32 = G->g32;
@@ -206,7 +216,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
         ea->role = off == kArgEvalFallback ? 1 : 0;
     }
     auto *wa = reinterpret_cast<WaveArgs<CT> *>(G->hargs + kArgWave);
-    wa->row_off = G->row_off[G->cur];
+    wa->rows = G->rows;
     wa->adj = adj;
     wa->p = G->p;
     wa->pc = static_cast<const CT *>(G->pc);
@@ -215,6 +225,11 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->switched = G->switched;
     wa->lvl[0] = G->wl[0];
     wa->lvl[1] = G->wl[1];
+    wa->lvg[0] = G->acc[0];
+    wa->lvg[1] = G->acc[1];
+    wa->dg = G->dg;
+    wa->list_cap = G->cap_n;
+    wa->tail_max = tail_max;
     wa->wstamp = G->wstamp;
     wa->stamp = G->stamp;
     wa->list[0] = G->list[0];
@@ -226,7 +241,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->push = push;
     wa->cand = G->cand;
     auto *aa = reinterpret_cast<AsyncArgs<CT> *>(G->hargs + kArgAsync);
-    aa->row_off = G->row_off[G->cur];
+    aa->rows = G->rows;
     aa->adj = adj;
     aa->p = G->p;
     aa->pc = static_cast<const CT *>(G->pc);
@@ -250,7 +265,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     aa->cand = G->cand;
     for (size_t off : {kArgMark, kArgMarkFallback}) {
         auto *ma = reinterpret_cast<MarkArgs<CT> *>(G->hargs + off);
-        ma->row_off = G->row_off[G->cur];
+        ma->rows = G->rows;
         ma->adj = adj;
         ma->dg = G->dg;
         ma->stamp = G->stamp;
@@ -396,10 +411,32 @@ pirrt_status launch_evaluate(pirrt_graph *G, cudaStream_t st, size_t off) {
                                          dev_arg<EvaluateArgs<CT>>(G, off));
 }
 
+// The wave and the rest of the iteration (pointer-jumping finish, marking,
+// advance) in one cooperative launch.
 template <typename CT>
-pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st) {
-    return launch_coop<WaveArgs<CT>>(G, st, wave_evaluate_kernel<CT>, G->wave_blocks, kWaveThreads,
-                                     dev_arg<WaveArgs<CT>>(G, kArgWave));
+pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st, cudaGraphConditionalHandle cond,
+                         int use_cond) {
+    cudaLaunchConfig_t cfg{};
+    cfg.gridDim = dim3(G->wave_blocks);
+    cfg.blockDim = dim3(kWaveThreads);
+    cfg.dynamicSmemBytes = 0;
+    cfg.stream = st;
+    cudaLaunchAttribute attr[1];
+    attr[0].id = cudaLaunchAttributeCooperative;
+    attr[0].val.cooperative = 1;
+    cfg.attrs = attr;
+    cfg.numAttrs = 1;
+    CK(cudaLaunchKernelEx(&cfg, wave_evaluate_kernel<CT>, dev_arg<WaveArgs<CT>>(G, kArgWave),
+                          dev_arg<EvaluateArgs<CT>>(G, kArgEvalFallback),
+                          dev_arg<MarkArgs<CT>>(G, kArgMarkFallback), cond, use_cond));
+    return PIRRT_OK;
+}
+
+// Kernel launches of one Replan iteration.
+int iteration_launches(int tile, bool jump, bool async) {
+    const int improve = tile == 0 ? 2 : 1;
+    if (jump) return improve + 3;
+    return improve + (async ? 5 : 1);
 }
 
 constexpr size_t kAsyncSmem = (size_t)kAsyncLocal * (sizeof(double) + 2 * sizeof(int32_t));
@@ -428,19 +465,21 @@ pirrt_status launch_mark(pirrt_graph *G, cudaStream_t st, size_t off) {
 }
 
 // One Replan iteration after Improve: the Evaluate strategy, then advance.
-// JUMP: pointer jumping + marking.  WAVE / AUTO: the top-down wave, then a
-// pointer-jumping finish and its marking, both no-ops unless the wave hit its
-// level cap.
+// JUMP: pointer jumping + marking + advance.  WAVE / AUTO: one launch (the
+// wave ends the iteration itself, see wave_evaluate_kernel).  ASYNC: the
+// walk, then a pointer-jumping finish and its marking, both no-ops unless
+// the walk gave up, then advance.
 template <typename CT>
 pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile, bool jump,
                               bool async, cudaGraphConditionalHandle cond, int use_cond) {
     pirrt_status rc;
     if ((rc = launch_improve<CT>(G, st, gs, tile))) return rc;
+    if (!jump && !async) return launch_wave<CT>(G, st, cond, use_cond);
     if (jump) {
         if ((rc = launch_evaluate<CT>(G, st, kArgEval))) return rc;
         if ((rc = launch_mark<CT>(G, st, kArgMark))) return rc;
     } else {
-        if ((rc = async ? launch_async<CT>(G, st) : launch_wave<CT>(G, st))) return rc;
+        if ((rc = launch_async<CT>(G, st))) return rc;
         pre_jump_kernel<<<1, 1, 0, st>>>(G->ctr);
         CKL();
         if ((rc = launch_evaluate<CT>(G, st, kArgEvalFallback))) return rc;
@@ -454,11 +493,12 @@ pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile,
 // The Replan loop as a CUDA graph: a WHILE conditional node whose body is one
 // iteration; advance_kernel sets the condition.  Cached per kernel choice.
 template <typename CT>
-pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, bool async,
+pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, bool async, int wave_ctas,
                       cudaGraphExec_t *out) {
     const unsigned long long key = ((unsigned long long)gs << 8) | ((unsigned long long)tile << 1) |
                                    (jump ? 1ull : 0ull) | ((unsigned long long)sizeof(CT) << 24) |
-                                   (async ? 1ull << 32 : 0ull);
+                                   (async ? 1ull << 32 : 0ull) |
+                                   ((unsigned long long)wave_ctas << 40);
     auto it = G->loops.find(key);
     if (it != G->loops.end()) {
         *out = it->second;
@@ -499,6 +539,24 @@ pirrt_status get_loop(pirrt_graph *G, int gs, int tile, bool jump, bool async,
     return PIRRT_OK;
 }
 
+// Pool space of every row for an insertion (ralloc), and its exclusive scan
+// (roff; roff[n_after] = the total).
+pirrt_status insert_plan_scan(pirrt_graph *G, int64_t n_old, int64_t n_after, int repack) {
+    const int64_t len = n_after + 1;
+    insert_plan<<<grid_for(len, kThreads, G->num_sms * 32), kThreads, 0, G->stream>>>(
+        n_old, n_after, G->rows, G->deg, G->ralloc, repack);
+    CKL();
+    const int64_t n_tiles = (len + kScanTile - 1) / kScanTile;
+    scan_tile_reduce<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->ralloc, len, G->tile_sums);
+    CKL();
+    scan_tile_sums<<<1, kThreads, 0, G->stream>>>(G->tile_sums, n_tiles);
+    CKL();
+    scan_tile_apply<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->ralloc, len, G->tile_sums,
+                                                                    G->roff);
+    CKL();
+    return PIRRT_OK;
+}
+
 template <typename CT>
 pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const int32_t *src,
                          const int32_t *dst, const CT *cost) {
@@ -515,8 +573,14 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
             n_edges, src, dst, cost, n_after, G->deg, G->ctr);
         CKL();
     }
+    // 2. plan the pool space of the rows that outgrow their room (scan); one
+    //    host read of the validation status and the space needed
+    pirrt_status rc = insert_plan_scan(G, n_old, n_after, 0);
+    if (rc) return rc;
     CK(cudaMemcpyAsync(&G->ctr_host->status, &G->ctr->status, sizeof(unsigned),
                        cudaMemcpyDeviceToHost, G->stream));
+    CK(cudaMemcpyAsync(G->hx, &G->roff[n_after], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                       G->stream));
     CK(cudaStreamSynchronize(G->stream));
     if (G->ctr_host->status) {
         CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
@@ -525,25 +589,46 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
                     "that is not finite and > 0",
                     (long long)n_after);
     }
-    // 2. new row offsets = old offsets + exclusive scan of the added counts
-    const int nxt = G->cur ^ 1;
-    const int64_t len = n_after + 1;
-    const int64_t n_tiles = (len + kScanTile - 1) / kScanTile;
-    scan_tile_reduce<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->deg, len, G->tile_sums);
-    CKL();
-    scan_tile_sums<<<1, kThreads, 0, G->stream>>>(G->tile_sums, n_tiles);
-    CKL();
-    scan_tile_apply<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(
-        G->deg, len, G->tile_sums, G->row_off[G->cur], n_old, G->row_off[nxt]);
-    CKL();
-    // 3. old rows into the new buffer, new entries at the row tails
-    const Entry<CT> *old_adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
-    Entry<CT> *new_adj = static_cast<Entry<CT> *>(G->adj[nxt]);
-    if (n_old > 0 && G->m > 0) {
-        insert_copy_rows<CT><<<grid_for(n_old * 32, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_old, G->row_off[G->cur], old_adj, G->row_off[nxt], new_adj);
+    const int64_t need = G->hx[0];
+    // 3. move those rows to the end of the pool, or repack every row into the
+    //    other pool when this one is used up; set every row's new length
+    const int move_blocks = grid_for((n_after + 31) / 32 * 32, kThreads, max_blocks);
+    if (G->pool_used + need <= G->pool_cap) {
+        Entry<CT> *pool = static_cast<Entry<CT> *>(G->adj[G->cur]);
+        insert_move_rows<CT><<<move_blocks, kThreads, 0, G->stream>>>(
+            n_old, n_after, G->rows, G->deg, G->ralloc, G->roff, (long long)G->pool_used, pool,
+            pool, G->ctr, 0);
         CKL();
+        G->pool_used += need;
+    } else {
+        const int nxt = G->cur ^ 1;
+        if (!G->adj[nxt]) {
+            const cudaError_t e =
+                cudaMalloc(&G->adj[nxt], G->entry_bytes * (size_t)(G->pool_cap + 16));
+            if (e != cudaSuccess) {
+                cudaGetLastError();
+                G->adj[nxt] = nullptr;
+                return fail(G, PIRRT_ERR_OOM, "insert_batch: no memory for a second CSR pool");
+            }
+        }
+        if ((rc = insert_plan_scan(G, n_old, n_after, 1))) return rc;
+        CK(cudaMemcpyAsync(G->hx, &G->roff[n_after], sizeof(int64_t), cudaMemcpyDeviceToHost,
+                           G->stream));
+        CK(cudaStreamSynchronize(G->stream));
+        const int64_t total = G->hx[0];
+        if (total > G->pool_cap)
+            return fail(G, PIRRT_ERR_CAPACITY, "insert_batch: repacked CSR needs %lld entries",
+                        (long long)total);
+        insert_move_rows<CT><<<move_blocks, kThreads, 0, G->stream>>>(
+            n_old, n_after, G->rows, G->deg, G->ralloc, G->roff, 0ll,
+            static_cast<const Entry<CT> *>(G->adj[G->cur]), static_cast<Entry<CT> *>(G->adj[nxt]),
+            G->ctr, 1);
+        CKL();
+        G->cur = nxt;
+        G->pool_used = total;
+        G->prof.launches += 4;
     }
+    Entry<CT> *new_adj = static_cast<Entry<CT> *>(G->adj[G->cur]);
     // 4. seed the new vertices (before the scatter, whose offers may reach them)
     if (n_new > 0) {
         insert_init_vertices<CT><<<grid_for(n_new, kThreads, max_blocks), kThreads, 0, G->stream>>>(
@@ -551,24 +636,27 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
             G->stamp, G->list[0], G->list[1], G->ctr);
         CKL();
     }
+    // 5. new entries at the row tails
     if (n_edges > 0) {
         insert_scatter<CT><<<grid_for(n_edges, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_edges, src, dst, cost, G->row_off[nxt], G->deg, new_adj, G->stamp, G->cfg.root,
+            n_edges, src, dst, cost, G->rows, G->deg, new_adj, G->stamp, G->cfg.root,
             G->list[0], G->list[1], G->g, G->cand, G->ctr);
         CKL();
     }
-    G->prof.launches += 3 + (n_edges > 0 ? 2 : 0) + (n_old > 0 && G->m > 0 ? 1 : 0) + (n_new > 0 ? 1 : 0);
+    G->prof.launches += 5 + (n_edges > 0 ? 2 : 0) + (n_new > 0 ? 1 : 0);
     G->prof.insert_calls += 1;
     G->prof.insert_new_entries += 2 * n_edges;
-    G->prof.insert_copied_entries += G->m;
     if (prof) {
         CK(cudaEventRecord(G->pev[7], G->stream));
         CK(cudaEventSynchronize(G->pev[7]));
         float ms = 0.f;
         CK(cudaEventElapsedTime(&ms, G->pev[6], G->pev[7]));
         G->prof.insert_ms += ms;
+        unsigned long long copied = 0;
+        CK(cudaMemcpy(&copied, &G->ctr->insert_copied, sizeof(copied), cudaMemcpyDeviceToHost));
+        G->prof.insert_copied_entries += (int64_t)(copied - G->copied_seen);
+        G->copied_seen = copied;
     }
-    G->cur = nxt;
     G->n = n_after;
     G->m = m_after;
     return PIRRT_OK;
@@ -582,7 +670,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         o.wave_levels < 0 || o.evaluate < PIRRT_EVAL_AUTO || o.evaluate > PIRRT_EVAL_ASYNC ||
         !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3) ||
         !(o.group == 0 || o.group == 2 || o.group == 4 || o.group == 8 || o.group == 16 ||
-          o.group == 32))
+          o.group == 32) ||
+        o.wave_ctas < 0 || o.wave_ctas > 2)
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = o.group, tile = o.tile;
@@ -612,8 +701,13 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     bool jump = mode == PIRRT_EVAL_JUMP ||
                 (mode == PIRRT_EVAL_AUTO && G->deep_hint && (G->exploits % 8) != 0);
     G->exploits += 1;
-    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0);
+    // one CTA walks levels of at most this many vertices (~34 CSR entries each
+    // on the 6-D roadmaps, a few passes of the CTA's threads)
+    const unsigned tail_max = o.wave_tail < 0 ? 0u : (o.wave_tail > 0 ? (unsigned)o.wave_tail : 64u);
+    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0, tail_max);
     if (rc) return rc;
+    const int wave_ctas = o.wave_ctas > 0 ? std::min(o.wave_ctas, G->wave_occ) : G->wave_occ;
+    G->wave_blocks = G->num_sms * wave_ctas;
     const bool prof = G->profiling != 0;
     const bool use_graph = !prof && o.host_loop == 0;
     double eps = o.eps;
@@ -635,7 +729,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     bool graph_ran = false;
     if (use_graph) {
         cudaGraphExec_t exec = nullptr;
-        rc = get_loop<CT>(G, gs, tile, jump, async, &exec);
+        rc = get_loop<CT>(G, gs, tile, jump, async, wave_ctas, &exec);
         if (rc == PIRRT_OK) {
             CK(cudaGraphLaunch(exec, G->stream));
             graph_ran = true;
@@ -653,20 +747,24 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 if ((rc = launch_evaluate<CT>(G, G->stream, kArgEval))) return rc;
                 if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
                 if ((rc = launch_mark<CT>(G, G->stream, kArgMark))) return rc;
-            } else {
-                if ((rc = async ? launch_async<CT>(G, G->stream) : launch_wave<CT>(G, G->stream)))
-                    return rc;
+            } else if (async) {
+                if ((rc = launch_async<CT>(G, G->stream))) return rc;
                 if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
                 pre_jump_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
                 CKL();
                 if ((rc = launch_evaluate<CT>(G, G->stream, kArgEvalFallback))) return rc;
                 if ((rc = launch_mark<CT>(G, G->stream, kArgMarkFallback))) return rc;
+            } else {
+                if ((rc = launch_wave<CT>(G, G->stream, cudaGraphConditionalHandle{}, 0))) return rc;
+                if (prof) CK(cudaEventRecord(G->pev[2], G->stream));
             }
             if (prof) CK(cudaEventRecord(G->pev[3], G->stream));
-            advance_kernel<<<1, 1, 0, G->stream>>>(G->ctr, cudaGraphConditionalHandle{}, 0);
-            CKL();
+            if (jump || async) {
+                advance_kernel<<<1, 1, 0, G->stream>>>(G->ctr, cudaGraphConditionalHandle{}, 0);
+                CKL();
+            }
             if ((rc = pull_counters(G))) return rc;
-            P.launches += jump ? 4 : 6;
+            P.launches += iteration_launches(tile, jump, async);
             const DevCounters *h = G->ctr_host;
             float t_imp = 0.f, t_eval = 0.f, t_mark = 0.f;
             if (prof) {
@@ -732,7 +830,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         const bool saw_deep = h.cum_jump_evals > 0;
         if (saw_deep || !jump || (G->exploits % 8) == 1) G->deep_hint = saw_deep ? 1 : 0;
     }
-    if (graph_ran) P.launches += (int64_t)h.iter * (jump ? 4 : 6);
+    if (graph_ran) P.launches += (int64_t)h.iter * iteration_launches(tile, jump, async);
     s.iterations = (int32_t)h.iter;
     s.converged = h.converged ? 1 : 0;
     s.relaxations = (int64_t)(h.relax + h.offers);
@@ -761,7 +859,7 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     const int blocks = grid_for(G->n, kThreads, G->num_sms * 32);
     CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
     policy_lookup_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
-        G->n, G->cfg.root, parent, G->row_off[G->cur], static_cast<const Entry<CT> *>(G->adj[G->cur]),
+        G->n, G->cfg.root, parent, G->rows, static_cast<const Entry<CT> *>(G->adj[G->cur]),
         tp, tc, G->ctr);
     CKL();
     CK(cudaMemcpyAsync(&G->ctr_host->status, &G->ctr->status, sizeof(unsigned),
@@ -775,7 +873,7 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     policy_commit_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
         G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g, G->g32);
     CKL();
-    pirrt_status rc = write_args<CT>(G, 0u, 1u, 0);
+    pirrt_status rc = write_args<CT>(G, 0u, 1u, 0, 0u);
     if (rc) return rc;
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr, 1u, 0ull);
     CKL();
@@ -797,13 +895,14 @@ void free_all(pirrt_graph *G) {
     G->loops.clear();
     if (G->capture) cudaStreamDestroy(G->capture);
     if (G->hargs) cudaFreeHost(G->hargs);
-    void *bufs[] = {G->dargs, G->pexport, G->row_off[0], G->row_off[1], G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
+    void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
                     G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage};
     for (void *q : bufs)
         if (q) cudaFree(q);
     if (G->ctr_host) cudaFreeHost(G->ctr_host);
+    if (G->hx) cudaFreeHost(G->hx);
     if (G->ev0) cudaEventDestroy(G->ev0);
     if (G->ev1) cudaEventDestroy(G->ev1);
     for (cudaEvent_t e : G->pev)
@@ -965,11 +1064,15 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
             return bail(e_ == cudaErrorMemoryAllocation ? PIRRT_ERR_OOM : PIRRT_ERR_CUDA); \
         }                                                                               \
     } while (0)
-    ALLOC(G->row_off[0], sizeof(int64_t) * (nv + 1));
-    ALLOC(G->row_off[1], sizeof(int64_t) * (nv + 1));
-    // +16 entries: a staged row copy is rounded up to 16 bytes past the row
-    ALLOC(G->adj[0], G->entry_bytes * (ne + 16));
-    ALLOC(G->adj[1], G->entry_bytes * (ne + 16));
+    ALLOC(G->rows, sizeof(RowExt) * nv);
+    ALLOC(G->ralloc, sizeof(int32_t) * (nv + 1));
+    ALLOC(G->roff, sizeof(int64_t) * (nv + 1));
+    // A pool holds every row with room to grow plus the space rows moved out
+    // of; a repack (1.25 x length + 2 per row) always fits.  The second pool
+    // is allocated by the first repack.  +16 entries: a staged row copy is
+    // rounded up to 16 bytes past the row.
+    G->pool_cap = 2 * (int64_t)ne + 4 * (int64_t)nv + 64;
+    ALLOC(G->adj[0], G->entry_bytes * (size_t)(G->pool_cap + 16));
     ALLOC(G->g, sizeof(double) * nv);
     ALLOC(G->g32, sizeof(float) * nv);
     ALLOC(G->p, sizeof(int32_t) * nv);
@@ -1000,6 +1103,8 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     if (cudaMallocHost((void **)&G->hargs, kArgBytes) != cudaSuccess) return bail(PIRRT_ERR_OOM);
     if (cudaStreamCreateWithFlags(&G->capture, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PIRRT_ERR_CUDA);
+    if (cudaMallocHost((void **)&G->hx, 2 * sizeof(int64_t)) != cudaSuccess)
+        return bail(PIRRT_ERR_OOM);
     if (cudaMallocHost((void **)&G->ctr_host, sizeof(DevCounters)) != cudaSuccess)
         return bail(PIRRT_ERR_OOM);
     if (cudaEventCreate(&G->ev0) != cudaSuccess || cudaEventCreate(&G->ev1) != cudaSuccess)
@@ -1026,7 +1131,8 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
         return bail(PIRRT_ERR_CUDA);
     wocc = std::min(wocc, wocc64);
     if (wocc < 1) return bail(PIRRT_ERR_CUDA);
-    G->wave_blocks = G->num_sms * std::min(wocc, 2);
+    G->wave_occ = std::min(wocc, 2);
+    G->wave_blocks = G->num_sms * G->wave_occ;
     int aocc = 0, aocc64 = 0;
     if (cudaFuncSetAttribute(async_evaluate_kernel<float>,
                              cudaFuncAttributeMaxDynamicSharedMemorySize, (int)kAsyncSmem) !=
@@ -1056,8 +1162,6 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
 pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     if (!G) return PIRRT_ERR_INVALID_ARG;
     CK(cudaSetDevice(G->cfg.device));
-    CK(cudaMemsetAsync(G->row_off[0], 0, sizeof(int64_t), G->stream));
-    CK(cudaMemsetAsync(G->row_off[1], 0, sizeof(int64_t), G->stream));
     CK(cudaMemsetAsync(G->stamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->swstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
@@ -1068,6 +1172,8 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemcpyAsync(&G->ctr->wave_epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice,
                        G->stream));
     CK(cudaStreamSynchronize(G->stream));
+    G->pool_used = 0;
+    G->copied_seen = 0;
     G->n = 0;
     G->m = 0;
     G->cur = 0;
@@ -1182,9 +1288,13 @@ pirrt_status pirrt_graph_get_parents(const pirrt_graph *Gc, int32_t *p_out, int6
 
 pirrt_status pirrt_graph_set_profiling(pirrt_graph *G, int enable) {
     if (!G) return PIRRT_ERR_INVALID_ARG;
+    CK(cudaSetDevice(G->cfg.device));
     G->profiling = enable ? 1 : 0;
     G->prof = pirrt_profile{};
     G->trace.clear();
+    CK(cudaStreamSynchronize(G->stream));
+    CK(cudaMemcpy(&G->copied_seen, &G->ctr->insert_copied, sizeof(G->copied_seen),
+                  cudaMemcpyDeviceToHost));
     return PIRRT_OK;
 }
 
@@ -1201,18 +1311,37 @@ pirrt_status pirrt_graph_get_profile(const pirrt_graph *G, pirrt_profile *out) {
     return PIRRT_OK;
 }
 
-pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *Gc, int64_t *row_off, int32_t *col,
-                                       void *cost, int on_device) {
-    pirrt_graph *G = const_cast<pirrt_graph *>(Gc);
-    if (!G) return PIRRT_ERR_INVALID_ARG;
-    CK(cudaSetDevice(G->cfg.device));
+extern "C++" {
+template <typename CT>
+pirrt_status export_impl(pirrt_graph *G, int64_t *row_off, int32_t *col, void *cost,
+                         int on_device) {
     const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    const int64_t n = G->n, len = n + 1;
+    const int max_blocks = G->num_sms * 32;
+    // compact offsets: exclusive scan of the row lengths
+    row_lengths<<<grid_for(len, kThreads, max_blocks), kThreads, 0, G->stream>>>(n, G->rows,
+                                                                               G->ralloc);
+    CKL();
+    const int64_t n_tiles = (len + kScanTile - 1) / kScanTile;
+    scan_tile_reduce<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->ralloc, len, G->tile_sums);
+    CKL();
+    scan_tile_sums<<<1, kThreads, 0, G->stream>>>(G->tile_sums, n_tiles);
+    CKL();
+    scan_tile_apply<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->ralloc, len, G->tile_sums,
+                                                                    G->roff);
+    CKL();
     if (row_off)
-        CK(cudaMemcpyAsync(row_off, G->row_off[G->cur], sizeof(int64_t) * (size_t)(G->n + 1), kind,
-                           G->stream));
+        CK(cudaMemcpyAsync(row_off, G->roff, sizeof(int64_t) * (size_t)len, kind, G->stream));
     if (G->m > 0 && (col || cost)) {
+        pirrt_status rc = ensure_stage(G, G->entry_bytes * (size_t)G->m);
+        if (rc) return rc;
+        Entry<CT> *packed = static_cast<Entry<CT> *>(G->stage);
+        export_rows<CT><<<grid_for((n + 31) / 32 * 32, kThreads, max_blocks), kThreads, 0,
+                          G->stream>>>(n, G->rows, G->roff,
+                                       static_cast<const Entry<CT> *>(G->adj[G->cur]), packed);
+        CKL();
         // entries are (col, cost) records: split with strided 2-D copies
-        const char *base = static_cast<const char *>(G->adj[G->cur]);
+        const char *base = static_cast<const char *>(G->stage);
         if (col)
             CK(cudaMemcpy2DAsync(col, sizeof(int32_t), base, G->entry_bytes, sizeof(int32_t),
                                  (size_t)G->m, kind, G->stream));
@@ -1224,6 +1353,16 @@ pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *Gc, int64_t *row_off, 
     }
     CK(cudaStreamSynchronize(G->stream));
     return PIRRT_OK;
+}
+}  // extern "C++"
+
+pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *Gc, int64_t *row_off, int32_t *col,
+                                       void *cost, int on_device) {
+    pirrt_graph *G = const_cast<pirrt_graph *>(Gc);
+    if (!G) return PIRRT_ERR_INVALID_ARG;
+    CK(cudaSetDevice(G->cfg.device));
+    if (G->cfg.cost_dtype == PIRRT_COST_F32) return export_impl<float>(G, row_off, col, cost, on_device);
+    return export_impl<double>(G, row_off, col, cost, on_device);
 }
 
 

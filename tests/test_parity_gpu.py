@@ -241,6 +241,55 @@ def test_csr_equals_host_sort_of_union(c2_small):
                 np.testing.assert_array_equal(cost[o2], cc[o])
 
 
+def _csr_matches(off, col, cost, uu, vv, cc, n):
+    """Packed export equals a host sort of both directions of the edge list."""
+    U = np.r_[uu, vv].astype(np.int64)
+    V = np.r_[vv, uu].astype(np.int64)
+    C = np.r_[cc, cc]
+    o = np.lexsort((C, V, U))
+    np.testing.assert_array_equal(off, np.searchsorted(U[o], np.arange(n + 1)))
+    rows = np.repeat(np.arange(n), np.diff(off))
+    o2 = np.lexsort((cost, col, rows))
+    np.testing.assert_array_equal(col[o2], V[o])
+    np.testing.assert_array_equal(cost[o2], C[o])
+
+
+@pytest.mark.parametrize("dtype", [np.float32, np.float64])
+def test_rows_that_outgrow_their_room_move_and_repack(dtype):
+    """Every row grows by two entries per block for 30 blocks: rows outgrow
+    their room again and again, move to the end of the pool, and the pool
+    runs out, so every row is repacked into the second pool (more than once).
+    After every few blocks the packed CSR equals a host sort of the union, and
+    the exploited tree equals Dijkstra on it."""
+    n, blocks = 3000, 30
+    rng = np.random.default_rng(5)
+    w = rng.uniform(1.0, 3.0, (blocks, n))
+    us, vs, cs = [], [], []
+    with P.Graph(n, n * blocks, 0, dtype) as D:
+        D.insert_batch(n, np.zeros(0, np.int32), np.zeros(0, np.int32), np.zeros(0, dtype))
+        D.set_profiling(True)
+        for b in range(blocks):
+            u = np.arange(n, dtype=np.int32)
+            v = ((u + b + 1) % n).astype(np.int32)
+            c = w[b].astype(dtype)
+            D.insert_batch(0, u, v, c)
+            us.append(u)
+            vs.append(v)
+            cs.append(c)
+            if b % 7 == 3 or b == blocks - 1:
+                uu, vv, cc = np.concatenate(us), np.concatenate(vs), np.concatenate(cs)
+                off, col, cost = D.get_adjacency()
+                _csr_matches(off, col, cost, uu, vv, cc, n)
+                D.exploit()
+                g, p = D.get_costs(), D.get_parents()
+                rm = W.Roadmap("grow", np.zeros((n, 2)), uu, vv, cc, np.zeros(n + 1, np.int64), n)
+                d, _ = O.dijkstra(n, uu, vv, cc.astype(np.float64))
+                assert_parity(rm, g, p, d)
+        prof = D.get_profile()
+    # moves and repacks copied old entries many times over
+    assert prof["insert_copied_entries"] > 2 * n * blocks
+
+
 # --------------------------------------------------------- edge cases ---
 
 def test_empty_and_vertex_only_batches():
@@ -425,6 +474,32 @@ def test_c3_wave_and_jump_identical_parents(c3_small):
     A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
     mask, _ = A.unambiguous(d)
     np.testing.assert_array_equal(pw[mask], pj[mask])
+
+
+@pytest.mark.parametrize("tail", [-1, 1, 512, 1_000_000])
+@pytest.mark.parametrize("which", ["c2", "c3"])
+def test_wave_tail_walk_is_bitwise_neutral(c2_small, c3_small, which, tail):
+    """Levels walked by one CTA without grid barriers (none, single-vertex
+    levels, levels up to a tile, every level) give the same schedule bit for
+    bit."""
+    rm = c2_small if which == "c2" else c3_small
+    g0, p0, s0 = gpu_schedule(rm, evaluate="wave", wave_tail=-1)
+    g1, p1, s1 = gpu_schedule(rm, evaluate="wave", wave_tail=tail)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+    assert [s["iterations"] for s in s0] == [s["iterations"] for s in s1]
+    assert [s["dense_sweeps"] for s in s0] == [s["dense_sweeps"] for s in s1]
+
+
+@pytest.mark.parametrize("ctas", [1, 2])
+def test_wave_grid_size_is_bitwise_neutral(c3_small, ctas):
+    """One or two wave CTAs per SM: the same schedule bit for bit."""
+    rm = c3_small
+    g0, p0, s0 = gpu_schedule(rm)
+    g1, p1, s1 = gpu_schedule(rm, wave_ctas=ctas)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+    assert [s["iterations"] for s in s0] == [s["iterations"] for s in s1]
 
 
 @pytest.mark.parametrize("which", ["c2", "c3"])

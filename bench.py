@@ -278,6 +278,7 @@ def run_ours(args) -> None:
     ms_per_step = total_ms / args.steps
 
     # end to end through the C ABI with pinned host buffers
+    e2e_steps = 0 if args.no_e2e else args.steps
     pin_u = torch.from_numpy(rm.u).pin_memory()
     pin_v = torch.from_numpy(rm.v).pin_memory()
     pin_c = torch.from_numpy(rm.cost).pin_memory()
@@ -287,7 +288,7 @@ def run_ours(args) -> None:
     barrier()
     t0 = time.perf_counter()
     e2e_relax = 0
-    for _ in range(args.steps):
+    for _ in range(e2e_steps):
         r, _ = step(device_inputs=False)
         G.get_costs(out_g)
         G.get_parents(out_p)
@@ -367,7 +368,7 @@ def run_ours(args) -> None:
                      "bytes_per_launch": round(dom_bytes / launches, 1),
                      "avg_launch_ms": round(dom_ms_avg, 5)},
         "kernels": kernels,
-        "e2e": {"value": round(e2e_relax / e2e_s, 1), "unit": UNIT,
+        "e2e": {"value": round(e2e_relax / e2e_s, 1) if e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
         "gpu_launches": int(round(prof["launches"] * args.steps / max(1, len(prof_times)))),
         "clocks": clocks,
@@ -595,6 +596,8 @@ def main():
                     help="run every exploit from the host loop (no CUDA graphs), e.g. under ncu")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-e2e", action="store_true",
+                    help="skip the end-to-end pass (e.g. for a profiler's launch list)")
     ap.add_argument("--trace", default=None, help="save the per-iteration trace (.npy)")
     args = ap.parse_args()
     if args.impl == "reference":

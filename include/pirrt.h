@@ -153,10 +153,14 @@ pirrt_status pirrt_graph_reset(pirrt_graph *g);
  * g = +inf and no parent, except g(root) = 0) and n_edges undirected edges
  * src[e] -- dst[e] with cost[e] (float or double per cost_dtype).  Endpoints
  * may be old or new vertices.  The new vertices and the endpoints of the
- * new edges seed the next exploit's Improve frontier.
+ * new edges seed the next exploit's Improve frontier, and each new edge
+ * offers both endpoints their candidate through it.  The new entries go to
+ * the tails of their rows; only rows that outgrow their room are moved.
  * Errors: PIRRT_ERR_CAPACITY, PIRRT_ERR_BAD_INPUT (ids outside
- * [0, n + n_new), src == dst, cost <= 0, NaN or Inf); on error the graph is
- * unchanged.  Synchronises the stream once to read the validation result. */
+ * [0, n + n_new), src == dst, cost <= 0, NaN or Inf), PIRRT_ERR_OOM (the
+ * second CSR pool could not be allocated); on error the graph is unchanged.
+ * Synchronises the stream once to read the validation result and the pool
+ * space the block needs (and once more when the pool is repacked). */
 pirrt_status pirrt_graph_insert_batch(pirrt_graph *g, int64_t n_new_vertices, int64_t n_edges,
                                       const int32_t *src, const int32_t *dst, const void *cost,
                                       int on_device);

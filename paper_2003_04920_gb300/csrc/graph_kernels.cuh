@@ -938,39 +938,48 @@ static __global__ void pre_jump_kernel(DevCounters *c) {
 // iteration cap), and make the list built by this iteration's Evaluate the
 // current one.  In a captured loop the decision drives the WHILE node.
 // Called by one thread, possibly at the end of a kernel whose other CTAs
-// wrote the counters: every access goes through L2 (volatile).
-__device__ __forceinline__ void advance_iteration(DevCounters *cc, cudaGraphConditionalHandle cond,
+// wrote the counters: every field is read through L2 (ld.global.cg, issued
+// together), then written back.
+__device__ __forceinline__ void advance_iteration(DevCounters *c, cudaGraphConditionalHandle cond,
                                                   int use_cond) {
     __threadfence();
-    volatile DevCounters *c = cc;
-    const unsigned sw = c->n_switched;
-    double dj = 0.0, eps = 0.0;
-    dj = __longlong_as_double((long long)c->dj_bits);
-    eps = __longlong_as_double((long long)c->eps_bits);
+    const unsigned sw = __ldcg(&c->n_switched);
+    const double dj = __longlong_as_double((long long)__ldcg(&c->dj_bits));
+    const double eps = __longlong_as_double((long long)__ldcg(&c->eps_bits));
+    const unsigned n_dg = __ldcg(&c->n_dg), levels = __ldcg(&c->wave_levels);
+    const unsigned dense_next = __ldcg(&c->dense_next), n_next = __ldcg(&c->n_next);
+    const unsigned dense = __ldcg(&c->dense), rounds = __ldcg(&c->rounds);
+    const unsigned jumped = __ldcg(&c->jumped), status = __ldcg(&c->status);
+    const unsigned long long switches = __ldcg(&c->switches);
+    const unsigned cwl = __ldcg(&c->cum_wave_levels), cjr = __ldcg(&c->cum_jump_rounds);
+    const unsigned cd = __ldcg(&c->cum_dense), cje = __ldcg(&c->cum_jump_evals);
+    const unsigned wave_epoch = __ldcg(&c->wave_epoch), iter = __ldcg(&c->iter) + 1u;
+    const unsigned max_iters = __ldcg(&c->max_iters), la = __ldcg(&c->la);
+    const unsigned epoch = __ldcg(&c->epoch);
     c->last_switched = sw;
-    c->last_dg = c->n_dg;
-    c->last_levels = c->wave_levels;
-    c->last_next = c->dense_next ? 0u : c->n_next;
-    c->last_dense = c->dense;
-    c->last_rounds = c->rounds;
-    c->last_jumped = c->jumped;
-    c->switches += sw;
-    c->cum_wave_levels += c->wave_levels;
-    c->cum_jump_rounds += c->rounds;
-    c->cum_dense += c->dense ? 1u : 0u;
-    c->cum_jump_evals += (c->jumped && sw) ? 1u : 0u;
-    c->wave_epoch += c->wave_levels + 1u;
-    c->iter += 1u;
+    c->last_dg = n_dg;
+    c->last_levels = levels;
+    c->last_next = dense_next ? 0u : n_next;
+    c->last_dense = dense;
+    c->last_rounds = rounds;
+    c->last_jumped = jumped;
+    c->switches = switches + sw;
+    c->cum_wave_levels = cwl + levels;
+    c->cum_jump_rounds = cjr + rounds;
+    c->cum_dense = cd + (dense ? 1u : 0u);
+    c->cum_jump_evals = cje + ((jumped && sw) ? 1u : 0u);
+    c->wave_epoch = wave_epoch + levels + 1u;
+    c->iter = iter;
     const bool stable = sw == 0u || dj <= eps;
-    const bool stop = stable || c->status != 0u || c->iter >= c->max_iters;
-    c->converged = (stable && c->status == 0u) ? 1u : 0u;
+    const bool stop = stable || status != 0u || iter >= max_iters;
+    c->converged = (stable && status == 0u) ? 1u : 0u;
     c->cont = stop ? 0u : 1u;
-    c->la ^= 1u;
-    c->epoch += 1u;
-    c->n_active = c->dense_next ? 0u : c->n_next;
-    c->dense = c->dense_next;
+    c->la = la ^ 1u;
+    c->epoch = epoch + 1u;
+    c->n_active = dense_next ? 0u : n_next;
+    c->dense = dense_next;
     c->dense_next = 0u;
-    clear_iteration(cc);
+    clear_iteration(c);
     __threadfence();
     if (use_cond) cudaGraphSetConditional(cond, stop ? 0u : 1u);
 }

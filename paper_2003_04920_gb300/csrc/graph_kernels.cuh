@@ -1,7 +1,8 @@
 // Kernels of the single-graph exploitation path of PI-RRT#:
-//   Batched-Extension insertion (Alg. 3; Sec. IV-A coordinate list merged
-//   into a device CSR), Improve (Alg. 2; Sec. IV-B), Evaluate (Alg. 2;
-//   Sec. IV-C) and the changed-vertex frontier.
+//   Batched-Extension insertion (Alg. 3; Sec. IV-A: a coordinate list added
+//   to a device CSR, here one whose rows keep room to grow), Improve (Alg. 2;
+//   Sec. IV-B), Evaluate (Alg. 2; Sec. IV-C), the changed-vertex frontier and
+//   the end of a Replan iteration.
 #pragma once
 
 #include <cfloat>

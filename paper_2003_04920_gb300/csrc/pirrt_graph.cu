@@ -3,10 +3,10 @@
 // All graph state (CSR, g, parents, work lists) stays resident on the
 // device.  A Replan (Alg. 2: Improve, then Evaluate, until no parent
 // switches) runs as one CUDA-graph launch whose WHILE node repeats the loop
-// body on the device -- Improve, Evaluate, and an advance kernel that tests
-// convergence and sets the loop condition -- so the host waits once per
-// exploit.  With profiling enabled the same kernels run from a host loop
-// that reads the counter block after every iteration.
+// body on the device -- Improve, then Evaluate, which ends the iteration by
+// testing convergence and setting the loop condition -- so the host waits
+// once per exploit.  With profiling enabled the same kernels run from a host
+// loop that reads the counter block after every iteration.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -67,7 +67,7 @@ struct pirrt_graph {
     double *acc[2] = {nullptr, nullptr};
     int32_t *done = nullptr;
     int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
-    unsigned *wstamp = nullptr;           // wave child dedup; first-change stamps
+    unsigned *wstamp = nullptr;           // first-change stamps of an Evaluate
     unsigned *swstamp = nullptr;          // barrier-free Evaluate: switched-vertex stamps
     unsigned long long *cand = nullptr;   // candidate offers for the next Improve
     AsyncQueue *aq = nullptr;             // barrier-free Evaluate: walk state

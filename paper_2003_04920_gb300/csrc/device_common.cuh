@@ -121,6 +121,7 @@ struct DevCounters {
     alignas(128) unsigned wave_cnt[3];  // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
     alignas(128) unsigned bar_count;   // grid barrier: arrivals
     alignas(128) unsigned bar_gen;     // grid barrier: generation
+    alignas(128) unsigned wave_ticket;  // CTAs done with a wave that ends without a barrier
     alignas(128) unsigned wl_count[kMaxJumpRounds + 2];  // pointer-jumping work-list sizes per round
     alignas(128) unsigned status;      // kStatus* bits
     unsigned long long switches;  // parent switches (whole exploit)

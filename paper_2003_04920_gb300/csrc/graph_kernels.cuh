@@ -1077,24 +1077,35 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     block_add(recomputed, &c->evaluated, sh.scan);
     block_add(offers, &c->offers, sh.scan);
     if (blockIdx.x == 0 && tid == 0) c->wave_levels = t;
-    // A grid barrier that timed out raised kStatusTimeout: skip to the end,
-    // which stops the loop.
-    bool ok = grid_barrier(c, nblocks) && *(volatile unsigned *)&c->status == 0u;
-    if (ok && *(volatile unsigned *)&c->wave_incomplete != 0u) {
+    // wave_incomplete was set before the last grid barrier, so every CTA takes
+    // the same branch.  A grid barrier that timed out raised kStatusTimeout:
+    // the iteration still ends, which stops the loop.
+    if (*(volatile unsigned *)&c->wave_incomplete != 0u) {
         // stopped at the level cap: pointer jumping finishes the values and
         // its changes are marked; the wave's changed list gives way
-        if (blockIdx.x == 0 && tid == 0) {
+        bool ok = grid_barrier(c, nblocks) && *(volatile unsigned *)&c->status == 0u;
+        if (ok && blockIdx.x == 0 && tid == 0) {
             c->n_dg = 0u;
             c->rounds = 0u;
             for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
         }
-        ok = grid_barrier(c, nblocks);
+        if (ok) ok = grid_barrier(c, nblocks);
         if (ok) ok = jump_evaluate<CT>(*ep);
         if (ok) ok = grid_barrier(c, nblocks);
         if (ok) mark_changed<CT>(*mp);
-        if (ok) grid_barrier(c, nblocks);
+        grid_barrier(c, nblocks);
+        if (blockIdx.x == 0 && tid == 0) advance_iteration(c, cond, use_cond);
+        return;
     }
-    if (blockIdx.x == 0 && tid == 0) advance_iteration(c, cond, use_cond);
+    // otherwise the last CTA to finish ends the iteration (no grid barrier)
+    __syncthreads();
+    if (tid == 0) {
+        __threadfence();
+        if (atomicAdd(&c->wave_ticket, 1u) == nblocks - 1u) {
+            c->wave_ticket = 0u;
+            advance_iteration(c, cond, use_cond);
+        }
+    }
 }
 
 

@@ -457,8 +457,12 @@ def run_batch(args) -> None:
             B.insert(i, u, v, c)
 
     fill()
+    # Improve from offers (tile 0) or full screened scans (tile 2), lane
+    # counts, the dense threshold and the Evaluate form
     cands = [dict(group=2), dict(group=4), dict(group=8), dict(group=4, dense_fraction=0.1),
-             dict(group=4, evaluate="wave"), dict(group=4, evaluate="jump")]
+             dict(group=4, dense_fraction=0.7), dict(group=2, tile=2), dict(group=4, tile=2),
+             dict(group=4, evaluate="wave"), dict(group=4, evaluate="jump"),
+             dict(group=4, wave_ctas=1)]
     best, idx, _ = B.autotune(cands)
 
     def timed(fn, k):

@@ -384,8 +384,9 @@ def run_ours(args) -> None:
 
 
 KERNEL_FILES = {"improve": ("improve_push.cuh", "improve_screen.cuh", "graph_kernels.cuh",
-                            "device_common.cuh"),
-                "evaluate": ("graph_kernels.cuh", "evaluate_async.cuh", "device_common.cuh"),
+                            "replan_iteration.cuh", "device_common.cuh"),
+                "evaluate": ("graph_kernels.cuh", "replan_iteration.cuh", "improve_push.cuh",
+                             "evaluate_async.cuh", "device_common.cuh"),
                 "insert": ("graph_kernels.cuh", "device_common.cuh")}
 
 

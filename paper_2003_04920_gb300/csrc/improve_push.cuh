@@ -20,10 +20,9 @@
 namespace pirrt {
 
 // One thread per listed vertex decides; G lanes per deciding vertex scan.
+// Any grid of up to 512-thread blocks; every thread of the block calls it.
 template <typename CT, int G>
-__global__ void __launch_bounds__(256, 4)
-improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
-    const ImproveArgs<CT> a = *ap;
+__device__ void improve_push_body(const ImproveArgs<CT> &a) {
     DevCounters *c = a.ctr;
     const int64_t tid0 = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
     const int64_t nthreads = (int64_t)gridDim.x * blockDim.x;
@@ -34,7 +33,7 @@ improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     }
     constexpr int kStageCap = 128;
     constexpr int kUnroll = 4;
-    __shared__ int32_t s_sw[256 / 32][kStageCap];
+    __shared__ int32_t s_sw[512 / 32][kStageCap];
     WarpStage<kStageCap> swq{s_sw[threadIdx.x >> 5], 0u};
     const int32_t *active = (c->la & 1u) ? a.list[1] : a.list[0];
     const int64_t count = (int64_t)c->n_active;
@@ -134,12 +133,19 @@ improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
         }
     }
     // one atomic per block and counter (thousands of warps end together)
-    __shared__ unsigned s_fl[256 / 32 + 1];
-    __shared__ unsigned long long s_red[256 / 32];
+    __shared__ unsigned s_fl[512 / 32 + 1];
+    __shared__ unsigned long long s_red[512 / 32];
     swq.flush_block(a.switched, &c->n_switched, s_fl);
     block_max(djmax, &c->dj_bits, s_red);
     block_add(relax, &c->relax, s_red);
     block_add(improved, &c->improved, s_red);
+}
+
+template <typename CT, int G>
+__global__ void __launch_bounds__(256, 4)
+improve_push_kernel(const ImproveArgs<CT> *__restrict__ ap) {
+    const ImproveArgs<CT> a = *ap;
+    improve_push_body<CT, G>(a);
 }
 
 }  // namespace pirrt

@@ -25,6 +25,7 @@
 #include "improve_push.cuh"
 #include "improve_screen.cuh"
 #include "improve_tma.cuh"
+#include "replan_iteration.cuh"
 #include "pirrt.h"
 
 using namespace pirrt;
@@ -377,11 +378,16 @@ pirrt_status launch_improve_push(pirrt_graph *G, cudaStream_t st) {
 //           costs use the exact G-lane kernel
 //   tile 1  staged: producer warp bulk-copies rows into a shared-memory ring
 //   tile 3  G lanes per vertex (default 8), exact FP64 for every candidate
+// with_push = false: tile 0 launches only its dense-sweep kernel (the offer
+// Improve then runs inside the wave's launch).
 template <typename CT>
-pirrt_status launch_improve(pirrt_graph *G, cudaStream_t st, int gs, int tile) {
+pirrt_status launch_improve(pirrt_graph *G, cudaStream_t st, int gs, int tile,
+                            bool with_push = true) {
     if (tile == 0) {
-        pirrt_status rc = launch_improve_push<CT>(G, st);
-        if (rc) return rc;
+        if (with_push) {
+            pirrt_status rc = launch_improve_push<CT>(G, st);
+            if (rc) return rc;
+        }
         tile = 2;
     }
     if (tile == 2) {
@@ -412,10 +418,11 @@ pirrt_status launch_evaluate(pirrt_graph *G, cudaStream_t st, size_t off) {
 }
 
 // The wave and the rest of the iteration (pointer-jumping finish, marking,
-// advance) in one cooperative launch.
+// advance) in one cooperative launch, with the offer Improve in front of it
+// when fused_improve is set.
 template <typename CT>
 pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st, cudaGraphConditionalHandle cond,
-                         int use_cond) {
+                         int use_cond, bool fused_improve = false) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(G->wave_blocks);
     cfg.blockDim = dim3(kWaveThreads);
@@ -426,17 +433,20 @@ pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st, cudaGraphConditionalHa
     attr[0].val.cooperative = 1;
     cfg.attrs = attr;
     cfg.numAttrs = 1;
+    const ImproveArgs<CT> *ip = fused_improve ? dev_arg<ImproveArgs<CT>>(G, kArgImprove) : nullptr;
     CK(cudaLaunchKernelEx(&cfg, wave_evaluate_kernel<CT>, dev_arg<WaveArgs<CT>>(G, kArgWave),
                           dev_arg<EvaluateArgs<CT>>(G, kArgEvalFallback),
-                          dev_arg<MarkArgs<CT>>(G, kArgMarkFallback), cond, use_cond));
+                          dev_arg<MarkArgs<CT>>(G, kArgMarkFallback), ip, cond, use_cond));
     return PIRRT_OK;
 }
 
-// Kernel launches of one Replan iteration.
-int iteration_launches(int tile, bool jump, bool async) {
+// Kernel launches of one Replan iteration (host loop; a captured wave
+// iteration with offers runs the offer Improve inside the wave's launch).
+int iteration_launches(int tile, bool jump, bool async, bool graph) {
     const int improve = tile == 0 ? 2 : 1;
     if (jump) return improve + 3;
-    return improve + (async ? 5 : 1);
+    if (async) return improve + 5;
+    return (graph && tile == 0) ? 2 : improve + 1;
 }
 
 constexpr size_t kAsyncSmem = (size_t)kAsyncLocal * (sizeof(double) + 2 * sizeof(int32_t));
@@ -473,6 +483,11 @@ template <typename CT>
 pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile, bool jump,
                               bool async, cudaGraphConditionalHandle cond, int use_cond) {
     pirrt_status rc;
+    if (!jump && !async && tile == 0) {
+        // the dense-sweep kernel, then Improve from offers and the wave in one launch
+        if ((rc = launch_improve<CT>(G, st, gs, tile, false))) return rc;
+        return launch_wave<CT>(G, st, cond, use_cond, true);
+    }
     if ((rc = launch_improve<CT>(G, st, gs, tile))) return rc;
     if (!jump && !async) return launch_wave<CT>(G, st, cond, use_cond);
     if (jump) {
@@ -764,7 +779,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
                 CKL();
             }
             if ((rc = pull_counters(G))) return rc;
-            P.launches += iteration_launches(tile, jump, async);
+            P.launches += iteration_launches(tile, jump, async, false);
             const DevCounters *h = G->ctr_host;
             float t_imp = 0.f, t_eval = 0.f, t_mark = 0.f;
             if (prof) {
@@ -830,7 +845,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         const bool saw_deep = h.cum_jump_evals > 0;
         if (saw_deep || !jump || (G->exploits % 8) == 1) G->deep_hint = saw_deep ? 1 : 0;
     }
-    if (graph_ran) P.launches += (int64_t)h.iter * iteration_launches(tile, jump, async);
+    if (graph_ran) P.launches += (int64_t)h.iter * iteration_launches(tile, jump, async, true);
     s.iterations = (int32_t)h.iter;
     s.converged = h.converged ? 1 : 0;
     s.relaxations = (int64_t)(h.relax + h.offers);

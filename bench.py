@@ -52,15 +52,19 @@ WORKLOADS = {
 
 
 def load_roadmap(name: str, n: int | None, block: int | None, trial: int):
+    """The workload's roadmap; ``block`` (the Batched-Extension block size S)
+    only changes how its edge list is cut, not the graph (Alg. 3: the final
+    graph does not depend on S)."""
     fn_name, _ = WORKLOADS[name]
     kw = dict(trial=trial)
     if n:
         kw["n"] = n
-    if block:
-        kw["block"] = block
     if name == "c2-companion":
         kw["companion"] = True
-    return W.cached(name, getattr(W, fn_name), **kw)
+    rm = W.cached(name, getattr(W, fn_name), **kw)
+    if block:
+        rm.block = int(block)
+    return rm
 
 
 def measured_peaks():

@@ -205,6 +205,23 @@ pirrt_status pirrt_graph_get_parents(const pirrt_graph *g, int32_t *p_out, int64
 pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *g, int64_t *row_off, int32_t *col,
                                        void *cost, int on_device);
 
+/* Checkpoint and resume (not in the paper; it keeps an expensive roadmap and
+ * its converged policy across processes).  pirrt_graph_save writes the graph
+ * to `path` (a file the caller names; overwritten): the CSR packed row by row,
+ * g, the parents and their edge costs, with the cost type and root in a
+ * header.  pirrt_graph_load replaces the contents of `g` with a saved graph
+ * of the same cost type and root that fits its capacities; the next exploit
+ * then starts with a sweep of every vertex (no frontier is saved), so an
+ * exploit right after a load of a converged graph converges in one Improve,
+ * and later insertions and exploits give the results the saved graph would
+ * have given.  Both synchronise the graph's stream.
+ * Errors: PIRRT_ERR_INVALID_ARG (NULL pointer, file that cannot be opened or
+ * written, other cost type or root), PIRRT_ERR_CAPACITY, PIRRT_ERR_BAD_INPUT
+ * (not a checkpoint, truncated or inconsistent); on a load error before the
+ * contents are replaced the graph is unchanged. */
+pirrt_status pirrt_graph_save(const pirrt_graph *g, const char *path);
+pirrt_status pirrt_graph_load(pirrt_graph *g, const char *path);
+
 /* Per-kernel accounting of one handle (tracing).  Launch counts are always
  * kept; device times are measured with CUDA events on the handle's stream
  * only while profiling is enabled.  Work units let a caller turn times into

@@ -119,6 +119,8 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_get_costs": (st, [vp, vp, i64, i32]),
         "pirrt_graph_get_parents": (st, [vp, vp, i64, i32]),
         "pirrt_graph_get_adjacency": (st, [vp, vp, vp, vp, i32]),
+        "pirrt_graph_save": (st, [vp, ctypes.c_char_p]),
+        "pirrt_graph_load": (st, [vp, ctypes.c_char_p]),
         "pirrt_graph_set_profiling": (st, [vp, i32]),
         "pirrt_graph_get_profile": (st, [vp, ctypes.POINTER(pirrt_profile)]),
         "pirrt_graph_get_trace": (i64, [vp, ctypes.POINTER(pirrt_trace_record), i64]),
@@ -326,6 +328,14 @@ class Graph:
                     self._lib.pirrt_graph_get_adjacency(self._h, off.ctypes.data, col.ctypes.data,
                                                         cost.ctypes.data, 0))
         return off, col, cost
+
+    def save(self, path: str):
+        """Checkpoint the graph (CSR, g, policy) to a file."""
+        self._check("pirrt_graph_save", self._lib.pirrt_graph_save(self._h, os.fsencode(path)))
+
+    def load(self, path: str):
+        """Replace this graph's contents with a checkpoint."""
+        self._check("pirrt_graph_load", self._lib.pirrt_graph_load(self._h, os.fsencode(path)))
 
 
 def pirrt_status_string(status: int) -> str:

@@ -1115,6 +1115,24 @@ policy_lookup_kernel(int64_t n, int32_t root, const int32_t *__restrict__ parent
     }
 }
 
+// Restore (checkpoint load): packed rows from their offsets, no room to grow
+// yet; the FP32 shadow from g; no pending offers.
+static __global__ void __launch_bounds__(kThreads)
+restore_rows(int64_t n, const int64_t *__restrict__ off, RowExt *__restrict__ rows,
+             const double *__restrict__ g, float *__restrict__ g32,
+             unsigned long long *__restrict__ cand) {
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x) {
+        RowExt r;
+        r.beg = off[v];
+        r.len = (int32_t)(off[v + 1] - off[v]);
+        r.cap = r.len;
+        rows[v] = r;
+        g32[v] = g32_of(g[v]);
+        cand[v] = kCandNone;
+    }
+}
+
 // Commit a looked-up policy and clear g (Evaluate refills it).
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)

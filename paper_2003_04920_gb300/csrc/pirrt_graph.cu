@@ -1327,13 +1327,12 @@ pirrt_status pirrt_graph_get_profile(const pirrt_graph *G, pirrt_profile *out) {
 }
 
 extern "C++" {
+// Packed copy of the CSR on the device: offsets in G->roff[0..n], entries in
+// G->stage[0..m).
 template <typename CT>
-pirrt_status export_impl(pirrt_graph *G, int64_t *row_off, int32_t *col, void *cost,
-                         int on_device) {
-    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+pirrt_status pack_csr(pirrt_graph *G) {
     const int64_t n = G->n, len = n + 1;
     const int max_blocks = G->num_sms * 32;
-    // compact offsets: exclusive scan of the row lengths
     row_lengths<<<grid_for(len, kThreads, max_blocks), kThreads, 0, G->stream>>>(n, G->rows,
                                                                                G->ralloc);
     CKL();
@@ -1345,16 +1344,27 @@ pirrt_status export_impl(pirrt_graph *G, int64_t *row_off, int32_t *col, void *c
     scan_tile_apply<<<(unsigned)n_tiles, kThreads, 0, G->stream>>>(G->ralloc, len, G->tile_sums,
                                                                     G->roff);
     CKL();
-    if (row_off)
-        CK(cudaMemcpyAsync(row_off, G->roff, sizeof(int64_t) * (size_t)len, kind, G->stream));
-    if (G->m > 0 && (col || cost)) {
+    if (G->m > 0) {
         pirrt_status rc = ensure_stage(G, G->entry_bytes * (size_t)G->m);
         if (rc) return rc;
-        Entry<CT> *packed = static_cast<Entry<CT> *>(G->stage);
         export_rows<CT><<<grid_for((n + 31) / 32 * 32, kThreads, max_blocks), kThreads, 0,
                           G->stream>>>(n, G->rows, G->roff,
-                                       static_cast<const Entry<CT> *>(G->adj[G->cur]), packed);
+                                       static_cast<const Entry<CT> *>(G->adj[G->cur]),
+                                       static_cast<Entry<CT> *>(G->stage));
         CKL();
+    }
+    return PIRRT_OK;
+}
+
+template <typename CT>
+pirrt_status export_impl(pirrt_graph *G, int64_t *row_off, int32_t *col, void *cost,
+                         int on_device) {
+    const cudaMemcpyKind kind = on_device ? cudaMemcpyDeviceToDevice : cudaMemcpyDeviceToHost;
+    pirrt_status rc = pack_csr<CT>(G);
+    if (rc) return rc;
+    if (row_off)
+        CK(cudaMemcpyAsync(row_off, G->roff, sizeof(int64_t) * (size_t)(G->n + 1), kind, G->stream));
+    if (G->m > 0 && (col || cost)) {
         // entries are (col, cost) records: split with strided 2-D copies
         const char *base = static_cast<const char *>(G->stage);
         if (col)
@@ -1369,7 +1379,141 @@ pirrt_status export_impl(pirrt_graph *G, int64_t *row_off, int32_t *col, void *c
     CK(cudaStreamSynchronize(G->stream));
     return PIRRT_OK;
 }
+
+// Checkpoint file: a header, then the packed CSR offsets (int64, n + 1), its
+// entries as stored (Entry<CT>, m), g (double, n), the parents with root
+// markers (int32, n) and the parent-edge costs (CT, n).
+struct CkptHeader {
+    char magic[8];
+    int32_t cost_dtype;
+    int32_t root;
+    int64_t n;
+    int64_t m;
+};
+constexpr char kCkptMagic[8] = {'P', 'I', 'R', 'R', 'T', 'G', '0', '1'};
+
+template <typename CT>
+pirrt_status save_impl(pirrt_graph *G, FILE *f) {
+    const int64_t n = G->n, m = G->m;
+    pirrt_status rc = pack_csr<CT>(G);
+    if (rc) return rc;
+    std::vector<int64_t> off((size_t)n + 1);
+    std::vector<unsigned char> ent((size_t)m * G->entry_bytes);
+    std::vector<double> g((size_t)n);
+    std::vector<int32_t> p((size_t)n);
+    std::vector<CT> pc((size_t)n);
+    CK(cudaMemcpyAsync(off.data(), G->roff, sizeof(int64_t) * off.size(), cudaMemcpyDeviceToHost,
+                       G->stream));
+    if (m > 0)
+        CK(cudaMemcpyAsync(ent.data(), G->stage, ent.size(), cudaMemcpyDeviceToHost, G->stream));
+    if (n > 0) {
+        CK(cudaMemcpyAsync(g.data(), G->g, sizeof(double) * (size_t)n, cudaMemcpyDeviceToHost,
+                           G->stream));
+        CK(cudaMemcpyAsync(p.data(), G->p, sizeof(int32_t) * (size_t)n, cudaMemcpyDeviceToHost,
+                           G->stream));
+        CK(cudaMemcpyAsync(pc.data(), G->pc, sizeof(CT) * (size_t)n, cudaMemcpyDeviceToHost,
+                           G->stream));
+    }
+    CK(cudaStreamSynchronize(G->stream));
+    CkptHeader h{};
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.cost_dtype = G->cfg.cost_dtype;
+    h.root = G->cfg.root;
+    h.n = n;
+    h.m = m;
+    bool ok = std::fwrite(&h, sizeof(h), 1, f) == 1 &&
+              std::fwrite(off.data(), sizeof(int64_t), off.size(), f) == off.size() &&
+              std::fwrite(ent.data(), 1, ent.size(), f) == ent.size() &&
+              std::fwrite(g.data(), sizeof(double), g.size(), f) == g.size() &&
+              std::fwrite(p.data(), sizeof(int32_t), p.size(), f) == p.size() &&
+              std::fwrite(pc.data(), sizeof(CT), pc.size(), f) == pc.size();
+    if (!ok) return fail(G, PIRRT_ERR_INVALID_ARG, "save: write failed");
+    return PIRRT_OK;
+}
+
+template <typename CT>
+pirrt_status load_impl(pirrt_graph *G, FILE *f, const CkptHeader &h) {
+    const int64_t n = h.n, m = h.m;
+    std::vector<int64_t> off((size_t)n + 1);
+    std::vector<unsigned char> ent((size_t)m * G->entry_bytes);
+    std::vector<double> g((size_t)n);
+    std::vector<int32_t> p((size_t)n);
+    std::vector<CT> pc((size_t)n);
+    bool ok = std::fread(off.data(), sizeof(int64_t), off.size(), f) == off.size() &&
+              std::fread(ent.data(), 1, ent.size(), f) == ent.size() &&
+              std::fread(g.data(), sizeof(double), g.size(), f) == g.size() &&
+              std::fread(p.data(), sizeof(int32_t), p.size(), f) == p.size() &&
+              std::fread(pc.data(), sizeof(CT), pc.size(), f) == pc.size();
+    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: file too short");
+    // offsets must be a packed CSR of m entries; parents in range
+    ok = off[0] == 0 && off[(size_t)n] == m;
+    for (int64_t v = 0; ok && v < n; ++v)
+        ok = off[(size_t)v + 1] >= off[(size_t)v] && p[(size_t)v] >= kRootMark &&
+             p[(size_t)v] < n;
+    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: inconsistent checkpoint");
+    pirrt_status rc = pirrt_graph_reset(G);
+    if (rc) return rc;
+    CK(cudaMemcpyAsync(G->roff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice,
+                       G->stream));
+    if (m > 0)
+        CK(cudaMemcpyAsync(G->adj[G->cur], ent.data(), ent.size(), cudaMemcpyHostToDevice,
+                           G->stream));
+    if (n > 0) {
+        CK(cudaMemcpyAsync(G->g, g.data(), sizeof(double) * (size_t)n, cudaMemcpyHostToDevice,
+                           G->stream));
+        CK(cudaMemcpyAsync(G->p, p.data(), sizeof(int32_t) * (size_t)n, cudaMemcpyHostToDevice,
+                           G->stream));
+        CK(cudaMemcpyAsync(G->pc, pc.data(), sizeof(CT) * (size_t)n, cudaMemcpyHostToDevice,
+                           G->stream));
+        restore_rows<<<grid_for(n, kThreads, G->num_sms * 32), kThreads, 0, G->stream>>>(
+            n, G->roff, G->rows, G->g, G->g32, G->cand);
+        CKL();
+    }
+    // the next Improve sweeps every vertex (no frontier survives a checkpoint)
+    const unsigned one = 1u;
+    CK(cudaMemcpyAsync(&G->ctr->dense, &one, sizeof(unsigned), cudaMemcpyHostToDevice, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    G->n = n;
+    G->m = m;
+    G->pool_used = m;
+    return PIRRT_OK;
+}
 }  // extern "C++"
+
+pirrt_status pirrt_graph_save(const pirrt_graph *Gc, const char *path) {
+    pirrt_graph *G = const_cast<pirrt_graph *>(Gc);
+    if (!G || !path) return PIRRT_ERR_INVALID_ARG;
+    CK(cudaSetDevice(G->cfg.device));
+    FILE *f = std::fopen(path, "wb");
+    if (!f) return fail(G, PIRRT_ERR_INVALID_ARG, "save: cannot open %s", path);
+    const pirrt_status rc = G->cfg.cost_dtype == PIRRT_COST_F32 ? save_impl<float>(G, f)
+                                                                : save_impl<double>(G, f);
+    if (std::fclose(f) != 0 && rc == PIRRT_OK)
+        return fail(G, PIRRT_ERR_INVALID_ARG, "save: cannot close %s", path);
+    return rc;
+}
+
+pirrt_status pirrt_graph_load(pirrt_graph *G, const char *path) {
+    if (!G || !path) return PIRRT_ERR_INVALID_ARG;
+    CK(cudaSetDevice(G->cfg.device));
+    FILE *f = std::fopen(path, "rb");
+    if (!f) return fail(G, PIRRT_ERR_INVALID_ARG, "load: cannot open %s", path);
+    CkptHeader h{};
+    pirrt_status rc = PIRRT_OK;
+    if (std::fread(&h, sizeof(h), 1, f) != 1 || std::memcmp(h.magic, kCkptMagic, 8) != 0 ||
+        h.n < 0 || h.m < 0)
+        rc = fail(G, PIRRT_ERR_BAD_INPUT, "load: not a graph checkpoint");
+    else if (h.cost_dtype != G->cfg.cost_dtype || h.root != G->cfg.root)
+        rc = fail(G, PIRRT_ERR_INVALID_ARG, "load: cost type or root differ from the graph's");
+    else if (h.n > G->cap_n || h.m > G->cap_e || h.m > G->pool_cap)
+        rc = fail(G, PIRRT_ERR_CAPACITY, "load: %lld vertices / %lld entries exceed the graph",
+                  (long long)h.n, (long long)h.m);
+    else
+        rc = G->cfg.cost_dtype == PIRRT_COST_F32 ? load_impl<float>(G, f, h)
+                                                 : load_impl<double>(G, f, h);
+    std::fclose(f);
+    return rc;
+}
 
 pirrt_status pirrt_graph_get_adjacency(const pirrt_graph *Gc, int64_t *row_off, int32_t *col,
                                        void *cost, int on_device) {

@@ -212,11 +212,16 @@ def run_ours(args) -> None:
         iters = 0
         for k in extra:
             extra[k] = 0
-        for v0, v1, e0, e1 in rm.blocks():
+        blocks = list(rm.blocks())
+        for b, (v0, v1, e0, e1) in enumerate(blocks):
             if device_inputs:
                 G.insert_batch(v1 - v0, dev_u[e0:e1], dev_v[e0:e1], dev_c[e0:e1])
             else:
                 G.insert_batch(v1 - v0, host_u[e0:e1], host_v[e0:e1], host_c[e0:e1])
+                if b + 1 < len(blocks) and not args.no_prefetch:
+                    # the next block's copy overlaps this exploit
+                    _, _, f0, f1 = blocks[b + 1]
+                    G.prefetch_batch(host_u[f0:f1], host_v[f0:f1], host_c[f0:f1])
             st = G.exploit(group=args.group, tile=args.tile, dense_fraction=args.dense_fraction,
                            evaluate=args.evaluate, wave_levels=args.wave_levels,
                            host_loop=args.host_loop, wave_tail=args.wave_tail,
@@ -375,7 +380,8 @@ def run_ours(args) -> None:
                      "avg_launch_ms": round(dom_ms_avg, 5)},
         "kernels": kernels,
         "e2e": {"value": round(e2e_relax / e2e_s, 1) if e2e_steps else None, "unit": UNIT,
-                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h)},
+                "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                "prefetch": not args.no_prefetch},
         "gpu_launches": int(timed_launches),
         "clocks": clocks,
     }
@@ -609,6 +615,9 @@ def main():
                     help="run every exploit from the host loop (no CUDA graphs), e.g. under ncu")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-prefetch", action="store_true",
+                    help="end-to-end pass: copy each block when it is inserted, not during the "
+                         "previous exploit")
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end pass (e.g. for a profiler's launch list)")
     ap.add_argument("--trace", default=None, help="save the per-iteration trace (.npy)")

@@ -165,6 +165,18 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *g, int64_t n_new_vertices, in
                                       const int32_t *src, const int32_t *dst, const void *cost,
                                       int on_device);
 
+/* Start copying the next block's host edge list to the device on a copy
+ * stream of the graph, so that the copy overlaps the current exploit (the
+ * paper's future work, Sec. VII, overlaps exploration with exploitation).
+ * The next pirrt_graph_insert_batch called with the same host pointers and
+ * edge count (on_device = 0) uses the copy instead of copying again; any
+ * other call discards it.  The caller keeps the three host buffers alive and
+ * unchanged until that insertion returns; with pageable (not page-locked)
+ * memory the copy may not overlap.  Errors: PIRRT_ERR_INVALID_ARG,
+ * PIRRT_ERR_OOM, PIRRT_ERR_CUDA. */
+pirrt_status pirrt_graph_prefetch_batch(pirrt_graph *g, int64_t n_edges, const int32_t *src,
+                                        const int32_t *dst, const void *cost);
+
 /* Replace the policy: parent[v] for v in [0, n) (-1 = none; parent[root]
  * must be -1), n = current vertex count.  Each parent edge must exist; its
  * cost is the cheapest parallel edge.  Evaluates g under the new policy

@@ -120,6 +120,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_get_parents": (st, [vp, vp, i64, i32]),
         "pirrt_graph_get_adjacency": (st, [vp, vp, vp, vp, i32]),
         "pirrt_graph_save": (st, [vp, ctypes.c_char_p]),
+        "pirrt_graph_prefetch_batch": (st, [vp, i64, vp, vp, vp]),
         "pirrt_graph_load": (st, [vp, ctypes.c_char_p]),
         "pirrt_graph_set_profiling": (st, [vp, i32]),
         "pirrt_graph_get_profile": (st, [vp, ctypes.POINTER(pirrt_profile)]),
@@ -261,6 +262,20 @@ class Graph:
         n_edges = len(ks) if ds == 0 else ks.numel()
         rc = self._lib.pirrt_graph_insert_batch(self._h, int(n_new), int(n_edges), ps, pd, pc, ds)
         self._check("pirrt_graph_insert_batch", rc)
+
+    def prefetch_batch(self, src, dst, cost):
+        """Copy the next block's host edge list on the graph's copy stream while
+        the current exploit runs; the next insert_batch with the same arrays
+        uses it.  Keep the arrays unchanged until then (page-locked memory lets
+        the copy overlap)."""
+        ps, ds, ks = _buf(src, np.int32)
+        pd, dd, kd = _buf(dst, np.int32)
+        pc, dc, kc = _buf(cost, self.cost_dtype)
+        if ds or dd or dc:
+            raise ValueError("prefetch_batch takes host arrays")
+        self._pre_keep = (ks, kd, kc)
+        self._check("pirrt_graph_prefetch_batch",
+                    self._lib.pirrt_graph_prefetch_batch(self._h, int(len(ks)), ps, pd, pc))
 
     def set_policy(self, parent):
         pp, dev, keep = _buf(parent, np.int32)

@@ -41,6 +41,13 @@ struct pirrt_graph {
     pirrt_config cfg{};
     cudaStream_t stream = nullptr;
     cudaStream_t capture = nullptr;  // private stream for recording loop bodies
+    cudaStream_t copy = nullptr;     // host-to-device prefetch of the next block
+    void *pre = nullptr;             // the prefetched block on the device
+    size_t pre_bytes = 0;
+    cudaEvent_t pre_done = nullptr;  // the prefetch copies finished (copy stream)
+    cudaEvent_t pre_free = nullptr;  // the insertion that read `pre` finished (graph stream)
+    const void *pre_src = nullptr, *pre_dst = nullptr, *pre_cost = nullptr;
+    int64_t pre_n = -1;              // edges of the pending prefetch; -1 = none
     int num_sms = 0;
     int64_t cap_n = 0, cap_e = 0;  // vertices, directed CSR entries
     int64_t n = 0, m = 0;
@@ -909,6 +916,13 @@ void free_all(pirrt_graph *G) {
         if (kv.second) cudaGraphExecDestroy(kv.second);
     G->loops.clear();
     if (G->capture) cudaStreamDestroy(G->capture);
+    if (G->copy) {
+        cudaStreamSynchronize(G->copy);
+        cudaStreamDestroy(G->copy);
+    }
+    if (G->pre) cudaFree(G->pre);
+    if (G->pre_done) cudaEventDestroy(G->pre_done);
+    if (G->pre_free) cudaEventDestroy(G->pre_free);
     if (G->hargs) cudaFreeHost(G->hargs);
     void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
@@ -1116,6 +1130,10 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->pexport, sizeof(int32_t) * nv);
 #undef ALLOC
     if (cudaMallocHost((void **)&G->hargs, kArgBytes) != cudaSuccess) return bail(PIRRT_ERR_OOM);
+    if (cudaStreamCreateWithFlags(&G->copy, cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->pre_done, cudaEventDisableTiming) != cudaSuccess ||
+        cudaEventCreateWithFlags(&G->pre_free, cudaEventDisableTiming) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
     if (cudaStreamCreateWithFlags(&G->capture, cudaStreamNonBlocking) != cudaSuccess)
         return bail(PIRRT_ERR_CUDA);
     if (cudaMallocHost((void **)&G->hx, 2 * sizeof(int64_t)) != cudaSuccess)
@@ -1214,6 +1232,24 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *G, int64_t n_new, int64_t n_e
     CK(cudaSetDevice(G->cfg.device));
     const int32_t *s = src, *d = dst;
     const void *c = cost;
+    const bool prefetched = !on_device && n_edges > 0 && G->pre_n == n_edges && G->pre_src == src &&
+                            G->pre_dst == dst && G->pre_cost == cost;
+    G->pre_n = -1;
+    if (prefetched) {
+        // the block was copied on the copy stream while the last exploit ran
+        CK(cudaStreamWaitEvent(G->stream, G->pre_done, 0));
+        const size_t a16 = (sizeof(int32_t) * (size_t)n_edges + 15) & ~size_t(15);
+        char *base = static_cast<char *>(G->pre);
+        s = reinterpret_cast<const int32_t *>(base);
+        d = reinterpret_cast<const int32_t *>(base + a16);
+        c = base + 2 * a16;
+        const pirrt_status rc =
+            G->cfg.cost_dtype == PIRRT_COST_F32
+                ? insert_impl<float>(G, n_new, n_edges, s, d, static_cast<const float *>(c))
+                : insert_impl<double>(G, n_new, n_edges, s, d, static_cast<const double *>(c));
+        CK(cudaEventRecord(G->pre_free, G->stream));
+        return rc;
+    }
     if (!on_device && n_edges > 0) {
         const size_t ib = sizeof(int32_t) * (size_t)n_edges;
         const size_t cb = G->cost_bytes * (size_t)n_edges;
@@ -1231,6 +1267,41 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *G, int64_t n_new, int64_t n_e
     if (G->cfg.cost_dtype == PIRRT_COST_F32)
         return insert_impl<float>(G, n_new, n_edges, s, d, static_cast<const float *>(c));
     return insert_impl<double>(G, n_new, n_edges, s, d, static_cast<const double *>(c));
+}
+
+pirrt_status pirrt_graph_prefetch_batch(pirrt_graph *G, int64_t n_edges, const int32_t *src,
+                                        const int32_t *dst, const void *cost) {
+    if (!G) return PIRRT_ERR_INVALID_ARG;
+    if (n_edges < 0 || (n_edges > 0 && (!src || !dst || !cost)))
+        return fail(G, PIRRT_ERR_INVALID_ARG, "prefetch_batch: negative size or NULL pointer");
+    CK(cudaSetDevice(G->cfg.device));
+    G->pre_n = -1;
+    if (n_edges == 0) return PIRRT_OK;
+    const size_t ib = sizeof(int32_t) * (size_t)n_edges;
+    const size_t cb = G->cost_bytes * (size_t)n_edges;
+    const size_t a16 = (ib + 15) & ~size_t(15);
+    const size_t bytes = 2 * a16 + cb;
+    if (bytes > G->pre_bytes) {
+        CK(cudaStreamSynchronize(G->copy));
+        CK(cudaEventSynchronize(G->pre_free));
+        if (G->pre) CK(cudaFree(G->pre));
+        G->pre = nullptr;
+        G->pre_bytes = 0;
+        CK(cudaMalloc(&G->pre, bytes));
+        G->pre_bytes = bytes;
+    }
+    // the insertion that read the buffer last must be done with it
+    CK(cudaStreamWaitEvent(G->copy, G->pre_free, 0));
+    char *base = static_cast<char *>(G->pre);
+    CK(cudaMemcpyAsync(base, src, ib, cudaMemcpyHostToDevice, G->copy));
+    CK(cudaMemcpyAsync(base + a16, dst, ib, cudaMemcpyHostToDevice, G->copy));
+    CK(cudaMemcpyAsync(base + 2 * a16, cost, cb, cudaMemcpyHostToDevice, G->copy));
+    CK(cudaEventRecord(G->pre_done, G->copy));
+    G->pre_src = src;
+    G->pre_dst = dst;
+    G->pre_cost = cost;
+    G->pre_n = n_edges;
+    return PIRRT_OK;
 }
 
 pirrt_status pirrt_graph_set_policy(pirrt_graph *G, const int32_t *parent, int64_t n, int on_device) {

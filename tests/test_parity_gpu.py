@@ -205,6 +205,29 @@ def test_block_size_does_not_change_results(c3_small):
     np.testing.assert_array_equal(p1[m1], p2[m1])
 
 
+def test_prefetched_blocks_match_plain_inserts(c2_small):
+    """Host blocks copied on the copy stream during the previous exploit (and a
+    prefetch that does not match the next insertion, which is discarded) give
+    the schedule of plain host inserts, bit for bit."""
+    rm = c2_small
+    u = np.ascontiguousarray(rm.u)
+    v = np.ascontiguousarray(rm.v)
+    c = np.ascontiguousarray(rm.cost)
+    blocks = list(rm.blocks())
+    g0, p0, _ = gpu_schedule(rm)
+    with P.Graph(rm.n, rm.m, 0, np.float32) as D:
+        for b, (v0, v1, e0, e1) in enumerate(blocks):
+            D.insert_batch(v1 - v0, u[e0:e1], v[e0:e1], c[e0:e1])
+            if b + 1 < len(blocks):
+                k = b + 1 if b % 3 else min(b + 2, len(blocks) - 1)  # every third one misses
+                _, _, f0, f1 = blocks[k]
+                D.prefetch_batch(u[f0:f1], v[f0:f1], c[f0:f1])
+            D.exploit()
+        g1, p1 = D.get_costs(), D.get_parents()
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+
+
 def test_device_and_host_inputs_agree(c2_small):
     rm = c2_small
     g0, p0, _ = gpu_schedule(rm)

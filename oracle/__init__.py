@@ -6,7 +6,9 @@ library: the C source ``pirrt_oracle.c`` is compiled with gcc into
 ``liboracle.so`` and driven through ctypes.
 
 * :class:`OracleGraph` -- O1, serial policy iteration following Alg. 2
-  (Replan = loop of Improve and Evaluate) on an adjacency-list graph.
+  (Replan = loop of Improve and Evaluate) on an adjacency-list graph, in the
+  goal-free form or, after ``set_goal``, the goal-directed form that prunes
+  the walk to the promising set (Sec. IV-C).
 * :func:`dijkstra` -- O2, FP64 Dijkstra (binary heap keyed (distance, id)).
   The correctness argument for Batched-Extension PI-RRT# (Sec. IV,
   "Correctness") says Replan reaches the optimal policy from any initial
@@ -62,6 +64,8 @@ def _declare(lib):
         "or_set_policy": (ctypes.c_int, [vp, vp]),
         "or_replan": (ctypes.c_int, [vp, f64, i64, vp]),
         "or_get": (None, [vp, vp, vp]),
+        "or_set_goal": (ctypes.c_int, [vp, i32, vp, i64]),
+        "or_get_promising": (None, [vp, vp]),
         "or_csr_build": (vp, [i64, i64, vp, vp, vp]),
         "or_csr_destroy": (None, [vp]),
         "or_csr_entries": (i64, [vp]),
@@ -154,6 +158,20 @@ class OracleGraph:
         self._lib.or_get(self._h, _p(g), _p(p))
         return g, p
 
+    def set_goal(self, goal: int, h=None) -> None:
+        """Goal-directed form (Sec. IV-C): x_goal and h(v) for v < len(h)
+        (0 beyond); goal = -1 switches it off."""
+        h = np.ascontiguousarray(np.zeros(0) if h is None else h, dtype=np.float64)
+        rc = self._lib.or_set_goal(self._h, int(goal), _p(h), len(h))
+        if rc:
+            raise OracleError("or_set_goal", rc)
+
+    def promising(self) -> np.ndarray:
+        """b(v) of the last Evaluate (the promising set B)."""
+        b = np.empty(self.n, dtype=np.uint8)
+        self._lib.or_get_promising(self._h, _p(b))
+        return b.astype(bool)
+
 
 class CSR:
     """Static merged adjacency for O2 and the checkers."""
@@ -228,14 +246,17 @@ def dijkstra(n: int, u, v, c, root: int = 0):
 
 
 def replan_schedule(rm, block: int | None = None, init_parent=None, eps: float = 0.0,
-                    lib=None, n_blocks: int | None = None):
+                    lib=None, n_blocks: int | None = None, goal: int | None = None, h=None):
     """Batched-Extension schedule (Alg. 3) on O1: insert block b (its vertices
     and the edges whose larger endpoint lies in it), then Replan.  With
     ``init_parent`` (one block holding every vertex) the policy is set to it
-    before the single Replan.  Returns (g, parent, per-block stats)."""
+    before the single Replan.  With ``goal`` the Replan is goal-directed
+    (Sec. IV-C) with heuristic ``h``.  Returns (g, parent, per-block stats)."""
     G = OracleGraph(rm.n, 0, lib=lib)
     stats = []
     try:
+        if goal is not None:
+            G.set_goal(goal, h)
         for i, (v0, v1, e0, e1) in enumerate(rm.blocks(block)):
             if n_blocks is not None and i >= n_blocks:
                 break

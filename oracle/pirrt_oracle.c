@@ -18,6 +18,12 @@
  *     reachable set = component of x_init, and the "unambiguous" mask
  *     (best and second-best candidates differ by more than a relative gap).
  *
+ * Goal-directed form (or_set_goal): with a goal x_goal and an admissible
+ *     heuristic h (a lower bound on the cost-to-go, Sec. III), Evaluate keeps
+ *     walking below a child only while it is promising, and Improve only
+ *     switches a vertex that its new parent makes promising (Sec. IV-C, the
+ *     promising set B of Sec. III and the vertex property b of Sec. IV-A).
+ *
  * Readings of the paper taken here (the paper is silent or loose on them):
  *  - Delta g is reset once per Improve call, before the vertex loop (Alg. 2
  *    shows the reset inside the loop, which would keep only the last vertex).
@@ -31,6 +37,23 @@
  *    equal minimisers the lowest id wins and a current parent that attains
  *    the minimum is kept (its candidate equals g(v) exactly, see Evaluate).
  *  - Parallel edges between the same pair keep the smallest cost.
+ *  - Improve measures a candidate against g_hat = g(pi(v)) + c(pi(v), v),
+ *    the value of v's current parent edge.  After an Evaluate that reached v
+ *    this is g(v) itself; the goal-directed form can leave g(v) unevaluated
+ *    (below a pruned vertex), and measuring against that stale g(v) could
+ *    switch v back and forth without progress.
+ *  - Promising test (goal-directed form): a vertex n is promising when
+ *    g(n) + h(n) < g(x_goal), strictly, with g(x_goal) taken at the start of
+ *    the Evaluate (the listing tests the popped parent's g and h, which would
+ *    admit every child of a promising vertex; the test on the child is the
+ *    definition of B).  The value g(x_goal) at the start makes the result
+ *    independent of the walk's order; it only prunes less than the running
+ *    value would.
+ *  - Improve in the goal-directed form examines every vertex but switches v
+ *    only if its best candidate makes it promising: g_hat + h(v) < g(x_goal)
+ *    (the lookahead key of RRT#).  This covers B and the neighbours of B that
+ *    the paper's Improve reaches (Sec. IV-C: promising vertices and their
+ *    neighbours are re-evaluated).
  *
  * Built with -ffp-contract=off: every sum below is one IEEE addition.
  */
@@ -66,6 +89,9 @@ typedef struct {
     double *g;      /* cost-to-come g_pi */
     int32_t *pi;    /* parent: pi(v) = (pi[v], v); -1 = none */
     double *pc;     /* cost of the policy edge, c(pi(v), v) */
+    int32_t goal;   /* x_goal of the goal-directed form; -1 = goal-free */
+    double *h;      /* heuristic cost-to-go h(v) >= 0 (goal-directed form) */
+    uint8_t *b;     /* promising bit b(v), rebuilt by every Evaluate */
 } or_graph;
 
 or_graph *or_create(int64_t cap_n, int32_t root)
@@ -79,8 +105,11 @@ or_graph *or_create(int64_t cap_n, int32_t root)
     G->g = (double *)malloc(sizeof(double) * (size_t)cap_n);
     G->pi = (int32_t *)malloc(sizeof(int32_t) * (size_t)cap_n);
     G->pc = (double *)malloc(sizeof(double) * (size_t)cap_n);
-    if (!G->adj || !G->g || !G->pi || !G->pc) {
-        free(G->adj); free(G->g); free(G->pi); free(G->pc); free(G);
+    G->h = (double *)calloc((size_t)cap_n, sizeof(double));
+    G->b = (uint8_t *)calloc((size_t)cap_n, 1);
+    G->goal = -1;
+    if (!G->adj || !G->g || !G->pi || !G->pc || !G->h || !G->b) {
+        free(G->adj); free(G->g); free(G->pi); free(G->pc); free(G->h); free(G->b); free(G);
         return NULL;
     }
     return G;
@@ -90,7 +119,27 @@ void or_destroy(or_graph *G)
 {
     if (!G) return;
     for (int64_t v = 0; v < G->cap_n; ++v) { free(G->adj[v].nbr); free(G->adj[v].c); }
-    free(G->adj); free(G->g); free(G->pi); free(G->pc); free(G);
+    free(G->adj); free(G->g); free(G->pi); free(G->pc); free(G->h); free(G->b); free(G);
+}
+
+/* Goal-directed form: x_goal = goal (-1 switches it off) and h(v) = h[v] for
+ * v < n_h, 0 beyond (0 is admissible).  h must be finite and >= 0. */
+int or_set_goal(or_graph *G, int32_t goal, const double *h, int64_t n_h)
+{
+    if (goal < -1 || goal >= G->cap_n || n_h < 0 || n_h > G->cap_n || (n_h > 0 && !h))
+        return OR_ERR_ARG;
+    for (int64_t x = 0; x < n_h; ++x)
+        if (!(h[x] >= 0.0) || !isfinite(h[x])) return OR_ERR_BAD_INPUT;
+    for (int64_t x = 0; x < G->cap_n; ++x) G->h[x] = x < n_h ? h[x] : 0.0;
+    G->goal = goal;
+    return OR_OK;
+}
+
+/* g(x_goal), +inf while x_goal is not in the graph or unreached; +inf in the
+ * goal-free form, where every reached vertex is promising. */
+static double goal_cost(const or_graph *G)
+{
+    return (G->goal >= 0 && G->goal < G->n) ? G->g[G->goal] : INFINITY;
 }
 
 int64_t or_num_vertices(const or_graph *G) { return G->n; }
@@ -176,9 +225,11 @@ static void normalise_all(or_graph *G)
 }
 
 /* Evaluate (Alg. 2): breadth-first walk of the policy tree from x_init,
- * g(n) <- c(v, n) + g(v) for every child n of v.  With no goal every reached
- * vertex is promising, so the walk is not truncated.  Returns the number of
- * vertices assigned, or -1 on allocation failure. */
+ * g(n) <- c(v, n) + g(v) for every child n of v, and B <- the children that
+ * are promising, g(n) + h(n) < g(x_goal); the walk continues below those
+ * only.  With no goal (or x_goal not reached yet) every reached vertex is
+ * promising and the walk covers the tree.  Returns the number of vertices
+ * assigned, or -1 on allocation failure. */
 static int64_t evaluate(or_graph *G)
 {
     int64_t n = G->n;
@@ -197,15 +248,21 @@ static int64_t evaluate(or_graph *G)
         if (G->pi[x] >= 0) kids[fill[G->pi[x]]++] = (int32_t)x;
     free(fill);
 
+    const double bound = goal_cost(G); /* g(x_goal) before this walk */
+    memset(G->b, 0, (size_t)n);
     int64_t head = 0, tail = 0, assigned = 0;
     queue[tail++] = G->root;
+    G->b[G->root] = 1;
     while (head < tail) {
         int32_t x = queue[head++];
         for (int64_t i = first[x]; i < first[x + 1]; ++i) {
             int32_t y = kids[i];
             G->g[y] = G->pc[y] + G->g[x];
             ++assigned;
-            queue[tail++] = y; /* h-test: g(x_goal) = +inf, always promising */
+            if (G->g[y] + G->h[y] < bound) { /* promising: y joins B */
+                queue[tail++] = y;
+                G->b[y] = 1;
+            }
         }
     }
     free(first); free(kids); free(queue);
@@ -213,28 +270,38 @@ static int64_t evaluate(or_graph *G)
 }
 
 /* Improve (Alg. 2): Jacobi relaxation.  For each vertex v except x_init,
- * g_hat <- g(v); for each neighbour n in ascending id, if c(n, v) + g(n) <
- * g_hat then g_hat <- that value and pi(v) <- n.  Delta g is the largest
- * g(v) - g_hat.  g is read only: every candidate uses the last Evaluate. */
+ * g_hat <- g(pi(v)) + c(pi(v), v) (+inf without a parent); for each
+ * neighbour n in ascending id, if c(n, v) + g(n) < g_hat then g_hat <- that
+ * value and n becomes the new parent -- taken only if it makes v promising,
+ * g_hat + h(v) < g(x_goal) (always, goal-free).  Delta g is the largest
+ * decrease taken.  g is read only: every candidate uses the last Evaluate. */
 static double improve(or_graph *G, int64_t *relax, int64_t *switched)
 {
     double dJ = 0.0;
+    const double bound = goal_cost(G);
     for (int64_t x = 0; x < G->n; ++x) {
         if (x == G->root) continue;
         const or_list *L = &G->adj[x];
-        double ghat = G->g[x];
+        const double cur = G->pi[x] >= 0 ? G->g[G->pi[x]] + G->pc[x] : INFINITY;
+        double ghat = cur;
+        int32_t best = -1;
+        double best_c = 0.0;
         for (int64_t i = 0; i < L->len; ++i) {
             double cand = L->c[i] + G->g[L->nbr[i]];
             if (cand < ghat) {
                 ghat = cand;
-                G->pi[x] = L->nbr[i];
-                G->pc[x] = L->c[i];
+                best = L->nbr[i];
+                best_c = L->c[i];
             }
         }
         *relax += L->len;
-        if (ghat < G->g[x]) ++*switched;
-        double d = G->g[x] - ghat;
-        if (d > dJ) dJ = d;
+        if (best >= 0 && ghat + G->h[x] < bound) {
+            G->pi[x] = best;
+            G->pc[x] = best_c;
+            ++*switched;
+            double d = cur - ghat;
+            if (d > dJ) dJ = d;
+        }
     }
     return dJ;
 }
@@ -292,6 +359,12 @@ void or_get(const or_graph *G, double *g, int32_t *parent)
         if (g) g[x] = G->g[x];
         if (parent) parent[x] = G->pi[x];
     }
+}
+
+/* The promising set B of the last Evaluate as bits b(v) (Sec. IV-A). */
+void or_get_promising(const or_graph *G, uint8_t *b)
+{
+    for (int64_t x = 0; x < G->n; ++x) b[x] = G->b[x];
 }
 
 /* ------------------------------------------------------------------------ */

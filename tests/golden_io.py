@@ -12,7 +12,7 @@ def _num(t: str) -> float:
 
 
 def load(name: str) -> dict:
-    out = dict(edges=[], init=None, iterations=None)
+    out = dict(edges=[], init=None, iterations=None, goal=None, h=None)
     with open(os.path.join(GOLDEN, name)) as f:
         for line in f:
             line = line.split("#", 1)[0].strip()
@@ -21,8 +21,10 @@ def load(name: str) -> dict:
             key, *vals = line.split()
             if key == "edge":
                 out["edges"].append((int(vals[0]), int(vals[1]), float(vals[2])))
-            elif key in ("n", "root", "iterations"):
+            elif key in ("n", "root", "iterations", "goal"):
                 out[key] = int(vals[0])
+            elif key == "h":
+                out["h"] = np.array([float(t) for t in vals])
             elif key == "g":
                 out["g"] = np.array([_num(t) for t in vals])
             elif key in ("parent", "init"):

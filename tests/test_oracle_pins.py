@@ -12,6 +12,10 @@
 * Lower bound g(v) >= |x_v - x_0| on any Euclidean roadmap.
 * Batched-Extension (Alg. 3): the final policy does not depend on S.
 * Iteration bound (Sec. IV): at most (optimal path length in edges) + 2.
+* Goal-directed form (Sec. IV-C): hand-solved pruning cases; g(x_goal) is
+  the shortest-path cost (admissible h), and so is g(v) of every v with
+  d(v) + h(v) < d(x_goal) (consistent h); no goal, an unreachable goal and
+  h = 0 reduce to the goal-free Replan or to Dijkstra's settled set.
 * Checkers flag planted violations; planted mistakes in a copy of the oracle
   source fail the pins above.
 """
@@ -45,9 +49,11 @@ def _scipy_sp(n, u, v, c, root=0):
     return scipy_dijkstra(M, directed=True, indices=root)
 
 
-def _o1(n, u, v, c, init=None, root=0, eps=0.0):
-    G = O.OracleGraph(n, root)
+def _o1(n, u, v, c, init=None, root=0, eps=0.0, goal=None, h=None, lib=None):
+    G = O.OracleGraph(n, root, lib=lib)
     G.insert(n, u, v, c)
+    if goal is not None:
+        G.set_goal(goal, h)
     if init is not None:
         G.set_policy(init)
     st = G.replan(eps=eps)
@@ -61,7 +67,8 @@ def _o1(n, u, v, c, init=None, root=0, eps=0.0):
 @pytest.mark.parametrize("name", golden_io.names())
 def test_golden_o1(name):
     gd = golden_io.load(name)
-    g, p, st = _o1(gd["n"], gd["u"], gd["v"], gd["c"], gd["init"], gd["root"])
+    g, p, st = _o1(gd["n"], gd["u"], gd["v"], gd["c"], gd["init"], gd["root"],
+                   goal=gd["goal"], h=gd["h"])
     np.testing.assert_array_equal(g, gd["g"])
     np.testing.assert_array_equal(p, gd["parent"])
     assert st["converged"]
@@ -72,7 +79,12 @@ def test_golden_o1(name):
 def test_golden_o2(name):
     gd = golden_io.load(name)
     d, _ = O.dijkstra(gd["n"], gd["u"], gd["v"], gd["c"], gd["root"])
-    np.testing.assert_array_equal(d, gd["g"])
+    if gd["goal"] is None:
+        np.testing.assert_array_equal(d, gd["g"])
+    else:  # only x_goal and the vertices promising at the optimum are fixed
+        sel = _goal_fixed(d, gd["h"], gd["goal"])
+        assert sel[gd["goal"]] and sel.sum() >= 2
+        np.testing.assert_array_equal(d[sel], gd["g"][sel])
 
 
 # ------------------------------------------------------- O2 vs library ---
@@ -237,6 +249,131 @@ def test_iteration_bound():
     assert st["iterations"] <= depth.max() + 2
 
 
+# ---------------------------------------- goal-directed form (Sec. IV-C) ---
+
+def _goal_fixed(d, h, goal, rel=1e-9):
+    """The vertices whose g a goal-directed Replan fixes: x_goal, and every v
+    with d(v) + h(v) < d(x_goal), by a relative margin so that rounding
+    cannot move a vertex across the boundary."""
+    sel = np.isfinite(d) & (d + h < d[goal] * (1.0 - rel))
+    sel[goal] = True
+    return sel
+
+
+def _goal_case(seed, target=(0.6, 0.6), scale=0.99):
+    """A 2-D roadmap of the C1 recipe, x_goal = the reachable vertex nearest to
+    ``target`` and h = scale x the Euclidean distance to x_goal, which is
+    consistent because every edge cost is a Euclidean length."""
+    rm = W.roadmap_c1(trial=seed)
+    d, _ = O.dijkstra(rm.n, rm.u, rm.v, rm.cost)
+    reach = np.flatnonzero(np.isfinite(d))
+    near = np.linalg.norm(rm.points[reach] - np.asarray(target), axis=1)
+    goal = int(reach[np.argmin(near)])
+    h = scale * np.linalg.norm(rm.points - rm.points[goal], axis=1)
+    return rm, d, goal, h
+
+
+def _goal_theorem_holds(seed, lib=None) -> bool:
+    rm, d, goal, h = _goal_case(seed)
+    g, _, st = _o1(rm.n, rm.u, rm.v, rm.cost, goal=goal, h=h, lib=lib)
+    sel = _goal_fixed(d, h, goal)
+    return bool(st["converged"] and np.allclose(g[sel], d[sel], rtol=1e-12, atol=0))
+
+
+def _parent_cost(rm, p):
+    """c(p(v), v) of the cheapest parallel edge, +inf where p(v) < 0."""
+    best = {}
+    for a, b, c in zip(rm.u.tolist(), rm.v.tolist(), np.asarray(rm.cost, np.float64).tolist()):
+        k = (min(a, b), max(a, b))
+        best[k] = min(best.get(k, math.inf), c)
+    return np.array([best[(min(v, int(q)), max(v, int(q)))] if q >= 0 else math.inf
+                     for v, q in enumerate(p)])
+
+
+@pytest.mark.parametrize("seed", range(3))
+def test_goal_directed_reaches_the_optimum_c1(seed):
+    rm, d, goal, h = _goal_case(seed)
+    g, p, st = _o1(rm.n, rm.u, rm.v, rm.cost, goal=goal, h=h)
+    _, _, st_free = _o1(rm.n, rm.u, rm.v, rm.cost)
+    assert st["converged"]
+    sel = _goal_fixed(d, h, goal)
+    np.testing.assert_allclose(g[sel], d[sel], rtol=1e-12, atol=0)
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost)
+    assert A.check_tree(p) == (0, -1)
+    # a stored g is never below the cost of its policy path
+    fin = np.isfinite(g)
+    assert np.all(g[fin] >= d[fin] * (1 - 1e-12))
+    kid = p >= 0
+    assert np.all(g[kid] >= g[p[kid]] + _parent_cost(rm, p)[kid])
+    # the pruning took effect: fewer values assigned, some vertices left
+    # above their shortest-path cost or unreached
+    assert st["evaluated"] < st_free["evaluated"]
+    assert np.sum(~np.isfinite(g) | (g > d * (1 + 1e-12))) > 0
+
+
+def test_goal_with_zero_heuristic_fixes_the_dijkstra_ball():
+    rm, d, goal, _ = _goal_case(1)
+    g, _, _ = _o1(rm.n, rm.u, rm.v, rm.cost, goal=goal, h=np.zeros(rm.n))
+    sel = _goal_fixed(d, np.zeros(rm.n), goal)
+    assert sel.sum() > 10
+    np.testing.assert_allclose(g[sel], d[sel], rtol=1e-12, atol=0)
+
+
+def test_goal_off_or_unreachable_is_the_goal_free_replan():
+    n = 300
+    rm = W.random_graph(77, n, 5 * n)
+    c = rm.cost.astype(np.float64)
+    h = np.random.default_rng(5).random(n + 1)
+    g0, p0, st0 = _o1(n + 1, rm.u, rm.v, c)
+    # x_goal = vertex n, which no edge reaches: g(x_goal) stays +inf
+    g1, p1, st1 = _o1(n + 1, rm.u, rm.v, c, goal=n, h=h)
+    np.testing.assert_array_equal(g0, g1)
+    np.testing.assert_array_equal(p0, p1)
+    assert st0 == st1
+    G = O.OracleGraph(n + 1)
+    G.insert(n + 1, rm.u, rm.v, c)
+    G.set_goal(3, h)
+    G.set_goal(-1, h)
+    st2 = G.replan()
+    g2, p2 = G.get()
+    G.close()
+    np.testing.assert_array_equal(g0, g2)
+    np.testing.assert_array_equal(p0, p2)
+    assert st0 == st2
+
+
+def test_goal_at_the_root_attaches_nothing():
+    n = 50
+    rm = W.random_graph(9, n, 4 * n)
+    g, p, st = _o1(n, rm.u, rm.v, rm.cost, goal=0, h=np.zeros(n))
+    assert g[0] == 0.0 and np.all(np.isinf(g[1:])) and np.all(p == -1)
+    assert st["iterations"] == 1 and st["switches"] == 0
+
+
+def test_goal_directed_schedule_fp32_knn():
+    rm = W.roadmap_c2(n=8000, block=500, companion=True)
+    c = rm.cost.astype(np.float64)
+    d, _ = O.dijkstra(rm.n, rm.u, rm.v, c)
+    reach = np.flatnonzero(np.isfinite(d))
+    goal = int(reach[np.argmin(np.linalg.norm(rm.points[reach] - 0.9, axis=1))])
+    h = 0.99 * np.linalg.norm(rm.points - rm.points[goal], axis=1)
+    sel = _goal_fixed(d, h, goal)
+    for block in (500, rm.n):
+        g, _, stats = O.replan_schedule(rm, block=block, goal=goal, h=h)
+        assert all(s["converged"] for s in stats)
+        np.testing.assert_allclose(g[sel], d[sel], rtol=1e-12, atol=0)
+
+
+def test_goal_rejects_bad_heuristic():
+    G = O.OracleGraph(4)
+    for bad in ([0.0, -1.0], [0.0, np.nan], [np.inf]):
+        with pytest.raises(O.OracleError):
+            G.set_goal(1, np.array(bad))
+    with pytest.raises(O.OracleError):
+        G.set_goal(4, None)
+    G.close()
+
+
 # ------------------------------------------------------------ checkers ---
 
 def test_checkers_flag_planted_violations():
@@ -277,10 +414,17 @@ MUTANTS = {
     "strict_to_nonstrict": ("if (cand < ghat) {", "if (cand <= ghat) {"),
     "dropped_parent_cost": ("G->g[y] = G->pc[y] + G->g[x];", "G->g[y] = G->g[x];"),
     "wrong_index_in_evaluate": ("G->g[y] = G->pc[y] + G->g[x];", "G->g[y] = G->pc[x] + G->g[x];"),
-    "stale_policy_cost": ("G->pc[x] = L->c[i];\n", "\n"),
-    "wrong_sign_delta": ("double d = G->g[x] - ghat;", "double d = ghat - G->g[x];"),
+    "stale_policy_cost": ("G->pc[x] = best_c;\n", "\n"),
+    "wrong_sign_delta": ("double d = cur - ghat;", "double d = ghat - cur;"),
     "parallel_edge_max": ("(L->nbr[j] == w && L->c[j] > c)", "(L->nbr[j] == w && L->c[j] < c)"),
     "dijkstra_dropped_cost": ("double nd = dist[x] + A->c[i];", "double nd = dist[x] + 1.0;"),
+    "promising_nonstrict": ("if (G->g[y] + G->h[y] < bound) {", "if (G->g[y] + G->h[y] <= bound) {"),
+    "promising_tests_parent": ("if (G->g[y] + G->h[y] < bound) {",
+                               "if (G->g[x] + G->h[x] < bound) {"),
+    "evaluate_ignores_h": ("if (G->g[y] + G->h[y] < bound) {", "if (G->g[y] < bound) {"),
+    "lookahead_nonstrict": ("ghat + G->h[x] < bound", "ghat + G->h[x] <= bound"),
+    "no_lookahead": ("if (best >= 0 && ghat + G->h[x] < bound) {", "if (best >= 0) {"),
+    "improve_ignores_h": ("ghat + G->h[x] < bound", "ghat < bound"),
 }
 
 
@@ -288,21 +432,20 @@ def _pins_pass(lib) -> bool:
     try:
         for name in golden_io.names():
             gd = golden_io.load(name)
-            G = O.OracleGraph(gd["n"], gd["root"], lib=lib)
-            G.insert(gd["n"], gd["u"], gd["v"], gd["c"])
-            if gd["init"] is not None:
-                G.set_policy(gd["init"])
-            st = G.replan()
-            g, p = G.get()
-            G.close()
+            g, p, st = _o1(gd["n"], gd["u"], gd["v"], gd["c"], gd["init"], gd["root"],
+                           goal=gd["goal"], h=gd["h"], lib=lib)
             if not (np.array_equal(g, gd["g"]) and np.array_equal(p, gd["parent"])
                     and st["iterations"] == gd["iterations"]):
                 return False
             A = O.CSR(gd["n"], gd["u"], gd["v"], gd["c"], lib=lib)
             d, _ = A.dijkstra()
             A.close()
-            if not np.array_equal(d, gd["g"]):
+            sel = (np.ones(gd["n"], dtype=bool) if gd["goal"] is None
+                   else _goal_fixed(d, gd["h"], gd["goal"]))
+            if not np.array_equal(d[sel], gd["g"][sel]):
                 return False
+        if not _goal_theorem_holds(0, lib):
+            return False
         for seed in range(3):
             rm = W.random_graph(300 + seed, 40, 120)
             A = O.CSR(40, rm.u, rm.v, rm.cost, lib=lib)

@@ -203,6 +203,16 @@ def run_ours(args) -> None:
     entry_bytes = 8 if cost_bytes == 4 else 16
     G = P.Graph(rm.n, rm.m, 0, rm.cost.dtype, device=local, stream=stream.cuda_stream)
     flush = torch.empty(2 * L2_BYTES // 4, dtype=torch.int32, device="cuda")
+    goal = None
+    if args.goal == "far":
+        # x_goal: the sample nearest to x_init reflected through the centre of
+        # the sampled box; h = 0.99 x the Euclidean distance to it (admissible
+        # and consistent: the edge costs are Euclidean lengths)
+        lo, hi = rm.points.min(axis=0), rm.points.max(axis=0)
+        target = (lo + hi) - rm.points[0]
+        goal = int(np.argmin(np.linalg.norm(rm.points - target, axis=1)))
+        h_goal = (0.99 * np.linalg.norm(rm.points - rm.points[goal], axis=1)).astype(np.float32)
+        G.set_goal(goal, h_goal)
 
     extra = {"wave_levels": 0, "jump_evaluates": 0, "dense_sweeps": 0, "switches": 0}
 
@@ -337,11 +347,15 @@ def run_ours(args) -> None:
     dom_bytes = kbytes[dom]
     achieved = (dom_bytes / launches) / (dom_ms_avg / 1e3) / 1e9 if dom_ms_avg > 0 else 0.0
     traffic = None
+    g_goal = None
+    if goal is not None:
+        g_goal = float(G.get_costs()[goal])
     tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
-        if tj.get("workload") == args.workload and tj.get("kernel_hash") == kernel_hash(dom):
+        if (tj.get("workload") == args.workload and tj.get("kernel_hash") == kernel_hash(dom)
+                and goal is None):
             traffic = tj.get("traffic_bytes_per_launch")
 
     line = {
@@ -354,6 +368,10 @@ def run_ours(args) -> None:
                    "vertices": rm.n, "undirected_edges": rm.m, "csr_entries": 2 * rm.m,
                    "blocks_per_step": n_blocks, "block_size": rm.block,
                    "evaluate": args.evaluate, "wave_tail": args.wave_tail,
+                   "goal": None if goal is None else {
+                       "vertex": goal, "g_goal": g_goal,
+                       "heuristic": "0.99 x Euclidean distance to x_goal (FP32)",
+                       "pruned_form": "goal-directed Replan, promising g + h < g(x_goal)"},
                    "wave_ctas": args.wave_ctas,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": dict(extra),
@@ -386,7 +404,8 @@ def run_ours(args) -> None:
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
-        line["cpu_baseline"] = cpu_baseline(rm, args.cpu_seconds)
+        line["cpu_baseline"] = cpu_baseline(rm, args.cpu_seconds, goal,
+                                            h_goal if goal is not None else None)
     G.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -413,11 +432,14 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()[:12]
 
 
-def oracle_prefix(rm, seconds: float) -> dict:
+def oracle_prefix(rm, seconds: float, goal=None, h=None) -> dict:
     """Serial policy iteration (the oracle, Alg. 2) on a prefix of the same
-    Batched-Extension schedule, block by block, until `seconds` have passed."""
+    Batched-Extension schedule, block by block, until `seconds` have passed
+    (goal-directed, Sec. IV-C, when `goal` is given)."""
     import oracle as O
     G = O.OracleGraph(rm.n)
+    if goal is not None:
+        G.set_goal(goal, np.asarray(h, dtype=np.float64))
     relax = 0
     blocks = 0
     t_exploit = 0.0
@@ -435,8 +457,8 @@ def oracle_prefix(rm, seconds: float) -> dict:
     return dict(relax=relax, blocks=blocks, seconds=t_exploit, n_present=min(rm.n, blocks * rm.block))
 
 
-def cpu_baseline(rm, seconds: float) -> dict:
-    r = oracle_prefix(rm, seconds)
+def cpu_baseline(rm, seconds: float, goal=None, h=None) -> dict:
+    r = oracle_prefix(rm, seconds, goal, h)
     return {"value": round(r["relax"] / r["seconds"], 1), "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
@@ -615,6 +637,8 @@ def main():
                     help="run every exploit from the host loop (no CUDA graphs), e.g. under ncu")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--goal", choices=("none", "far"), default="none",
+                    help="goal-directed Replan toward the sample opposite x_init")
     ap.add_argument("--no-prefetch", action="store_true",
                     help="end-to-end pass: copy each block when it is inserted, not during the "
                          "previous exploit")

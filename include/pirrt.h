@@ -165,6 +165,36 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *g, int64_t n_new_vertices, in
                                       const int32_t *src, const int32_t *dst, const void *cost,
                                       int on_device);
 
+/* Goal-directed Replan (Sec. IV-C; the promising set B of Sec. III and the
+ * vertex properties h and b of Sec. IV-A).  goal = x_goal (a vertex id below
+ * the capacity, inserted already or later), or -1 to return to the
+ * goal-free form.  h[v], v < n_h, is a heuristic cost-to-go from v to
+ * x_goal (host memory, FP32, finite and >= 0; vertices from n_h on get 0);
+ * it must be admissible -- no larger than the cost of any path from v to
+ * x_goal -- for g(x_goal) to stay optimal, and consistent (h(u) <= c(u, v) +
+ * h(v) on every edge) for the promising set below to be exact.
+ *
+ * With a goal, a vertex is promising when g(v) + h(v) < g(x_goal), g(x_goal)
+ * taken as each Replan iteration begins.  Improve switches v only if the new
+ * value makes v promising; the top-down Evaluate lowers g of every child it
+ * reaches but expands (scans the row of, lowers the children of) only
+ * promising vertices, so g below a vertex that is not promising may stay
+ * above the cost of its policy path.  At a stable policy g(x_goal) is the
+ * shortest-path cost, and so is g(v) of every v with d(v) + h(v) <
+ * d(x_goal) (d = shortest-path cost) when h is consistent.  Pointer-jumping
+ * Evaluates (deep trees, PIRRT_EVAL_JUMP) and the barrier-free walk do not
+ * prune; they only do more work.
+ *
+ * Changing the goal or h after a goal-directed exploit makes the next exploit
+ * first evaluate the whole tree and sweep every vertex (like set_policy).
+ * pirrt_graph_save evaluates the whole tree first.  The goal and h are not
+ * part of a checkpoint; they survive pirrt_graph_reset and _load.  h takes
+ * 4 bytes per vertex of capacity, allocated on the first call with a goal.
+ * Synchronises the stream.  Errors: PIRRT_ERR_INVALID_ARG (goal or n_h out of
+ * range, NULL h with n_h > 0), PIRRT_ERR_BAD_INPUT (negative, NaN or infinite
+ * h), PIRRT_ERR_OOM. */
+pirrt_status pirrt_graph_set_goal(pirrt_graph *g, int32_t goal, const float *h, int64_t n_h);
+
 /* Start copying the next block's host edge list to the device on a copy
  * stream of the graph, so that the copy overlaps the current exploit (the
  * paper's future work, Sec. VII, overlaps exploration with exploitation).

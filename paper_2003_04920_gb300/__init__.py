@@ -121,6 +121,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_get_adjacency": (st, [vp, vp, vp, vp, i32]),
         "pirrt_graph_save": (st, [vp, ctypes.c_char_p]),
         "pirrt_graph_prefetch_batch": (st, [vp, i64, vp, vp, vp]),
+        "pirrt_graph_set_goal": (st, [vp, ctypes.c_int32, vp, i64]),
         "pirrt_graph_load": (st, [vp, ctypes.c_char_p]),
         "pirrt_graph_set_profiling": (st, [vp, i32]),
         "pirrt_graph_get_profile": (st, [vp, ctypes.POINTER(pirrt_profile)]),
@@ -276,6 +277,14 @@ class Graph:
         self._pre_keep = (ks, kd, kc)
         self._check("pirrt_graph_prefetch_batch",
                     self._lib.pirrt_graph_prefetch_batch(self._h, int(len(ks)), ps, pd, pc))
+
+    def set_goal(self, goal: int, h=None):
+        """Goal-directed Replan (Sec. IV-C): x_goal and the heuristic h(v) for
+        v < len(h) (host, FP32; 0 beyond).  goal = -1 returns to the goal-free
+        form."""
+        h = np.ascontiguousarray(np.zeros(0) if h is None else h, dtype=np.float32)
+        self._check("pirrt_graph_set_goal",
+                    self._lib.pirrt_graph_set_goal(self._h, int(goal), h.ctypes.data, int(len(h))))
 
     def set_policy(self, parent):
         pp, dev, keep = _buf(parent, np.int32)

@@ -144,6 +144,11 @@ struct DevCounters {
     unsigned converged;           // the last advance saw a stable policy
     unsigned jumped;              // this iteration's Evaluate ran pointer jumping
     unsigned long long eps_bits;  // Delta g threshold (bits of a double >= 0)
+    // Goal-directed Replan (Sec. IV-C): &g[x_goal] (null = goal-free), and
+    // g(x_goal) as the current iteration began -- the bound of the promising
+    // test, the same for every CTA and every kernel of the iteration.
+    const double *goal_g;
+    unsigned long long bound_bits;
     // last completed iteration (read by the host after advance)
     unsigned last_switched, last_dg, last_levels, last_next, last_dense, last_rounds, last_jumped;
     // whole-exploit totals

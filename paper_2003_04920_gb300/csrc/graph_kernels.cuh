@@ -360,7 +360,22 @@ struct ImproveArgs {
     int32_t push;            // list sweeps run from offers (improve_push_kernel); this
                              // kernel then only runs dense sweeps
     unsigned long long *cand;
+    const float *h;          // goal-directed Replan: heuristic h(v); null = goal-free
 };
+
+// Goal-directed Replan (Sec. IV-C).  A vertex v is promising when
+// g(v) + h(v) < g(x_goal), with h an admissible heuristic and g(x_goal) as
+// the iteration began (bound_bits).  Improve takes a switch only if the new
+// value makes v promising; the wave expands (offers, marks, lowers the
+// children of) only promising vertices.  Without a goal h is null and every
+// vertex passes.
+__device__ __forceinline__ double goal_bound(const DevCounters *c, const float *h) {
+    return h != nullptr ? __longlong_as_double((long long)__ldcg(&c->bound_bits)) : CUDART_INF;
+}
+
+__device__ __forceinline__ bool promising(const float *h, int32_t v, double value, double bound) {
+    return h == nullptr || value + (double)__ldg(&h[v]) < bound;
+}
 
 // G lanes cooperate on one vertex: each lane scans every G-th entry of the
 // row, four entries in flight at a time (loads first, then the g gathers),
@@ -382,6 +397,7 @@ improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     if (a.push && !dense) return;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const unsigned long long gpol = policy_evict_last();
+    const double bound = goal_bound(a.ctr, a.h);
 
     unsigned long long relax = 0, improved = 0;
     for (int64_t item = (int64_t)blockIdx.x * groups_per_block + threadIdx.x / G; item < count;
@@ -433,7 +449,7 @@ improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
         if (lane_g == 0 && a.p[v] != kRootMark) {
             const int32_t pv = a.p[v];
             const double cur = pv >= 0 ? a.g[pv] + (double)a.pc[v] : CUDART_INF;
-            if (best < cur) {
+            if (best < cur && promising(a.h, v, best, bound)) {
                 a.p[v] = bu;
                 a.pc[v] = bw;
                 const unsigned slot = atomicAdd(&a.ctr->n_switched, 1u);
@@ -721,6 +737,7 @@ struct WaveArgs {
     unsigned long long *cand;
     unsigned tail_max;        // levels of at most this many vertices: one CTA, no grid barrier
     int64_t list_cap;         // capacity of lvl[] / lvg[]
+    const float *h;           // goal-directed Replan: heuristic h(v); null = goal-free
 };
 
 // Level 0 holds the switched vertices: each takes g(s) = g(p(s)) + c(p(s), s).
@@ -777,6 +794,7 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
     unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
     const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
     const bool offering = a.push && marking;
+    const double bound = goal_bound(c, a.h);
     for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
         const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
         int deg = 0;
@@ -800,10 +818,14 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
             }
             if (u >= 0) {
                 first = atomicExch(&a.wstamp[u], tag) != tag;
-                int64_t b, e;
-                row_range(a.rows, u, b, e);
-                deg = (int)(e - b);
-                sh.base[tid] = b;
+                // a vertex that is not promising keeps its lowered g but is
+                // not expanded: its subtree and neighbours are left as they are
+                if (promising(a.h, u, gu, bound)) {
+                    int64_t b, e;
+                    row_range(a.rows, u, b, e);
+                    deg = (int)(e - b);
+                    sh.base[tid] = b;
+                }
             }
         }
         sh.u[tid] = u;
@@ -957,6 +979,9 @@ __device__ __forceinline__ void advance_iteration(DevCounters *c, cudaGraphCondi
     const unsigned wave_epoch = __ldcg(&c->wave_epoch), iter = __ldcg(&c->iter) + 1u;
     const unsigned max_iters = __ldcg(&c->max_iters), la = __ldcg(&c->la);
     const unsigned epoch = __ldcg(&c->epoch);
+    const double *goal_g = c->goal_g;
+    if (goal_g != nullptr)
+        c->bound_bits = __ldcg(reinterpret_cast<const unsigned long long *>(goal_g));
     c->last_switched = sw;
     c->last_dg = n_dg;
     c->last_levels = levels;
@@ -1012,6 +1037,9 @@ static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
     c->cum_dense = 0u;
     c->cum_jump_rounds = 0u;
     c->cum_jump_evals = 0u;
+    c->bound_bits = c->goal_g != nullptr
+                        ? *reinterpret_cast<const unsigned long long *>(c->goal_g)
+                        : 0x7ff0000000000000ull;
 }
 
 // Parents as reported through the ABI: the root marker becomes -1.

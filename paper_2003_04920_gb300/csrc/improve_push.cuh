@@ -41,6 +41,7 @@ __device__ void improve_push_body(const ImproveArgs<CT> &a) {
     const int lane = threadIdx.x & 31, grp = lane / G, gl = lane & (G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     const int64_t wid = tid0 >> 5, nwarps = nthreads >> 5;
+    const double bound = goal_bound(c, a.h);
     unsigned long long relax = 0, improved = 0, djmax = 0;
 
     for (int64_t base = wid * 32; base < count; base += nwarps * 32) {
@@ -57,7 +58,10 @@ __device__ void improve_push_body(const ImproveArgs<CT> &a) {
                 if (cb != kCandNone) a.cand[v] = kCandNone;
                 if (pv != kRootMark) {
                     if (pv >= 0) cur = ld_g(&a.g[pv], gpol) + widen(a.pc[v]);
-                    want = cb < kCandNone && __longlong_as_double((long long)cb) < cur;
+                    // goal-directed: an offer that cannot make v promising is
+                    // dropped (the row's best is no larger than any offer)
+                    const double cv = __longlong_as_double((long long)cb);
+                    want = cb < kCandNone && cv < cur && promising(a.h, v, cv, bound);
                     improved += 1;
                 }
             }
@@ -119,7 +123,7 @@ __device__ void improve_push_body(const ImproveArgs<CT> &a) {
                 relax += (unsigned long long)(e - b);
                 if (bv < kCandNone) {
                     const double best = __longlong_as_double((long long)bv);
-                    if (best < scur) {
+                    if (best < scur && promising(a.h, sv, best, bound)) {
                         a.p[sv] = bid;
                         a.pc[sv] = bw;
                         sw = true;

@@ -43,6 +43,7 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
     if (a.push && !dense) return;  // list sweeps run from offers
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const float kInf = __int_as_float(0x7f800000);
+    const double bound = goal_bound(a.ctr, a.h);
     unsigned long long relax = 0, improved = 0, djmax = 0;
     // whole warps iterate together so the appends below are warp-collective.
     // The next iteration's vertex and row extent are loaded one iteration
@@ -167,7 +168,7 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
                 const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
                 if (bv <= kInfBits) {
                     const double best = __longlong_as_double((long long)bv);
-                    if (best < cur) {
+                    if (best < cur && promising(a.h, v, best, bound)) {
                         a.p[v] = bid;
                         a.pc[v] = __uint_as_float(bw);
                         sw = true;

@@ -122,6 +122,7 @@ improve_tma_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     const bool dense = a.ctr->dense != 0u;
     const int64_t count = dense ? a.n : (int64_t)a.ctr->n_active;
     const int64_t n_tiles = (count + kTV - 1) / kTV;
+    const double bound = goal_bound(a.ctr, a.h);
 
     if (tid == 0) {
         for (int s = 0; s < kStages; ++s) {
@@ -356,7 +357,7 @@ improve_tma_kernel(const ImproveArgs<CT> *__restrict__ ap) {
                 const double cur = pv >= 0 ? gp + widen(pcv) : CUDART_INF;
                 if (bv <= kInfBits) {
                     const double best = __longlong_as_double((long long)bv);
-                    if (best < cur) {
+                    if (best < cur && promising(a.h, v, best, bound)) {
                         a.p[v] = bid;
                         a.pc[v] = CostBits<CT>::back(bw);
                         sw = true;

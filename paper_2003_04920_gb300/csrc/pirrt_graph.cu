@@ -83,6 +83,10 @@ struct pirrt_graph {
     int async_dirty = 0;                  // an exploit failed: reset the walk state first
     int32_t *pexport = nullptr;           // parents as reported (root marker -> -1)
     int deep_hint = 0;                    // AUTO: recent exploits met waves past the cap
+    float *h = nullptr;                   // goal-directed Replan: heuristic h(v), cap_n entries
+    int32_t goal = -1;                    // x_goal; -1 = goal-free
+    int stale = 0;        // an exploit pruned subtrees: some g below them are not up to date
+    int goal_dirty = 0;   // the goal or h changed since the last exploit
     int exploits = 0;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned mirror
@@ -94,9 +98,11 @@ struct pirrt_graph {
         unsigned dense_limit = 0, max_levels = 0;
         int push = -1;
         unsigned tail_max = 0;
+        const float *h = nullptr;
         bool operator==(const ArgsKey &o) const {
             return n == o.n && cur == o.cur && dense_limit == o.dense_limit &&
-                   max_levels == o.max_levels && push == o.push && tail_max == o.tail_max;
+                   max_levels == o.max_levels && push == o.push && tail_max == o.tail_max &&
+                   h == o.h;
         }
     } args_key;
     std::map<unsigned long long, cudaGraphExec_t> loops;  // captured Replan loops
@@ -185,6 +191,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     key.max_levels = max_levels;
     key.push = push;
     key.tail_max = tail_max;
+    key.h = G->goal >= 0 ? G->h : nullptr;
     if (key == G->args_key) return PIRRT_OK;
     std::memset(G->hargs, 0, kArgBytes);
     const Entry<CT> *adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
@@ -203,6 +210,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     ia->root = G->cfg.root;
     ia->push = push;
     ia->cand = G->cand;
+    ia->h = key.h;
     for (size_t off : {kArgEval, kArgEvalFallback, kArgEvalForce}) {
         auto *ea = reinterpret_cast<EvaluateArgs<CT> *>(G->hargs + off);
         ea->p = G->p;
@@ -248,6 +256,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->max_levels = max_levels;
     wa->push = push;
     wa->cand = G->cand;
+    wa->h = key.h;
     auto *aa = reinterpret_cast<AsyncArgs<CT> *>(G->hargs + kArgAsync);
     aa->rows = G->rows;
     aa->adj = adj;
@@ -298,6 +307,9 @@ template <typename A>
 const A *dev_arg(pirrt_graph *G, size_t off) {
     return reinterpret_cast<const A *>(G->dargs + off);
 }
+
+template <typename CT>
+pirrt_status reevaluate_impl(pirrt_graph *G);
 
 // Cooperative launch (all CTAs co-resident for the grid barrier); works on a
 // capturing stream as well.
@@ -695,6 +707,13 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
           o.group == 32) ||
         o.wave_ctas < 0 || o.wave_ctas > 2)
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
+    if (G->stale && G->goal_dirty) {
+        // subtrees pruned for the previous goal or h: bring every g up to date
+        const pirrt_status rr = reevaluate_impl<CT>(G);
+        if (rr) return rr;
+    }
+    G->goal_dirty = 0;
+    if (G->goal >= 0) G->stale = 1;
     const int64_t max_iters = o.max_iters > 0 ? o.max_iters : G->n + 2;
     const int gs = o.group, tile = o.tile;
     const double frac = o.dense_fraction > 0.0 ? o.dense_fraction : 0.35;
@@ -895,6 +914,15 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     policy_commit_kernel<CT><<<blocks, kThreads, 0, G->stream>>>(
         G->n, G->cfg.root, tp, tc, G->p, static_cast<CT *>(G->pc), G->g, G->g32);
     CKL();
+    return reevaluate_impl<CT>(G);
+}
+
+// Evaluate the whole policy tree (pointer jumping, no pruning) and make the
+// next Improve sweep every vertex: after set_policy, and in the goal-directed
+// form after the goal or h changed, since subtrees pruned for the old goal
+// may hold values that are not up to date.
+template <typename CT>
+pirrt_status reevaluate_impl(pirrt_graph *G) {
     pirrt_status rc = write_args<CT>(G, 0u, 1u, 0, 0u);
     if (rc) return rc;
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(G->ctr, 1u, 0ull);
@@ -907,6 +935,22 @@ pirrt_status set_policy_impl(pirrt_graph *G, const int32_t *parent) {
     CKL();
     const unsigned one = 1u;
     CK(cudaMemcpyAsync(&G->ctr->dense, &one, sizeof(unsigned), cudaMemcpyHostToDevice, G->stream));
+    CK(cudaStreamSynchronize(G->stream));
+    G->stale = 0;
+    return PIRRT_OK;
+}
+
+// Point the counter block at g(x_goal) (null without a goal) and give a goal
+// not yet inserted g = +inf, so that the bound read at each iteration is
+// defined.  Synchronous: the host sources live on the stack.
+pirrt_status apply_goal(pirrt_graph *G) {
+    const double *gg = G->goal >= 0 ? G->g + G->goal : nullptr;
+    CK(cudaMemcpyAsync(&G->ctr->goal_g, &gg, sizeof(gg), cudaMemcpyHostToDevice, G->stream));
+    if (G->goal >= 0 && G->goal >= G->n) {
+        const double inf = HUGE_VAL;
+        CK(cudaMemcpyAsync(G->g + G->goal, &inf, sizeof(double), cudaMemcpyHostToDevice,
+                           G->stream));
+    }
     CK(cudaStreamSynchronize(G->stream));
     return PIRRT_OK;
 }
@@ -927,7 +971,7 @@ void free_all(pirrt_graph *G) {
     void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
-                    G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage};
+                    G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage, G->h};
     for (void *q : bufs)
         if (q) cudaFree(q);
     if (G->ctr_host) cudaFreeHost(G->ctr_host);
@@ -1213,8 +1257,10 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     G->args_key = pirrt_graph::ArgsKey{};
     G->deep_hint = 0;
     G->exploits = 0;
+    G->stale = 0;
+    G->goal_dirty = 0;
     G->last_error.clear();
-    return PIRRT_OK;
+    return apply_goal(G);  // the goal and h stay configured
 }
 
 pirrt_status pirrt_graph_insert_batch(pirrt_graph *G, int64_t n_new, int64_t n_edges,
@@ -1267,6 +1313,33 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *G, int64_t n_new, int64_t n_e
     if (G->cfg.cost_dtype == PIRRT_COST_F32)
         return insert_impl<float>(G, n_new, n_edges, s, d, static_cast<const float *>(c));
     return insert_impl<double>(G, n_new, n_edges, s, d, static_cast<const double *>(c));
+}
+
+pirrt_status pirrt_graph_set_goal(pirrt_graph *G, int32_t goal, const float *h, int64_t n_h) {
+    if (!G) return PIRRT_ERR_INVALID_ARG;
+    if (goal < -1 || goal >= G->cap_n || n_h < 0 || n_h > G->cap_n || (n_h > 0 && !h))
+        return fail(G, PIRRT_ERR_INVALID_ARG,
+                    "set_goal: goal %d or %lld heuristic values outside the capacity %lld", goal,
+                    (long long)n_h, (long long)G->cap_n);
+    for (int64_t v = 0; v < n_h; ++v)
+        if (!(h[v] >= 0.0f) || !std::isfinite(h[v]))
+            return fail(G, PIRRT_ERR_BAD_INPUT, "set_goal: h[%lld] is negative or not finite",
+                        (long long)v);
+    CK(cudaSetDevice(G->cfg.device));
+    if (goal >= 0) {
+        if (!G->h && cudaMalloc(&G->h, sizeof(float) * (size_t)G->cap_n) != cudaSuccess) {
+            G->h = nullptr;
+            return fail(G, PIRRT_ERR_OOM, "set_goal: no room for h");
+        }
+        CK(cudaMemsetAsync(G->h, 0, sizeof(float) * (size_t)G->cap_n, G->stream));
+        if (n_h > 0)
+            CK(cudaMemcpyAsync(G->h, h, sizeof(float) * (size_t)n_h, cudaMemcpyHostToDevice,
+                               G->stream));
+    }
+    G->goal = goal;
+    G->goal_dirty = 1;
+    G->args_key = pirrt_graph::ArgsKey{};
+    return apply_goal(G);
 }
 
 pirrt_status pirrt_graph_prefetch_batch(pirrt_graph *G, int64_t n_edges, const int32_t *src,
@@ -1466,7 +1539,11 @@ constexpr char kCkptMagic[8] = {'P', 'I', 'R', 'R', 'T', 'G', '0', '1'};
 template <typename CT>
 pirrt_status save_impl(pirrt_graph *G, FILE *f) {
     const int64_t n = G->n, m = G->m;
-    pirrt_status rc = pack_csr<CT>(G);
+    pirrt_status rc = PIRRT_OK;
+    // goal-directed: subtrees below pruned vertices are brought up to date,
+    // so that the file holds g of the whole policy tree
+    if (G->stale && (rc = reevaluate_impl<CT>(G))) return rc;
+    rc = pack_csr<CT>(G);
     if (rc) return rc;
     std::vector<int64_t> off((size_t)n + 1);
     std::vector<unsigned char> ent((size_t)m * G->entry_bytes);

@@ -31,6 +31,8 @@ def test_golden(name, dtype):
     gd = golden_io.load(name)
     with P.Graph(gd["n"], len(gd["u"]), gd["root"], dtype) as G:
         G.insert_batch(gd["n"], gd["u"], gd["v"], gd["c"].astype(dtype))
+        if gd["goal"] is not None:
+            G.set_goal(gd["goal"], gd["h"])
         if gd["init"] is not None:
             G.set_policy(gd["init"])
         st = G.exploit()

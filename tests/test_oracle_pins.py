@@ -364,6 +364,36 @@ def test_goal_directed_schedule_fp32_knn():
         np.testing.assert_allclose(g[sel], d[sel], rtol=1e-12, atol=0)
 
 
+@pytest.mark.parametrize("seed", range(40))
+def test_goal_directed_bruteforce_tiny(seed):
+    """Points in the plane, edge costs at least the Euclidean distance, so
+    h(v) = |x_v - x_goal| is consistent; every simple path is enumerated."""
+    rng = np.random.default_rng(1000 + seed)
+    n = int(rng.integers(3, 9))
+    x = rng.random((n, 2))
+    pairs = [(a, b) for a in range(n) for b in range(a + 1, n) if rng.random() < 0.6]
+    if not pairs:
+        pairs = [(0, 1)]
+    u = np.array([a for a, _ in pairs], dtype=np.int32)
+    v = np.array([b for _, b in pairs], dtype=np.int32)
+    c = np.linalg.norm(x[u] - x[v], axis=1) * (1.0 + rng.random(len(u)))
+    ref, _ = _all_simple_paths_min(n, u, v, c)
+    goal = int(rng.integers(1, n))
+    h = np.linalg.norm(x - x[goal], axis=1) * rng.choice([0.0, 0.5, 1.0])
+    g, p, st = _o1(n, u, v, c, goal=goal, h=h)
+    assert st["converged"]
+    if math.isinf(ref[goal]):  # no goal cost ever: the goal-free result
+        g0, p0, _ = _o1(n, u, v, c)
+        np.testing.assert_array_equal(g, g0)
+        np.testing.assert_array_equal(p, p0)
+        return
+    np.testing.assert_allclose(g[goal], ref[goal], rtol=1e-12, atol=0)
+    sel = np.isfinite(ref) & (ref + h < ref[goal] * (1 - 1e-9))
+    np.testing.assert_allclose(g[sel], ref[sel], rtol=1e-12, atol=0)
+    fin = np.isfinite(g)
+    assert np.all(g[fin] >= ref[fin] * (1 - 1e-12))
+
+
 def test_goal_rejects_bad_heuristic():
     G = O.OracleGraph(4)
     for bad in ([0.0, -1.0], [0.0, np.nan], [np.inf]):

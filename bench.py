@@ -577,6 +577,126 @@ def run_batch(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+SWEEP_S = (1, 3, 10, 30, 100, 300, 1000, 3000)
+
+
+def sweep_case(n: int, trial: int, goal: bool):
+    """The block-size sweep's query (Sec. VI: a 2-D query, N samples in
+    batches of S).  The unit square with 200 circles r ~ U[0.01, 0.04] (an
+    obstacle covering either end is redrawn); vertex 0 = x_init = (0.05, 0.05)
+    and vertex 1 = x_goal = (0.95, 0.95), both in V from the start as in
+    Alg. 1, then N - 2 uniform free samples; k = ceil(2e ln N), FP32 costs.
+    Goal-directed Replan (Sec. IV-C) with h = 0.99 x the Euclidean distance to
+    x_goal, or no goal."""
+    scene = W.c5_scene(900 + trial)
+    rng = np.random.default_rng(6 * 1000 + trial)
+    ends = np.array([W.C5_X_INIT, W.C5_X_GOAL], dtype=np.float64)
+    pts = np.vstack([ends, W.free_uniform(rng, scene, n - 2)])
+    rm = W.roadmap_from_points("sweep", pts, scene)
+    if not goal:
+        return rm, None, None
+    h = (0.99 * np.linalg.norm(rm.points - rm.points[1], axis=1)).astype(np.float32)
+    return rm, 1, h
+
+
+def sweep_gpu(rm, goal, h, s_list, reps: int) -> dict:
+    """Insertion plus exploitation of the whole schedule for each S on the
+    GPU: wall time from the first insertion to the last exploit's result
+    (each exploit returns its statistics to the host), median of `reps` runs
+    after one warm-up run; blocks resident in device memory."""
+    import torch
+
+    import paper_2003_04920_gb300 as P
+    P.load_library()
+    dev = [torch.from_numpy(a).cuda() for a in (rm.u, rm.v, rm.cost)]
+    out = {}
+    with P.Graph(rm.n, rm.m, 0, rm.cost.dtype,
+                 stream=torch.cuda.current_stream().cuda_stream) as G:
+        if goal is not None:
+            G.set_goal(goal, h)
+        for S in s_list:
+            blocks = list(rm.blocks(S))
+            times = []
+            for r in range(reps + 1):
+                G.reset()
+                torch.cuda.synchronize()
+                t0 = time.perf_counter()
+                relax = iters = 0
+                for v0, v1, e0, e1 in blocks:
+                    G.insert_batch(v1 - v0, dev[0][e0:e1], dev[1][e0:e1], dev[2][e0:e1])
+                    st = G.exploit()
+                    relax += st["relaxations"]
+                    iters += st["iterations"]
+                torch.cuda.synchronize()
+                if r:
+                    times.append(time.perf_counter() - t0)
+            g = G.get_costs()
+            out[S] = {"ms": round(1e3 * statistics.median(times), 3), "blocks": len(blocks),
+                      "iterations": iters, "relaxations": relax,
+                      "g_goal": None if goal is None else float(g[goal])}
+    return out
+
+
+def sweep_oracle(rm, goal, h, s_list, seconds: float) -> dict:
+    """The same schedules on the oracle (serial policy iteration, one core),
+    insertion plus Replan timed block by block; a schedule that passes
+    `seconds` stops there and reports the blocks it finished."""
+    import oracle as O
+    out = {}
+    for S in s_list:
+        blocks = list(rm.blocks(S))
+        G = O.OracleGraph(rm.n)
+        if goal is not None:
+            G.set_goal(goal, np.asarray(h, dtype=np.float64))
+        spent = 0.0
+        done = relax = iters = 0
+        for v0, v1, e0, e1 in blocks:
+            t0 = time.perf_counter()
+            G.insert(v1 - v0, rm.u[e0:e1], rm.v[e0:e1], rm.cost[e0:e1].astype(np.float64))
+            st = G.replan()
+            spent += time.perf_counter() - t0
+            relax += st["relaxations"]
+            iters += st["iterations"]
+            done += 1
+            if spent > seconds:
+                break
+        g, _ = G.get()
+        G.close()
+        full = done == len(blocks)
+        out[S] = {"ms": round(1e3 * spent, 3), "blocks": len(blocks), "blocks_done": done,
+                  "complete": full, "iterations": iters, "relaxations": relax,
+                  "g_goal": float(g[goal]) if (goal is not None and full) else None}
+    return out
+
+
+def run_sweep(args) -> None:
+    """Planning time against the block size S (Sec. VI's Batched-Extension
+    experiment) at each N of --sweep-n, on the GPU and on the oracle, as one
+    JSON line.  Not the benchmark's headline: every run here fits in L2."""
+    ns = [int(x) for x in args.sweep_n.split(",")]
+    s_list = [int(x) for x in args.sweep_s.split(",")]
+    legs = set(args.sweep_legs.split(","))
+    rows = []
+    for n in ns:
+        rm, goal, h = sweep_case(n, args.trial, args.goal != "none")
+        ss = [S for S in s_list if S <= n]
+        gpu = sweep_gpu(rm, goal, h, ss, max(1, args.steps)) if "gpu" in legs else {}
+        cpu = sweep_oracle(rm, goal, h, ss, args.cpu_seconds) if "oracle" in legs else {}
+        for S in ss:
+            rows.append({"n": n, "S": S, "gpu": gpu.get(S), "oracle": cpu.get(S)})
+    line = {"experiment": "block-size sweep (Sec. VI, Batched-Extension)",
+            "unit": "ms of insertion plus exploitation for the whole schedule",
+            "workload": "2-D unit square, 200 circles r~U[0.01,0.04], x_init=(0.05,0.05) "
+                        "vertex 0, x_goal=(0.95,0.95) vertex 1, k=ceil(2e ln N), FP32 costs, "
+                        "FP64 g",
+            "goal": "x_goal = vertex 1, h = 0.99 x Euclidean distance"
+                    if args.goal != "none" else None,
+            "oracle": {"kind": "oracle", "cores": 1, "budget_s": args.cpu_seconds,
+                       "host": os.uname().machine},
+            "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
 def run_reference(args) -> None:
     world = int(os.environ.get("WORLD_SIZE", "1"))
     rank = int(os.environ.get("RANK", "0"))
@@ -618,7 +738,7 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4"], default="c3")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "sweep"], default="c3")
     ap.add_argument("--graphs", type=int, default=512, help="members of the batched workload")
     ap.add_argument("--n", type=int, default=None, help="override the vertex count")
     ap.add_argument("--block", type=int, default=None, help="override the block size S")
@@ -637,8 +757,13 @@ def main():
                     help="run every exploit from the host loop (no CUDA graphs), e.g. under ncu")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
-    ap.add_argument("--goal", choices=("none", "far"), default="none",
-                    help="goal-directed Replan toward the sample opposite x_init")
+    ap.add_argument("--goal", choices=("none", "far"), default=None,
+                    help="goal-directed Replan toward the sample opposite x_init (default: "
+                         "none, except for the sweep's query)")
+    ap.add_argument("--sweep-n", default="10000,30000", help="sweep: vertex counts")
+    ap.add_argument("--sweep-s", default=",".join(str(x) for x in SWEEP_S),
+                    help="sweep: block sizes")
+    ap.add_argument("--sweep-legs", default="gpu,oracle", help="sweep: gpu, oracle or both")
     ap.add_argument("--no-prefetch", action="store_true",
                     help="end-to-end pass: copy each block when it is inserted, not during the "
                          "previous exploit")
@@ -646,7 +771,11 @@ def main():
                     help="skip the end-to-end pass (e.g. for a profiler's launch list)")
     ap.add_argument("--trace", default=None, help="save the per-iteration trace (.npy)")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.workload == "sweep":
+        if args.impl == "reference":
+            args.sweep_legs = "oracle"
+        run_sweep(args)
+    elif args.impl == "reference":
         run_reference(args)
     elif args.workload == "c4":
         run_batch(args)

@@ -55,6 +55,29 @@ def test_null_handles_are_rejected(lib):
     lib.pirrt_graph_destroy(None)
 
 
+def test_null_handles_are_rejected_by_every_graph_call(lib):
+    """Each graph entry point answers PIRRT_ERR_INVALID_ARG to a NULL handle
+    before touching the device (no GPU here)."""
+    vp, i64, i32 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32
+    calls = {
+        "pirrt_graph_reset": ([vp], (None,)),
+        "pirrt_graph_insert_batch": ([vp, i64, i64, vp, vp, vp, ctypes.c_int],
+                                     (None, 0, 0, None, None, None, 0)),
+        "pirrt_graph_prefetch_batch": ([vp, i64, vp, vp, vp], (None, 0, None, None, None)),
+        "pirrt_graph_set_goal": ([vp, i32, vp, i64], (None, 0, None, 0)),
+        "pirrt_graph_set_policy": ([vp, vp, i64, ctypes.c_int], (None, None, 0, 0)),
+        "pirrt_graph_get_costs": ([vp, vp, i64, ctypes.c_int], (None, None, 0, 0)),
+        "pirrt_graph_get_parents": ([vp, vp, i64, ctypes.c_int], (None, None, 0, 0)),
+        "pirrt_graph_save": ([vp, ctypes.c_char_p], (None, b"x")),
+        "pirrt_graph_load": ([vp, ctypes.c_char_p], (None, b"x")),
+    }
+    for name, (argtypes, args) in calls.items():
+        fn = getattr(lib, name)
+        fn.restype = ctypes.c_int
+        fn.argtypes = argtypes
+        assert fn(*args) == 1, name
+
+
 def test_library_links_no_driver_library():
     path = B.build()
     import subprocess

@@ -200,9 +200,11 @@ pirrt_status pirrt_graph_set_goal(pirrt_graph *g, int32_t goal, const float *h, 
  * paper's future work, Sec. VII, overlaps exploration with exploitation).
  * The next pirrt_graph_insert_batch called with the same host pointers and
  * edge count (on_device = 0) uses the copy instead of copying again; any
- * other call discards it.  The caller keeps the three host buffers alive and
- * unchanged until that insertion returns; with pageable (not page-locked)
- * memory the copy may not overlap.  Errors: PIRRT_ERR_INVALID_ARG,
+ * other call discards it (waiting for its copies to end).  The caller keeps
+ * the three host buffers alive and unchanged until the next
+ * pirrt_graph_insert_batch or pirrt_graph_prefetch_batch call on the graph
+ * returns, or the graph is destroyed; with pageable (not page-locked) memory
+ * the copy may not overlap.  Errors: PIRRT_ERR_INVALID_ARG,
  * PIRRT_ERR_OOM, PIRRT_ERR_CUDA. */
 pirrt_status pirrt_graph_prefetch_batch(pirrt_graph *g, int64_t n_edges, const int32_t *src,
                                         const int32_t *dst, const void *cost);

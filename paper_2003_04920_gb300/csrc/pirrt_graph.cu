@@ -1278,9 +1278,15 @@ pirrt_status pirrt_graph_insert_batch(pirrt_graph *G, int64_t n_new, int64_t n_e
     CK(cudaSetDevice(G->cfg.device));
     const int32_t *s = src, *d = dst;
     const void *c = cost;
-    const bool prefetched = !on_device && n_edges > 0 && G->pre_n == n_edges && G->pre_src == src &&
-                            G->pre_dst == dst && G->pre_cost == cost;
+    const bool pending = G->pre_n >= 0;
+    const bool prefetched = pending && !on_device && n_edges > 0 && G->pre_n == n_edges &&
+                            G->pre_src == src && G->pre_dst == dst && G->pre_cost == cost;
     G->pre_n = -1;
+    if (pending && !prefetched) {
+        // a prefetch this insertion does not use: its copies end before control
+        // returns, so that the caller may release those host buffers
+        CK(cudaStreamSynchronize(G->copy));
+    }
     if (prefetched) {
         // the block was copied on the copy stream while the last exploit ran
         CK(cudaStreamWaitEvent(G->stream, G->pre_done, 0));
@@ -1348,6 +1354,11 @@ pirrt_status pirrt_graph_prefetch_batch(pirrt_graph *G, int64_t n_edges, const i
     if (n_edges < 0 || (n_edges > 0 && (!src || !dst || !cost)))
         return fail(G, PIRRT_ERR_INVALID_ARG, "prefetch_batch: negative size or NULL pointer");
     CK(cudaSetDevice(G->cfg.device));
+    if (G->pre_n >= 0) {
+        // an earlier prefetch that no insertion used: its copies end first, so
+        // that the caller may release those host buffers
+        CK(cudaStreamSynchronize(G->copy));
+    }
     G->pre_n = -1;
     if (n_edges == 0) return PIRRT_OK;
     const size_t ib = sizeof(int32_t) * (size_t)n_edges;

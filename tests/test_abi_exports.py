@@ -78,6 +78,46 @@ def test_null_handles_are_rejected_by_every_graph_call(lib):
         assert fn(*args) == 1, name
 
 
+C_CALLER = r"""
+#include <stddef.h>
+#include <stdint.h>
+#include "pirrt.h"
+int main(void) {
+    float h[4] = {0};
+    int32_t src[3] = {0, 1, 2}, dst[3] = {1, 2, 3};
+    float cost[3] = {1, 1, 1};
+    double g_out[4];
+    int32_t p_out[4];
+    pirrt_config cfg = {.max_vertices = 4, .max_edges = 3, .root = 0,
+                        .cost_dtype = PIRRT_COST_F32, .device = 0, .stream = NULL};
+    pirrt_graph *g = NULL;
+    if (pirrt_graph_create(&cfg, &g) != PIRRT_OK) return 1;
+    pirrt_graph_set_goal(g, 3, h, 4);
+    pirrt_graph_insert_batch(g, 4, 3, src, dst, cost, 0);
+    pirrt_exploit_stats st;
+    pirrt_graph_exploit(g, NULL, &st);
+    pirrt_graph_get_costs(g, g_out, 4, 0);
+    pirrt_graph_get_parents(g, p_out, 4, 0);
+    pirrt_graph_destroy(g);
+    return 0;
+}
+"""
+
+
+def test_header_is_c11_and_a_c_caller_links(tmp_path):
+    """include/pirrt.h compiles as C11 with warnings as errors, and a C caller
+    links against the library (it is not run: that needs a GPU)."""
+    import subprocess
+    path = B.build()
+    src = tmp_path / "caller.c"
+    src.write_text(C_CALLER)
+    exe = tmp_path / "caller"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Wextra", "-Werror", f"-I{HEADER_DIR}",
+                    str(src), "-o", str(exe), path, f"-Wl,-rpath,{os.path.dirname(path)}"],
+                   check=True)
+    assert exe.exists()
+
+
 def test_library_links_no_driver_library():
     path = B.build()
     import subprocess

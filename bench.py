@@ -459,10 +459,11 @@ def oracle_prefix(rm, seconds: float, goal=None, h=None) -> dict:
 
 def cpu_baseline(rm, seconds: float, goal=None, h=None) -> dict:
     r = oracle_prefix(rm, seconds, goal, h)
+    form = "" if goal is None else f"goal-directed toward vertex {goal} (Sec. IV-C), "
     return {"value": round(r["relax"] / r["seconds"], 1), "unit": UNIT, "cores": 1,
             "kind": "oracle",
             "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
-            "sample": f"serial policy iteration (Alg. 2) on the first {r['blocks']} of "
+            "sample": f"serial policy iteration (Alg. 2), {form}on the first {r['blocks']} of "
                       f"{rm.n_blocks()} blocks of the same schedule ({r['n_present']} vertices), "
                       f"Improve sweeping every vertex each round; {r['relax']} relaxations "
                       f"in {r['seconds']:.2f} s"}

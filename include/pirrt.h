@@ -11,7 +11,8 @@
  *     Sec. IV-A, the edge list is merged into a CSR on the device),
  *   - Replan (Alg. 2): Improve (every vertex re-selects its parent as the
  *     argmin over neighbours u of g(u) + c(u, v)) and Evaluate (recompute g
- *     under the new parent tree), repeated until no parent changes.
+ *     under the new parent tree), repeated until no parent changes;
+ *     optionally goal-directed (Sec. IV-C, pirrt_graph_set_goal).
  *
  * Conventions shared by every entry point:
  *   - Vertex ids are dense int32: insert_batch appends ids [n, n + n_new).
@@ -22,7 +23,9 @@
  *   - Pointers flagged "on_device" are CUDA device pointers (any allocator,
  *     e.g. PyTorch's); otherwise they are host pointers.  The caller owns
  *     every buffer it passes; the library reads inputs before the call
- *     returns and never retains caller pointers.
+ *     returns and never retains caller pointers, except
+ *     pirrt_graph_prefetch_batch, whose copies read the host buffers after
+ *     it returns (its comment gives how long they must stay).
  *   - All device work is ordered on the stream given at create time
  *     (NULL = legacy default stream).  Calls that return results to the
  *     host (exploit, get_*) synchronise that stream before returning.

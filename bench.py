@@ -214,16 +214,22 @@ def run_ours(args) -> None:
         h_goal = (0.99 * np.linalg.norm(rm.points - rm.points[goal], axis=1)).astype(np.float32)
         G.set_goal(goal, h_goal)
 
-    extra = {"wave_levels": 0, "jump_evaluates": 0, "dense_sweeps": 0, "switches": 0}
+    extra = {"wave_levels": 0, "jump_evaluates": 0, "dense_sweeps": 0, "switches": 0,
+             "improve_entries": 0, "offers": 0}
+    block_ms = []  # per-block device time of the last step run with block_times=True
 
-    def step(device_inputs=True):
+    def step(device_inputs=True, block_times=False):
         G.reset()
         relax = 0
         iters = 0
         for k in extra:
             extra[k] = 0
         blocks = list(rm.blocks())
+        ev = []
         for b, (v0, v1, e0, e1) in enumerate(blocks):
+            if block_times:
+                ev.append(torch.cuda.Event(enable_timing=True))
+                ev[-1].record(stream)
             if device_inputs:
                 G.insert_batch(v1 - v0, dev_u[e0:e1], dev_v[e0:e1], dev_c[e0:e1])
             else:
@@ -240,6 +246,11 @@ def run_ours(args) -> None:
             iters += st["iterations"]
             for k in extra:
                 extra[k] += st[k]
+        if block_times:
+            ev.append(torch.cuda.Event(enable_timing=True))
+            ev[-1].record(stream)
+            ev[-1].synchronize()
+            block_ms[:] = [ev[i].elapsed_time(ev[i + 1]) for i in range(len(blocks))]
         return relax, iters
 
     def barrier():
@@ -258,8 +269,11 @@ def run_ours(args) -> None:
     # the per-kernel split comes from profiled steps run right after the
     # timed ones; "profiled": the timed steps themselves run the host loop
     # with an event pair around every kernel.
+    timed_extra = []
+
     def timed_steps(k):
         ts, rs, its = [], [], []
+        timed_extra.clear()
         for _ in range(k):
             flush.fill_(1)
             torch.cuda.synchronize()
@@ -272,11 +286,14 @@ def run_ours(args) -> None:
             ts.append(e0.elapsed_time(e1))
             rs.append(r)
             its.append(it)
+            timed_extra.append(dict(extra))
         return ts, rs, its
 
     with ClockSampler(local) as clk:
         G.set_profiling(args.timing == "profiled")
         times, relaxes, iters_all = timed_steps(args.steps)
+        improve_only = float(sum(e["improve_entries"] for e in timed_extra))
+        step_extra = dict(timed_extra[-1]) if timed_extra else dict(extra)
         # the library counts its kernel launches also while not profiling
         timed_launches = G.get_profile()["launches"]
         if args.timing == "graph":
@@ -296,6 +313,8 @@ def run_ours(args) -> None:
     total_relax = float(sum(relaxes))
     total_ms, total_relax = reduce_over_ranks(total_ms, total_relax, world, "cuda")
     value = total_relax / (total_ms / 1e3)
+    improve_ms, improve_only = reduce_over_ranks(float(sum(times)), improve_only, world, "cuda")
+    value_improve_only = improve_only / (improve_ms / 1e3)
     ms_per_step = total_ms / args.steps
 
     # end to end through the C ABI with pinned host buffers
@@ -362,6 +381,10 @@ def run_ours(args) -> None:
         "metric": METRIC, "value": round(value, 1), "unit": UNIT, "n_gpus": world,
         "steps": args.steps, "warmup": args.warmup, "ms_per_step": round(ms_per_step, 3),
         "ms_per_batch": round(ms_per_step / n_blocks, 4),
+        "value_improve_only": round(value_improve_only, 1),
+        "value_note": ("value counts every candidate g(u) + c(u, v) formed: the adjacency entries "
+                       "Improve scans plus the candidates Evaluate offers to the next Improve; "
+                       "value_improve_only counts the Improve scans alone"),
         "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
         "data": "synthetic (seeded roadmap generator)",
         "config": {"workload": f"{args.workload}: {WORKLOADS[args.workload][1]}",
@@ -374,7 +397,7 @@ def run_ours(args) -> None:
                        "pruned_form": "goal-directed Replan, promising g + h < g(x_goal)"},
                    "wave_ctas": args.wave_ctas,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
-                   "per_step": dict(extra),
+                   "per_step": step_extra,
                    "improve_kernel": {0: "candidate offers; dense sweeps by lane groups with "
                                          "FP32 screening",
                                       2: "lane groups, FP32 screening", 1: "staged bulk copies",
@@ -404,8 +427,13 @@ def run_ours(args) -> None:
         "clocks": clocks,
     }
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
+        # per-block device times of one more (untimed) step, for a GPU figure
+        # over exactly the block prefix the oracle covers
+        step(block_times=True)
         line["cpu_baseline"] = cpu_baseline(rm, args.cpu_seconds, goal,
-                                            h_goal if goal is not None else None)
+                                            h_goal if goal is not None else None,
+                                            gpu_block_ms=list(block_ms),
+                                            dijkstra=not args.no_dijkstra)
     G.close()
     if rank == 0:
         print(json.dumps(line), flush=True)
@@ -457,16 +485,44 @@ def oracle_prefix(rm, seconds: float, goal=None, h=None) -> dict:
     return dict(relax=relax, blocks=blocks, seconds=t_exploit, n_present=min(rm.n, blocks * rm.block))
 
 
-def cpu_baseline(rm, seconds: float, goal=None, h=None) -> dict:
+def dijkstra_baseline(rm) -> dict:
+    """O2, the oracle's FP64 binary-heap Dijkstra (1 core), on the final graph
+    of the schedule: the shortest-path tree that every Replan converges to
+    (Sec. V), computed once from scratch."""
+    import oracle as O
+    t0 = time.perf_counter()
+    A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+    t1 = time.perf_counter()
+    A.dijkstra(0)
+    t2 = time.perf_counter()
+    entries = A.entries()
+    A.close()
+    return {"kind": "oracle O2 (FP64 binary-heap Dijkstra)", "cores": 1,
+            "ms": round(1e3 * (t2 - t1), 1), "csr_build_ms": round(1e3 * (t1 - t0), 1),
+            "edges_scanned_per_s": round(entries / (t2 - t1), 1),
+            "sample": f"final graph of the schedule: {rm.n} vertices, {entries} adjacency entries, "
+                      "one shortest-path tree from x_init"}
+
+
+def cpu_baseline(rm, seconds: float, goal=None, h=None, gpu_block_ms=None,
+                 dijkstra: bool = False) -> dict:
     r = oracle_prefix(rm, seconds, goal, h)
     form = "" if goal is None else f"goal-directed toward vertex {goal} (Sec. IV-C), "
-    return {"value": round(r["relax"] / r["seconds"], 1), "unit": UNIT, "cores": 1,
-            "kind": "oracle",
-            "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
-            "sample": f"serial policy iteration (Alg. 2), {form}on the first {r['blocks']} of "
-                      f"{rm.n_blocks()} blocks of the same schedule ({r['n_present']} vertices), "
-                      f"Improve sweeping every vertex each round; {r['relax']} relaxations "
-                      f"in {r['seconds']:.2f} s"}
+    out = {"value": round(r["relax"] / r["seconds"], 1), "unit": UNIT, "cores": 1,
+           "kind": "oracle",
+           "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
+           "sample": f"serial policy iteration (Alg. 2), {form}on the first {r['blocks']} of "
+                     f"{rm.n_blocks()} blocks of the same schedule ({r['n_present']} vertices), "
+                     f"Improve sweeping every vertex each round; {r['relax']} relaxations "
+                     f"in {r['seconds']:.2f} s (exploitation only)"}
+    if gpu_block_ms:
+        k = min(r["blocks"], len(gpu_block_ms))
+        out["gpu_ms_per_batch_same_prefix"] = round(sum(gpu_block_ms[:k]) / k, 4)
+        out["gpu_prefix_note"] = (f"GPU insertion plus exploitation per block over the same first "
+                                  f"{k} blocks, CUDA events, one step")
+    if dijkstra:
+        out["dijkstra"] = dijkstra_baseline(rm)
+    return out
 
 
 def run_batch(args) -> None:
@@ -758,6 +814,8 @@ def main():
                     help="run every exploit from the host loop (no CUDA graphs), e.g. under ncu")
     ap.add_argument("--cpu-seconds", type=float, default=15.0)
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-dijkstra", action="store_true",
+                    help="skip the oracle Dijkstra (O2) baseline on the final graph")
     ap.add_argument("--goal", choices=("none", "far"), default=None,
                     help="goal-directed Replan toward the sample opposite x_init (default: "
                          "none, except for the sweep's query)")

@@ -130,6 +130,14 @@ typedef struct {
     int32_t jump_evaluates; /* Evaluate calls done (or finished) by pointer jumping */
     float ms_exploit;       /* device time of the call, CUDA events on the graph's stream */
     int32_t graph_launch;   /* 1 if the loop ran as one CUDA-graph launch */
+    int64_t improve_entries; /* adjacency entries scanned by Improve alone (the relaxations of
+                               a pull-only Improve); the same for every run of the same input */
+    int64_t offers;         /* candidates formed by Evaluate for the next Improve (tile 0):
+                               relaxations = improve_entries + offers.  A vertex that Evaluate
+                               lowers twice (its new parent was switched in the same round and
+                               not yet lowered when it was read) forms its candidates twice,
+                               so this count can differ by a fraction of a percent between
+                               runs of the same input; the results do not. */
 } pirrt_exploit_stats;
 
 typedef struct pirrt_graph pirrt_graph;   /* opaque, library-owned */
@@ -228,8 +236,11 @@ pirrt_status pirrt_graph_set_policy(pirrt_graph *g, const int32_t *parent, int64
  * c(p(v), v) computed the same way, so a current parent attaining the
  * minimum is kept and otherwise the lowest id wins.  Only vertices with a
  * neighbour whose g changed (or seeded by insertion) are re-examined.
- * Evaluate recomputes g(v) = g(p(v)) + c(p(v), v) from the root by pointer
- * jumping in FP64.  Blocks until done; stats may be NULL.
+ * Evaluate recomputes g(v) = g(p(v)) + c(p(v), v) in FP64 below the
+ * switched vertices, by default top-down level by level (the wave of
+ * PIRRT_EVAL_WAVE), handing over to pointer jumping when a wave passes its
+ * level cap (PIRRT_EVAL_AUTO); see the Evaluate strategies above.  Blocks
+ * until done; stats may be NULL.
  * Errors: PIRRT_ERR_NOT_CONVERGED (max_iters reached; the state stays
  * consistent and exploit may be called again), PIRRT_ERR_BAD_TREE,
  * PIRRT_ERR_DEVICE_TIMEOUT, PIRRT_ERR_CUDA. */
@@ -315,28 +326,51 @@ int64_t pirrt_graph_get_trace(const pirrt_graph *g, pirrt_trace_record *out, int
 
 /* Evaluate that allocates nothing.  The paper has no counterpart: this is a
  * service for callers that cannot call cudaMalloc when they need g -- a
- * real-time planning loop that fixes all of its memory at start-up, or code
- * recording into a CUDA stream capture, where allocation calls are refused.
+ * real-time planning loop that fixes all of its memory at start-up and must
+ * not stall on, or fail in, the allocator in the middle of a control cycle.
  * It computes g(v) = g(parent(v)) + parent_cost[v] from the root by the same
  * pointer-jumping kernel as the graph handle, FP64 throughout:
  *   n            vertex count, at most 262,144 (PIRRT_ERR_CAPACITY beyond)
- *   root         vertex with g = 0
- *   parent       device int32[n]: parent id, -1 for the root / unreached
- *   parent_cost  device double[n]: cost of the edge (parent[v], v)
+ *   root         vertex with g = 0 (its parent entry is ignored)
+ *   parent       device int32[n]: parent id in [0, n), or -1 for unreached
+ *   parent_cost  device double[n]: cost of the edge (parent[v], v), finite
+ *                and >= 0 wherever parent[v] != -1
  *   g_out        device double[n], written: +inf where the chain does not
  *                reach the root
  *   stream       cudaStream_t (NULL = legacy default stream)
- * The caller owns all four arrays.  Scratch lives in one file-scope device
- * array of about 11.5 MB that every GPU loading the library holds until the
- * process exits.  The first call on a device (with that device current)
- * resolves the array's device address and the launch shape; make that first
- * call before any stream capture.  Every call shares the array and clears
- * what it needs, so calls that overlap on the GPU (other streams, other host
- * threads) race: serialise them.  Synchronises the stream to read the
- * status.  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_CAPACITY, PIRRT_ERR_BAD_TREE
- * (a cycle), PIRRT_ERR_DEVICE_TIMEOUT, PIRRT_ERR_CUDA. */
+ * The caller owns all four arrays.  The policy is checked on the device
+ * before the evaluation follows it: a parent id outside [0, n) other than -1,
+ * or a bad cost, gives PIRRT_ERR_BAD_INPUT with g_out holding only the
+ * initial values (0 at the root, +inf elsewhere).  Scratch lives in one
+ * file-scope device array of about 11.5 MB that every GPU loading the library
+ * holds until the process exits.  The first call on a device (with that
+ * device current) resolves the array's device address and the launch shape.
+ * Every call shares the array and clears what it needs, so calls that
+ * overlap on the GPU (other streams, other host threads) race: serialise
+ * them.  The call reads its status word back and synchronises the stream
+ * before it returns.  Errors: PIRRT_ERR_INVALID_ARG, PIRRT_ERR_CAPACITY,
+ * PIRRT_ERR_BAD_INPUT, PIRRT_ERR_BAD_TREE (a cycle: the pointer-jumping round
+ * limit ends the kernel), PIRRT_ERR_DEVICE_TIMEOUT, PIRRT_ERR_CUDA. */
 pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const int32_t *parent,
                                     const double *parent_cost, double *g_out, void *stream);
+
+/* Failure detection self-test (the paper has no counterpart: its planner has
+ * no device-side waits that could stall).  Every wait in the exploitation
+ * kernels is bounded and ends in a status bit instead of a hang; this runs
+ * one such wait where nothing will ever end it, under a short limit:
+ *   which = PIRRT_SELFTEST_GRID_BARRIER: the grid barrier of the cooperative
+ *           kernels, in a grid of two CTAs one of which leaves without
+ *           arriving; limit = polls, 1 .. 2^20 (each about 0.1 to 1 us);
+ *   which = PIRRT_SELFTEST_MBARRIER: the mbarrier wait of the staged Improve
+ *           on a barrier that nothing arrives at; limit = nanoseconds of the
+ *           global timer, 1 .. 10^9.
+ * The kernel's status word is read back and mapped as after an exploit, so a
+ * correct build returns PIRRT_ERR_DEVICE_TIMEOUT and leaves the device usable
+ * (no fault, no trap).  Runs on the current device and `stream` (NULL =
+ * legacy default stream) and synchronises it.  Errors: PIRRT_ERR_INVALID_ARG
+ * (which or limit out of range), PIRRT_ERR_CUDA. */
+enum { PIRRT_SELFTEST_GRID_BARRIER = 0, PIRRT_SELFTEST_MBARRIER = 1 };
+pirrt_status pirrt_selftest_wait(int32_t which, int64_t limit, void *stream);
 
 /* ------------------------------------------------------------------------
  * Batched form: many independent planning graphs exploited together.

@@ -36,6 +36,8 @@ PIRRT_EVAL_AUTO = 0
 PIRRT_EVAL_WAVE = 1
 PIRRT_EVAL_JUMP = 2
 PIRRT_EVAL_ASYNC = 3
+PIRRT_SELFTEST_GRID_BARRIER = 0
+PIRRT_SELFTEST_MBARRIER = 1
 EVALUATE_MODES = {"auto": PIRRT_EVAL_AUTO, "wave": PIRRT_EVAL_WAVE, "jump": PIRRT_EVAL_JUMP,
                   "async": PIRRT_EVAL_ASYNC}
 
@@ -61,7 +63,8 @@ class pirrt_exploit_stats(ctypes.Structure):
                 ("switches", ctypes.c_int64), ("evaluated", ctypes.c_int64),
                 ("jump_rounds", ctypes.c_int32), ("dense_sweeps", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("jump_evaluates", ctypes.c_int32),
-                ("ms_exploit", ctypes.c_float), ("graph_launch", ctypes.c_int32)]
+                ("ms_exploit", ctypes.c_float), ("graph_launch", ctypes.c_int32),
+                ("improve_entries", ctypes.c_int64), ("offers", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         return {name: getattr(self, name) for name, _ in self._fields_}
@@ -131,6 +134,7 @@ def load_library(path: str = LIB_PATH):
         "pirrt_graph_last_error": (ctypes.c_char_p, [vp]),
         "pirrt_status_string": (ctypes.c_char_p, [st]),
         "pirrt_evaluate_noalloc": (st, [i64, ctypes.c_int32, vp, vp, vp, vp]),
+        "pirrt_selftest_wait": (st, [ctypes.c_int32, i64, vp]),
         "pirrt_batch_create": (st, [ctypes.c_int32, vp, vp, vp, ctypes.c_int32, ctypes.c_int32, vp,
                                     ctypes.POINTER(vp)]),
         "pirrt_batch_destroy": (None, [vp]),
@@ -384,14 +388,41 @@ def run_schedule(graph: Graph, roadmap, block: int | None = None, on_device_inpu
 
 def pirrt_evaluate_noalloc(parent, parent_cost, g_out, root: int = 0, stream=None) -> int:
     """Evaluate g from device tensors without any allocation by the library
-    (scratch in a static device array, at most 262,144 vertices).  Returns
-    the pirrt_status code."""
+    (scratch in a static device array, at most 262,144 vertices).  ``parent``
+    is int32, ``parent_cost`` and ``g_out`` are float64, all three contiguous
+    CUDA tensors of one length on one device.  Returns the pirrt_status code."""
+    import torch
     lib = load_library()
+    for name, t, dt in (("parent", parent, torch.int32), ("parent_cost", parent_cost, torch.float64),
+                        ("g_out", g_out, torch.float64)):
+        if not isinstance(t, torch.Tensor) or not t.is_cuda:
+            raise TypeError(f"{name} must be a CUDA tensor")
+        if t.dtype != dt:
+            raise TypeError(f"{name} must be {dt}, got {t.dtype}")
+        if not t.is_contiguous():
+            raise ValueError(f"{name} must be contiguous")
     n = int(parent.numel())
+    if parent_cost.numel() != n or g_out.numel() != n:
+        raise ValueError("parent, parent_cost and g_out must have the same length")
+    if parent_cost.device != parent.device or g_out.device != parent.device:
+        raise ValueError("parent, parent_cost and g_out must be on one device")
+    dev = parent.device.index or 0
+    with torch.cuda.device(dev):
+        if stream is None:
+            stream = _current_stream_ptr(dev)
+        return int(lib.pirrt_evaluate_noalloc(n, int(root), parent.data_ptr(),
+                                              parent_cost.data_ptr(), g_out.data_ptr(), stream))
+
+
+def pirrt_selftest_wait(which: int, limit: int, stream=None) -> int:
+    """Run one bounded device wait that nothing will end (failure detection
+    self-test): ``which`` = PIRRT_SELFTEST_GRID_BARRIER (limit in polls) or
+    PIRRT_SELFTEST_MBARRIER (limit in ns).  Returns the pirrt_status code,
+    PIRRT_ERR_DEVICE_TIMEOUT when the wait gave up as designed."""
+    lib = load_library()
     if stream is None:
-        stream = _current_stream_ptr(parent.device.index or 0)
-    return int(lib.pirrt_evaluate_noalloc(n, int(root), parent.data_ptr(), parent_cost.data_ptr(),
-                                          g_out.data_ptr(), stream))
+        stream = _current_stream_ptr(0)
+    return int(lib.pirrt_selftest_wait(int(which), int(limit), stream))
 
 
 def exploit_opts(eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,

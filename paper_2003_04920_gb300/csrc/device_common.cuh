@@ -350,9 +350,11 @@ __device__ __forceinline__ void block_reserve2_dyn(unsigned na, unsigned nb, uns
 }
 
 // Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded: on timeout the block raises kStatusTimeout and the
-// caller returns.  Returns false on timeout.
-__device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks) {
+// wait is bounded (spin_limit polls, each followed by a short sleep): on
+// timeout the block raises kStatusTimeout and the caller returns.  Returns
+// false on timeout.
+__device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks,
+                                             unsigned long long spin_limit = kBarrierSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
@@ -368,7 +370,7 @@ __device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks) {
         } else {
             unsigned long long spins = 0;
             while (*gen == my_gen) {
-                if (++spins > kBarrierSpinLimit) {
+                if (++spins > spin_limit) {
                     atomicOr(&c->status, kStatusTimeout);
                     ok = 0;
                     break;

@@ -45,8 +45,9 @@ __device__ __forceinline__ void mbar_arrive(unsigned long long *bar) {
     asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(smem_addr(bar)) : "memory");
 }
 
-// Bounded wait for the phase with the given parity; false after kWaitNs.
-__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity) {
+// Bounded wait for the phase with the given parity; false after wait_ns.
+__device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned parity,
+                                          unsigned long long wait_ns = kWaitNs) {
     const unsigned a = smem_addr(bar);
     const unsigned long long t0 = global_ns();
     for (;;) {
@@ -59,7 +60,7 @@ __device__ __forceinline__ bool mbar_wait(unsigned long long *bar, unsigned pari
             : "r"(a), "r"(parity)
             : "memory");
         if (done) return true;
-        if (global_ns() - t0 > kWaitNs) return false;
+        if (global_ns() - t0 > wait_ns) return false;
     }
 }
 

@@ -87,6 +87,7 @@ struct pirrt_graph {
     int32_t goal = -1;                    // x_goal; -1 = goal-free
     int stale = 0;        // an exploit pruned subtrees: some g below them are not up to date
     int goal_dirty = 0;   // the goal or h changed since the last exploit
+    int recover = 0;      // an exploit stopped on a device timeout: re-evaluate first
     int exploits = 0;
     DevCounters *ctr = nullptr;
     DevCounters *ctr_host = nullptr;  // pinned mirror
@@ -707,6 +708,16 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
           o.group == 32) ||
         o.wave_ctas < 0 || o.wave_ctas > 2)
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
+    if (G->recover) {
+        // the last exploit stopped on a device timeout part-way through an
+        // iteration: clear the status word and rebuild g from the policy
+        // (every vertex), so that the next Improve starts from a consistent
+        // state and sweeps every vertex
+        CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
+        const pirrt_status rr = reevaluate_impl<CT>(G);
+        if (rr) return rr;
+        G->recover = 0;
+    }
     if (G->stale && G->goal_dirty) {
         // subtrees pruned for the previous goal or h: bring every g up to date
         const pirrt_status rr = reevaluate_impl<CT>(G);
@@ -875,6 +886,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     s.iterations = (int32_t)h.iter;
     s.converged = h.converged ? 1 : 0;
     s.relaxations = (int64_t)(h.relax + h.offers);
+    s.improve_entries = (int64_t)h.relax;
+    s.offers = (int64_t)h.offers;
     s.improved = (int64_t)h.improved;
     s.evaluated = (int64_t)h.evaluated;
     s.switches = (int64_t)h.switches;
@@ -885,6 +898,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     s.ms_exploit = ms;
     s.graph_launch = graph_ran ? 1 : 0;
     if (st) *st = s;
+    if (h.status & kStatusTimeout) G->recover = 1;
     if ((rc = status_from_bits(G, h.status))) return rc;
     if (!h.converged)
         return fail(G, PIRRT_ERR_NOT_CONVERGED, "exploit: %lld Improve rounds without convergence",
@@ -1259,6 +1273,7 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     G->exploits = 0;
     G->stale = 0;
     G->goal_dirty = 0;
+    G->recover = 0;
     G->last_error.clear();
     return apply_goal(G);  // the goal and h stay configured
 }
@@ -1604,12 +1619,30 @@ pirrt_status load_impl(pirrt_graph *G, FILE *f, const CkptHeader &h) {
               std::fread(p.data(), sizeof(int32_t), p.size(), f) == p.size() &&
               std::fread(pc.data(), sizeof(CT), pc.size(), f) == pc.size();
     if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: file too short");
-    // offsets must be a packed CSR of m entries; parents in range
+    // Everything a kernel will follow is checked here, before any copy: the
+    // offsets are a packed CSR of m entries; every entry's column is another
+    // vertex in [0, n) and its cost finite and > 0; only the root carries the
+    // root marker; every other parent is -1 or a vertex in [0, n) other than
+    // itself, with a finite parent-edge cost >= 0; g is not NaN and >= 0.
     ok = off[0] == 0 && off[(size_t)n] == m;
+    for (int64_t v = 0; ok && v < n; ++v) ok = off[(size_t)v + 1] >= off[(size_t)v];
+    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: inconsistent row offsets");
+    const Entry<CT> *en = reinterpret_cast<const Entry<CT> *>(ent.data());
     for (int64_t v = 0; ok && v < n; ++v)
-        ok = off[(size_t)v + 1] >= off[(size_t)v] && p[(size_t)v] >= kRootMark &&
-             p[(size_t)v] < n;
-    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: inconsistent checkpoint");
+        for (int64_t i = off[(size_t)v]; ok && i < off[(size_t)v + 1]; ++i) {
+            const double w = (double)en[i].w;
+            ok = en[i].col >= 0 && en[i].col < n && en[i].col != v && w > 0.0 && w <= DBL_MAX;
+        }
+    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: adjacency entry out of range");
+    for (int64_t v = 0; ok && v < n; ++v) {
+        const int32_t q = p[(size_t)v];
+        const double c = (double)pc[(size_t)v];
+        const double gv = g[(size_t)v];
+        if (v == h.root) ok = q == kRootMark && gv == 0.0;
+        else ok = q == -1 || (q >= 0 && q < n && q != v && c >= 0.0 && c <= DBL_MAX);
+        ok = ok && gv >= 0.0;  // rejects NaN; +inf marks an unreached vertex
+    }
+    if (!ok) return fail(G, PIRRT_ERR_BAD_INPUT, "load: inconsistent policy");
     pirrt_status rc = pirrt_graph_reset(G);
     if (rc) return rc;
     CK(cudaMemcpyAsync(G->roff, off.data(), sizeof(int64_t) * off.size(), cudaMemcpyHostToDevice,

@@ -3,13 +3,16 @@
 // byte of scratch memory taken from one file-scope device array.
 //
 // Some callers cannot call cudaMalloc at the time they need this: a real-time
-// planning loop that fixes all of its memory at start-up, or code that records
-// its work into a CUDA stream capture, where allocation calls are not allowed.
-// They pass their own inputs and outputs; the scratch (work lists, running
-// sums, the counter block) lives in kScratchBytes of static device memory that
-// every GPU loading this library keeps until the process exits.
+// planning loop that fixes all of its memory at start-up and must not stall
+// on the allocator (or fail on it) in the middle of a control cycle.  They
+// pass their own inputs and outputs; the scratch (work lists, running sums,
+// the counter block, the kernel's argument block) lives in kScratchBytes of
+// static device memory that every GPU loading this library keeps until the
+// process exits.  The call reads a status word back and synchronises its
+// stream, so it is meant for plain streams, not for recording into a graph.
 #include <cuda_runtime.h>
 
+#include <cfloat>
 #include <cstdint>
 #include <functional>
 #include <mutex>
@@ -45,17 +48,41 @@ struct DeviceSetup {
 };
 DeviceSetup g_setup[kMaxDevices];
 
-// g(root) = 0, every other vertex +inf, counters cleared: the evaluate kernel
-// only writes vertices whose parent chain reaches the root.
-__global__ void noalloc_prepare(int64_t n, int32_t root, double *g, DevCounters *ctr) {
+// Clear the counter block and store the kernel's arguments in the scratch
+// array (the evaluate kernel reads them from device memory).  One warp.
+__global__ void noalloc_write_args(EvaluateArgs<double> a, EvaluateArgs<double> *dargs,
+                                   DevCounters *ctr) {
+    unsigned *w = reinterpret_cast<unsigned *>(ctr);
+    for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / sizeof(unsigned)); i += blockDim.x)
+        w[i] = 0u;
+    if (threadIdx.x == 0) *dargs = a;
+}
+
+// g(root) = 0, every other vertex +inf (the evaluate kernel only writes
+// vertices whose parent chain reaches the root), and a check of the caller's
+// policy before any kernel follows it: every parent of a vertex other than
+// the root is -1 or an id in [0, n), and every used parent-edge cost is
+// finite and >= 0.  A violation raises kStatusBadInput.
+__global__ void noalloc_prepare(int64_t n, int32_t root, const int32_t *__restrict__ parent,
+                                const double *__restrict__ cost, double *__restrict__ g,
+                                DevCounters *ctr) {
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
-    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride)
+    bool bad = false;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n; v += stride) {
         g[v] = (v == root) ? 0.0 : CUDART_INF;
-    if (blockIdx.x == 0) {
-        unsigned *w = reinterpret_cast<unsigned *>(ctr);
-        for (int i = threadIdx.x; i < (int)(sizeof(DevCounters) / sizeof(unsigned)); i += blockDim.x)
-            w[i] = 0u;
+        if (v == root) continue;
+        const int32_t pv = parent[v];
+        if (pv == -1) continue;
+        const double c = cost[v];
+        if (pv < 0 || (int64_t)pv >= n || !(c >= 0.0 && c <= DBL_MAX)) bad = true;
     }
+    if (__syncthreads_or(bad) && threadIdx.x == 0) atomicOr(&ctr->status, kStatusBadInput);
+}
+
+// The evaluate kernel runs (n_switched = 1; it is launched with force = 0)
+// only if the policy passed the check.
+__global__ void noalloc_gate(DevCounters *ctr) {
+    ctr->n_switched = __ldcg(&ctr->status) == 0u ? 1u : 0u;
 }
 
 void setup_device(DeviceSetup &s) {
@@ -117,16 +144,18 @@ extern "C" pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const in
     a.ctr = ctr;
     a.n = n;
     a.root = root;
-    a.force = 1;
+    a.force = 0;  // gated by noalloc_gate
     a.role = 0;
 
     cudaStream_t st = static_cast<cudaStream_t>(stream);
-    const int pb = (int)((n + kThreads - 1) / kThreads);
-    noalloc_prepare<<<pb < 1024 ? pb : 1024, kThreads, 0, st>>>(n, root, g_out, ctr);
+    noalloc_write_args<<<1, 32, 0, st>>>(a, dargs, ctr);
     if (cudaGetLastError() != cudaSuccess) return PIRRT_ERR_CUDA;
-    // pageable source: the call returns once `a` has been read
-    if (cudaMemcpyAsync(dargs, &a, sizeof(a), cudaMemcpyHostToDevice, st) != cudaSuccess)
-        return PIRRT_ERR_CUDA;
+    const int pb = (int)((n + kThreads - 1) / kThreads);
+    noalloc_prepare<<<pb < 1024 ? pb : 1024, kThreads, 0, st>>>(n, root, parent, parent_cost,
+                                                                 g_out, ctr);
+    if (cudaGetLastError() != cudaSuccess) return PIRRT_ERR_CUDA;
+    noalloc_gate<<<1, 1, 0, st>>>(ctr);
+    if (cudaGetLastError() != cudaSuccess) return PIRRT_ERR_CUDA;
     const EvaluateArgs<double> *argp = dargs;
     void *args[] = {&argp};
     if (cudaLaunchCooperativeKernel((const void *)evaluate_kernel<double>, dim3(s.blocks),
@@ -138,6 +167,7 @@ extern "C" pirrt_status pirrt_evaluate_noalloc(int64_t n, int32_t root, const in
             cudaSuccess ||
         cudaStreamSynchronize(st) != cudaSuccess)
         return PIRRT_ERR_CUDA;
+    if (status & kStatusBadInput) return PIRRT_ERR_BAD_INPUT;
     if (status & kStatusTimeout) return PIRRT_ERR_DEVICE_TIMEOUT;
     if (status & kStatusBadTree) return PIRRT_ERR_BAD_TREE;
     return PIRRT_OK;

@@ -92,3 +92,47 @@ def test_load_rejects_bad_files_and_mismatches(tmp_path):
         with pytest.raises(P.PirrtError) as e:
             D.load(path)
         assert e.value.status == P.PIRRT_ERR_CAPACITY
+
+
+def _corrupt(src, dst, field, value):
+    """Copy checkpoint `src` to `dst` with one value replaced: the first
+    adjacency entry's column ("col"), or a non-root vertex's parent ("parent")."""
+    import struct
+    raw = bytearray(open(src, "rb").read())
+    magic, dtype, root, n, m = struct.unpack_from("<8siiqq", raw, 0)
+    hdr = 32
+    ent = 8 if dtype == P.PIRRT_COST_F32 else 16
+    if field == "col":
+        struct.pack_into("<i", raw, hdr + 8 * (n + 1), value)
+    else:
+        v = 1 if root != 1 else 2
+        off_p = hdr + 8 * (n + 1) + ent * m + 8 * n
+        struct.pack_into("<i", raw, off_p + 4 * v, value)
+    open(dst, "wb").write(bytes(raw))
+    return n
+
+
+def test_load_rejects_out_of_range_ids_before_any_copy(tmp_path):
+    """A column id equal to n, or the root marker on a vertex other than the
+    root, is caught on the host before anything reaches the device; the graph
+    keeps its contents and still exploits."""
+    rm = W.roadmap_c1()
+    path = str(tmp_path / "c1.ckpt")
+    with P.Graph(rm.n, rm.m, 0, np.float64) as A:
+        A.insert_batch(rm.n, rm.u, rm.v, rm.cost)
+        A.exploit()
+        A.save(path)
+        g = A.get_costs()
+    n = _corrupt(path, str(tmp_path / "col.ckpt"), "col", rm.n)
+    assert n == rm.n
+    _corrupt(path, str(tmp_path / "mark.ckpt"), "parent", -2)
+    _corrupt(path, str(tmp_path / "par.ckpt"), "parent", rm.n + 5)
+    with P.Graph(rm.n, rm.m, 0, np.float64) as B:
+        B.insert_batch(rm.n, rm.u, rm.v, rm.cost)
+        for name in ("col", "mark", "par"):
+            with pytest.raises(P.PirrtError) as e:
+                B.load(str(tmp_path / f"{name}.ckpt"))
+            assert e.value.status == P.PIRRT_ERR_BAD_INPUT, name
+        assert B.n == rm.n
+        assert B.exploit()["converged"] == 1
+        np.testing.assert_array_equal(B.get_costs(), g)

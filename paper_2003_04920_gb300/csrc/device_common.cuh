@@ -119,8 +119,7 @@ struct DevCounters {
     alignas(128) unsigned n_next;      // size of the list being built for the next Improve
     alignas(128) unsigned n_dg;        // vertices whose g changed in the current Evaluate
     alignas(128) unsigned wave_cnt[3];  // top-down Evaluate: list sizes of levels t, t+1, t+2 (mod 3)
-    alignas(128) unsigned bar_count;   // grid barrier: arrivals
-    alignas(128) unsigned bar_gen;     // grid barrier: generation
+    alignas(128) unsigned bar_count;   // grid barrier: arrivals (low bits) and phase (top bit)
     alignas(128) unsigned wave_ticket;  // CTAs done with a wave that ends without a barrier
     alignas(128) unsigned wl_count[kMaxJumpRounds + 2];  // pointer-jumping work-list sizes per round
     alignas(128) unsigned status;      // kStatus* bits
@@ -143,6 +142,7 @@ struct DevCounters {
     unsigned cont;                // the loop continues (set by advance)
     unsigned converged;           // the last advance saw a stable policy
     unsigned jumped;              // this iteration's Evaluate ran pointer jumping
+    unsigned g32_stale;           // a wave with offers changed g without its FP32 shadow
     unsigned long long eps_bits;  // Delta g threshold (bits of a double >= 0)
     // Goal-directed Replan (Sec. IV-C): &g[x_goal] (null = goal-free), and
     // g(x_goal) as the current iteration began -- the bound of the promising
@@ -349,34 +349,33 @@ __device__ __forceinline__ void block_reserve2_dyn(unsigned na, unsigned nb, uns
     __syncthreads();
 }
 
-// Grid-wide barrier for a cooperative launch (all blocks co-resident).  The
-// wait is bounded (spin_limit polls, each followed by a short sleep): on
-// timeout the block raises kStatusTimeout and the caller returns.  Returns
-// false on timeout.
+// Grid-wide barrier for a cooperative launch (all blocks co-resident).  One
+// word counts arrivals: every block adds 1 except block 0, which adds
+// 2^31 - (nblocks - 1), so the last arrival flips the top bit and leaves the
+// low bits as they were (0 between barriers).  A block waits for the flip of
+// the top bit it saw on arrival; nobody resets the word, so a slow block can
+// never miss its barrier's completion (begin_exploit_kernel clears the word
+// between launches).  The wait is bounded (spin_limit polls, each followed by
+// a short sleep): on timeout the block raises kStatusTimeout and the caller
+// returns.  Returns false on timeout.
 __device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks,
                                              unsigned long long spin_limit = kBarrierSpinLimit) {
     __shared__ int s_ok;
     __syncthreads();
     if (threadIdx.x == 0) {
-        volatile unsigned *gen = &c->bar_gen;
-        const unsigned my_gen = *gen;
+        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
         __threadfence();
-        const unsigned prev = atomicAdd(&c->bar_count, 1u);
+        const unsigned old = atomicAdd(&c->bar_count, inc);
+        volatile unsigned *word = &c->bar_count;
         int ok = 1;
-        if (prev == nblocks - 1u) {
-            atomicExch(&c->bar_count, 0u);
-            __threadfence();
-            atomicAdd(&c->bar_gen, 1u);
-        } else {
-            unsigned long long spins = 0;
-            while (*gen == my_gen) {
-                if (++spins > spin_limit) {
-                    atomicOr(&c->status, kStatusTimeout);
-                    ok = 0;
-                    break;
-                }
-                __nanosleep(100);
+        unsigned long long spins = 0;
+        while (((old ^ *word) & 0x80000000u) == 0u) {
+            if (++spins > spin_limit) {
+                atomicOr(&c->status, kStatusTimeout);
+                ok = 0;
+                break;
             }
+            __nanosleep(32);
         }
         __threadfence();
         s_ok = ok;

@@ -614,7 +614,10 @@ __device__ bool jump_evaluate(const EvaluateArgs<CT> &a) {
         if (!grid_barrier(c, nblocks)) return false;
     }
     block_add(finished, &c->evaluated, s_scan);
-    if (blockIdx.x == 0 && threadIdx.x == 0) c->rounds = (unsigned)(r - 1);
+    if (blockIdx.x == 0 && threadIdx.x == 0) {
+        c->rounds = (unsigned)(r - 1);
+        c->g32_stale = 0u;  // every vertex with a parent got its shadow above
+    }
     return true;
 }
 
@@ -652,7 +655,9 @@ struct MarkArgs {
 
 // Frontier marking (and offers) for the changed list, any grid.  The list
 // and g may have been written earlier in the same kernel by other CTAs, so
-// they are read through L2.
+// they are read through L2.  With offers only a neighbour whose g the offer
+// beats is offered and listed (g is final after pointer jumping); without,
+// every neighbour is listed.
 template <typename CT>
 __device__ void mark_changed(const MarkArgs<CT> &a) {
     DevCounters *c = a.ctr;
@@ -687,11 +692,19 @@ __device__ void mark_changed(const MarkArgs<CT> &a) {
             if (i < e) {
                 const Entry<CT> en = a.adj[i];
                 u = en.col;
-                if (a.push && u != a.root) {
-                    offer(a.cand, u, gx + widen(en.w));
-                    ++offers;
+                if (u != a.root) {
+                    if (a.push) {
+                        // g is final here: an offer not below g(u) can never win
+                        ++offers;
+                        const double val = gx + widen(en.w);
+                        if (val < __ldcg(&a.g[u])) {
+                            offer(a.cand, u, val);
+                            pred = atomicExch(&a.stamp[u], epoch) != epoch;
+                        }
+                    } else {
+                        pred = atomicExch(&a.stamp[u], epoch) != epoch;
+                    }
                 }
-                pred = u != a.root && atomicExch(&a.stamp[u], epoch) != epoch;
             }
             stq.push(pred, u, next, &c->n_next);
         }
@@ -738,6 +751,7 @@ struct WaveArgs {
     unsigned tail_max;        // levels of at most this many vertices: one CTA, no grid barrier
     int64_t list_cap;         // capacity of lvl[] / lvg[]
     const float *h;           // goal-directed Replan: heuristic h(v); null = goal-free
+    int64_t n;                // vertex count (bulk refresh of the FP32 shadow)
 };
 
 // Level 0 holds the switched vertices: each takes g(s) = g(p(s)) + c(p(s), s).
@@ -784,7 +798,8 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
                                            int64_t lo, int64_t hi, unsigned tag, unsigned epoch,
                                            int32_t *next, unsigned long long gpol,
                                            unsigned long long &recomputed,
-                                           unsigned long long &offers, bool children) {
+                                           unsigned long long &offers, bool children,
+                                           bool over_limit = false) {
     DevCounters *c = a.ctr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
     const int32_t *in = ((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0];
@@ -792,7 +807,9 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
     int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
     double *outg = ((t & 1u) != 0u) ? a.lvg[0] : a.lvg[1];
     unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
-    const bool marking = *(volatile unsigned *)&c->dense_next == 0u;
+    // over_limit: with offers the caller counts the wave's changes itself
+    // (see wave_evaluate_kernel) and stops the marking past the dense limit
+    const bool marking = !over_limit && *(volatile unsigned *)&c->dense_next == 0u;
     const bool offering = a.push && marking;
     const double bound = goal_bound(c, a.h);
     for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
@@ -817,6 +834,10 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
                 gu = __ldcg(&ing[s0 + tid]);
             }
             if (u >= 0) {
+                // each changed vertex is counted once; without offers the wave
+                // also lists it (its FP32 shadow is refreshed from the list),
+                // with offers it keeps only the count (the shadow is refreshed
+                // in bulk when a dense sweep is next, see wave_evaluate_kernel)
                 first = atomicExch(&a.wstamp[u], tag) != tag;
                 // a vertex that is not promising keeps its lowered g but is
                 // not expanded: its subtree and neighbours are left as they are
@@ -853,8 +874,12 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
             const unsigned nf = (unsigned)(run >> 32);
             unsigned base = 0;
             if (nf) {
-                base = atomicAdd(&c->n_dg, nf);
-                if (base + nf > a.dense_limit) *(volatile unsigned *)&c->dense_next = 1u;
+                if (a.push) {
+                    atomicAdd(&c->n_dg, nf);  // count only: no slot is needed, no wait
+                } else {
+                    base = atomicAdd(&c->n_dg, nf);
+                    if (base + nf > a.dense_limit) *(volatile unsigned *)&c->dense_next = 1u;
+                }
             }
             sh.scan[NW] = base;
             sh.seg[kWaveThreads] = (int)(run & 0xffffffffull);
@@ -863,7 +888,7 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
         {
             const unsigned long long ex = sh.scan[warp] + incl - xv;
             sh.seg[tid] = (int)(ex & 0xffffffffull);
-            if (first) a.dg[(unsigned)sh.scan[NW] + (unsigned)(ex >> 32)] = u;
+            if (first && !a.push) a.dg[(unsigned)sh.scan[NW] + (unsigned)(ex >> 32)] = u;
         }
         __syncthreads();
         const int total = sh.seg[kWaveThreads];
@@ -888,22 +913,45 @@ __device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT>
                     // c(u, w) of this entry; with parallel edges the cheaper one
                     // wins the minimum, as Improve chose it
                     gx[j] = sh.gu[l] + widen(en.w);
-                    if (offering && en.col != a.root) {
-                        offer(a.cand, en.col, gx[j]);
-                        ++offers;
-                    }
+                    if (offering && en.col != a.root) ++offers;
                 }
             }
+            // every load of this batch in flight at once: the parent of each
+            // neighbour and, for the offers, its current g
+            int32_t px[kWaveUnroll];
+            double gold[kWaveUnroll];
+#pragma unroll
+            for (int j = 0; j < kWaveUnroll; ++j) {
+                px[j] = -1;
+                gold[j] = 0.0;
+                if (own[j] >= 0) {
+                    if (children || offering) px[j] = __ldcg(&a.p[x[j]]);
+                    if (offering) gold[j] = ld_g_cg(&a.g[x[j]], gpol);
+                }
+            }
+            // then every atomic of the batch.  A child is lowered.  With offers,
+            // a neighbour w that is not a child is offered g(u) + c(u, w) and
+            // joins the next Improve list only if that beats its g now: g only
+            // falls within an Evaluate and cur(w) = g(p(w)) + c(p(w), w) <= g(w)
+            // once it ends, so an offer not below g(w) can never win (and a
+            // child's offer equals its own cost).  Without offers every
+            // neighbour is marked.
             unsigned childm = 0, markm = 0;
 #pragma unroll
             for (int j = 0; j < kWaveUnroll; ++j) {
                 if (own[j] >= 0) {
-                    if (children && __ldcg(&a.p[x[j]]) == sh.u[own[j]]) {
+                    const bool child = children && px[j] == sh.u[own[j]];
+                    if (child) {
                         const unsigned long long b = (unsigned long long)__double_as_longlong(gx[j]);
                         if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[x[j]]), b) > b)
                             childm |= 1u << j;
+                    } else if (offering) {
+                        if (x[j] != a.root && gx[j] < gold[j]) {
+                            offer(a.cand, x[j], gx[j]);
+                            if (atomicExch(&a.stamp[x[j]], epoch) != epoch) markm |= 1u << j;
+                        }
                     }
-                    if (marking && x[j] != a.root && __ldcg(&a.stamp[x[j]]) != epoch &&
+                    if (marking && !a.push && x[j] != a.root && __ldcg(&a.stamp[x[j]]) != epoch &&
                         atomicExch(&a.stamp[x[j]], epoch) != epoch)
                         markm |= 1u << j;
                 }
@@ -941,7 +989,6 @@ __device__ __forceinline__ void clear_iteration(DevCounters *c) {
     c->dj_bits = 0ull;
     c->n_dg = 0u;
     c->rounds = 0u;
-    c->bar_count = 0u;
     for (int r = 0; r < kMaxJumpRounds + 2; ++r) c->wl_count[r] = 0u;
 }
 
@@ -1022,6 +1069,7 @@ static __global__ void advance_kernel(DevCounters *c, cudaGraphConditionalHandle
 static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
                                             unsigned long long eps_bits) {
     clear_iteration(c);
+    c->bar_count = 0u;  // no kernel of the graph runs now (see grid_barrier)
     c->relax = 0ull;
     c->improved = 0ull;
     c->evaluated = 0ull;
@@ -1040,6 +1088,24 @@ static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
     c->bound_bits = c->goal_g != nullptr
                         ? *reinterpret_cast<const unsigned long long *>(c->goal_g)
                         : 0x7ff0000000000000ull;
+}
+
+// The FP32 shadow of g for every vertex, when a wave with offers left it out
+// of date (g32_stale) and the next Improve reads it: a dense sweep (dense) or
+// an Improve kernel without offers (always_if_stale).  Any grid.
+static __global__ void __launch_bounds__(kThreads)
+refresh_g32_kernel(DevCounters *c, int64_t n, const double *__restrict__ g,
+                   float *__restrict__ g32, int always_if_stale) {
+    if (__ldcg(&c->g32_stale) == 0u) return;
+    if (!always_if_stale && __ldcg(&c->dense) == 0u) return;
+    for (int64_t v = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; v < n;
+         v += (int64_t)gridDim.x * blockDim.x)
+        g32[v] = g32_of(g[v]);
+}
+
+// Reset the shadow's flag once refresh_g32_kernel has run (one thread).
+static __global__ void refresh_g32_done(DevCounters *c, int always_if_stale) {
+    if (always_if_stale || c->dense != 0u) c->g32_stale = 0u;
 }
 
 // Parents as reported through the ABI: the root marker becomes -1.

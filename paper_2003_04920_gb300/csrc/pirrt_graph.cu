@@ -258,6 +258,7 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->push = push;
     wa->cand = G->cand;
     wa->h = key.h;
+    wa->n = G->n;
     auto *aa = reinterpret_cast<AsyncArgs<CT> *>(G->hargs + kArgAsync);
     aa->rows = G->rows;
     aa->adj = adj;
@@ -775,8 +776,19 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     begin_exploit_kernel<<<1, 1, 0, G->stream>>>(
         G->ctr, (unsigned)std::min<int64_t>(max_iters, 0xffffffffll), eps_bits);
     CKL();
+    // waves with offers leave the FP32 shadow of g out of date until a dense
+    // sweep needs it; Improve kernels without offers and the barrier-free walk
+    // read or keep it all the time, so they get it refreshed first
+    {
+        const int always = (tile != 0 || async) ? 1 : 0;
+        refresh_g32_kernel<<<grid_for(G->n, kThreads, G->num_sms * 8), kThreads, 0, G->stream>>>(
+            G->ctr, G->n, G->g, G->g32, always);
+        CKL();
+        refresh_g32_done<<<1, 1, 0, G->stream>>>(G->ctr, always);
+        CKL();
+    }
     pirrt_profile &P = G->prof;
-    P.launches += 1;
+    P.launches += 3;
     pirrt_exploit_stats s{};
     bool graph_ran = false;
     if (use_graph) {

@@ -38,11 +38,19 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     const int tid = threadIdx.x;
     const unsigned long long gpol = policy_evict_last();
     unsigned long long recomputed = 0, offers = 0;
+    // With offers the wave keeps no changed list, only its size n_dg (each
+    // changed vertex counted once): after every level barrier each CTA reads it
+    // with the next level's size, and past the dense limit the marking stops
+    // and the next sweep is dense (whichever way this Evaluate ends).
+    const bool push = a.push != 0;
     unsigned t = 0;
     for (;;) {
         int64_t count =
             t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
+        const unsigned ndg = push ? *(volatile unsigned *)&c->n_dg : 0u;
         if (count == 0) break;
+        const bool over = push && ndg > a.dense_limit;
+        if (over && tid == 0) *(volatile unsigned *)&c->dense_next = 1u;
         if (t >= a.max_levels || count > a.list_cap) {
             // Stop: this level's vertices were lowered but not expanded.  Scan
             // their rows for the frontier and the offers only; pointer jumping
@@ -56,18 +64,19 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
             const int64_t per = (count + nblocks - 1) / nblocks;
             const int64_t lo = (int64_t)blockIdx.x * per;
             const int64_t hi = lo + per < count ? lo + per : count;
-            wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, false);
+            wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, false, over);
             grid_barrier(c, nblocks);
             break;
         }
         if (count <= (int64_t)a.tail_max) {
             // a thin level: CTA 0 walks on alone while the levels stay thin
             if (blockIdx.x == 0) {
+                bool over_t = over;
                 for (;;) {
                     if (tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
                     __syncthreads();
                     wave_level<CT>(a, sh, t, 0, count, tag, epoch, next, gpol, recomputed, offers,
-                                   true);
+                                   true, over_t);
                     ++t;
                     if (tid == 0) s_t = *(volatile unsigned *)&c->wave_cnt[t % 3];
                     __syncthreads();
@@ -76,6 +85,14 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
                     if (count == 0 || count > (int64_t)a.tail_max || count > a.list_cap ||
                         t >= a.max_levels)
                         break;
+                    if (push) {
+                        // n_dg holds this CTA's own additions (same thread)
+                        if (tid == 0) s_t = *(volatile unsigned *)&c->n_dg;
+                        __syncthreads();
+                        over_t = s_t > a.dense_limit;
+                        __syncthreads();
+                        if (over_t && tid == 0) *(volatile unsigned *)&c->dense_next = 1u;
+                    }
                 }
                 if (tid == 0) c->wave_t = t;
             }
@@ -87,15 +104,31 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
         const int64_t per = (count + nblocks - 1) / nblocks;
         const int64_t lo = (int64_t)blockIdx.x * per;
         const int64_t hi = lo + per < count ? lo + per : count;
-        wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, true);
+        wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, true, over);
         ++t;
         if (!grid_barrier(c, nblocks)) break;
     }
-    // the FP32 shadow of every changed vertex, from its final g
-    const unsigned n_dg = *(volatile unsigned *)&c->n_dg;
-    for (unsigned i = blockIdx.x * kWaveThreads + tid; i < n_dg; i += nblocks * kWaveThreads) {
-        const int32_t w = __ldcg(&a.dg[i]);
-        a.g32[w] = g32_of(__ldcg(&a.g[w]));
+    if (!push) {
+        // the FP32 shadow of every changed vertex, from its final g
+        const unsigned n_dg = *(volatile unsigned *)&c->n_dg;
+        for (unsigned i = blockIdx.x * kWaveThreads + tid; i < n_dg; i += nblocks * kWaveThreads) {
+            const int32_t w = __ldcg(&a.dg[i]);
+            a.g32[w] = g32_of(__ldcg(&a.g[w]));
+        }
+    } else if (*(volatile unsigned *)&c->wave_incomplete == 0u) {
+        // past the dense limit the next sweep is dense and reads the FP32
+        // shadow, so every vertex's shadow is refreshed now; otherwise it is
+        // left out of date and flagged (refresh_g32_kernel brings it up to
+        // date before any Improve that reads it)
+        const bool dense_next = *(volatile unsigned *)&c->n_dg > a.dense_limit;
+        if (blockIdx.x == 0 && tid == 0) {
+            if (dense_next) c->dense_next = 1u;
+            c->g32_stale = dense_next ? 0u : 1u;
+        }
+        if (dense_next)
+            for (int64_t v = (int64_t)blockIdx.x * kWaveThreads + tid; v < a.n;
+                 v += (int64_t)nblocks * kWaveThreads)
+                a.g32[v] = g32_of(__ldcg(&a.g[v]));
     }
     block_add(recomputed, &c->evaluated, sh.scan);
     block_add(offers, &c->offers, sh.scan);

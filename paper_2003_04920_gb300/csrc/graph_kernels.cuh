@@ -290,12 +290,18 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
             eb.w = w;
             adj[sa] = ea;
             adj[sb] = eb;
-            // the new edge offers each endpoint the other's candidate
+            // the new edge offers each endpoint the other's candidate; an
+            // endpoint joins the next Improve list only if that candidate beats
+            // its g (g >= cur, so a candidate not below g can never win; a new
+            // vertex has g = +inf and joins with its first finite neighbour)
             const double ga = g[a], gb = g[b];
-            if (b != root && ga < CUDART_INF) offer(cand, b, ga + widen(w));
-            if (a != root && gb < CUDART_INF) offer(cand, a, gb + widen(w));
-            pa = a != root && atomicExch(&stamp[a], epoch) != epoch;
-            pb = b != root && atomicExch(&stamp[b], epoch) != epoch;
+            const double va = gb + widen(w), vb = ga + widen(w);
+            const bool ua = a != root && gb < CUDART_INF && va < ga;
+            const bool ub = b != root && ga < CUDART_INF && vb < gb;
+            if (ub) offer(cand, b, vb);
+            if (ua) offer(cand, a, va);
+            pa = ua && atomicExch(&stamp[a], epoch) != epoch;
+            pb = ub && atomicExch(&stamp[b], epoch) != epoch;
         }
         __shared__ unsigned long long s_scan[kThreads / 32 + 2];
         unsigned ba, bb;
@@ -306,29 +312,25 @@ insert_scatter(int64_t n_edges, const int32_t *__restrict__ src, const int32_t *
     }
 }
 
-// Seed the new vertices: g = +inf (0 for the root), no parent, and put them
-// on the next Improve frontier.
+// Seed the new vertices: g = +inf (0 for the root), no parent, no offer.
+// They join the next Improve frontier through the offers of their new edges
+// (insert_scatter).
 template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_init_vertices(int64_t n_old, int64_t n_after, int32_t root, double *__restrict__ g,
                      float *__restrict__ g32, int32_t *__restrict__ p, CT *__restrict__ pc,
                      unsigned long long *__restrict__ cand, unsigned *__restrict__ stamp,
                      int32_t *__restrict__ list0, int32_t *__restrict__ list1, DevCounters *ctr) {
-    const unsigned epoch = ctr->epoch;
-    int32_t *active = (ctr->la & 1u) ? list1 : list0;
     const int64_t stride = (int64_t)gridDim.x * blockDim.x;
     for (int64_t base = n_old + (int64_t)blockIdx.x * blockDim.x; base < n_after; base += stride) {
         const int64_t v = base + threadIdx.x;
-        bool pred = false;
         if (v < n_after) {
             g[v] = (v == root) ? 0.0 : CUDART_INF;
             g32[v] = (v == root) ? 0.0f : __int_as_float(0x7f800000);
             p[v] = (v == root) ? kRootMark : -1;
             pc[v] = CT(0);
             cand[v] = kCandNone;
-            pred = v != root && atomicExch(&stamp[v], epoch) != epoch;
         }
-        warp_append(pred, (int32_t)v, active, &ctr->n_active);
     }
 }
 

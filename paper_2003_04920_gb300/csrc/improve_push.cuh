@@ -19,8 +19,13 @@
 
 namespace pirrt {
 
-// One thread per listed vertex decides; G lanes per deciding vertex scan.
-// Any grid of up to 512-thread blocks; every thread of the block calls it.
+// The list is split evenly over the CTAs.  One thread per listed vertex
+// decides; the deciding vertices of a chunk of up to blockDim.x listed
+// vertices are compacted in shared memory, then scanned by G lanes each,
+// blockDim.x / G vertices at a time, so that every CTA scans about the same
+// number of rows (most listed vertices decide: the offers that list them are
+// the ones that beat the vertex's g).  Any grid of up to 512-thread blocks;
+// every thread of the block calls it.
 template <typename CT, int G>
 __device__ void improve_push_body(const ImproveArgs<CT> &a) {
     DevCounters *c = a.ctr;
@@ -34,74 +39,83 @@ __device__ void improve_push_body(const ImproveArgs<CT> &a) {
     constexpr int kStageCap = 128;
     constexpr int kUnroll = 4;
     __shared__ int32_t s_sw[512 / 32][kStageCap];
+    __shared__ int32_t s_dv[512];     // deciding vertices of the chunk
+    __shared__ double s_cur[512];     // ... and their cur = g(p(v)) + c(p(v), v)
+    __shared__ unsigned s_nd;
     WarpStage<kStageCap> swq{s_sw[threadIdx.x >> 5], 0u};
     const int32_t *active = (c->la & 1u) ? a.list[1] : a.list[0];
     const int64_t count = (int64_t)c->n_active;
     const unsigned long long gpol = policy_evict_last();
-    const int lane = threadIdx.x & 31, grp = lane / G, gl = lane & (G - 1);
+    const int tid = threadIdx.x, lane = tid & 31;
+    const int gl = lane & (G - 1), grp = tid / G, ngrp = (int)blockDim.x / G;
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
-    const int64_t wid = tid0 >> 5, nwarps = nthreads >> 5;
     const double bound = goal_bound(c, a.h);
     unsigned long long relax = 0, improved = 0, djmax = 0;
 
-    for (int64_t base = wid * 32; base < count; base += nwarps * 32) {
+    const int64_t per = (count + gridDim.x - 1) / gridDim.x;
+    const int64_t lo = (int64_t)blockIdx.x * per;
+    const int64_t hi = lo + per < count ? lo + per : count;
+    for (int64_t base = lo; base < hi; base += blockDim.x) {
         // ---- one thread per listed vertex: take its offer, compare with cur
-        const int64_t i = base + lane;
-        int32_t v = -1;
-        double cur = CUDART_INF;
-        bool want = false;
-        if (i < count) {
-            v = __ldg(&active[i]);
+        if (tid == 0) s_nd = 0u;
+        __syncthreads();
+        const int64_t i = base + tid;
+        if (i < hi) {
+            const int32_t v = __ldg(&active[i]);
             if (v != a.root) {
                 const int32_t pv = a.p[v];
                 const unsigned long long cb = a.cand[v];
                 if (cb != kCandNone) a.cand[v] = kCandNone;
                 if (pv != kRootMark) {
+                    double cur = CUDART_INF;
                     if (pv >= 0) cur = ld_g(&a.g[pv], gpol) + widen(a.pc[v]);
                     // goal-directed: an offer that cannot make v promising is
                     // dropped (the row's best is no larger than any offer)
                     const double cv = __longlong_as_double((long long)cb);
-                    want = cb < kCandNone && cv < cur && promising(a.h, v, cv, bound);
+                    if (cb < kCandNone && cv < cur && promising(a.h, v, cv, bound)) {
+                        const unsigned k = atomicAdd(&s_nd, 1u);
+                        s_dv[k] = v;
+                        s_cur[k] = cur;
+                    }
                     improved += 1;
                 }
             }
         }
+        __syncthreads();
+        const int nd = (int)s_nd;
         // ---- deciding vertices: G lanes each scan the row exactly
-        unsigned todo = __ballot_sync(0xffffffffu, want);
-        while (todo) {
-            unsigned t = todo;  // this group's vertex: the grp-th deciding lane
-            for (int k = 0; k < grp && t; ++k) t &= t - 1u;
-            const bool mine = t != 0u;
-            const int s_lane = mine ? __ffs(t) - 1 : 0;
-            const int32_t sv = __shfl_sync(0xffffffffu, v, s_lane);
-            const double scur = __shfl_sync(0xffffffffu, cur, s_lane);
-            // drop the vertices taken in this round
-            for (int k = 0; k < 32 / G && todo; ++k) todo &= todo - 1u;
+        for (int r0 = 0; r0 < nd; r0 += ngrp) {
+            const int k = r0 + grp;
+            const bool mine = k < nd;
+            int32_t sv = 0;
+            double scur = 0.0;
             unsigned long long bv = kCandNone + 1ull;
             int32_t bid = INT_MAX;
             CT bw = CT(0);
             int64_t b = 0, e = 0;
             if (mine) {
+                sv = s_dv[k];
+                scur = s_cur[k];
                 row_range(a.rows, sv, b, e);
                 for (int64_t i0 = b + gl; i0 < e; i0 += (int64_t)G * kUnroll) {
                     Entry<CT> en[kUnroll];
 #pragma unroll
-                    for (int k = 0; k < kUnroll; ++k)
-                        if (i0 + k * G < e) en[k] = ld_stream(&a.adj[i0 + k * G]);
+                    for (int q = 0; q < kUnroll; ++q)
+                        if (i0 + q * G < e) en[q] = ld_stream(&a.adj[i0 + q * G]);
                     double gv[kUnroll];
 #pragma unroll
-                    for (int k = 0; k < kUnroll; ++k)
-                        gv[k] = (i0 + k * G < e) ? ld_g(&a.g[en[k].col], gpol) : CUDART_INF;
+                    for (int q = 0; q < kUnroll; ++q)
+                        gv[q] = (i0 + q * G < e) ? ld_g(&a.g[en[q].col], gpol) : CUDART_INF;
 #pragma unroll
-                    for (int k = 0; k < kUnroll; ++k) {
-                        if (i0 + k * G < e) {
+                    for (int q = 0; q < kUnroll; ++q) {
+                        if (i0 + q * G < e) {
                             const unsigned long long vb =
-                                (unsigned long long)__double_as_longlong(gv[k] + widen(en[k].w));
-                            if (vb < bv || (vb == bv && (en[k].col < bid ||
-                                                         (en[k].col == bid && en[k].w < bw)))) {
+                                (unsigned long long)__double_as_longlong(gv[q] + widen(en[q].w));
+                            if (vb < bv || (vb == bv && (en[q].col < bid ||
+                                                         (en[q].col == bid && en[q].w < bw)))) {
                                 bv = vb;
-                                bid = en[k].col;
-                                bw = en[k].w;
+                                bid = en[q].col;
+                                bw = en[q].w;
                             }
                         }
                     }
@@ -135,6 +149,7 @@ __device__ void improve_push_body(const ImproveArgs<CT> &a) {
             }
             swq.push(sw, sv, a.switched, &c->n_switched);
         }
+        __syncthreads();  // s_dv / s_cur / s_nd are rewritten by the next chunk
     }
     // one atomic per block and counter (thousands of warps end together)
     __shared__ unsigned s_fl[512 / 32 + 1];

@@ -495,7 +495,7 @@ def dijkstra_baseline(rm) -> dict:
     t1 = time.perf_counter()
     A.dijkstra(0)
     t2 = time.perf_counter()
-    entries = A.entries()
+    entries = A.entries
     A.close()
     return {"kind": "oracle O2 (FP64 binary-heap Dijkstra)", "cores": 1,
             "ms": round(1e3 * (t2 - t1), 1), "csr_build_ms": round(1e3 * (t1 - t0), 1),

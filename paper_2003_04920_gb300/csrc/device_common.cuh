@@ -122,6 +122,8 @@ struct DevCounters {
     alignas(128) unsigned bar_count;   // grid barrier: arrivals (low bits) and phase (top bit)
     alignas(128) unsigned wave_ticket;  // CTAs done with a wave that ends without a barrier
     alignas(128) unsigned wl_count[kMaxJumpRounds + 2];  // pointer-jumping work-list sizes per round
+    alignas(128) unsigned n_touched;   // insertion: old rows gaining entries (list length)
+    alignas(128) unsigned long long pool_cursor;  // insertion: pool room taken by the block
     alignas(128) unsigned status;      // kStatus* bits
     unsigned long long switches;  // parent switches (whole exploit)
     unsigned long long insert_copied;  // CSR entries moved by insertions (graph lifetime)

@@ -38,20 +38,38 @@ template <typename CT>
 __global__ void __launch_bounds__(kThreads)
 insert_validate_count(int64_t n_edges, const int32_t *__restrict__ src,
                       const int32_t *__restrict__ dst, const CT *__restrict__ cost,
-                      int64_t n_after, int32_t *__restrict__ deg, DevCounters *ctr) {
-    for (int64_t e = blockIdx.x * (int64_t)blockDim.x + threadIdx.x; e < n_edges;
-         e += (int64_t)gridDim.x * blockDim.x) {
-        const int32_t a = src[e], b = dst[e];
-        const double c = (double)cost[e];
-        const bool ok = a >= 0 && b >= 0 && a < n_after && b < n_after && a != b &&
-                        c > 0.0 && c <= DBL_MAX;  // rejects NaN, +inf, <= 0
-        if (!ok) {
-            atomicOr(&ctr->status, kStatusBadInput);
-            continue;
+                      int64_t n_old, int64_t n_after, int32_t *__restrict__ deg,
+                      int32_t *__restrict__ touched, DevCounters *ctr) {
+    // an old row gaining its first new entry joins the touched list (the new
+    // rows [n_old, n_after) are handled as a range)
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < n_edges;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t e = base + threadIdx.x;
+        bool ta = false, tb = false;
+        int32_t a = 0, b = 0;
+        if (e < n_edges) {
+            a = src[e];
+            b = dst[e];
+            const double c = (double)cost[e];
+            const bool ok = a >= 0 && b >= 0 && a < n_after && b < n_after && a != b &&
+                            c > 0.0 && c <= DBL_MAX;  // rejects NaN, +inf, <= 0
+            if (!ok) {
+                atomicOr(&ctr->status, kStatusBadInput);
+            } else {
+                ta = atomicAdd(&deg[a], 1) == 0 && a < n_old;
+                tb = atomicAdd(&deg[b], 1) == 0 && b < n_old;
+            }
         }
-        atomicAdd(&deg[a], 1);
-        atomicAdd(&deg[b], 1);
+        warp_append(ta, a, touched, &ctr->n_touched);
+        warp_append(tb, b, touched, &ctr->n_touched);
     }
+}
+
+// Room a moving row reserves: 1.5x its new length + 4 (a few moves over a
+// row's life); a repacked row gets 1.25x + 2, so a repack always fits a pool
+// of 2 x (directed entries) + 4 x (vertices).
+__device__ __forceinline__ int32_t row_room(int32_t need, bool repack) {
+    return repack ? need + (need >> 2) + 2 : need + (need >> 1) + 4;
 }
 
 // Exclusive scan, first pass: one partial sum per tile of kScanTile entries.
@@ -138,18 +156,111 @@ scan_tile_apply(const int32_t *__restrict__ deg, int64_t len,
     }
 }
 
+// Start of an insertion: empty touched list, no room taken, no error.
+static __global__ void insert_begin_kernel(DevCounters *c) {
+    c->n_touched = 0u;
+    c->pool_cursor = 0ull;
+    c->status = 0u;
+}
+
+// Item k of the rows an insertion changes: the touched old rows, then the new
+// rows [n_old, n_after).
+__device__ __forceinline__ int64_t changed_row(int64_t k, int64_t nt, const int32_t *touched,
+                                               int64_t n_old) {
+    return k < nt ? (int64_t)touched[k] : n_old + (k - nt);
+}
+
+// Plan without a scan: a changed row that would overflow (every new row with
+// entries) takes room at the end of the pool from a cursor, one atomic per
+// block; pool offsets (relative to the cursor's base) go to off[v].  Rows
+// keep their relative order within a block only, which nothing relies on.
+static __global__ void __launch_bounds__(kThreads)
+insert_plan_list(int64_t n_old, int64_t n_after, const int32_t *__restrict__ touched,
+                 const RowExt *__restrict__ rows, const int32_t *__restrict__ deg,
+                 int32_t *__restrict__ alloc, int64_t *__restrict__ off, DevCounters *ctr) {
+    const int64_t nt = (int64_t)__ldcg(&ctr->n_touched);
+    const int64_t total = nt + (n_after - n_old);
+    __shared__ long long s_base;
+    for (int64_t base = blockIdx.x * (int64_t)blockDim.x; base < total;
+         base += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t k = base + threadIdx.x;
+        int32_t a = 0;
+        int64_t v = -1;
+        if (k < total) {
+            v = changed_row(k, nt, touched, n_old);
+            const int32_t len = v < n_old ? rows[v].len : 0;
+            const int32_t cap = v < n_old ? rows[v].cap : 0;
+            const int32_t need = len + deg[v];
+            if (need > cap) a = row_room(need, false);
+            alloc[v] = a;
+        }
+        long long tot;
+        const long long ex = block_exclusive_scan(a, &tot);
+        if (threadIdx.x == 0)
+            s_base = tot ? (long long)atomicAdd(&ctr->pool_cursor, (unsigned long long)tot) : 0;
+        __syncthreads();
+        if (a > 0) off[v] = s_base + ex;
+        __syncthreads();
+    }
+}
+
+// Move the changed rows that took new room (their old entries first) to pool
+// offset base + off[v], and set every changed row's extent to its length
+// after the block.  One warp per 32 changed rows.
+template <typename CT>
+__global__ void __launch_bounds__(kThreads)
+insert_move_list(int64_t n_old, int64_t n_after, const int32_t *__restrict__ touched,
+                 RowExt *__restrict__ rows, const int32_t *__restrict__ deg,
+                 const int32_t *__restrict__ alloc, const int64_t *__restrict__ off,
+                 long long base, Entry<CT> *__restrict__ pool, DevCounters *ctr) {
+    const int lane = threadIdx.x & 31;
+    const int64_t nt = (int64_t)__ldcg(&ctr->n_touched);
+    const int64_t total = nt + (n_after - n_old);
+    const int64_t warps = (int64_t)gridDim.x * (blockDim.x >> 5);
+    unsigned long long copied = 0;
+    for (int64_t w0 = ((int64_t)blockIdx.x * (blockDim.x >> 5) + (threadIdx.x >> 5)) * 32;
+         w0 < total; w0 += warps * 32) {
+        const int64_t k = w0 + lane;
+        long long ob = 0, nb = 0;
+        int32_t len = 0;
+        bool move = false;
+        if (k < total) {
+            const int64_t v = changed_row(k, nt, touched, n_old);
+            RowExt r{0, 0, 0};
+            if (v < n_old) r = rows[v];
+            const int32_t a = alloc[v];
+            len = r.len;
+            ob = r.beg;
+            RowExt nr = r;
+            nr.len = r.len + deg[v];
+            if (a > 0) {
+                nb = base + off[v];
+                nr.beg = nb;
+                nr.cap = a;
+                move = len > 0;
+            }
+            rows[v] = nr;
+        }
+        unsigned todo = __ballot_sync(0xffffffffu, move);
+        while (todo) {
+            const int l = __ffs(todo) - 1;
+            todo &= todo - 1u;
+            const long long sb = __shfl_sync(0xffffffffu, ob, l);
+            const long long db = __shfl_sync(0xffffffffu, nb, l);
+            const int32_t n = __shfl_sync(0xffffffffu, len, l);
+            for (int32_t q = lane; q < n; q += 32) pool[db + q] = ld_stream(&pool[sb + q]);
+            copied += (unsigned long long)n;
+        }
+    }
+    if (lane == 0 && copied) atomicAdd(&ctr->insert_copied, copied);
+}
+
 // Slack CSR.  Every row owns adj[beg, beg + cap) of a pool and fills it from
 // the front; a block's new entries go to the row tails.  A row that would
 // overflow moves to fresh space at the end of the pool with room to grow, so
 // an insertion copies only the rows that moved, not the whole graph.  When
 // the pool is used up, every row is repacked into a second pool.
 
-// Room a moving row reserves: 1.5x its new length + 4 (a few moves over a
-// row's life); a repacked row gets 1.25x + 2, so a repack always fits a pool
-// of 2 x (directed entries) + 4 x (vertices).
-__device__ __forceinline__ int32_t row_room(int32_t need, bool repack) {
-    return repack ? need + (need >> 2) + 2 : need + (need >> 1) + 4;
-}
 
 // Plan: the pool space each row must take (0: stays where it is).
 // alloc[n_after] = 0 closes the scan.

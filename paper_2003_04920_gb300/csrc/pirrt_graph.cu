@@ -58,6 +58,7 @@ struct pirrt_graph {
     int64_t pool_cap = 0;          // entries per pool
     int64_t pool_used = 0;         // entries taken in the live pool (rows, slack, moved-out)
     int32_t *ralloc = nullptr;     // insertion: pool space per row
+    int32_t *touched = nullptr;    // insertion: old rows gaining entries
     int64_t *roff = nullptr;       // insertion / export: exclusive scan
     unsigned long long copied_seen = 0;
     int64_t *hx = nullptr;         // pinned host scalars read back by insertion
@@ -93,6 +94,8 @@ struct pirrt_graph {
     DevCounters *ctr_host = nullptr;  // pinned mirror
     unsigned char *dargs = nullptr;   // device copies of the kernel argument structs
     unsigned char *hargs = nullptr;   // pinned host staging of the same
+    cudaEvent_t args_ev = nullptr;    // the last copy of the staging was consumed
+    int args_pending = 0;
     struct ArgsKey {
         int64_t n = -1;
         int cur = -1;
@@ -194,6 +197,9 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     key.tail_max = tail_max;
     key.h = G->goal >= 0 ? G->h : nullptr;
     if (key == G->args_key) return PIRRT_OK;
+    // the pinned staging is rewritten only after its last copy has been
+    // consumed (long done by now: every exploit ends with a synchronisation)
+    if (G->args_pending) CK(cudaEventSynchronize(G->args_ev));
     std::memset(G->hargs, 0, kArgBytes);
     const Entry<CT> *adj = static_cast<const Entry<CT> *>(G->adj[G->cur]);
     auto *ia = reinterpret_cast<ImproveArgs<CT> *>(G->hargs + kArgImprove);
@@ -299,8 +305,8 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
         ma->cand = G->cand;
     }
     CK(cudaMemcpyAsync(G->dargs, G->hargs, kArgBytes, cudaMemcpyHostToDevice, G->stream));
-    // the pinned staging is rewritten only after this copy has been consumed
-    CK(cudaStreamSynchronize(G->stream));
+    CK(cudaEventRecord(G->args_ev, G->stream));
+    G->args_pending = 1;
     G->args_key = key;
     return PIRRT_OK;
 }
@@ -601,25 +607,33 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
     const int max_blocks = G->num_sms * 32;
     const bool prof = G->profiling != 0;
     if (prof) CK(cudaEventRecord(G->pev[6], G->stream));
-    // 1. validate and count new entries per row (into scratch only)
-    CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(n_after + 1), G->stream));
-    CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
+    // 1. validate and count new entries per row (deg is all zero between
+    //    insertions: the scatter below takes every count back); the old rows
+    //    gaining entries form the touched list
+    insert_begin_kernel<<<1, 1, 0, G->stream>>>(G->ctr);
+    CKL();
     if (n_edges > 0) {
         insert_validate_count<CT><<<grid_for(n_edges, kThreads, max_blocks), kThreads, 0, G->stream>>>(
-            n_edges, src, dst, cost, n_after, G->deg, G->ctr);
+            n_edges, src, dst, cost, n_old, n_after, G->deg, G->touched, G->ctr);
         CKL();
     }
-    // 2. plan the pool space of the rows that outgrow their room (scan); one
-    //    host read of the validation status and the space needed
-    pirrt_status rc = insert_plan_scan(G, n_old, n_after, 0);
-    if (rc) return rc;
+    // 2. room at the end of the pool for the changed rows that would overflow,
+    //    from a cursor (no scan over every row); one host read of the
+    //    validation status and the room taken
+    const int64_t changed_max = std::min<int64_t>(2 * n_edges, n_old) + n_new;
+    if (changed_max > 0) {
+        insert_plan_list<<<grid_for(changed_max, kThreads, max_blocks), kThreads, 0, G->stream>>>(
+            n_old, n_after, G->touched, G->rows, G->deg, G->ralloc, G->roff, G->ctr);
+        CKL();
+    }
     CK(cudaMemcpyAsync(&G->ctr_host->status, &G->ctr->status, sizeof(unsigned),
                        cudaMemcpyDeviceToHost, G->stream));
-    CK(cudaMemcpyAsync(G->hx, &G->roff[n_after], sizeof(int64_t), cudaMemcpyDeviceToHost,
+    CK(cudaMemcpyAsync(G->hx, &G->ctr->pool_cursor, sizeof(int64_t), cudaMemcpyDeviceToHost,
                        G->stream));
     CK(cudaStreamSynchronize(G->stream));
     if (G->ctr_host->status) {
         CK(cudaMemsetAsync(&G->ctr->status, 0, sizeof(unsigned), G->stream));
+        CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(n_after + 1), G->stream));
         return fail(G, PIRRT_ERR_BAD_INPUT,
                     "insert_batch: edge with an id outside [0, %lld), a self loop, or a cost "
                     "that is not finite and > 0",
@@ -627,16 +641,19 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
     }
     const int64_t need = G->hx[0];
     // 3. move those rows to the end of the pool, or repack every row into the
-    //    other pool when this one is used up; set every row's new length
-    const int move_blocks = grid_for((n_after + 31) / 32 * 32, kThreads, max_blocks);
+    //    other pool when this one is used up; set every changed row's new length
     if (G->pool_used + need <= G->pool_cap) {
-        Entry<CT> *pool = static_cast<Entry<CT> *>(G->adj[G->cur]);
-        insert_move_rows<CT><<<move_blocks, kThreads, 0, G->stream>>>(
-            n_old, n_after, G->rows, G->deg, G->ralloc, G->roff, (long long)G->pool_used, pool,
-            pool, G->ctr, 0);
-        CKL();
+        if (changed_max > 0) {
+            Entry<CT> *pool = static_cast<Entry<CT> *>(G->adj[G->cur]);
+            insert_move_list<CT><<<grid_for((changed_max + 31) / 32 * 32, kThreads, max_blocks),
+                                   kThreads, 0, G->stream>>>(
+                n_old, n_after, G->touched, G->rows, G->deg, G->ralloc, G->roff,
+                (long long)G->pool_used, pool, G->ctr);
+            CKL();
+        }
         G->pool_used += need;
     } else {
+        const int move_blocks = grid_for((n_after + 31) / 32 * 32, kThreads, max_blocks);
         const int nxt = G->cur ^ 1;
         if (!G->adj[nxt]) {
             const cudaError_t e =
@@ -644,17 +661,20 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
             if (e != cudaSuccess) {
                 cudaGetLastError();
                 G->adj[nxt] = nullptr;
+                CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(n_after + 1), G->stream));
                 return fail(G, PIRRT_ERR_OOM, "insert_batch: no memory for a second CSR pool");
             }
         }
-        if ((rc = insert_plan_scan(G, n_old, n_after, 1))) return rc;
+        if (const pirrt_status rc = insert_plan_scan(G, n_old, n_after, 1)) return rc;
         CK(cudaMemcpyAsync(G->hx, &G->roff[n_after], sizeof(int64_t), cudaMemcpyDeviceToHost,
                            G->stream));
         CK(cudaStreamSynchronize(G->stream));
         const int64_t total = G->hx[0];
-        if (total > G->pool_cap)
+        if (total > G->pool_cap) {
+            CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(n_after + 1), G->stream));
             return fail(G, PIRRT_ERR_CAPACITY, "insert_batch: repacked CSR needs %lld entries",
                         (long long)total);
+        }
         insert_move_rows<CT><<<move_blocks, kThreads, 0, G->stream>>>(
             n_old, n_after, G->rows, G->deg, G->ralloc, G->roff, 0ll,
             static_cast<const Entry<CT> *>(G->adj[G->cur]), static_cast<Entry<CT> *>(G->adj[nxt]),
@@ -679,7 +699,7 @@ pirrt_status insert_impl(pirrt_graph *G, int64_t n_new, int64_t n_edges, const i
             G->list[0], G->list[1], G->g, G->cand, G->ctr);
         CKL();
     }
-    G->prof.launches += 5 + (n_edges > 0 ? 2 : 0) + (n_new > 0 ? 1 : 0);
+    G->prof.launches += 1 + (n_edges > 0 ? 2 : 0) + (changed_max > 0 ? 2 : 0) + (n_new > 0 ? 1 : 0);
     G->prof.insert_calls += 1;
     G->prof.insert_new_entries += 2 * n_edges;
     if (prof) {
@@ -994,7 +1014,7 @@ void free_all(pirrt_graph *G) {
     if (G->pre_done) cudaEventDestroy(G->pre_done);
     if (G->pre_free) cudaEventDestroy(G->pre_free);
     if (G->hargs) cudaFreeHost(G->hargs);
-    void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
+    void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->touched, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
                     G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
                     G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage, G->h};
@@ -1007,6 +1027,7 @@ void free_all(pirrt_graph *G) {
     for (cudaEvent_t e : G->pev)
         if (e) cudaEventDestroy(e);
     if (G->it_start) cudaEventDestroy(G->it_start);
+    if (G->args_ev) cudaEventDestroy(G->args_ev);
 }
 
 // Snapshot of the mutable exploit state, for the autotuner's repeated trials.
@@ -1165,6 +1186,7 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     } while (0)
     ALLOC(G->rows, sizeof(RowExt) * nv);
     ALLOC(G->ralloc, sizeof(int32_t) * (nv + 1));
+    ALLOC(G->touched, sizeof(int32_t) * nv);
     ALLOC(G->roff, sizeof(int64_t) * (nv + 1));
     // A pool holds every row with room to grow plus the space rows moved out
     // of; a repack (1.25 x length + 2 per row) always fits.  The second pool
@@ -1215,6 +1237,8 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     for (cudaEvent_t &e : G->pev)
         if (cudaEventCreate(&e) != cudaSuccess) return bail(PIRRT_ERR_CUDA);
     if (cudaEventCreate(&G->it_start) != cudaSuccess) return bail(PIRRT_ERR_CUDA);
+    if (cudaEventCreateWithFlags(&G->args_ev, cudaEventDisableTiming) != cudaSuccess)
+        return bail(PIRRT_ERR_CUDA);
     int occ = 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, evaluate_kernel<float>, kThreads, 0) !=
         cudaSuccess)
@@ -1269,6 +1293,8 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->swstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->ctr, 0, sizeof(DevCounters), G->stream));
+    // insertions count into deg and leave it all zero
+    CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(G->cap_n + 1), G->stream));
     // stamps start at 0, so the first list uses stamp value 1
     const unsigned one = 1u;
     CK(cudaMemcpyAsync(&G->ctr->epoch, &one, sizeof(unsigned), cudaMemcpyHostToDevice, G->stream));

@@ -23,6 +23,7 @@ from __future__ import annotations
 
 import argparse
 import json
+import math
 import os
 import statistics
 import subprocess
@@ -734,10 +735,19 @@ def run_sweep(args) -> None:
     s_list = [int(x) for x in args.sweep_s.split(",")]
     legs = set(args.sweep_legs.split(","))
     rows = []
+    clocks = None
     for n in ns:
         rm, goal, h = sweep_case(n, args.trial, args.goal != "none")
         ss = [S for S in s_list if S <= n]
-        gpu = sweep_gpu(rm, goal, h, ss, max(1, args.steps)) if "gpu" in legs else {}
+        gpu = {}
+        if "gpu" in legs:
+            with ClockSampler(0) as clk:
+                gpu = sweep_gpu(rm, goal, h, ss, max(1, args.steps))
+            c = clk.summary()
+            clocks = c if clocks is None else {
+                "sm_mhz": c["sm_mhz"], "sm_max_mhz": c["sm_max_mhz"],
+                "reasons": sorted(set(clocks["reasons"]) | set(c["reasons"])),
+                "samples": clocks["samples"] + c["samples"]}
         cpu = sweep_oracle(rm, goal, h, ss, args.cpu_seconds) if "oracle" in legs else {}
         for S in ss:
             rows.append({"n": n, "S": S, "gpu": gpu.get(S), "oracle": cpu.get(S)})
@@ -749,8 +759,119 @@ def run_sweep(args) -> None:
             "goal": "x_goal = vertex 1, h = 0.99 x Euclidean distance"
                     if args.goal != "none" else None,
             "oracle": {"kind": "oracle", "cores": 1, "budget_s": args.cpu_seconds,
-                       "host": os.uname().machine},
+                       "host": os.uname().machine, "host_cores": os.cpu_count()},
+            "gpu_repeats": max(1, args.steps) if "gpu" in legs else 0,
+            "gpu_timing": "median of the repeats after one warm-up run, wall time from the "
+                          "first insertion to the last exploit's statistics",
+            "clocks": clocks,
             "rows": rows}
+    print(json.dumps(line), flush=True)
+
+
+def run_explore(args) -> None:
+    """Exploration overlapped with exploitation (the asynchronous form the
+    paper leaves to future work, Sec. VII) on the 6-D workload's scene law:
+    every block's Extend step -- its samples' nearest predecessors, collision
+    checks, edge costs -- built on the GPU (workloads.gpu.Explorer), then
+    inserted and exploited to a stable policy.  Two passes over the same
+    roadmap: one stream doing exploration then exploitation block after block,
+    and two streams, the exploration of block b + 1 running while block b is
+    exploited (double-buffered edge blocks, events between the streams)."""
+    import torch
+
+    import paper_2003_04920_gb300 as P
+    from paper_2003_04920_gb300.workloads import gpu as GG
+
+    torch.cuda.set_device(0)
+    P.load_library()
+    GG.load()
+    n = args.n or 4_000_000
+    S = args.block or 50_000
+    k = 30
+    seed = 3 * 1000 + args.trial
+    scene = W._draw_scene(np.random.default_rng(seed), 6, -math.pi, math.pi, 64, 0.3, 0.8, [])
+    lo_pri, hi_pri = torch.cuda.Stream.priority_range() if hasattr(torch.cuda.Stream, "priority_range") \
+        else (0, -1)
+    sx = torch.cuda.Stream(priority=hi_pri)   # exploitation
+    se = torch.cuda.Stream(priority=lo_pri)   # exploration
+    X = GG.Explorer(scene, n, k, seed, S, stream=se.cuda_stream)
+    G = P.Graph(n, n * k, 0, np.float32, stream=sx.cuda_stream)
+    blocks = [(v0, min(n, v0 + S)) for v0 in range(0, n, S)]
+
+    def sequential():
+        G.reset()
+        it = 0
+        for b, (v0, v1) in enumerate(blocks):
+            u, v, c, cnt = X.extend(v0, v1, b & 1, stream=sx.cuda_stream)
+            sx.synchronize()
+            m = int(cnt.item())
+            G.insert_batch(v1 - v0, u[:m], v[:m], c[:m])
+            it += G.exploit()["iterations"]
+        return it
+
+    def overlapped():
+        G.reset()
+        it = 0
+        ready = [torch.cuda.Event(), torch.cuda.Event()]
+        freed = [torch.cuda.Event(), torch.cuda.Event()]
+        nxt = X.extend(blocks[0][0], blocks[0][1], 0, stream=se.cuda_stream)
+        ready[0].record(se)
+        for b, (v0, v1) in enumerate(blocks):
+            u, v, c, cnt = nxt
+            ready[b & 1].synchronize()  # the block's edge count is on the host
+            m = int(cnt.item())
+            sx.wait_event(ready[b & 1])
+            G.insert_batch(v1 - v0, u[:m], v[:m], c[:m])
+            freed[b & 1].record(sx)
+            if b + 1 < len(blocks):
+                # the next block's Extend on its own stream, into the other buffer
+                # (free once the insertion of block b - 1 has read it)
+                if b >= 1:
+                    se.wait_event(freed[(b + 1) & 1])
+                nxt = X.extend(blocks[b + 1][0], blocks[b + 1][1], (b + 1) & 1,
+                               stream=se.cuda_stream)
+                ready[(b + 1) & 1].record(se)
+            it += G.exploit()["iterations"]
+        return it
+
+    def explore_only():
+        for b, (v0, v1) in enumerate(blocks):
+            X.extend(v0, v1, b & 1, stream=se.cuda_stream)
+        se.synchronize()
+
+    def timed(fn, reps):
+        ts, out = [], None
+        for _ in range(reps):
+            torch.cuda.synchronize()
+            t0 = time.perf_counter()
+            out = fn()
+            torch.cuda.synchronize()
+            ts.append(1e3 * (time.perf_counter() - t0))
+        return statistics.median(ts), out
+
+    for _ in range(max(1, args.warmup)):
+        sequential()
+        overlapped()
+    reps = max(1, args.steps)
+    with ClockSampler(0) as clk:
+        t_exp, _ = timed(explore_only, reps)
+        t_seq, it_seq = timed(sequential, reps)
+        t_ovl, it_ovl = timed(overlapped, reps)
+    g_ovl = G.get_costs()
+    sequential()
+    same = bool(np.array_equal(G.get_costs(), g_ovl))
+    G.close()
+    X.close()
+    line = {"experiment": "exploration overlapped with exploitation (Sec. VII)",
+            "workload": f"6-D [-pi,pi]^6, 64 hyperspheres r~U[0.3,0.8], N={n}, each vertex joined "
+                        f"to its {k} nearest predecessors, 16-point edge check, FP32 costs, "
+                        f"blocks of {S}, Extend on the GPU",
+            "unit": "ms per step (all blocks: Extend, insertion, exploitation to a stable policy)",
+            "repeats": reps, "timing": "median wall time, host clock, device synchronised",
+            "explore_only_ms": round(t_exp, 2), "sequential_ms": round(t_seq, 2),
+            "overlapped_ms": round(t_ovl, 2), "saved_ms": round(t_seq - t_ovl, 2),
+            "iterations": {"sequential": it_seq, "overlapped": it_ovl},
+            "same_costs": same, "clocks": clk.summary()}
     print(json.dumps(line), flush=True)
 
 
@@ -795,7 +916,8 @@ def main():
     ap.add_argument("--steps", type=int, default=3)
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--impl", choices=("ours", "reference"), default="ours")
-    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "sweep"], default="c3")
+    ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "sweep", "explore"],
+                    default="c3")
     ap.add_argument("--graphs", type=int, default=512, help="members of the batched workload")
     ap.add_argument("--n", type=int, default=None, help="override the vertex count")
     ap.add_argument("--block", type=int, default=None, help="override the block size S")
@@ -838,6 +960,8 @@ def main():
         run_reference(args)
     elif args.workload == "c4":
         run_batch(args)
+    elif args.workload == "explore":
+        run_explore(args)
     else:
         run_ours(args)
 

@@ -56,6 +56,19 @@ def load():
     lib.rgg_sample.argtypes = [i32, f64, f64, i32, vp, vp, ctypes.c_uint64, i64, vp, vp, vp]
     lib.rgg_knn.restype = ctypes.c_int
     lib.rgg_knn.argtypes = [i32, f64, f64, i64, vp, i32, f64, vp, vp]
+    lib.rgg_explore_create.restype = ctypes.c_int
+    lib.rgg_explore_create.argtypes = [i32, f64, f64, i32, vp, vp, ctypes.c_uint64, i64, i32, i32,
+                                       i32, i32, i64, vp, ctypes.POINTER(vp)]
+    lib.rgg_explore_block.restype = ctypes.c_int
+    lib.rgg_explore_block.argtypes = [vp, i64, i64, vp, vp, vp, vp, vp]
+    lib.rgg_explore_points.restype = vp
+    lib.rgg_explore_points.argtypes = [vp]
+    lib.rgg_explore_size.restype = i64
+    lib.rgg_explore_size.argtypes = [vp]
+    lib.rgg_explore_copy_points.restype = ctypes.c_int
+    lib.rgg_explore_copy_points.argtypes = [vp, vp, vp]
+    lib.rgg_explore_destroy.restype = None
+    lib.rgg_explore_destroy.argtypes = [vp]
     lib.rgg_edges.restype = ctypes.c_int
     lib.rgg_edges.argtypes = [i32, i64, vp, i32, vp, i32, vp, vp, i32, i32, i32, vp, vp, vp, vp,
                               i64, vp, vp]
@@ -204,3 +217,62 @@ def roadmap_c3_gpu(trial: int = 0, n: int = 4_000_000, block: int = 50_000) -> D
     r ~ U[0.3, 0.8], k = 30, 16 points per segment, FP32 costs, blocks of 5e4
     (same scene law and seed as the host generator's; Philox samples)."""
     return roadmap_nd("c3-gpu", 3 * 1000 + trial, n, 6, 64, 0.3, 0.8, 30, block)
+
+
+class Explorer:
+    """Incremental exploration, one Batched-Extension block at a time (the
+    Extend step of RRT#, Alg. 3): vertex i is joined to its k nearest
+    predecessors by collision-free edges.  ``extend(v0, v1, slot, stream)``
+    enqueues the block's edge construction on `stream` into one of two
+    device buffers (`slot` 0 or 1) and returns (u, v, cost, count), count being
+    a page-locked host tensor filled when the stream gets there: the work of
+    the next block can run on its own stream while the current one is
+    exploited (Sec. VII).  The graph does not depend on the block size."""
+
+    def __init__(self, scene: Scene, n: int, k: int, seed: int, max_block: int,
+                 exact_segment: bool = False, n_check: int = 16, cost_dtype=np.float32,
+                 stream=None):
+        import torch
+        self._lib = load()
+        self.scene, self.n, self.k = scene, int(n), int(k)
+        self.cost_dtype = np.dtype(cost_dtype)
+        c, r = _scene_dev(scene)
+        h = ctypes.c_void_p()
+        st = stream if stream is not None else _stream()
+        _check("rgg_explore_create", self._lib.rgg_explore_create(
+            scene.dim, float(scene.lo), float(scene.hi), len(scene.radii), c.data_ptr(),
+            r.data_ptr(), int(seed) & 0xFFFFFFFFFFFFFFFF, self.n, self.k,
+            0 if exact_segment else 1, int(n_check), 1 if self.cost_dtype == np.float64 else 0,
+            int(max_block), st, ctypes.byref(h)))
+        self._h = h
+        torch.cuda.synchronize()
+        tdt = torch.float64 if self.cost_dtype == np.float64 else torch.float32
+        cap = int(max_block) * self.k
+        self.bufs = [(torch.empty(cap, dtype=torch.int32, device="cuda"),
+                      torch.empty(cap, dtype=torch.int32, device="cuda"),
+                      torch.empty(cap, dtype=tdt, device="cuda")) for _ in range(2)]
+        self.counts = [torch.zeros(1, dtype=torch.int64).pin_memory() for _ in range(2)]
+
+    def extend(self, v0: int, v1: int, slot: int, stream=None):
+        u, v, c = self.bufs[slot]
+        cnt = self.counts[slot]
+        st = stream if stream is not None else _stream()
+        _check("rgg_explore_block", self._lib.rgg_explore_block(
+            self._h, int(v0), int(v1), u.data_ptr(), v.data_ptr(), c.data_ptr(),
+            cnt.data_ptr(), st))
+        return u, v, c, cnt
+
+    def points(self):
+        """The samples as a CUDA float64 tensor (n x dim), copied."""
+        import torch
+        out = torch.empty((self.n, self.scene.dim), dtype=torch.float64, device="cuda")
+        _check("rgg_explore_copy_points",
+               self._lib.rgg_explore_copy_points(self._h, out.data_ptr(), _stream()))
+        return out
+
+    def close(self):
+        if getattr(self, "_h", None):
+            self._lib.rgg_explore_destroy(self._h)
+            self._h = None
+
+    __del__ = close

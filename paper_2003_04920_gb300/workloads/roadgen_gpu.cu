@@ -244,11 +244,98 @@ __device__ __forceinline__ float d2_32(const float *a, const float *b, int dim) 
     return s;
 }
 
+// The k smallest (d2, id) among the grid's points with id < id_limit, other
+// than qid itself, kept sorted in bd / bi; returns how many were found (k
+// unless fewer candidates exist).  Cells are scanned by growing boxes of cells
+// around the query's cell until the box holds the ball of the k-th distance;
+// a cell whose box lies farther than the k-th distance is skipped.
+__device__ int knn_search(const Grid &g, int k, const float *q, int qid, int id_limit,
+                          const float *__restrict__ spts, const int *__restrict__ sid,
+                          const long long *__restrict__ start, float *bd, int *bi) {
+    const int dim = g.dim;
+    int qc[kMaxDim];
+    for (int d = 0; d < dim; ++d) qc[d] = cell_coord(g, q[d]);
+    int cnt = 0;
+    int slo[kMaxDim], shi[kMaxDim];
+    bool scanned = false;
+    for (int r = 1;; ++r) {
+        int blo[kMaxDim], bhi[kMaxDim];
+        if (cnt < k) {
+            for (int d = 0; d < dim; ++d) {
+                blo[d] = max(0, qc[d] - r);
+                bhi[d] = min(g.G - 1, qc[d] + r);
+            }
+        } else {
+            const float w = sqrtf(bd[k - 1]) * 1.0001f + 1e-6f;
+            for (int d = 0; d < dim; ++d) {
+                blo[d] = cell_coord(g, q[d] - w);
+                bhi[d] = cell_coord(g, q[d] + w);
+            }
+        }
+        bool same = scanned;
+        if (scanned)
+            for (int d = 0; d < dim; ++d) {
+                blo[d] = min(blo[d], slo[d]);
+                bhi[d] = max(bhi[d], shi[d]);
+                same = same && blo[d] == slo[d] && bhi[d] == shi[d];
+            }
+        if (same && cnt == k) break;
+        bool whole = true;
+        for (int d = 0; d < dim; ++d) whole = whole && blo[d] == 0 && bhi[d] == g.G - 1;
+        if (same && whole) break;  // every candidate seen: fewer than k exist
+        // every cell of the box that the previous box did not hold
+        int c[kMaxDim];
+        for (int d = 0; d < dim; ++d) c[d] = blo[d];
+        for (;;) {
+            bool inside_old = scanned;
+            long long id = 0, mul = 1;
+            float box = 0.f;
+            for (int d = 0; d < dim; ++d) {
+                inside_old = inside_old && c[d] >= slo[d] && c[d] <= shi[d];
+                id += (long long)c[d] * mul;
+                mul *= g.G;
+                const float a0 = (float)(g.lo + c[d] * g.cw), a1 = (float)(g.lo + (c[d] + 1) * g.cw);
+                const float e = q[d] < a0 ? a0 - q[d] : (q[d] > a1 ? q[d] - a1 : 0.f);
+                box += e * e;
+            }
+            const bool prune = cnt == k && box > bd[k - 1] * 1.0001f + 1e-6f;
+            if (!inside_old && !prune) {
+                for (long long p = start[id]; p < start[id + 1]; ++p) {
+                    const int pid = sid[p];
+                    if (pid == qid || pid >= id_limit) continue;
+                    const float dd = d2_32(q, spts + p * dim, dim);
+                    if (cnt == k && (dd > bd[k - 1] || (dd == bd[k - 1] && pid > bi[k - 1])))
+                        continue;
+                    int at = cnt < k ? cnt : k - 1;
+                    while (at > 0 && (bd[at - 1] > dd || (bd[at - 1] == dd && bi[at - 1] > pid))) {
+                        bd[at] = bd[at - 1];
+                        bi[at] = bi[at - 1];
+                        --at;
+                    }
+                    bd[at] = dd;
+                    bi[at] = pid;
+                    if (cnt < k) ++cnt;
+                }
+            }
+            int d = 0;
+            while (d < dim && c[d] == bhi[d]) {
+                c[d] = blo[d];
+                ++d;
+            }
+            if (d == dim) break;
+            ++c[d];
+        }
+        for (int d = 0; d < dim; ++d) {
+            slo[d] = blo[d];
+            shi[d] = bhi[d];
+        }
+        scanned = true;
+    }
+    return cnt;
+}
+
 // One thread per point, in cell order (neighbouring threads scan the same
-// cells).  The k smallest (d2, id) are kept sorted.  Cells are scanned by
-// growing boxes of cells around the query's cell until the box holds the ball
-// of the k-th distance; a cell whose box lies farther than the k-th distance
-// is skipped.
+// cells): the k nearest among all points.
 __global__ void __launch_bounds__(kT)
 knn_kernel(long long n, Grid g, int k, const float *__restrict__ spts, const int *__restrict__ sid,
            const long long *__restrict__ start, int *__restrict__ knn) {
@@ -256,91 +343,30 @@ knn_kernel(long long n, Grid g, int k, const float *__restrict__ spts, const int
     for (long long s = blockIdx.x * (long long)blockDim.x + threadIdx.x; s < n;
          s += (long long)gridDim.x * blockDim.x) {
         float q[kMaxDim];
-        int qc[kMaxDim];
-        for (int d = 0; d < dim; ++d) {
-            q[d] = spts[s * dim + d];
-            qc[d] = cell_coord(g, q[d]);
-        }
+        for (int d = 0; d < dim; ++d) q[d] = spts[s * dim + d];
         const int qid = sid[s];
         float bd[kMaxK];
         int bi[kMaxK];
-        int cnt = 0;
-        int slo[kMaxDim], shi[kMaxDim];
-        bool scanned = false;
-        for (int r = 1;; ++r) {
-            int blo[kMaxDim], bhi[kMaxDim];
-            if (cnt < k) {
-                for (int d = 0; d < dim; ++d) {
-                    blo[d] = max(0, qc[d] - r);
-                    bhi[d] = min(g.G - 1, qc[d] + r);
-                }
-            } else {
-                const float w = sqrtf(bd[k - 1]) * 1.0001f + 1e-6f;
-                for (int d = 0; d < dim; ++d) {
-                    blo[d] = cell_coord(g, q[d] - w);
-                    bhi[d] = cell_coord(g, q[d] + w);
-                }
-            }
-            bool same = scanned;
-            if (scanned)
-                for (int d = 0; d < dim; ++d) {
-                    blo[d] = min(blo[d], slo[d]);
-                    bhi[d] = max(bhi[d], shi[d]);
-                    same = same && blo[d] == slo[d] && bhi[d] == shi[d];
-                }
-            if (same && cnt == k) break;
-            bool whole = true;
-            for (int d = 0; d < dim; ++d) whole = whole && blo[d] == 0 && bhi[d] == g.G - 1;
-            if (same && whole) break;  // every point seen (k < n keeps this from happening)
-            // every cell of the box that the previous box did not hold
-            int c[kMaxDim];
-            for (int d = 0; d < dim; ++d) c[d] = blo[d];
-            for (;;) {
-                bool inside_old = scanned;
-                long long id = 0, mul = 1;
-                float box = 0.f;
-                for (int d = 0; d < dim; ++d) {
-                    inside_old = inside_old && c[d] >= slo[d] && c[d] <= shi[d];
-                    id += (long long)c[d] * mul;
-                    mul *= g.G;
-                    const float a0 = (float)(g.lo + c[d] * g.cw), a1 = (float)(g.lo + (c[d] + 1) * g.cw);
-                    const float e = q[d] < a0 ? a0 - q[d] : (q[d] > a1 ? q[d] - a1 : 0.f);
-                    box += e * e;
-                }
-                const bool prune = cnt == k && box > bd[k - 1] * 1.0001f + 1e-6f;
-                if (!inside_old && !prune) {
-                    for (long long p = start[id]; p < start[id + 1]; ++p) {
-                        const int pid = sid[p];
-                        if (pid == qid) continue;
-                        const float dd = d2_32(q, spts + p * dim, dim);
-                        if (cnt == k && (dd > bd[k - 1] || (dd == bd[k - 1] && pid > bi[k - 1])))
-                            continue;
-                        int at = cnt < k ? cnt : k - 1;
-                        while (at > 0 && (bd[at - 1] > dd || (bd[at - 1] == dd && bi[at - 1] > pid))) {
-                            bd[at] = bd[at - 1];
-                            bi[at] = bi[at - 1];
-                            --at;
-                        }
-                        bd[at] = dd;
-                        bi[at] = pid;
-                        if (cnt < k) ++cnt;
-                    }
-                }
-                int d = 0;
-                while (d < dim && c[d] == bhi[d]) {
-                    c[d] = blo[d];
-                    ++d;
-                }
-                if (d == dim) break;
-                ++c[d];
-            }
-            for (int d = 0; d < dim; ++d) {
-                slo[d] = blo[d];
-                shi[d] = bhi[d];
-            }
-            scanned = true;
-        }
+        const int cnt = knn_search(g, k, q, qid, 0x7fffffff, spts, sid, start, bd, bi);
         for (int a = 0; a < k; ++a) knn[(long long)qid * k + a] = a < cnt ? bi[a] : -1;
+    }
+}
+
+// Vertices [q0, q1): the k nearest among the vertices that precede each one
+// (the grid holds vertices [0, q1)), -1 where fewer exist.  Row i - q0 of knn.
+__global__ void __launch_bounds__(kT)
+knn_pred_kernel(long long q0, long long q1, Grid g, int k, const double *__restrict__ pts,
+                const float *__restrict__ spts, const int *__restrict__ sid,
+                const long long *__restrict__ start, int *__restrict__ knn) {
+    const int dim = g.dim;
+    for (long long i = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < q1;
+         i += (long long)gridDim.x * blockDim.x) {
+        float q[kMaxDim];
+        for (int d = 0; d < dim; ++d) q[d] = (float)pts[i * dim + d];
+        float bd[kMaxK];
+        int bi[kMaxK];
+        const int cnt = knn_search(g, k, q, (int)i, (int)i, spts, sid, start, bd, bi);
+        for (int a = 0; a < k; ++a) knn[(i - q0) * k + a] = a < cnt ? bi[a] : -1;
     }
 }
 
@@ -640,5 +666,216 @@ extern "C" int rgg_edges(int32_t dim, int64_t n, const double *points, int32_t k
     }
     RG_CKL();
     RG_CK(cudaStreamSynchronize(st));
+    return 0;
+}
+
+// ---- incremental exploration ------------------------------------------------
+
+namespace {
+
+// Links of the new vertices [v0, v1) to their nearest predecessors that are
+// collision-free with a positive length: keep flags and a count per row.
+__global__ void pred_edge_mark(long long v0, long long v1, int dim, const double *__restrict__ pts,
+                               int k, const int *__restrict__ knn, int n_obs,
+                               const double *__restrict__ centers, const double *__restrict__ radii,
+                               int mode, int n_check, unsigned char *__restrict__ keep,
+                               int *__restrict__ rowc) {
+    for (long long i = v0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v1;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i - v0;
+        int c = 0;
+        for (int a = 0; a < k; ++a) {
+            const int j = knn[r * k + a];
+            bool ok = j >= 0;
+            if (ok) {
+                const double *pa = pts + (long long)j * dim, *pb = pts + i * dim;
+                ok = d2_64(pa, pb, dim) > 0.0 &&
+                     segment_free(pa, pb, dim, n_obs, centers, radii, mode, n_check);
+            }
+            keep[r * k + a] = ok ? 1 : 0;
+            c += ok ? 1 : 0;
+        }
+        rowc[r] = c;
+    }
+}
+
+template <typename CT>
+__global__ void pred_edge_emit(long long v0, long long v1, int dim, const double *__restrict__ pts,
+                               int k, const int *__restrict__ knn,
+                               const unsigned char *__restrict__ keep,
+                               const long long *__restrict__ rowoff, int *__restrict__ eu,
+                               int *__restrict__ ev, CT *__restrict__ ec) {
+    for (long long i = v0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v1;
+         i += (long long)gridDim.x * blockDim.x) {
+        const long long r = i - v0;
+        long long at = rowoff[r];
+        for (int a = 0; a < k; ++a) {
+            if (!keep[r * k + a]) continue;
+            const int j = knn[r * k + a];
+            eu[at] = j;
+            ev[at] = (int)i;
+            ec[at] = (CT)__dsqrt_rn(d2_64(pts + (long long)j * dim, pts + i * dim, dim));
+            ++at;
+        }
+    }
+}
+
+// Grid of cells of about the k-th neighbour distance for `m` points spread
+// over the box (at most 2^24 cells).
+Grid grid_for_density(int dim, double lo, double hi, long long m, int k) {
+    const double span = hi - lo;
+    const double unit = std::pow(M_PI, dim / 2.0) / std::tgamma(dim / 2.0 + 1.0);
+    const double cell =
+        std::pow((double)k * std::pow(span, dim) / ((double)std::max(m, 1ll) * unit), 1.0 / dim);
+    int G = std::max(1, (int)std::floor(span / cell));
+    while (std::pow((double)G, dim) > (double)(1 << 24) && G > 1) --G;
+    return Grid{dim, G, lo, span / G};
+}
+
+long long cells_of(const Grid &g) {
+    long long c = 1;
+    for (int d = 0; d < g.dim; ++d) c *= g.G;
+    return c;
+}
+
+}  // namespace
+
+struct rgg_explorer {
+    int dim = 0;
+    double lo = 0.0, hi = 0.0;
+    int n_obs = 0, k = 0, mode = 0, n_check = 0, cost_f64 = 0;
+    long long n = 0, max_block = 0, cells_max = 0;
+    double *centers = nullptr, *radii = nullptr, *pts = nullptr;
+    float *spts = nullptr;
+    int *sid = nullptr, *cnt = nullptr, *knn = nullptr, *rowc = nullptr;
+    long long *cell_of = nullptr, *start = nullptr, *rowoff = nullptr, *tiles = nullptr;
+    unsigned char *keep = nullptr;
+};
+
+extern "C" void rgg_explore_destroy(rgg_explorer *x) {
+    if (!x) return;
+    void *bufs[] = {x->centers, x->radii, x->pts, x->spts, x->sid, x->cnt, x->knn, x->rowc,
+                    x->cell_of, x->start, x->rowoff, x->tiles, x->keep};
+    for (void *b : bufs)
+        if (b) cudaFree(b);
+    delete x;
+}
+
+extern "C" int rgg_explore_create(int32_t dim, double lo, double hi, int32_t n_obs,
+                                  const double *centers, const double *radii, uint64_t seed,
+                                  int64_t n, int32_t k, int32_t mode, int32_t n_check,
+                                  int32_t cost_f64, int64_t max_block, void *stream,
+                                  rgg_explorer **out) {
+    if (!out) return 1;
+    *out = nullptr;
+    if (dim < 1 || dim > kMaxDim || !(hi > lo) || n < 2 || k < 1 || k > kMaxK || max_block < 1 ||
+        (mode != 0 && mode != 1) || (mode == 1 && n_check < 1) || n_obs < 0 ||
+        (n_obs > 0 && (!centers || !radii)))
+        return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    rgg_explorer *x = new rgg_explorer;
+    x->dim = dim;
+    x->lo = lo;
+    x->hi = hi;
+    x->n_obs = n_obs;
+    x->k = k;
+    x->mode = mode;
+    x->n_check = n_check;
+    x->cost_f64 = cost_f64;
+    x->n = n;
+    x->max_block = std::min<long long>(max_block, n);
+    const Grid gmax = grid_for_density(dim, lo, hi, n, k);
+    x->cells_max = 1;
+    for (long long m = 1; m <= n; m *= 2) x->cells_max = std::max(x->cells_max, cells_of(grid_for_density(dim, lo, hi, m, k)));
+    x->cells_max = std::max(x->cells_max, cells_of(gmax));
+    const long long mb = x->max_block;
+    bool ok = cudaMalloc(&x->centers, sizeof(double) * std::max(1, n_obs * dim)) == cudaSuccess &&
+              cudaMalloc(&x->radii, sizeof(double) * std::max(1, n_obs)) == cudaSuccess &&
+              cudaMalloc(&x->pts, sizeof(double) * n * dim) == cudaSuccess &&
+              cudaMalloc(&x->spts, sizeof(float) * n * dim) == cudaSuccess &&
+              cudaMalloc(&x->sid, sizeof(int) * n) == cudaSuccess &&
+              cudaMalloc(&x->cell_of, sizeof(long long) * n) == cudaSuccess &&
+              cudaMalloc(&x->cnt, sizeof(int) * (x->cells_max + 1)) == cudaSuccess &&
+              cudaMalloc(&x->start, sizeof(long long) * (x->cells_max + 1)) == cudaSuccess &&
+              cudaMalloc(&x->tiles, sizeof(long long) *
+                                        (std::max(x->cells_max, mb) + 1 + kTile) / kTile) == cudaSuccess &&
+              cudaMalloc(&x->knn, sizeof(int) * mb * k) == cudaSuccess &&
+              cudaMalloc(&x->keep, mb * k) == cudaSuccess &&
+              cudaMalloc(&x->rowc, sizeof(int) * (mb + 1)) == cudaSuccess &&
+              cudaMalloc(&x->rowoff, sizeof(long long) * (mb + 1)) == cudaSuccess;
+    if (!ok) {
+        cudaGetLastError();
+        rgg_explore_destroy(x);
+        return 2;
+    }
+    if (n_obs > 0 &&
+        (cudaMemcpyAsync(x->centers, centers, sizeof(double) * n_obs * dim,
+                         cudaMemcpyDeviceToDevice, st) != cudaSuccess ||
+         cudaMemcpyAsync(x->radii, radii, sizeof(double) * n_obs, cudaMemcpyDeviceToDevice, st) !=
+             cudaSuccess)) {
+        rgg_explore_destroy(x);
+        return 2;
+    }
+    int64_t tried = 0;
+    const int rc = rgg_sample(dim, lo, hi, n_obs, x->centers, x->radii, seed, n, x->pts, &tried, st);
+    if (rc) {
+        rgg_explore_destroy(x);
+        return rc;
+    }
+    *out = x;
+    return 0;
+}
+
+extern "C" int rgg_explore_block(rgg_explorer *x, int64_t v0, int64_t v1, int32_t *u, int32_t *v,
+                                 void *cost, int64_t *m_pinned, void *stream) {
+    if (!x || v0 < 0 || v1 <= v0 || v1 > x->n || v1 - v0 > x->max_block || !u || !v || !cost ||
+        !m_pinned)
+        return 1;
+    cudaStream_t st = static_cast<cudaStream_t>(stream);
+    const int dim = x->dim, k = x->k;
+    const long long nb = v1 - v0;
+    // the grid over the vertices present, [0, v1)
+    const Grid g = grid_for_density(dim, x->lo, x->hi, v1, k);
+    const long long cells = cells_of(g);
+    if (cells > x->cells_max) return 1;
+    RG_CK(cudaMemsetAsync(x->cnt, 0, sizeof(int) * (cells + 1), st));
+    cell_count<<<grid_of(v1), kT, 0, st>>>(v1, g, x->pts, x->cell_of, x->cnt);
+    RG_CKL();
+    if (int rc = exclusive_scan(x->cnt, cells + 1, x->start, x->tiles, st)) return rc;
+    RG_CK(cudaMemsetAsync(x->cnt, 0, sizeof(int) * (cells + 1), st));
+    cell_scatter<<<grid_of(v1), kT, 0, st>>>(v1, dim, x->pts, x->cell_of, x->start, x->cnt,
+                                             x->spts, x->sid);
+    RG_CKL();
+    // nearest predecessors of the new vertices, then their edges
+    knn_pred_kernel<<<grid_of(nb), kT, 0, st>>>(v0, v1, g, k, x->pts, x->spts, x->sid, x->start,
+                                                x->knn);
+    RG_CKL();
+    pred_edge_mark<<<grid_of(nb), kT, 0, st>>>(v0, v1, dim, x->pts, k, x->knn, x->n_obs,
+                                               x->centers, x->radii, x->mode, x->n_check, x->keep,
+                                               x->rowc);
+    RG_CKL();
+    RG_CK(cudaMemsetAsync(x->rowc + nb, 0, sizeof(int), st));
+    if (int rc = exclusive_scan(x->rowc, nb + 1, x->rowoff, x->tiles, st)) return rc;
+    RG_CK(cudaMemcpyAsync(m_pinned, x->rowoff + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
+    if (x->cost_f64)
+        pred_edge_emit<double><<<grid_of(nb), kT, 0, st>>>(v0, v1, dim, x->pts, k, x->knn, x->keep,
+                                                           x->rowoff, u, v,
+                                                           static_cast<double *>(cost));
+    else
+        pred_edge_emit<float><<<grid_of(nb), kT, 0, st>>>(v0, v1, dim, x->pts, k, x->knn, x->keep,
+                                                          x->rowoff, u, v,
+                                                          static_cast<float *>(cost));
+    RG_CKL();
+    return 0;
+}
+
+extern "C" const double *rgg_explore_points(const rgg_explorer *x) { return x ? x->pts : nullptr; }
+
+extern "C" int64_t rgg_explore_size(const rgg_explorer *x) { return x ? x->n : -1; }
+
+extern "C" int rgg_explore_copy_points(const rgg_explorer *x, double *out, void *stream) {
+    if (!x || !out) return 1;
+    RG_CK(cudaMemcpyAsync(out, x->pts, sizeof(double) * x->n * x->dim, cudaMemcpyDeviceToDevice,
+                          static_cast<cudaStream_t>(stream)));
     return 0;
 }

@@ -65,6 +65,38 @@ int rgg_edges(int32_t dim, int64_t n, const double *points, int32_t k, const int
               int32_t n_check, int32_t cost_f64, int32_t *u, int32_t *v, void *cost,
               int64_t *edge_start, int64_t cap, int64_t *m, void *stream);
 
+/* Incremental exploration: the Extend step of RRT# one Batched-Extension
+ * block at a time (Alg. 3), for running on its own stream while the previous
+ * block is exploited (the asynchronous exploration the paper leaves to future
+ * work, Sec. VII).  Vertex i joins the k vertices nearest to it among the
+ * vertices 0 .. i-1 (FP32 squared distance as for rgg_knn, ties by id;
+ * every predecessor while i <= k) by the collision-free, positive-length
+ * edges among those links, cost = sqrt of the FP64 squared length.  The
+ * roadmap therefore does not depend on the block size.  The n free samples
+ * are drawn at create time (rgg_sample's definition, same seed rule). */
+typedef struct rgg_explorer rgg_explorer;
+
+int rgg_explore_create(int32_t dim, double lo, double hi, int32_t n_obs, const double *centers,
+                       const double *radii, uint64_t seed, int64_t n, int32_t k, int32_t mode,
+                       int32_t n_check, int32_t cost_f64, int64_t max_block, void *stream,
+                       rgg_explorer **out);
+
+/* The edges of the new vertices [v0, v1) (v1 - v0 <= max_block): (u, v) with
+ * u < v = the new vertex, ordered by v then by nearness, into u / v / cost
+ * (room for (v1 - v0) * k edges), all ordered on `stream` with no host
+ * synchronisation; *m_pinned (page-locked host memory) receives the edge
+ * count when the stream gets there. */
+int rgg_explore_block(rgg_explorer *x, int64_t v0, int64_t v1, int32_t *u, int32_t *v, void *cost,
+                      int64_t *m_pinned, void *stream);
+
+/* The samples (device FP64, n x dim) and their number; a copy of them into
+ * out (device, n x dim), ordered on `stream`. */
+const double *rgg_explore_points(const rgg_explorer *x);
+int64_t rgg_explore_size(const rgg_explorer *x);
+int rgg_explore_copy_points(const rgg_explorer *x, double *out, void *stream);
+
+void rgg_explore_destroy(rgg_explorer *x);
+
 #ifdef __cplusplus
 }
 #endif

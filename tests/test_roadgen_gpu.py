@@ -250,3 +250,70 @@ def test_gpu_roadmap_schedule_matches_dijkstra():
     host = rm.to_host()
     d, _ = O.dijkstra(host.n, host.u, host.v, host.cost.astype(np.float64))
     assert_parity(host, g, p, d)
+
+
+# ------------------------------------------------------------- exploration
+
+def pred_knn_np(pts, k):
+    """Vertex i's k nearest among vertices 0 .. i-1 (FP32, ties by id)."""
+    p32 = pts.astype(np.float32)
+    out = np.full((len(p32), k), -1, dtype=np.int32)
+    for i in range(1, len(p32)):
+        d = d2_seq(p32[i][None, :], p32[:i])
+        order = np.lexsort((np.arange(i), d))[:k]
+        out[i, :len(order)] = order
+    return out
+
+
+def pred_edges_np(pts, nbr, scene, exact, n_check, cost_dtype):
+    out_u, out_v, out_c = [], [], []
+    for i in range(len(pts)):
+        for j in nbr[i].tolist():
+            if j < 0:
+                continue
+            a, b = pts[j], pts[i]
+            s = 0.0
+            for d in range(len(a)):
+                t = a[d] - b[d]
+                s = s + t * t
+            if s > 0.0 and segment_free_np(a, b, scene.centers, scene.radii, exact, n_check):
+                out_u.append(j)
+                out_v.append(i)
+                out_c.append(math.sqrt(s))
+    return (np.array(out_u, dtype=np.int32), np.array(out_v, dtype=np.int32),
+            np.array(out_c, dtype=np.float64).astype(cost_dtype))
+
+
+def _explore_all(G, scene, n, k, seed, S, exact=False):
+    import torch
+    x = G.Explorer(scene, n, k, seed, S, exact_segment=exact)
+    us, vs, cs = [], [], []
+    for b, v0 in enumerate(range(0, n, S)):
+        v1 = min(n, v0 + S)
+        u, v, c, cnt = x.extend(v0, v1, b & 1)
+        torch.cuda.synchronize()
+        m = int(cnt.item())
+        us.append(u[:m].cpu().numpy())
+        vs.append(v[:m].cpu().numpy())
+        cs.append(c[:m].cpu().numpy())
+    pts = x.points().cpu().numpy()
+    x.close()
+    return pts, np.concatenate(us), np.concatenate(vs), np.concatenate(cs)
+
+
+@pytest.mark.gpu
+def test_gpu_exploration_matches_cpu_reference_and_block_size():
+    torch, G = _gpu()
+    scene = W._draw_scene(np.random.default_rng(41), 6, -math.pi, math.pi, 64, 0.3, 0.8, [])
+    n, k, seed = 1800, 20, 4242
+    pts, u, v, c = _explore_all(G, scene, n, k, seed, 500)
+    np.testing.assert_array_equal(pts, sample_np(scene, n, seed))
+    wu, wv, wc = pred_edges_np(pts, pred_knn_np(pts, k), scene, False, 16, np.float32)
+    np.testing.assert_array_equal(u, wu)
+    np.testing.assert_array_equal(v, wv)
+    np.testing.assert_array_equal(c, wc)
+    # the roadmap does not depend on the block size (Alg. 3)
+    _, u2, v2, c2 = _explore_all(G, scene, n, k, seed, 1800)
+    np.testing.assert_array_equal(u2, u)
+    np.testing.assert_array_equal(v2, v)
+    np.testing.assert_array_equal(c2, c)

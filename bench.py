@@ -45,6 +45,10 @@ L2_BYTES = 129 * 1024 * 1024
 WORKLOADS = {
     "c3": ("roadmap_c3", "6-D [-pi,pi]^6, 64 hyperspheres r~U[0.3,0.8], N=4e6, k=30, "
                          "16-point edge check, FP32 costs, FP64 g, blocks of 5e4"),
+    "c3-gpu": ("roadmap_c3_gpu", "6-D [-pi,pi]^6, 64 hyperspheres r~U[0.3,0.8], N=4e6, k=30, "
+                                 "16-point edge check, FP32 costs, FP64 g, blocks of 5e4; the "
+                                 "same law built by the GPU generator (Philox samples, grid "
+                                 "k-NN; another instance, another x_init)"),
     "c2": ("roadmap_c2", "2-D unit square, 200 circles r~U[0.02,0.08], N=1e6, k=76, FP32 costs, "
                          "FP64 g, blocks of 1e4"),
     "c2-companion": ("roadmap_c2", "2-D unit square, 200 circles r~U[0.01,0.04], N=1e6, k=76, "
@@ -60,6 +64,21 @@ def load_roadmap(name: str, n: int | None, block: int | None, trial: int):
     kw = dict(trial=trial)
     if n:
         kw["n"] = n
+    if fn_name == "roadmap_c3_gpu":
+        # seconds on the device, no on-disk cache; host copies for the pinned
+        # end-to-end pass and the oracle legs
+        import torch
+
+        from paper_2003_04920_gb300.workloads import gpu as GG
+        GG.build()
+        GG.load()
+        if block:
+            kw["block"] = int(block)
+        drm = GG.roadmap_c3_gpu(**kw)
+        rm = drm.to_host()
+        del drm
+        torch.cuda.empty_cache()
+        return rm
     if name == "c2-companion":
         kw["companion"] = True
     rm = W.cached(name, getattr(W, fn_name), **kw)
@@ -218,6 +237,10 @@ def run_ours(args) -> None:
     extra = {"wave_levels": 0, "jump_evaluates": 0, "dense_sweeps": 0, "switches": 0,
              "improve_entries": 0, "offers": 0}
     block_ms = []  # per-block device time of the last step run with block_times=True
+    traffic_block = -1 if args.traffic_block is None else \
+        (args.traffic_block % n_blocks if n_blocks else -1)
+    traffic_window = {}
+    prof_on = [False]
 
     def step(device_inputs=True, block_times=False):
         G.reset()
@@ -239,10 +262,28 @@ def run_ours(args) -> None:
                     # the next block's copy overlaps this exploit
                     _, _, f0, f1 = blocks[b + 1]
                     G.prefetch_batch(host_u[f0:f1], host_v[f0:f1], host_c[f0:f1])
+            window = b == traffic_block and prof_on[0] and not traffic_window
+            if window:
+                # the exploit whose Evaluate launches a profiler captures by
+                # this NVTX range (DRAM counters over a few launches)
+                torch.cuda.nvtx.range_push("traffic_window")
+                before = G.get_profile()
             st = G.exploit(group=args.group, tile=args.tile, dense_fraction=args.dense_fraction,
                            evaluate=args.evaluate, wave_levels=args.wave_levels,
                            host_loop=args.host_loop, wave_tail=args.wave_tail,
                            wave_ctas=args.wave_ctas)
+            if window:
+                torch.cuda.synchronize()
+                torch.cuda.nvtx.range_pop()
+                after = G.get_profile()
+                d = {k: after[k] - before[k] for k in ("evaluate_launches", "evaluate_vertices",
+                                                       "evaluate_offers", "evaluate_ms")}
+                traffic_window.update(block=b, evaluate_calls=int(d["evaluate_launches"]),
+                                      evaluate_ms=round(float(d["evaluate_ms"]), 4),
+                                      algorithmic_bytes=int(evaluate_bytes(
+                                          {"evaluate_vertices": d["evaluate_vertices"],
+                                           "evaluate_offers": d["evaluate_offers"]},
+                                          entry_bytes, cost_bytes)))
             relax += st["relaxations"]
             iters += st["iterations"]
             for k in extra:
@@ -292,6 +333,7 @@ def run_ours(args) -> None:
 
     with ClockSampler(local) as clk:
         G.set_profiling(args.timing == "profiled")
+        prof_on[0] = args.timing == "profiled"
         times, relaxes, iters_all = timed_steps(args.steps)
         improve_only = float(sum(e["improve_entries"] for e in timed_extra))
         step_extra = dict(timed_extra[-1]) if timed_extra else dict(extra)
@@ -299,6 +341,7 @@ def run_ours(args) -> None:
         timed_launches = G.get_profile()["launches"]
         if args.timing == "graph":
             G.set_profiling(True)
+            prof_on[0] = True
             prof_times, _, _ = timed_steps(args.profile_steps)
         else:
             prof_times = times
@@ -306,6 +349,7 @@ def run_ours(args) -> None:
         if args.trace:
             np.save(args.trace, G.get_trace())
         G.set_profiling(False)
+        prof_on[0] = False
     barrier()
     clocks = clk.summary()
     prof_ms = float(sum(prof_times))
@@ -370,7 +414,9 @@ def run_ours(args) -> None:
     g_goal = None
     if goal is not None:
         g_goal = float(G.get_costs()[goal])
-    tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
+    tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic_{args.workload}.json")
+    if not os.path.exists(tpath):
+        tpath = os.path.join(ROOT, "profiles", f"{dom}_traffic.json")
     if os.path.exists(tpath):
         with open(tpath) as f:
             tj = json.load(f)
@@ -427,6 +473,8 @@ def run_ours(args) -> None:
         "gpu_launches": int(timed_launches),
         "clocks": clocks,
     }
+    if traffic_window:
+        line["traffic_window"] = traffic_window
     if rank == 0 and world == 1 and not args.no_cpu_baseline:
         # per-block device times of one more (untimed) step, for a GPU figure
         # over exactly the block prefix the oracle covers
@@ -629,6 +677,8 @@ def run_batch(args) -> None:
         "gpu_launches": int(timed_launches),
         "clocks": clocks,
     }
+    if traffic_window:
+        line["traffic_window"] = traffic_window
     for G in solos:
         G.close()
     B.close()
@@ -951,6 +1001,10 @@ def main():
     ap.add_argument("--no-e2e", action="store_true",
                     help="skip the end-to-end pass (e.g. for a profiler's launch list)")
     ap.add_argument("--trace", default=None, help="save the per-iteration trace (.npy)")
+    ap.add_argument("--traffic-block", type=int, default=None,
+                    help="mark this block's exploit with the NVTX range 'traffic_window' while "
+                         "profiling and report its Evaluate calls and algorithmic bytes "
+                         "(negative: from the end)")
     args = ap.parse_args()
     if args.workload == "sweep":
         if args.impl == "reference":

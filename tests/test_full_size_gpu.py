@@ -2,7 +2,8 @@
 bench.py times.
 
 The whole Batched-Extension schedule (Alg. 3) of the 6-D roadmap (N =
-4,000,000, k = 30, blocks of 50,000: 80 exploitation rounds) and of the 2-D
+4,000,000, k = 30, blocks of 50,000: 80 exploitation rounds; built both by
+the GPU generator, as the benchmark does, and by the host generator) and of the 2-D
 roadmap (N = 1,000,000, k = 76, blocks of 10,000: 100 rounds) runs from
 device-resident blocks with the default options, every exploit one CUDA-graph
 launch, exactly as in the benchmark's timed steps.  The oracle cannot replay
@@ -69,12 +70,23 @@ def _check(rm, g, p):
     return mask
 
 
+def _gpu_c3(trial=0):
+    """The 6-D roadmap as the benchmark builds it: on the GPU generator."""
+    from paper_2003_04920_gb300.workloads import gpu as GG
+    GG.build()
+    drm = GG.roadmap_c3_gpu(trial=trial)
+    rm = drm.to_host()
+    del drm
+    return rm
+
+
 @pytest.mark.parametrize("name,fn,kw,check_block", [
+    ("c3-gpu", _gpu_c3, dict(trial=0), 39),
     ("c3", W.roadmap_c3, dict(trial=0), 39),
     ("c2-companion", W.roadmap_c2, dict(trial=0, companion=True), 49),
 ])
 def test_full_size_schedule_matches_dijkstra(torch, name, fn, kw, check_block):
-    rm = W.cached(name, fn, **kw)
+    rm = fn(**kw) if name == "c3-gpu" else W.cached(name, fn, **kw)
     mid, g, p, stats = _full_schedule(torch, rm, check_block)
     assert len(stats) == rm.n_blocks()
     assert all(s["converged"] == 1 for s in stats)

@@ -441,7 +441,12 @@ pirrt_graph *pirrt_batch_graph(pirrt_batch *b);
  *   a1 = W1g grid + W1n z + b1, h1 = relu(a1); a2 = W2 h1 + b2, h2 = relu(a2);
  *   y = sigmoid(W3 h2 + b3).
  * BF16 weights and layer inputs on the tensor cores with FP32 accumulation,
- * FP32 master weights trained by Adam.  Training is implicit maximum-
+ * FP32 master weights trained by Adam.  The forward pass of forward, sample,
+ * imle_select and of train_step's K draws per target runs by default as one
+ * fused tcgen05 kernel (all three contractions with TMEM accumulators, the
+ * activations kept on chip, 128 rows per tile); the layer-by-layer path
+ * (mma.sync GEMMs, activations in HBM) computes the backward pass and can be
+ * selected for the forward pass too (pirrt_proposal_set_options).  Training is implicit maximum-
  * likelihood estimation: for each target sample, K noise draws go through the
  * network and only the draw nearest the target is pulled towards it.
  * Parameters are packed FP32 in the order W1g [256 x 4096], W1n [256 x 8],
@@ -449,6 +454,9 @@ pirrt_graph *pirrt_batch_graph(pirrt_batch *b);
  * All array arguments are device pointers; noise is supplied by the caller.
  * ------------------------------------------------------------------------ */
 typedef struct pirrt_proposal pirrt_proposal;
+
+/* Forward kernels for pirrt_proposal_set_options. */
+enum { PIRRT_MLP_FORWARD_TCGEN05 = 0, PIRRT_MLP_FORWARD_LAYERED = 1 };
 
 /* Number of packed parameters (1,117,186). */
 int64_t pirrt_proposal_num_params(void);
@@ -459,14 +467,38 @@ pirrt_status pirrt_proposal_create(int32_t max_scenes, int32_t max_rows, uint64_
                                    int32_t device, void *stream, pirrt_proposal **out);
 void pirrt_proposal_destroy(pirrt_proposal *p);
 
+/* forward_kernel: PIRRT_MLP_FORWARD_TCGEN05 (default) or
+ * PIRRT_MLP_FORWARD_LAYERED for the forward passes listed above;
+ * keep_activations != 0: every later forward pass also leaves h1 and h2 (BF16)
+ * of its rows for pirrt_proposal_get_activations (a diagnostic; the fused
+ * kernel then writes them to HBM).  PIRRT_ERR_INVALID_ARG for an unknown
+ * kernel. */
+pirrt_status pirrt_proposal_set_options(pirrt_proposal *p, int32_t forward_kernel,
+                                        int32_t keep_activations);
+
+/* Device time (CUDA events on the handle's stream) of the last fused forward
+ * kernel launch, in ms; PIRRT_ERR_INVALID_ARG before the first one. */
+pirrt_status pirrt_proposal_kernel_ms(const pirrt_proposal *p, float *ms);
+
+/* Copy h1 and h2 ([rows x 256] BF16 bit patterns, row-major) of the last
+ * forward pass into device buffers h1_out / h2_out (either may be NULL).
+ * Needs keep_activations for the fused kernel; rows must not exceed the rows
+ * of that pass (PIRRT_ERR_INVALID_ARG). */
+pirrt_status pirrt_proposal_get_activations(const pirrt_proposal *p, int32_t rows,
+                                            uint16_t *h1_out, uint16_t *h2_out);
+
 /* Replace / read the FP32 master weights (n = num_params); set clears the
  * Adam state and the accumulated gradient. */
 pirrt_status pirrt_proposal_set_weights(pirrt_proposal *p, const float *w, int64_t n);
 pirrt_status pirrt_proposal_get_weights(const pirrt_proposal *p, float *w, int64_t n);
 
 /* Samples: out_xy[r] = network(grids[scene[r]], noise[r]) for r < rows.
- * grids: [n_scenes x 4096] FP32 0/1; scene: int32[rows]; noise: [rows x 8];
- * out_xy: [rows x 2]. */
+ * grids: [n_scenes x 4096] FP32 0/1; scene: int32[rows], each in
+ * [0, n_scenes); noise: [rows x 8], 16-byte aligned; out_xy: [rows x 2],
+ * 8-byte aligned.  A scene index out of range gives PIRRT_ERR_BAD_INPUT (the
+ * row is computed for scene 0); a tensor-core wait that expires gives
+ * PIRRT_ERR_DEVICE_TIMEOUT.  The same rules hold for sample, imle_select and
+ * train_step. */
 pirrt_status pirrt_proposal_forward(pirrt_proposal *p, int32_t n_scenes, const float *grids,
                                     int32_t rows, const int32_t *scene, const float *noise,
                                     float *out_xy);

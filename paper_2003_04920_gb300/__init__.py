@@ -163,6 +163,9 @@ def load_library(path: str = LIB_PATH):
                                          ctypes.POINTER(ctypes.c_float)]),
         "pirrt_proposal_get_grads": (st, [vp, vp, i64]),
         "pirrt_proposal_zero_grads": (st, [vp]),
+        "pirrt_proposal_set_options": (st, [vp, ctypes.c_int32, ctypes.c_int32]),
+        "pirrt_proposal_get_activations": (st, [vp, ctypes.c_int32, vp, vp]),
+        "pirrt_proposal_kernel_ms": (st, [vp, ctypes.POINTER(ctypes.c_float)]),
         "pirrt_proposal_train_step": (st, [vp, ctypes.c_int32, vp, ctypes.c_int32, vp, vp,
                                            ctypes.c_int32, vp, ctypes.c_float,
                                            ctypes.POINTER(ctypes.c_float)]),
@@ -575,8 +578,14 @@ class Proposal:
             raise PirrtError(call, rc)
 
     @staticmethod
-    def _dev(x):
-        assert x.is_cuda and x.is_contiguous()
+    def _dev(x, dtype: str = "float32"):
+        """Device pointer of a contiguous CUDA tensor of the given dtype."""
+        import torch
+        want = {"float32": torch.float32, "int32": torch.int32}[dtype]
+        if not (isinstance(x, torch.Tensor) and x.is_cuda and x.is_contiguous()):
+            raise ValueError("expected a contiguous CUDA tensor")
+        if x.dtype != want:
+            raise TypeError(f"expected a {dtype} tensor, got {x.dtype}")
         return x.data_ptr()
 
     def get_weights(self):
@@ -600,12 +609,43 @@ class Proposal:
     def zero_grads(self):
         self._check("pirrt_proposal_zero_grads", self._lib.pirrt_proposal_zero_grads(self._h))
 
+    FORWARD_KERNELS = {"tcgen05": 0, "layered": 1}
+
+    def set_options(self, forward_kernel: str = "tcgen05", keep_activations: bool = False):
+        """Forward kernel of forward / sample / imle_select / train_step's
+        draws ("tcgen05": the fused tensor-core kernel, "layered": GEMM per
+        layer) and whether forward passes leave h1, h2 for get_activations."""
+        if forward_kernel not in self.FORWARD_KERNELS:
+            raise ValueError(f"forward_kernel must be one of {sorted(self.FORWARD_KERNELS)}")
+        self._check("pirrt_proposal_set_options",
+                    self._lib.pirrt_proposal_set_options(self._h,
+                                                         self.FORWARD_KERNELS[forward_kernel],
+                                                         1 if keep_activations else 0))
+
+    def kernel_ms(self) -> float:
+        """Device time of the last fused forward kernel (CUDA events), ms."""
+        ms = ctypes.c_float(0)
+        self._check("pirrt_proposal_kernel_ms",
+                    self._lib.pirrt_proposal_kernel_ms(self._h, ctypes.byref(ms)))
+        return float(ms.value)
+
+    def get_activations(self, rows: int):
+        """h1, h2 of the last forward pass's first `rows` rows as BF16 bit
+        patterns (int16 CUDA tensors [rows, 256])."""
+        import torch
+        h1 = torch.empty((int(rows), 256), dtype=torch.int16, device="cuda")
+        h2 = torch.empty((int(rows), 256), dtype=torch.int16, device="cuda")
+        self._check("pirrt_proposal_get_activations",
+                    self._lib.pirrt_proposal_get_activations(self._h, int(rows), h1.data_ptr(),
+                                                             h2.data_ptr()))
+        return h1, h2
+
     def forward(self, grids, scene, noise):
         import torch
         out = torch.empty((scene.numel(), 2), dtype=torch.float32, device="cuda")
         self._check("pirrt_proposal_forward",
                     self._lib.pirrt_proposal_forward(self._h, grids.shape[0], self._dev(grids),
-                                                     scene.numel(), self._dev(scene),
+                                                     scene.numel(), self._dev(scene, "int32"),
                                                      self._dev(noise), out.data_ptr()))
         return out
 
@@ -616,7 +656,7 @@ class Proposal:
         out = torch.empty((scene.numel(), 2), dtype=torch.float32, device="cuda")
         self._check("pirrt_proposal_sample",
                     self._lib.pirrt_proposal_sample(self._h, grids.shape[0], self._dev(grids),
-                                                    scene.numel(), self._dev(scene),
+                                                    scene.numel(), self._dev(scene, "int32"),
                                                     self._dev(noise), self._dev(uniform_xy),
                                                     self._dev(coin), float(learned_fraction),
                                                     out.data_ptr()))
@@ -627,7 +667,7 @@ class Proposal:
         pick = torch.empty(targets.shape[0], dtype=torch.int32, device="cuda")
         self._check("pirrt_proposal_imle_select",
                     self._lib.pirrt_proposal_imle_select(self._h, grids.shape[0], self._dev(grids),
-                                                         targets.shape[0], self._dev(draw_scene),
+                                                         targets.shape[0], self._dev(draw_scene, "int32"),
                                                          self._dev(targets), int(K),
                                                          self._dev(noise), pick.data_ptr()))
         return pick
@@ -636,7 +676,7 @@ class Proposal:
         loss = ctypes.c_float(0)
         self._check("pirrt_proposal_backward",
                     self._lib.pirrt_proposal_backward(self._h, grids.shape[0], self._dev(grids),
-                                                      scene.numel(), self._dev(scene),
+                                                      scene.numel(), self._dev(scene, "int32"),
                                                       self._dev(noise), self._dev(targets),
                                                       ctypes.byref(loss)))
         return float(loss.value)
@@ -652,7 +692,7 @@ class Proposal:
         loss = ctypes.c_float(0)
         self._check("pirrt_proposal_train_step",
                     self._lib.pirrt_proposal_train_step(self._h, grids.shape[0], self._dev(grids),
-                                                        targets.shape[0], self._dev(target_scene),
+                                                        targets.shape[0], self._dev(target_scene, "int32"),
                                                         self._dev(targets), int(K),
                                                         self._dev(noise), float(lr),
                                                         ctypes.byref(loss)))

@@ -25,9 +25,10 @@ constexpr int kOut = 2;
 // C[M x N] (FP32, row-major, leading dim ldc) = A[M x K] * B[N x K]^T, A and
 // B BF16 row-major with K contiguous ("NT").  M and N multiples of 64, K a
 // multiple of 32, all leading dimensions multiples of 8 elements.  A 64 x 64
-// CTA tile, four warps of 32 x 32, K in steps of 32 staged in shared memory;
-// fragments are read with 32-bit shared loads in the m16n8k16 register
-// layout.  beta = 0 overwrites C, 1 accumulates into it.
+// CTA tile (M tiles along grid x, N tiles along grid y), four warps of
+// 32 x 32, K in steps of 32 staged in shared memory; fragments are read with
+// 32-bit shared loads in the m16n8k16 register layout.  beta = 0 overwrites
+// C, 1 accumulates into it.
 // ---------------------------------------------------------------------------
 constexpr int kGT = 64, kGK = 32;
 
@@ -47,7 +48,7 @@ gemm_nt_bf16(int M, int N, int K, const __nv_bfloat16 *__restrict__ A, int lda,
     __shared__ __align__(16) __nv_bfloat16 sA[kGT][kGK + 8];  // +8: fewer bank conflicts
     __shared__ __align__(16) __nv_bfloat16 sB[kGT][kGK + 8];
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int m0 = blockIdx.y * kGT, n0 = blockIdx.x * kGT;
+    const int m0 = blockIdx.x * kGT, n0 = blockIdx.y * kGT;
     const int wm = (warp >> 1) * 32, wn = (warp & 1) * 32;
     const int gid = lane >> 2, tig = lane & 3;
     float acc[2][4][4] = {};

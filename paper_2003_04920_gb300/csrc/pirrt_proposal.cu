@@ -9,6 +9,7 @@
 #include <vector>
 
 #include "mlp_kernels.cuh"
+#include "mlp_tc.cuh"
 #include "pirrt.h"
 
 using namespace pirrt::mlp;
@@ -46,7 +47,16 @@ struct pirrt_proposal {
     float *loss = nullptr;
     int32_t *draw_scene = nullptr, *pick = nullptr;  // [R], [R]
     float *zsel = nullptr;                           // [R x 8]
+    float *hgb = nullptr;                            // [S x 256]: W1g grid + b1
+    int *status = nullptr;                           // fused kernel's error bits
     int64_t adam_t = 0;
+    int num_sms = 0;
+    int forward_kernel = PIRRT_MLP_FORWARD_TCGEN05;
+    int keep_activations = 0;
+    int last_rows = 0;       // rows of the last forward pass
+    int last_has_acts = 0;   // whether that pass left h1 / h2 in HBM
+    cudaEvent_t kev[2] = {nullptr, nullptr};  // around the last fused kernel
+    int kev_recorded = 0;
 };
 
 namespace {
@@ -67,7 +77,7 @@ int blocks_for(int64_t n) {
 
 pirrt_status gemm(pirrt_proposal *P, int M, int N, int K, const __nv_bfloat16 *A, int lda,
                   const __nv_bfloat16 *B, int ldb, float *C, int ldc, int beta) {
-    dim3 grid(N / kGT, M / kGT);
+    dim3 grid(M / kGT, N / kGT);
     gemm_nt_bf16<<<grid, 128, 0, P->stream>>>(M, N, K, A, lda, B, ldb, C, ldc, beta);
     PCK(cudaGetLastError());
     return PIRRT_OK;
@@ -114,12 +124,101 @@ pirrt_status forward_rows(pirrt_proposal *P, int rows, const int32_t *scene, con
     return PIRRT_OK;
 }
 
+// hgb[s][j] = hg[s][j] + b1[j]: the per-scene part of layer 1 (the first
+// addition of the layered path's layer-1 sum, in the same order)
+__global__ void scene_bias(int n_scenes, const float *__restrict__ hg, const float *__restrict__ b1,
+                           float *__restrict__ hgb) {
+    for (int i = blockIdx.x * blockDim.x + threadIdx.x; i < n_scenes * kHidden;
+         i += gridDim.x * blockDim.x)
+        hgb[i] = hg[i] + b1[i % kHidden];
+}
+
+// The fused tcgen05 forward pass over `rows` rows (after scene_features):
+// y and / or the mixture `out` (see tc::FwdArgs).  The error bits are read
+// after the caller's stream synchronisation (read_status).
+pirrt_status forward_fused(pirrt_proposal *P, int n_scenes, int rows, const int32_t *scene,
+                           const float *z, float *y, const float *uniform_xy, const float *coin,
+                           float frac, float *out) {
+    if (rows < 1 || rows > P->max_rows) return PIRRT_ERR_CAPACITY;
+    if (reinterpret_cast<uintptr_t>(z) % 16 || reinterpret_cast<uintptr_t>(y) % 8 ||
+        reinterpret_cast<uintptr_t>(out) % 8 || reinterpret_cast<uintptr_t>(uniform_xy) % 8)
+        return PIRRT_ERR_INVALID_ARG;
+    PCK(cudaMemsetAsync(P->status, 0, sizeof(int), P->stream));
+    scene_bias<<<blocks_for((int64_t)n_scenes * kHidden), 256, 0, P->stream>>>(n_scenes, P->hg,
+                                                                              P->w + ob1, P->hgb);
+    PCK(cudaGetLastError());
+    tc::FwdArgs a{};
+    a.rows = rows;
+    a.n_scenes = n_scenes;
+    a.hgb = P->hgb;
+    a.scene = scene;
+    a.z = z;
+    a.W1n = P->w + oW1n;
+    a.W2b = P->W2b;
+    a.b2 = P->w + ob2;
+    a.W3b = P->W3b;
+    a.b3 = P->w + ob3;
+    a.y = y;
+    a.uniform_xy = uniform_xy;
+    a.coin = coin;
+    a.frac = frac;
+    a.out = out;
+    a.cap_h1 = P->keep_activations ? P->h1 : nullptr;
+    a.cap_h2 = P->keep_activations ? P->h2 : nullptr;
+    a.status = P->status;
+    const int tiles = (rows + tc::kRowsPerTile - 1) / tc::kRowsPerTile;
+    const int grid = tiles < P->num_sms ? tiles : P->num_sms;
+    PCK(cudaEventRecord(P->kev[0], P->stream));
+    tc::mlp_forward_tc<<<grid, tc::kThreads, tc::kSmemBytes, P->stream>>>(a);
+    PCK(cudaGetLastError());
+    PCK(cudaEventRecord(P->kev[1], P->stream));
+    P->kev_recorded = 1;
+    P->last_rows = rows;
+    P->last_has_acts = P->keep_activations;
+    return PIRRT_OK;
+}
+
+// Error bits of the last fused pass (call after a stream synchronisation).
+pirrt_status read_status(pirrt_proposal *P) {
+    int st = 0;
+    PCK(cudaMemcpy(&st, P->status, sizeof(int), cudaMemcpyDeviceToHost));
+    if (st & tc::kErrTimeout) return PIRRT_ERR_DEVICE_TIMEOUT;
+    if (st & tc::kErrScene) return PIRRT_ERR_BAD_INPUT;
+    return PIRRT_OK;
+}
+
+// The forward pass of `rows` rows by the selected kernel into y (P->y if
+// null); a mixture into `out` when given.
+pirrt_status forward_any(pirrt_proposal *P, int n_scenes, int rows, const int32_t *scene,
+                         const float *z, float *y, const float *uniform_xy, const float *coin,
+                         float frac, float *out) {
+    if (P->forward_kernel == PIRRT_MLP_FORWARD_TCGEN05)
+        return forward_fused(P, n_scenes, rows, scene, z, y ? y : P->y, uniform_xy, coin, frac,
+                             out);
+    pirrt_status rc = forward_rows(P, rows, scene, z);
+    if (rc) return rc;
+    PCK(cudaMemsetAsync(P->status, 0, sizeof(int), P->stream));
+    P->last_rows = rows;
+    P->last_has_acts = 1;
+    if (y && y != P->y)
+        PCK(cudaMemcpyAsync(y, P->y, sizeof(float) * kOut * (size_t)rows, cudaMemcpyDeviceToDevice,
+                            P->stream));
+    if (out) {
+        mix_samples<<<blocks_for(rows), 256, 0, P->stream>>>(rows, P->y, uniform_xy, coin, frac, out);
+        PCK(cudaGetLastError());
+    }
+    return PIRRT_OK;
+}
+
 void free_all(pirrt_proposal *P) {
     void *bufs[] = {P->w, P->m, P->v, P->grad, P->W1gb, P->W2b, P->W2Tb, P->W3b, P->gridb,
                     P->gridT, P->hg, P->a1, P->a2, P->dh1, P->da2f, P->h1, P->h1T, P->h2,
-                    P->da2b, P->da2T, P->y, P->D, P->DT, P->loss, P->draw_scene, P->pick, P->zsel};
+                    P->da2b, P->da2T, P->y, P->D, P->DT, P->loss, P->draw_scene, P->pick, P->zsel,
+                    P->hgb, P->status};
     for (void *b : bufs)
         if (b) cudaFree(b);
+    for (cudaEvent_t &e : P->kev)
+        if (e) cudaEventDestroy(e);
 }
 
 // splitmix64: a counter-based generator for the initial weights
@@ -192,7 +291,16 @@ pirrt_status pirrt_proposal_create(int32_t max_scenes, int32_t max_rows, uint64_
     PA(P->draw_scene, sizeof(int32_t) * R);
     PA(P->pick, sizeof(int32_t) * R);
     PA(P->zsel, f * R * kNoise);
+    PA(P->hgb, f * S * kHidden);
+    PA(P->status, sizeof(int));
 #undef PA
+    if (cudaEventCreate(&P->kev[0]) != cudaSuccess || cudaEventCreate(&P->kev[1]) != cudaSuccess ||
+        cudaDeviceGetAttribute(&P->num_sms, cudaDevAttrMultiProcessorCount, device) != cudaSuccess ||
+        cudaFuncSetAttribute(tc::mlp_forward_tc, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                             tc::kSmemBytes) != cudaSuccess) {
+        cudaGetLastError();
+        return bail(PIRRT_ERR_CUDA);
+    }
     // He-uniform initial weights (fan-in of each layer), zero biases
     std::vector<float> h(kParams, 0.f);
     uint64_t st = seed;
@@ -255,11 +363,11 @@ pirrt_status pirrt_proposal_forward(pirrt_proposal *P, int32_t n_scenes, const f
     PCK(cudaSetDevice(P->device));
     pirrt_status rc = scene_features(P, n_scenes, grids);
     if (rc) return rc;
-    if ((rc = forward_rows(P, rows, scene, noise))) return rc;
-    PCK(cudaMemcpyAsync(out_xy, P->y, sizeof(float) * kOut * (size_t)rows, cudaMemcpyDeviceToDevice,
-                        P->stream));
+    if ((rc = forward_any(P, n_scenes, rows, scene, noise, out_xy, nullptr, nullptr, 0.f,
+                          nullptr)))
+        return rc;
     PCK(cudaStreamSynchronize(P->stream));
-    return PIRRT_OK;
+    return read_status(P);
 }
 
 pirrt_status pirrt_proposal_sample(pirrt_proposal *P, int32_t n_scenes, const float *grids,
@@ -272,12 +380,11 @@ pirrt_status pirrt_proposal_sample(pirrt_proposal *P, int32_t n_scenes, const fl
     PCK(cudaSetDevice(P->device));
     pirrt_status rc = scene_features(P, n_scenes, grids);
     if (rc) return rc;
-    if ((rc = forward_rows(P, rows, scene, noise))) return rc;
-    mix_samples<<<blocks_for(rows), 256, 0, P->stream>>>(rows, P->y, uniform_xy, coin,
-                                                          learned_fraction, out_xy);
-    PCK(cudaGetLastError());
+    if ((rc = forward_any(P, n_scenes, rows, scene, noise, nullptr, uniform_xy, coin,
+                          learned_fraction, out_xy)))
+        return rc;
     PCK(cudaStreamSynchronize(P->stream));
-    return PIRRT_OK;
+    return read_status(P);
 }
 
 pirrt_status pirrt_proposal_imle_select(pirrt_proposal *P, int32_t n_scenes, const float *grids,
@@ -287,13 +394,16 @@ pirrt_status pirrt_proposal_imle_select(pirrt_proposal *P, int32_t n_scenes, con
     if (!P || !grids || !draw_scene || !targets || !noise || !pick || K < 1 || n_targets < 1)
         return PIRRT_ERR_INVALID_ARG;
     PCK(cudaSetDevice(P->device));
+    if ((int64_t)n_targets * K > P->max_rows) return PIRRT_ERR_CAPACITY;
     pirrt_status rc = scene_features(P, n_scenes, grids);
     if (rc) return rc;
-    if ((rc = forward_rows(P, n_targets * K, draw_scene, noise))) return rc;
+    if ((rc = forward_any(P, n_scenes, n_targets * K, draw_scene, noise, nullptr, nullptr, nullptr,
+                          0.f, nullptr)))
+        return rc;
     imle_select<<<blocks_for(n_targets), 256, 0, P->stream>>>(n_targets, K, P->y, targets, pick);
     PCK(cudaGetLastError());
     PCK(cudaStreamSynchronize(P->stream));
-    return PIRRT_OK;
+    return read_status(P);
 }
 
 pirrt_status pirrt_proposal_backward(pirrt_proposal *P, int32_t n_scenes, const float *grids,
@@ -304,6 +414,8 @@ pirrt_status pirrt_proposal_backward(pirrt_proposal *P, int32_t n_scenes, const 
     pirrt_status rc = scene_features(P, n_scenes, grids);
     if (rc) return rc;
     if ((rc = forward_rows(P, rows, scene, noise))) return rc;
+    P->last_rows = rows;
+    P->last_has_acts = 1;
     const int Rp = pad64(rows), Sp = pad64(n_scenes);
     output_backward<<<kHidden, 256, 0, P->stream>>>(rows, Rp, P->y, targets, P->h2, P->W3b, P->a2,
                                                    P->grad + oW3, P->grad + ob3, P->da2b, P->da2T,
@@ -371,7 +483,9 @@ pirrt_status pirrt_proposal_train_step(pirrt_proposal *P, int32_t n_scenes, cons
     PCK(cudaGetLastError());
     pirrt_status rc = scene_features(P, n_scenes, grids);
     if (rc) return rc;
-    if ((rc = forward_rows(P, n_targets * K, P->draw_scene, noise))) return rc;
+    if ((rc = forward_any(P, n_scenes, n_targets * K, P->draw_scene, noise, nullptr, nullptr,
+                          nullptr, 0.f, nullptr)))
+        return rc;
     imle_select<<<blocks_for(n_targets), 256, 0, P->stream>>>(n_targets, K, P->y, targets, P->pick);
     gather_noise<<<blocks_for((int64_t)n_targets * kNoise), 256, 0, P->stream>>>(n_targets, K, noise,
                                                                                 P->pick, P->zsel);
@@ -379,7 +493,36 @@ pirrt_status pirrt_proposal_train_step(pirrt_proposal *P, int32_t n_scenes, cons
     if ((rc = pirrt_proposal_backward(P, n_scenes, grids, n_targets, target_scene, P->zsel, targets,
                                       loss_out)))
         return rc;
+    // the selection pass's error bits (the backward pass synchronised)
+    if ((rc = read_status(P))) return rc;
     return pirrt_proposal_adam(P, lr, 0.9f, 0.999f, 1e-8f);
+}
+
+pirrt_status pirrt_proposal_set_options(pirrt_proposal *P, int32_t forward_kernel,
+                                        int32_t keep_activations) {
+    if (!P || (forward_kernel != PIRRT_MLP_FORWARD_TCGEN05 &&
+               forward_kernel != PIRRT_MLP_FORWARD_LAYERED))
+        return PIRRT_ERR_INVALID_ARG;
+    P->forward_kernel = forward_kernel;
+    P->keep_activations = keep_activations ? 1 : 0;
+    return PIRRT_OK;
+}
+
+pirrt_status pirrt_proposal_kernel_ms(const pirrt_proposal *P, float *ms) {
+    if (!P || !ms || !P->kev_recorded) return PIRRT_ERR_INVALID_ARG;
+    PCK(cudaEventSynchronize(P->kev[1]));
+    PCK(cudaEventElapsedTime(ms, P->kev[0], P->kev[1]));
+    return PIRRT_OK;
+}
+
+pirrt_status pirrt_proposal_get_activations(const pirrt_proposal *P, int32_t rows,
+                                            uint16_t *h1_out, uint16_t *h2_out) {
+    if (!P || rows < 1 || rows > P->last_rows || !P->last_has_acts) return PIRRT_ERR_INVALID_ARG;
+    const size_t bytes = sizeof(__nv_bfloat16) * kHidden * (size_t)rows;
+    if (h1_out) PCK(cudaMemcpyAsync(h1_out, P->h1, bytes, cudaMemcpyDeviceToDevice, P->stream));
+    if (h2_out) PCK(cudaMemcpyAsync(h2_out, P->h2, bytes, cudaMemcpyDeviceToDevice, P->stream));
+    PCK(cudaStreamSynchronize(P->stream));
+    return PIRRT_OK;
 }
 
 pirrt_status pirrt_proposal_zero_grads(pirrt_proposal *P) {

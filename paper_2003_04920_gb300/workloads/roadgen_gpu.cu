@@ -14,7 +14,7 @@ namespace {
 
 constexpr int kT = 256;
 constexpr int kMaxDim = 8;
-constexpr int kMaxK = 64;
+constexpr int kMaxK = 128;
 
 #define RG_CK(x)                                 \
     do {                                         \
@@ -352,15 +352,35 @@ knn_kernel(long long n, Grid g, int k, const float *__restrict__ spts, const int
     }
 }
 
-// Vertices [q0, q1): the k nearest among the vertices that precede each one
-// (the grid holds vertices [0, q1)), -1 where fewer exist.  Row i - q0 of knn.
+// The new vertices [v0, m) in the grid's cell order (positions p of the
+// sorted ids with sid[p] >= v0): flags, then a compaction by their scan.
+__global__ void query_flags(long long m, long long v0, const int *__restrict__ sid,
+                            int *__restrict__ flag) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m;
+         p += (long long)gridDim.x * blockDim.x)
+        flag[p] = sid[p] >= v0 ? 1 : 0;
+}
+
+__global__ void query_compact(long long m, long long v0, const int *__restrict__ sid,
+                              const long long *__restrict__ pos, int *__restrict__ qlist) {
+    for (long long p = blockIdx.x * (long long)blockDim.x + threadIdx.x; p < m;
+         p += (long long)gridDim.x * blockDim.x)
+        if (sid[p] >= v0) qlist[pos[p]] = sid[p];
+}
+
+// Vertices [q0, q1), visited in cell order (qlist, so that neighbouring
+// threads scan the same cells): the k nearest among the vertices that precede
+// each one (the grid holds vertices [0, q1)), -1 where fewer exist.  Row
+// i - q0 of knn.
 __global__ void __launch_bounds__(kT)
 knn_pred_kernel(long long q0, long long q1, Grid g, int k, const double *__restrict__ pts,
                 const float *__restrict__ spts, const int *__restrict__ sid,
-                const long long *__restrict__ start, int *__restrict__ knn) {
+                const long long *__restrict__ start, const int *__restrict__ qlist,
+                int *__restrict__ knn) {
     const int dim = g.dim;
-    for (long long i = q0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < q1;
-         i += (long long)gridDim.x * blockDim.x) {
+    for (long long t = blockIdx.x * (long long)blockDim.x + threadIdx.x; t < q1 - q0;
+         t += (long long)gridDim.x * blockDim.x) {
+        const long long i = qlist[t];
         float q[kMaxDim];
         for (int d = 0; d < dim; ++d) q[d] = (float)pts[i * dim + d];
         float bd[kMaxK];
@@ -675,27 +695,29 @@ namespace {
 
 // Links of the new vertices [v0, v1) to their nearest predecessors that are
 // collision-free with a positive length: keep flags and a count per row.
+// One thread per (new vertex, link), vertices in cell order: keep flags and
+// the per-row count of the collision-free, positive-length links (rowc
+// cleared before).
 __global__ void pred_edge_mark(long long v0, long long v1, int dim, const double *__restrict__ pts,
-                               int k, const int *__restrict__ knn, int n_obs,
-                               const double *__restrict__ centers, const double *__restrict__ radii,
-                               int mode, int n_check, unsigned char *__restrict__ keep,
-                               int *__restrict__ rowc) {
-    for (long long i = v0 + blockIdx.x * (long long)blockDim.x + threadIdx.x; i < v1;
-         i += (long long)gridDim.x * blockDim.x) {
+                               int k, const int *__restrict__ knn, const int *__restrict__ qlist,
+                               int n_obs, const double *__restrict__ centers,
+                               const double *__restrict__ radii, int mode, int n_check,
+                               unsigned char *__restrict__ keep, int *__restrict__ rowc) {
+    const long long total = (v1 - v0) * k;
+    for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < total;
+         e += (long long)gridDim.x * blockDim.x) {
+        const long long i = qlist[e / k];
+        const int a = (int)(e % k);
         const long long r = i - v0;
-        int c = 0;
-        for (int a = 0; a < k; ++a) {
-            const int j = knn[r * k + a];
-            bool ok = j >= 0;
-            if (ok) {
-                const double *pa = pts + (long long)j * dim, *pb = pts + i * dim;
-                ok = d2_64(pa, pb, dim) > 0.0 &&
-                     segment_free(pa, pb, dim, n_obs, centers, radii, mode, n_check);
-            }
-            keep[r * k + a] = ok ? 1 : 0;
-            c += ok ? 1 : 0;
+        const int j = knn[r * k + a];
+        bool ok = j >= 0;
+        if (ok) {
+            const double *pa = pts + (long long)j * dim, *pb = pts + i * dim;
+            ok = d2_64(pa, pb, dim) > 0.0 &&
+                 segment_free(pa, pb, dim, n_obs, centers, radii, mode, n_check);
         }
-        rowc[r] = c;
+        keep[r * k + a] = ok ? 1 : 0;
+        if (ok) atomicAdd(&rowc[r], 1);
     }
 }
 
@@ -748,14 +770,17 @@ struct rgg_explorer {
     double *centers = nullptr, *radii = nullptr, *pts = nullptr;
     float *spts = nullptr;
     int *sid = nullptr, *cnt = nullptr, *knn = nullptr, *rowc = nullptr;
+    int *qflag = nullptr, *qlist = nullptr;
     long long *cell_of = nullptr, *start = nullptr, *rowoff = nullptr, *tiles = nullptr;
+    long long *qpos = nullptr;
     unsigned char *keep = nullptr;
 };
 
 extern "C" void rgg_explore_destroy(rgg_explorer *x) {
     if (!x) return;
     void *bufs[] = {x->centers, x->radii, x->pts, x->spts, x->sid, x->cnt, x->knn, x->rowc,
-                    x->cell_of, x->start, x->rowoff, x->tiles, x->keep};
+                    x->cell_of, x->start, x->rowoff, x->tiles, x->keep, x->qflag, x->qlist,
+                    x->qpos};
     for (void *b : bufs)
         if (b) cudaFree(b);
     delete x;
@@ -798,7 +823,10 @@ extern "C" int rgg_explore_create(int32_t dim, double lo, double hi, int32_t n_o
               cudaMalloc(&x->cnt, sizeof(int) * (x->cells_max + 1)) == cudaSuccess &&
               cudaMalloc(&x->start, sizeof(long long) * (x->cells_max + 1)) == cudaSuccess &&
               cudaMalloc(&x->tiles, sizeof(long long) *
-                                        (std::max(x->cells_max, mb) + 1 + kTile) / kTile) == cudaSuccess &&
+                                        (std::max<long long>(x->cells_max, n) + 1 + kTile) / kTile) == cudaSuccess &&
+              cudaMalloc(&x->qflag, sizeof(int) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&x->qpos, sizeof(long long) * (n + 1)) == cudaSuccess &&
+              cudaMalloc(&x->qlist, sizeof(int) * mb) == cudaSuccess &&
               cudaMalloc(&x->knn, sizeof(int) * mb * k) == cudaSuccess &&
               cudaMalloc(&x->keep, mb * k) == cudaSuccess &&
               cudaMalloc(&x->rowc, sizeof(int) * (mb + 1)) == cudaSuccess &&
@@ -846,15 +874,21 @@ extern "C" int rgg_explore_block(rgg_explorer *x, int64_t v0, int64_t v1, int32_
     cell_scatter<<<grid_of(v1), kT, 0, st>>>(v1, dim, x->pts, x->cell_of, x->start, x->cnt,
                                              x->spts, x->sid);
     RG_CKL();
+    // the new vertices in cell order
+    query_flags<<<grid_of(v1), kT, 0, st>>>(v1, v0, x->sid, x->qflag);
+    RG_CKL();
+    if (int rc = exclusive_scan(x->qflag, v1, x->qpos, x->tiles, st)) return rc;
+    query_compact<<<grid_of(v1), kT, 0, st>>>(v1, v0, x->sid, x->qpos, x->qlist);
+    RG_CKL();
     // nearest predecessors of the new vertices, then their edges
     knn_pred_kernel<<<grid_of(nb), kT, 0, st>>>(v0, v1, g, k, x->pts, x->spts, x->sid, x->start,
-                                                x->knn);
+                                                x->qlist, x->knn);
     RG_CKL();
-    pred_edge_mark<<<grid_of(nb), kT, 0, st>>>(v0, v1, dim, x->pts, k, x->knn, x->n_obs,
-                                               x->centers, x->radii, x->mode, x->n_check, x->keep,
-                                               x->rowc);
+    RG_CK(cudaMemsetAsync(x->rowc, 0, sizeof(int) * (nb + 1), st));
+    pred_edge_mark<<<grid_of(nb * k), kT, 0, st>>>(v0, v1, dim, x->pts, k, x->knn, x->qlist,
+                                                   x->n_obs, x->centers, x->radii, x->mode,
+                                                   x->n_check, x->keep, x->rowc);
     RG_CKL();
-    RG_CK(cudaMemsetAsync(x->rowc + nb, 0, sizeof(int), st));
     if (int rc = exclusive_scan(x->rowc, nb + 1, x->rowoff, x->tiles, st)) return rc;
     RG_CK(cudaMemcpyAsync(m_pinned, x->rowoff + nb, sizeof(int64_t), cudaMemcpyDeviceToHost, st));
     if (x->cost_f64)

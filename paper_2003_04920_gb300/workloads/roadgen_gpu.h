@@ -52,7 +52,7 @@ int rgg_sample(int32_t dim, double lo, double hi, int32_t n_obs, const double *c
 
 /* k nearest neighbours (ids, nearest first) of every point, by a uniform grid
  * of cells of side about `cell` (0 = chosen from n, k and the box).  knn: n x k
- * int32.  Needs k < n, k <= 64. */
+ * int32.  Needs k < n, k <= 128. */
 int rgg_knn(int32_t dim, double lo, double hi, int64_t n, const double *points, int32_t k,
             double cell, int32_t *knn, void *stream);
 

@@ -67,3 +67,40 @@ def test_train_and_compare_small(torch):
     summ = L.summarize(res)[2000]
     assert summ["scenes"] == 3
     prop.close(); ev.close()
+
+
+def test_device_pipeline_comparison_reports_signs(torch, record_property):
+    """The device-resident workflow at a small scale: GPU-built roadmaps,
+    near-path targets, IMLE training, reference paths, the four arms
+    (uniform, learned mixture, ideal mixture, fixed corridor) paired by
+    scene, the spread check, and the sign of each arm's paired difference.
+    A proposal that puts half of the samples near the optimal path (the
+    ideal arm) must make the start-goal path cheaper than uniform sampling;
+    the learned arm's sign is reported, not asserted."""
+    from paper_2003_04920_gb300 import Proposal
+    grids, targets, costs, kept = L.dev_training_set(range(12), 6000, band=0.02, chunk=6)
+    assert len(kept) > 0 and grids.shape == (len(kept), 4096)
+    for s, t in zip(kept, targets):
+        assert t.shape[1] == 2 and t.shape[0] > 0
+        assert not W.c5_scene(s).inside(t.cpu().numpy().astype(np.float64)).any()
+    assert np.all(costs >= np.linalg.norm(L.X_GOAL - L.X_INIT) - 1e-9)
+    prop = Proposal(4, 4 * 32 * 8, seed=1)
+    losses, _ = L.train(prop, grids, targets, 200, scenes_per_step=4, targets_per_scene=32, K=8)
+    assert np.all(np.isfinite(losses)) and losses[-20:].mean() < losses[:20].mean()
+    ev = Proposal(1, 1 << 16, seed=1)
+    ev.set_weights(prop.get_weights())
+    seeds = list(range(2000, 2016))
+    refs = L.reference_paths(seeds, 40_000)
+    res = L.dev_compare(ev, seeds, [8000], refs, chunk=8)
+    table = L.paired_table(res)["8000"]
+    for arm in ("learned", "ideal", "corridor"):
+        assert table[arm]["both_solved"] > 0
+        assert table[arm]["sign"] in ("cheaper", "costlier", "no difference")
+        record_property(f"{arm}_sign", table[arm]["sign"])
+        record_property(f"{arm}_paired_diff", table[arm]["paired_diff"])
+    assert table["ideal"]["paired_diff"] < 0, table["ideal"]
+    sp = L.spread(ev, seeds, refs, m=4000)
+    assert 0.0 <= sp["within_band"] <= 1.0 and 0.0 <= sp["path_coverage"] <= 1.0
+    print({arm: (table[arm]["sign"], table[arm]["paired_diff"]) for arm in
+           ("learned", "ideal", "corridor")}, sp)
+    prop.close(); ev.close()

@@ -102,9 +102,11 @@ def _upload(torch, prop, params, grids, scene, z, target):
     return dev(grids), dev(scene), dev(z), dev(target)
 
 
-def test_forward_matches_oracle_elementwise(torch):
+@pytest.mark.parametrize("kernel", ["tcgen05", "layered"])
+def test_forward_matches_oracle_elementwise(torch, kernel):
     params, grids, scene, z, target = _dyadic(seed=0)
     prop = P.Proposal(8, 1024, seed=3)
+    prop.set_options(kernel)
     gd, sd, zd, _ = _upload(torch, prop, params, grids, scene, z, target)
     y = prop.forward(gd, sd, zd).cpu().numpy().astype(np.float64)
     f = M.forward(params, grids, scene, z.astype(np.float64), rounded=True)
@@ -253,4 +255,86 @@ def test_sample_mixture(torch):
         learned = coin < frac
         np.testing.assert_array_equal(out[learned], y[learned])
         np.testing.assert_array_equal(out[~learned], uni[~learned])
+    prop.close()
+
+
+def _bf16_ulps(a, b):
+    """Distance in BF16 steps between two arrays of BF16 bit patterns (int16)."""
+    def key(x):
+        x = x.astype(np.int32) & 0xFFFF
+        return np.where(x & 0x8000, -(x & 0x7FFF), x)
+    return np.abs(key(a) - key(b))
+
+
+def _bf16_value(bits):
+    """FP64 values of BF16 bit patterns (int16)."""
+    u = (bits.astype(np.int32) & 0xFFFF).astype(np.uint32) << 16
+    return u.view(np.float32).astype(np.float64)
+
+
+def _bf16_step(x):
+    """One BF16 step at |x| (0 at 0)."""
+    ax = np.abs(x)
+    e = np.floor(np.log2(np.where(ax > 0, ax, 1.0)))
+    return np.where(ax > 0, 2.0 ** (e - 7), 0.0)
+
+
+@pytest.mark.parametrize("rows", [1, 128, 152 * 128 * 2 + 77])
+def test_fused_forward_matches_layered(torch, rows):
+    """The fused tcgen05 kernel against the layer-by-layer path on the same
+    weights (He-uniform, not dyadic), element by element.  Both round h1,
+    h2 to BF16 after FP32 sums taken in different orders, so an activation
+    near a BF16 rounding midpoint may land one step apart; such a step then
+    moves every later sum of its row.  The bounds follow that propagation:
+    h1 at most one BF16 step apart (and rarely); h2 within the h1 differences
+    carried through |W2| plus FP32 accumulation (ACC per unit of sum |terms|)
+    plus one BF16 step; y within a quarter (the sigmoid's slope bound) of
+    the h2 differences carried through |W3| plus accumulation.  The largest
+    case spans more than two passes of the persistent grid, scenes mixed
+    within tiles, and a ragged last tile."""
+    rng = np.random.default_rng(rows)
+    S = 5
+    grids = (rng.random((S, M.GRID)) < 0.25).astype(np.float32)
+    scene = rng.integers(0, S, rows).astype(np.int32)
+    z = rng.normal(size=(rows, M.NOISE)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prop = P.Proposal(S, rows, seed=31)
+    out = {}
+    for kernel in ("layered", "tcgen05"):
+        prop.set_options(kernel, keep_activations=True)
+        y = prop.forward(dev(grids), dev(scene), dev(z)).cpu().numpy().astype(np.float64)
+        h1, h2 = (t.cpu().numpy() for t in prop.get_activations(rows))
+        out[kernel] = (y, h1, h2)
+    w = M.unpack(prop.get_weights().cpu().numpy().astype(np.float64))
+    W2b, W3b = np.abs(M.bf16(w["W2"])), np.abs(M.bf16(w["W3"]))
+    (yl, h1l, h2l), (yf, h1f, h2f) = out["layered"], out["tcgen05"]
+    d1 = _bf16_ulps(h1f, h1l)
+    assert d1.max() <= 1 and (d1 > 0).mean() < 1e-3, (d1.max(), (d1 > 0).mean())
+    v1l, v1f = _bf16_value(h1l), _bf16_value(h1f)
+    v2l, v2f = _bf16_value(h2l), _bf16_value(h2f)
+    bound2 = (np.abs(v1f - v1l) @ W2b.T + ACC * (np.abs(v1l) @ W2b.T)
+              + np.maximum(_bf16_step(v2l), _bf16_step(v2f)))
+    bad = np.abs(v2f - v2l) > bound2
+    assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(v2f - v2l) - bound2)))
+    assert (_bf16_ulps(h2f, h2l) > 0).mean() < 0.05
+    bound3 = 0.25 * (np.abs(v2f - v2l) @ W3b.T + ACC * (np.abs(v2l) @ W3b.T)) + 2.0 ** -21
+    bad = np.abs(yf - yl) > bound3
+    assert not bad.any(), (int(bad.sum()), float(np.max(np.abs(yf - yl) - bound3)))
+    assert np.all(np.isfinite(yf)) and np.all((yf >= 0) & (yf <= 1))
+    prop.close()
+
+
+def test_fused_forward_rejects_scene_out_of_range(torch):
+    rng = np.random.default_rng(5)
+    grids = (rng.random((3, M.GRID)) < 0.25).astype(np.float32)
+    scene = np.array([0, 1, 2, 7] * 40, dtype=np.int32)
+    z = rng.normal(size=(len(scene), M.NOISE)).astype(np.float32)
+    dev = lambda a: torch.from_numpy(np.ascontiguousarray(a)).cuda()
+    prop = P.Proposal(3, 256, seed=1)
+    with pytest.raises(P.PirrtError) as e:
+        prop.forward(dev(grids), dev(scene), dev(z))
+    assert e.value.status == P.PIRRT_ERR_BAD_INPUT
+    # the handle stays usable
+    y = prop.forward(dev(grids), dev(scene % 3), dev(z)).cpu().numpy()
+    assert np.all((y >= 0) & (y <= 1))
     prop.close()

@@ -209,12 +209,16 @@ def _gpu():
 
 
 @pytest.mark.gpu
-@pytest.mark.parametrize("case", ["6d-points", "2d-exact"])
+@pytest.mark.parametrize("case", ["6d-points", "2d-exact", "2d-large-k"])
 def test_gpu_generator_matches_cpu_reference(case):
     torch, G = _gpu()
     if case == "6d-points":
         scene = W._draw_scene(np.random.default_rng(31), 6, -math.pi, math.pi, 64, 0.3, 0.8, [])
         n, k, exact, seed, cost_dtype = 1500, 24, False, 0x1234_5678_9ABC, np.float32
+    elif case == "2d-large-k":
+        # k = ceil(2e ln N) at N = 10^6 (the 2-D and learned-proposal roadmaps)
+        scene = W._draw_scene(np.random.default_rng(33), 2, 0.0, 1.0, 200, 0.01, 0.04, [])
+        n, k, exact, seed, cost_dtype = 2500, 76, True, 5005, np.float32
     else:
         scene = W._draw_scene(np.random.default_rng(32), 2, 0.0, 1.0, 60, 0.01, 0.05, [])
         n, k, exact, seed, cost_dtype = 3000, 16, True, 77, np.float64

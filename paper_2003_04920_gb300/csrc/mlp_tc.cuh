@@ -13,28 +13,33 @@
 //   layer 1: D[128 x 256] = Z[128 x 16] * W1n'[256 x 16]^T   (K padded 8 -> 16)
 //            h1 = relu(D + (W1g grid + b1)[scene])  -> H (shared, BF16)
 //   layer 2: D[128 x 256] = H[128 x 256] * W2[256 x 256]^T
-//            h2 = relu(D + b2)                       -> H (overwrites h1)
-//   layer 3: D[128 x 16]  = H[128 x 256] * W3'[16 x 256]^T  (N padded 2 -> 16)
-//            y = sigmoid(D[:, 0:2] + b3)
+//            h2 = relu(D + b2), rounded to BF16, kept in registers
+//   layer 3: y = sigmoid(W3 h2 + b3): two FP32 dot products per row on the
+//            CUDA cores (N = 2 is too narrow for an MMA round trip), each
+//            thread over its 128 columns, the two halves added in shared
+//            memory
 //
 // The grid part of layer 1 (one 4096 x 256 product per scene) is computed
 // once per call outside this kernel; W1g grid + b1 arrives per scene.  The
 // rounding points are those of the unfused path: BF16 weights, BF16 noise,
 // BF16 h1 and h2, FP32 accumulation, FP32 bias additions and sigmoid.
 //
-// Persistent: one CTA of 256 threads per SM (about 214 KB of shared memory:
+// Persistent: one CTA of 256 threads per SM (about 205 KB of shared memory:
 // W2 stays resident across tiles), tiles strided over the grid.  One thread
-// issues the MMAs.  Layers 1 and 2 are issued as two N = 128 halves, each
-// committed to its own mbarrier, so the first half's epilogue runs while the
-// tensor core computes the second (layer 2's h2 is stored only after both
-// halves are done, since both read h1 from the same buffer).  Every wait is
-// bounded; a thread whose wait expires reports it at the next CTA barrier
-// (__syncthreads_or), the CTA stops, waits a bounded time more for its MMAs in
-// flight, frees its tensor memory and returns with an error bit set.
+// issues the MMAs.  Layer 2 is issued as two N = 128 halves, each committed to
+// its own mbarrier, so the first half's epilogue runs while the tensor core
+// computes the second; right behind them the same thread issues the next
+// tile's layer 1 into the other half of a 512-column TMEM allocation (its
+// noise was prefetched into registers and staged while this tile's layer-1
+// epilogue ran), so a tile starts with its layer-1 result already waiting.
+// Every wait is bounded; a thread whose wait expires reports it at the next
+// CTA barrier (__syncthreads_or), the CTA stops, waits a bounded time more
+// for its MMAs in flight, frees its tensor memory and returns with an error
+// bit set.
 //
 // Operand layouts in shared memory (K-major, i.e. each row's K elements
 // contiguous, as tcgen05 descriptors describe them):
-//   * 128-byte swizzle for H, W2 and W3': 8-row groups of 8 x 128 bytes, the
+//   * 128-byte swizzle for H and W2: 8-row groups of 8 x 128 bytes, the
 //     16-byte chunk c of row r stored at chunk c ^ (r mod 8); K in blocks of
 //     64 elements, one such block of all rows after another;
 //   * no swizzle for the K = 16 operands Z and W1n': 8 x 16-byte core
@@ -53,24 +58,23 @@ namespace tc {
 
 constexpr int kRowsPerTile = 128;
 constexpr int kThreads = 256;
-constexpr uint32_t kTmemCols = 256;
-constexpr int kN3 = 16;   // layer-3 N padded to the smallest M = 128 shape
+constexpr uint32_t kTmemCols = 512;  // two 256-column accumulators (alternate tiles)
 constexpr int kK1 = 16;   // layer-1 K padded to one MMA step
 
 // shared-memory map, offsets from a 1024-byte-aligned base
 constexpr int kW2Bytes = kHidden * kHidden * 2;     // 131072
 constexpr int kHBytes = kRowsPerTile * kHidden * 2;  // 65536
-constexpr int kW3Bytes = kN3 * kHidden * 2;          // 8192
 constexpr int kZBytes = kRowsPerTile * kK1 * 2;      // 4096
 constexpr int kW1Bytes = kHidden * kK1 * 2;          // 8192
 constexpr int oW2 = 0;
 constexpr int oH = oW2 + kW2Bytes;
-constexpr int oW3 = oH + kHBytes;
-constexpr int oZ = oW3 + kW3Bytes;
+constexpr int oZ = oH + kHBytes;
 constexpr int oW1 = oZ + kZBytes;
-constexpr int oB2 = oW1 + kW1Bytes;         // 256 FP32
-constexpr int oBar = oB2 + kHidden * 4;     // two mbarriers (column halves), 8 bytes each
-constexpr int oTmem = oBar + 16;            // TMEM base address written by tcgen05.alloc
+constexpr int oB2 = oW1 + kW1Bytes;          // b2: 256 FP32
+constexpr int oW3 = oB2 + kHidden * 4;       // BF16 W3 as FP32, column-interleaved [256][2]
+constexpr int oY = oW3 + kHidden * 2 * 4;    // partial layer-3 sums [2 halves][128 rows][2]
+constexpr int oBar = oY + 2 * kRowsPerTile * 2 * 4;  // mbarriers: layer-2 halves, layer 1
+constexpr int oTmem = oBar + 24;             // TMEM base address written by tcgen05.alloc
 constexpr int kSmemUsed = oTmem + 4;
 constexpr int kSmemBytes = kSmemUsed + 1024;  // + alignment slack
 
@@ -165,36 +169,9 @@ __device__ __forceinline__ bool bar_wait(uint64_t *bar, uint32_t parity, unsigne
     }
 }
 
-// 32 consecutive FP32 columns of this thread's TMEM lane; the wait that
-// completes the load is tied to the registers so no use is scheduled before it
-__device__ __forceinline__ void tmem_ld32(uint32_t taddr, float (&v)[32]) {
-    uint32_t r[32];
-    asm volatile(
-        "tcgen05.ld.sync.aligned.32x32b.x32.b32 "
-        "{%0,%1,%2,%3,%4,%5,%6,%7,%8,%9,%10,%11,%12,%13,%14,%15,"
-        "%16,%17,%18,%19,%20,%21,%22,%23,%24,%25,%26,%27,%28,%29,%30,%31}, [%32];"
-        : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
-          "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]),
-          "=r"(r[13]), "=r"(r[14]), "=r"(r[15]), "=r"(r[16]), "=r"(r[17]), "=r"(r[18]),
-          "=r"(r[19]), "=r"(r[20]), "=r"(r[21]), "=r"(r[22]), "=r"(r[23]), "=r"(r[24]),
-          "=r"(r[25]), "=r"(r[26]), "=r"(r[27]), "=r"(r[28]), "=r"(r[29]), "=r"(r[30]),
-          "=r"(r[31])
-        : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;"
-                 : "+r"(r[0]), "+r"(r[1]), "+r"(r[2]), "+r"(r[3]), "+r"(r[4]), "+r"(r[5]),
-                   "+r"(r[6]), "+r"(r[7]), "+r"(r[8]), "+r"(r[9]), "+r"(r[10]), "+r"(r[11]),
-                   "+r"(r[12]), "+r"(r[13]), "+r"(r[14]), "+r"(r[15]), "+r"(r[16]), "+r"(r[17]),
-                   "+r"(r[18]), "+r"(r[19]), "+r"(r[20]), "+r"(r[21]), "+r"(r[22]), "+r"(r[23]),
-                   "+r"(r[24]), "+r"(r[25]), "+r"(r[26]), "+r"(r[27]), "+r"(r[28]), "+r"(r[29]),
-                   "+r"(r[30]), "+r"(r[31])
-                 :
-                 : "memory");
-#pragma unroll
-    for (int i = 0; i < 32; ++i) v[i] = __uint_as_float(r[i]);
-}
-
-// 64 consecutive FP32 columns of this thread's TMEM lane (two 32-column
-// loads completed by one wait)
+// 64 consecutive FP32 columns of this thread's TMEM lane: two 32-column
+// loads completed by one wait, which is tied to the registers so that no use
+// is scheduled before it
 __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
     uint32_t r[64];
 #define PIRRT_TC_LD32(base, dst)                                                                 \
@@ -227,16 +204,6 @@ __device__ __forceinline__ void tmem_ld64(uint32_t taddr, float (&v)[64]) {
     for (int i = 0; i < 64; ++i) v[i] = __uint_as_float(r[i]);
 }
 
-__device__ __forceinline__ void tmem_ld2(uint32_t taddr, float &a, float &b) {
-    uint32_t r0, r1;
-    asm volatile("tcgen05.ld.sync.aligned.32x32b.x2.b32 {%0,%1}, [%2];"
-                 : "=r"(r0), "=r"(r1)
-                 : "r"(taddr));
-    asm volatile("tcgen05.wait::ld.sync.aligned;" : "+r"(r0), "+r"(r1) : : "memory");
-    a = __uint_as_float(r0);
-    b = __uint_as_float(r1);
-}
-
 __device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
     const __nv_bfloat162 p = __floats2bfloat162_rn(lo, hi);
     return *reinterpret_cast<const uint32_t *>(&p);
@@ -262,20 +229,8 @@ struct FwdArgs {
     int *status;                   // error bits (kErr*)
 };
 
-// h = relu(v + bias) for 64 columns, packed to BF16 pairs
-__device__ __forceinline__ void bias_relu_pack(const float (&v)[64], const float *bias,
-                                               uint32_t *p) {
-#pragma unroll
-    for (int i = 0; i < 64; i += 4) {
-        const float4 b = *reinterpret_cast<const float4 *>(bias + i);
-        const float a0 = b.x + v[i], a1 = b.y + v[i + 1], a2 = b.z + v[i + 2], a3 = b.w + v[i + 3];
-        p[i / 2] = pack_bf16(a0 > 0.f ? a0 : 0.f, a1 > 0.f ? a1 : 0.f);
-        p[i / 2 + 1] = pack_bf16(a2 > 0.f ? a2 : 0.f, a3 > 0.f ? a3 : 0.f);
-    }
-}
-
-// 64 packed columns (32 words) of row r from column c0 into the swizzled H
-// (and the optional HBM copy)
+// 64 packed columns (32 words) of row `row` from column c0 into the swizzled
+// H, and the optional HBM copy of row r
 __device__ __forceinline__ void store_h(uint8_t *sm, int row, int c0, const uint32_t *p,
                                         __nv_bfloat16 *cap, bool valid, int r) {
 #pragma unroll
@@ -286,31 +241,45 @@ __device__ __forceinline__ void store_h(uint8_t *sm, int row, int c0, const uint
     }
 }
 
+// 64 packed columns (32 words) into the HBM copy of row r only
+__device__ __forceinline__ void store_cap(const uint32_t *p, __nv_bfloat16 *cap, int r, int c0) {
+#pragma unroll
+    for (int q = 0; q < 8; ++q)
+        *reinterpret_cast<uint4 *>(cap + (size_t)r * kHidden + c0 + q * 8) =
+            make_uint4(p[4 * q], p[4 * q + 1], p[4 * q + 2], p[4 * q + 3]);
+}
+
+// noise of row r as BF16 pairs (zeros past the last row)
+__device__ __forceinline__ uint4 load_z(const float *z, int r, bool valid) {
+    if (!valid) return make_uint4(0u, 0u, 0u, 0u);
+    const float4 z0 = *reinterpret_cast<const float4 *>(z + (size_t)r * kNoise);
+    const float4 z1 = *reinterpret_cast<const float4 *>(z + (size_t)r * kNoise + 4);
+    return make_uint4(pack_bf16(z0.x, z0.y), pack_bf16(z0.z, z0.w), pack_bf16(z1.x, z1.y),
+                      pack_bf16(z1.z, z1.w));
+}
+
 __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
     extern __shared__ uint8_t smem_raw[];
     const uint32_t raw = saddr(smem_raw);
     uint8_t *sm = smem_raw + (((raw + 1023u) & ~1023u) - raw);
     const uint32_t sb = saddr(sm);
-    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + oBar);  // [0]: columns 0..127, [1]: 128..255
+    // bar[0], bar[1]: layer-2 column halves; bar[2]: layer 1
+    uint64_t *bar = reinterpret_cast<uint64_t *>(sm + oBar);
     uint32_t *s_tmem = reinterpret_cast<uint32_t *>(sm + oTmem);
     float *s_b2 = reinterpret_cast<float *>(sm + oB2);
+    float2 *s_w3 = reinterpret_cast<float2 *>(sm + oW3);  // (W3[0][j], W3[1][j])
+    float2 *s_y = reinterpret_cast<float2 *>(sm + oY);    // [half][row]
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int quad = warp & 3, half = warp >> 2;  // TMEM lane quadrant, column half
     const int row = quad * 32 + lane;              // row of the tile (TMEM lane)
     const int col0 = half * 128;                   // first column of this thread
 
-    // resident operands: W2, W3' (rows 2..15 zero), W1n' (K 8..15 zero), the
-    // zero K half of Z, b2
+    // resident operands: W2 (swizzled), W1n' (K 8..15 zero), the zero K half
+    // of Z, b2, W3 (BF16 values as FP32)
     for (int i = tid; i < kHidden * (kHidden / 8); i += kThreads) {
         const int n = i >> 5, c = i & 31;
         const uint4 v = *reinterpret_cast<const uint4 *>(A.W2b + (size_t)n * kHidden + c * 8);
         *reinterpret_cast<uint4 *>(sm + oW2 + sw128(n, c * 8, kHidden)) = v;
-    }
-    for (int i = tid; i < kN3 * (kHidden / 8); i += kThreads) {
-        const int n = i >> 5, c = i & 31;
-        uint4 v = make_uint4(0u, 0u, 0u, 0u);
-        if (n < kOut) v = *reinterpret_cast<const uint4 *>(A.W3b + (size_t)n * kHidden + c * 8);
-        *reinterpret_cast<uint4 *>(sm + oW3 + sw128(n, c * 8, kN3)) = v;
     }
     for (int n = tid; n < kHidden; n += kThreads) {
         const float *w = A.W1n + n * kNoise;
@@ -319,12 +288,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
                        pack_bf16(w[6], w[7]));
         *reinterpret_cast<uint4 *>(sm + oW1 + plain16(n, 1)) = make_uint4(0u, 0u, 0u, 0u);
         s_b2[n] = A.b2[n];
+        s_w3[n] = make_float2(__bfloat162float(A.W3b[n]), __bfloat162float(A.W3b[kHidden + n]));
     }
-    if (tid < kRowsPerTile)
-        *reinterpret_cast<uint4 *>(sm + oZ + plain16(tid, 1)) = make_uint4(0u, 0u, 0u, 0u);
+    const int ntiles = (A.rows + kRowsPerTile - 1) / kRowsPerTile;
+    int tile = blockIdx.x;
+    if (half == 0) {
+        *reinterpret_cast<uint4 *>(sm + oZ + plain16(row, 1)) = make_uint4(0u, 0u, 0u, 0u);
+        const int r = tile * kRowsPerTile + row;
+        *reinterpret_cast<uint4 *>(sm + oZ + plain16(row, 0)) = load_z(A.z, r, r < A.rows);
+    }
     if (tid == 0) {
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar)) : "memory");
-        asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + 1)) : "memory");
+        for (int b = 0; b < 3; ++b)
+            asm volatile("mbarrier.init.shared::cta.b64 [%0], 1;" ::"r"(saddr(bar + b)) : "memory");
         asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
     }
     if (warp == 0) {
@@ -338,17 +313,29 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
     __syncthreads();
     fence_after();
     const uint32_t tmem = *s_tmem;
-    const uint32_t my_tmem = tmem + ((uint32_t)(quad * 32) << 16) + (uint32_t)col0;
+    const uint32_t lane_off = (uint32_t)(quad * 32) << 16;
     const float b30 = A.b3[0], b31 = A.b3[1];
-    const uint32_t id128 = idesc_bf16(kRowsPerTile, 128), id16 = idesc_bf16(kRowsPerTile, kN3);
-    const int ntiles = (A.rows + kRowsPerTile - 1) / kRowsPerTile;
-    uint32_t cA = 0, cB = 0;  // completions of bar[0] / bar[1] before this tile
-    uint32_t nA = 0, nB = 0;  // commits issued to bar[0] / bar[1] (thread 0)
-    bool bad = false;         // a wait of this thread expired
+    const uint32_t id128 = idesc_bf16(kRowsPerTile, 128);
+    uint32_t nA = 0, nB = 0, nC = 0;  // commits issued per barrier (thread 0)
+    bool bad = false;                 // a wait of this thread expired
 
-    for (int tile = blockIdx.x; tile < ntiles; tile += gridDim.x) {
+    // layer 1 of tile `t` into accumulator `acc` (two N = 128 halves, one commit)
+    auto issue_layer1 = [&](uint32_t acc) {
+#pragma unroll
+        for (int h = 0; h < 2; ++h)
+            mma(acc + h * 128, smem_desc(sb + oZ, 128, 256, 0),
+                smem_desc(sb + oW1 + plain16(h * 128, 0), 128, 256, 0), id128, 0u);
+        commit(bar + 2);
+        ++nC;
+    };
+    if (tid == 0) issue_layer1(tmem);
+
+    for (uint32_t it = 0; tile < ntiles; ++it, tile += gridDim.x) {
+        const uint32_t acc = tmem + (it & 1u) * 256u;  // this tile's accumulator
         const int r = tile * kRowsPerTile + row;
         const bool valid = r < A.rows;
+        const int next = tile + (int)gridDim.x;
+        const int rn = next * kRowsPerTile + row;
         int s = 0;
         if (valid) {
             s = A.scene[r];
@@ -356,39 +343,18 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
                 if (half == 0) atomicOr(A.status, kErrScene);
                 s = 0;
             }
-            if (half == 0) {
-                const float4 z0 = *reinterpret_cast<const float4 *>(A.z + (size_t)r * kNoise);
-                const float4 z1 = *reinterpret_cast<const float4 *>(A.z + (size_t)r * kNoise + 4);
-                *reinterpret_cast<uint4 *>(sm + oZ + plain16(row, 0)) =
-                    make_uint4(pack_bf16(z0.x, z0.y), pack_bf16(z0.z, z0.w),
-                               pack_bf16(z1.x, z1.y), pack_bf16(z1.z, z1.w));
-            }
-        } else if (half == 0) {
-            *reinterpret_cast<uint4 *>(sm + oZ + plain16(row, 0)) = make_uint4(0u, 0u, 0u, 0u);
         }
-        fence_async_smem();
-        fence_before();
-        if (__syncthreads_or(bad)) break;
-        // layer 1, two column halves: D[:, h*128 ..] = Z W1n'[h*128 ..]^T
-        if (tid == 0) {
-            fence_after();
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-                mma(tmem + h * 128, smem_desc(sb + oZ, 128, 256, 0),
-                    smem_desc(sb + oW1 + plain16(h * 128, 0), 128, 256, 0), id128, 0u);
-                commit(bar + h);
-            }
-            ++nA;
-            ++nB;
-        }
-        if (!bar_wait(bar + half, (half ? cB : cA) & 1u, kMmaWaitNs)) bad = true;
+        // the next tile's noise, in flight while this tile's layer 1 finishes
+        uint4 zn = make_uint4(0u, 0u, 0u, 0u);
+        if (half == 0 && next < ntiles) zn = load_z(A.z, rn, rn < A.rows);
+        if (!bar_wait(bar + 2, it & 1u, kMmaWaitNs)) bad = true;
         fence_after();
         {
             const float *hrow = A.hgb + (size_t)s * kHidden + col0;
 #pragma unroll 1
             for (int c = 0; c < 128; c += 64) {
                 float v[64];
-                tmem_ld64(my_tmem + c, v);
+                tmem_ld64(acc + lane_off + col0 + c, v);
                 uint32_t p[32];
 #pragma unroll
                 for (int i = 0; i < 64; i += 4) {
@@ -401,10 +367,14 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
                 store_h(sm, row, col0 + c, p, A.cap_h1, valid, r);
             }
         }
+        // layer 1 of this tile is complete (waited above): stage the next noise
+        if (half == 0 && next < ntiles)
+            *reinterpret_cast<uint4 *>(sm + oZ + plain16(row, 0)) = zn;
         fence_async_smem();
         fence_before();
         if (__syncthreads_or(bad)) break;
-        // layer 2, two column halves: D[:, h*128 ..] = H W2[h*128 ..]^T, K = 256
+        // layer 2, two column halves into this tile's accumulator; then the
+        // next tile's layer 1 into the other one
         if (tid == 0) {
             fence_after();
 #pragma unroll
@@ -412,7 +382,7 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
 #pragma unroll 1
                 for (int kk = 0; kk < kHidden / 16; ++kk) {
                     const uint32_t kb = kk >> 2, sub = (kk & 3) * 32;
-                    mma(tmem + h * 128,
+                    mma(acc + h * 128,
                         smem_desc(sb + oH + kb * (kRowsPerTile * 128) + sub, 16, 1024, 2),
                         smem_desc(sb + oW2 + kb * (kHidden * 128) + h * 16384 + sub, 16, 1024, 2),
                         id128, kk > 0 ? 1u : 0u);
@@ -421,69 +391,70 @@ __global__ void __launch_bounds__(kThreads, 1) mlp_forward_tc(const FwdArgs A) {
             }
             ++nA;
             ++nB;
+            if (next < ntiles) issue_layer1(tmem + ((it + 1) & 1u) * 256u);
         }
-        if (!bar_wait(bar + half, ((half ? cB : cA) + 1) & 1u, kMmaWaitNs)) bad = true;
+        if (!bar_wait(bar + half, it & 1u, kMmaWaitNs)) bad = true;
         fence_after();
         {
-            uint32_t p[64];
-#pragma unroll
+            float y0 = 0.f, y1 = 0.f;
+#pragma unroll 1
             for (int c = 0; c < 128; c += 64) {
                 float v[64];
-                tmem_ld64(my_tmem + c, v);
-                bias_relu_pack(v, s_b2 + col0 + c, p + c / 2);
-            }
-            // both halves of layer 2 read h1 from H: store h2 once both are done
-            if (half == 0 && !bar_wait(bar + 1, (cB + 1) & 1u, kMmaWaitNs)) bad = true;
-            store_h(sm, row, col0, p, A.cap_h2, valid, r);
-            store_h(sm, row, col0 + 64, p + 32, A.cap_h2, valid, r);
-        }
-        fence_async_smem();
-        fence_before();
-        if (__syncthreads_or(bad)) break;
-        // layer 3: D[:, 0:16] = H W3'^T
-        if (tid == 0) {
-            fence_after();
-#pragma unroll 1
-            for (int kk = 0; kk < kHidden / 16; ++kk) {
-                const uint32_t kb = kk >> 2, sub = (kk & 3) * 32;
-                mma(tmem, smem_desc(sb + oH + kb * (kRowsPerTile * 128) + sub, 16, 1024, 2),
-                    smem_desc(sb + oW3 + kb * (kN3 * 128) + sub, 16, 1024, 2), id16,
-                    kk > 0 ? 1u : 0u);
-            }
-            commit(bar);
-            ++nA;
-        }
-        if (half == 0) {
-            if (!bar_wait(bar, (cA + 2) & 1u, kMmaWaitNs)) bad = true;
-            fence_after();
-            float d0, d1;
-            tmem_ld2(tmem + ((uint32_t)(quad * 32) << 16), d0, d1);
-            if (valid) {
-                const float y0 = 1.f / (1.f + __expf(-(d0 + b30)));
-                const float y1 = 1.f / (1.f + __expf(-(d1 + b31)));
-                if (A.y) *reinterpret_cast<float2 *>(A.y + 2 * (size_t)r) = make_float2(y0, y1);
-                if (A.out) {
-                    const bool learned = A.coin[r] < A.frac;
-                    const float2 u = *reinterpret_cast<const float2 *>(A.uniform_xy + 2 * (size_t)r);
-                    *reinterpret_cast<float2 *>(A.out + 2 * (size_t)r) =
-                        learned ? make_float2(y0, y1) : u;
+                tmem_ld64(acc + lane_off + col0 + c, v);
+                uint32_t p[32];
+#pragma unroll
+                for (int i = 0; i < 64; i += 4) {
+                    const float4 b = *reinterpret_cast<const float4 *>(s_b2 + col0 + c + i);
+                    const float a0 = v[i] + b.x, a1 = v[i + 1] + b.y;
+                    const float a2 = v[i + 2] + b.z, a3 = v[i + 3] + b.w;
+                    const uint32_t q0 = pack_bf16(a0 > 0.f ? a0 : 0.f, a1 > 0.f ? a1 : 0.f);
+                    const uint32_t q1 = pack_bf16(a2 > 0.f ? a2 : 0.f, a3 > 0.f ? a3 : 0.f);
+                    p[i / 2] = q0;
+                    p[i / 2 + 1] = q1;
+                    // layer 3 on the BF16 h2 values
+                    const float h[4] = {__uint_as_float(q0 << 16), __uint_as_float(q0 & 0xFFFF0000u),
+                                        __uint_as_float(q1 << 16), __uint_as_float(q1 & 0xFFFF0000u)};
+#pragma unroll
+                    for (int e = 0; e < 4; ++e) {
+                        const float2 w = s_w3[col0 + c + i + e];
+                        y0 += h[e] * w.x;
+                        y1 += h[e] * w.y;
+                    }
                 }
+                // (h2 stays in registers: the other half's layer-2 MMA may
+                // still be reading h1 from H)
+                if (A.cap_h2 && valid) store_cap(p, A.cap_h2, r, col0 + c);
             }
+            s_y[half * kRowsPerTile + row] = make_float2(y0, y1);
         }
-        cA += 3;
-        cB += 2;
-        // this tile's TMEM reads and shared-memory use end before the next MMAs
+        // both halves' partial sums (and, before H is rewritten by the next
+        // tile, both layer-2 halves) are complete past this barrier
         fence_before();
         if (__syncthreads_or(bad)) break;
+        if (half == 0 && valid) {
+            const float2 pa = s_y[row], pb = s_y[kRowsPerTile + row];
+            const float y0 = 1.f / (1.f + __expf(-(pa.x + pb.x + b30)));
+            const float y1 = 1.f / (1.f + __expf(-(pa.y + pb.y + b31)));
+            if (A.y) *reinterpret_cast<float2 *>(A.y + 2 * (size_t)r) = make_float2(y0, y1);
+            if (A.out) {
+                const bool learned = A.coin[r] < A.frac;
+                const float2 u = *reinterpret_cast<const float2 *>(A.uniform_xy + 2 * (size_t)r);
+                *reinterpret_cast<float2 *>(A.out + 2 * (size_t)r) =
+                    learned ? make_float2(y0, y1) : u;
+            }
+        }
     }
     // a wait expired somewhere: record it and give the MMAs in flight (the
     // last commit to each barrier) a bounded time more before the tensor
     // memory is released
     const int any_bad = __syncthreads_or(bad);
-    if (any_bad && tid == 0) {
-        atomicOr(A.status, kErrTimeout);
+    if (tid == 0) {
+        if (any_bad) atomicOr(A.status, kErrTimeout);
+        // a layer 1 issued for a tile this CTA did not reach (never, unless
+        // the loop stopped early) is waited for as well
         if (nA > 0) bar_wait(bar, (nA - 1) & 1u, kMmaWaitNs);
         if (nB > 0) bar_wait(bar + 1, (nB - 1) & 1u, kMmaWaitNs);
+        if (nC > 0) bar_wait(bar + 2, (nC - 1) & 1u, kMmaWaitNs);
     }
     fence_before();
     __syncthreads();

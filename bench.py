@@ -271,7 +271,9 @@ def run_ours(args) -> None:
             st = G.exploit(group=args.group, tile=args.tile, dense_fraction=args.dense_fraction,
                            evaluate=args.evaluate, wave_levels=args.wave_levels,
                            host_loop=args.host_loop, wave_tail=args.wave_tail,
-                           wave_ctas=args.wave_ctas)
+                           wave_ctas=args.wave_ctas, wave_local=args.wave_local,
+                           wave_local_max=args.wave_local_max,
+                           wave_local_step=args.wave_local_step)
             if window:
                 torch.cuda.synchronize()
                 torch.cuda.nvtx.range_pop()
@@ -442,7 +444,9 @@ def run_ours(args) -> None:
                        "vertex": goal, "g_goal": g_goal,
                        "heuristic": "0.99 x Euclidean distance to x_goal (FP32)",
                        "pruned_form": "goal-directed Replan, promising g + h < g(x_goal)"},
-                   "wave_ctas": args.wave_ctas,
+                   "wave_ctas": args.wave_ctas, "wave_local": args.wave_local,
+                   "wave_local_max": args.wave_local_max,
+                   "wave_local_step": args.wave_local_step,
                    "iterations_per_step": iters_all[-1], "relaxations_per_step": relaxes[-1],
                    "per_step": step_extra,
                    "improve_kernel": {0: "candidate offers; dense sweeps by lane groups with "
@@ -467,6 +471,7 @@ def run_ours(args) -> None:
                      "bytes_per_launch": round(dom_bytes / launches, 1),
                      "avg_launch_ms": round(dom_ms_avg, 5)},
         "kernels": kernels,
+        "wave_level_profile": level_profile(prof, clocks),
         "e2e": {"value": round(e2e_relax / e2e_s, 1) if e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "prefetch": not args.no_prefetch},
@@ -960,6 +965,31 @@ def run_reference(args) -> None:
     print(json.dumps(line), flush=True)
 
 
+def level_profile(prof: dict, clocks: dict) -> dict:
+    """The top-down Evaluate's levels by size (from the profiled step): how
+    many levels of each size bucket, the vertices they held, and the time of
+    one level (CTA 0's clock from a level's start to the next one's, the grid
+    barrier included), converted with the SM clock sampled under load."""
+    mhz = clocks.get("sm_mhz") or clocks.get("sm_max_mhz") or 2070.0
+    to_us = lambda cyc: cyc / mhz
+    rows = []
+    for b, (n, items, cyc) in enumerate(zip(prof["level_count"], prof["level_vertices"],
+                                            prof["level_cycles"])):
+        if n:
+            lo = 1 << (b - 1) if b > 0 else 0
+            rows.append({"vertices_lo": lo, "vertices_hi": (1 << b) - 1, "levels": n,
+                         "vertices": items, "us_total": round(to_us(cyc), 1),
+                         "us_per_level": round(to_us(cyc) / n, 2)})
+    calls = prof["wave_calls"]
+    return {"sm_mhz": mhz, "wave_launches": calls, "buckets": rows,
+            "levels_us_total": round(to_us(sum(prof["level_cycles"])), 1),
+            "pre_us_total": round(to_us(prof["wave_pre_cycles"]), 1),
+            "post_us_total": round(to_us(prof["wave_post_cycles"]), 1),
+            "jump_finish_us_total": round(to_us(prof["wave_jump_cycles"]), 1),
+            "note": "pre: Improve from offers and its grid barrier inside the wave launch; "
+                    "post: after the last level; jump_finish: pointer jumping after a level cap"}
+
+
 def main():
     ap = argparse.ArgumentParser(description=__doc__.split("\n")[0])
     ap.add_argument("--gpus", type=int, default=1)
@@ -980,6 +1010,12 @@ def main():
     ap.add_argument("--wave-ctas", type=int, default=0, help="wave CTAs per SM (0 tuned)")
     ap.add_argument("--wave-tail", type=int, default=0,
                     help="levels of at most this many vertices walked by one CTA (0 tuned, <0 off)")
+    ap.add_argument("--wave-local", type=int, default=0,
+                    help="tree levels a CTA walks on its own per grid step (0 tuned, <0 none)")
+    ap.add_argument("--wave-local-max", type=int, default=0,
+                    help="local walks go on while the local list holds at most this many (0 tuned)")
+    ap.add_argument("--wave-local-step", type=int, default=0,
+                    help="local walks only in grid steps of at most this many vertices (0 tuned)")
     ap.add_argument("--timing", choices=("graph", "profiled"), default="graph")
     ap.add_argument("--profile-steps", type=int, default=1)
     ap.add_argument("--host-loop", action="store_true",

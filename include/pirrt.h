@@ -94,9 +94,18 @@ typedef struct {
                                always uses the host loop. */
     double dense_fraction;  /* changed vertices, as a fraction of |V|, above which the next
                                Improve sweeps every vertex instead of a list; 0 = tuned */
-    int32_t wave_tail;      /* top-down Evaluate: levels of at most this many vertices are
-                               walked by one CTA without grid barriers; 0 = tuned, < 0 = off */
+    int32_t wave_tail;      /* top-down Evaluate: grid steps of at most this many vertices
+                               are walked by one CTA, with no level limit and no grid barrier;
+                               0 = tuned, < 0 = off */
     int32_t wave_ctas;      /* top-down Evaluate: CTAs per SM (1 or 2); 0 = tuned */
+    int32_t wave_local;     /* top-down Evaluate: tree levels a CTA walks on its own, from the
+                               children it lowered, before they join the next grid step;
+                               0 = tuned, < 0 = none (one level per grid step) */
+    int32_t wave_local_max; /* ... while its list of such children holds at most this many
+                               vertices (a wider subtree is shared by the whole grid at the
+                               next step); 1 .. 512, 0 = tuned */
+    int32_t wave_local_step; /* ... in grid steps of at most this many vertices (a CTA walking on
+                               alone in a wider step would hold back the others); 0 = tuned */
 } pirrt_exploit_opts;
 
 /* Evaluate strategies.  All compute g(v) = g(p(v)) + c(p(v), v) from the root
@@ -104,8 +113,10 @@ typedef struct {
  *   WAVE  -- top-down over the policy tree, level by level, only below the
  *            vertices whose parent switched, pruning where g is unchanged; the
  *            next Improve frontier is marked in the same row scan.  Sums are
- *            taken root-to-leaf, one addition per edge, as in Alg. 2.  Levels
- *            are separated by a grid-wide barrier.
+ *            taken root-to-leaf, one addition per edge, as in Alg. 2.  Work is
+ *            shared out in grid steps separated by a grid-wide barrier; within
+ *            a step each CTA walks the children it lowered for a few levels on
+ *            its own (g lowered by an atomic minimum, as in ASYNC).
  *   JUMP  -- pointer jumping (parent doubling) over every vertex in about
  *            log2(depth) rounds; the sums are reassociated (within a few ulp).
  *   ASYNC -- the same walk as WAVE without level barriers: each CTA follows
@@ -297,12 +308,24 @@ typedef struct {
     int64_t evaluate_vertices, evaluate_visits, mark_vertices;
     int64_t insert_new_entries, insert_copied_entries;
     int64_t evaluate_offers;  /* candidates offered by Evaluate to the next Improve (tile 0) */
+    /* Level trace of the top-down Evaluate (wave launches while profiling):
+     * bucket b counts the levels of 2^(b-1) .. 2^b - 1 vertices (the last
+     * bucket every larger one), the vertices they held, and the SM cycles of
+     * one CTA from each level's start to the next level's start (so the level's
+     * grid barrier is included).  wave_pre_cycles: the cycles of a wave launch
+     * before its first level (Improve from offers and its barrier);
+     * wave_post_cycles: after its last level; wave_jump_cycles: in the
+     * pointer-jumping finish after a level cap; wave_calls: the launches
+     * traced.  Cycles are of the SM clock; divide by it for time. */
+    int64_t level_count[24], level_vertices[24], level_cycles[24];
+    int64_t wave_pre_cycles, wave_post_cycles, wave_jump_cycles, wave_calls;
 } pirrt_profile;
 
 /* Clear the profile and turn event timing on (enable = 1) or off (0). */
 pirrt_status pirrt_graph_set_profiling(pirrt_graph *g, int enable);
 
-/* Copy the profile accumulated since the last pirrt_graph_set_profiling. */
+/* Copy the profile accumulated since the last pirrt_graph_set_profiling
+ * (synchronises the graph's stream to read the device-side level trace). */
 pirrt_status pirrt_graph_get_profile(const pirrt_graph *g, pirrt_profile *out);
 
 /* One Replan iteration as seen while profiling is enabled (tracing). */

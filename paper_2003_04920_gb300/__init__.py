@@ -54,7 +54,8 @@ class pirrt_exploit_opts(ctypes.Structure):
                 ("group", ctypes.c_int32), ("tile", ctypes.c_int32), ("evaluate", ctypes.c_int32),
                 ("wave_levels", ctypes.c_int32), ("host_loop", ctypes.c_int32),
                 ("dense_fraction", ctypes.c_double), ("wave_tail", ctypes.c_int32),
-                ("wave_ctas", ctypes.c_int32)]
+                ("wave_ctas", ctypes.c_int32), ("wave_local", ctypes.c_int32),
+                ("wave_local_max", ctypes.c_int32), ("wave_local_step", ctypes.c_int32)]
 
 
 class pirrt_exploit_stats(ctypes.Structure):
@@ -80,10 +81,18 @@ class pirrt_profile(ctypes.Structure):
                 ("improve_switches", ctypes.c_int64), ("evaluate_vertices", ctypes.c_int64),
                 ("evaluate_visits", ctypes.c_int64), ("mark_vertices", ctypes.c_int64),
                 ("insert_new_entries", ctypes.c_int64), ("insert_copied_entries", ctypes.c_int64),
-                ("evaluate_offers", ctypes.c_int64)]
+                ("evaluate_offers", ctypes.c_int64),
+                ("level_count", ctypes.c_int64 * 24), ("level_vertices", ctypes.c_int64 * 24),
+                ("level_cycles", ctypes.c_int64 * 24), ("wave_pre_cycles", ctypes.c_int64),
+                ("wave_post_cycles", ctypes.c_int64), ("wave_jump_cycles", ctypes.c_int64),
+                ("wave_calls", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
-        return {name: getattr(self, name) for name, _ in self._fields_}
+        out = {}
+        for name, _ in self._fields_:
+            v = getattr(self, name)
+            out[name] = list(v) if isinstance(v, ctypes.Array) else v
+        return out
 
 
 class pirrt_trace_record(ctypes.Structure):
@@ -302,9 +311,11 @@ class Graph:
     def exploit(self, eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                 dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
                 host_loop: bool = False, wave_tail: int = 0, wave_ctas: int = 0,
+                wave_local: int = 0, wave_local_max: int = 0, wave_local_step: int = 0,
                 check: bool = True) -> dict:
         opts = exploit_opts(eps, max_iters, group, tile, dense_fraction, evaluate, wave_levels,
-                            host_loop, wave_tail, wave_ctas)
+                            host_loop, wave_tail, wave_ctas, wave_local, wave_local_max,
+                            wave_local_step)
         st = pirrt_exploit_stats()
         rc = self._lib.pirrt_graph_exploit(self._h, ctypes.byref(opts), ctypes.byref(st))
         out = st.as_dict()
@@ -431,10 +442,12 @@ def pirrt_selftest_wait(which: int, limit: int, stream=None) -> int:
 def exploit_opts(eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                  dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
                  host_loop: bool = False, wave_tail: int = 0,
-                 wave_ctas: int = 0) -> pirrt_exploit_opts:
+                 wave_ctas: int = 0, wave_local: int = 0,
+                 wave_local_max: int = 0, wave_local_step: int = 0) -> pirrt_exploit_opts:
     return pirrt_exploit_opts(float(eps), int(max_iters), int(group), int(tile),
                               EVALUATE_MODES[evaluate], int(wave_levels), int(bool(host_loop)),
-                              float(dense_fraction), int(wave_tail), int(wave_ctas))
+                              float(dense_fraction), int(wave_tail), int(wave_ctas),
+                              int(wave_local), int(wave_local_max), int(wave_local_step))
 
 
 class Batch:

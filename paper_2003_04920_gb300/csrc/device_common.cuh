@@ -22,6 +22,10 @@ constexpr unsigned long long kBarrierSpinLimit = 1ull << 25;
 // 40 rounds sits on a cycle.
 constexpr int kMaxJumpRounds = 40;
 
+// Size buckets of the level trace: bucket b holds the top-down Evaluate
+// levels of 2^(b-1) .. 2^b - 1 vertices (the last bucket: every larger one).
+constexpr int kLevelBuckets = 24;
+
 // One adjacency entry of the device CSR.  FP32 costs pack (col, c) into 8 B
 // so one 8-byte load fetches both; FP64 costs use a 16 B entry.
 template <typename CT>
@@ -131,8 +135,7 @@ struct DevCounters {
     unsigned rounds;              // pointer-jumping rounds of the current Evaluate
     unsigned dense;               // current Improve sweeps every vertex
     unsigned dense_next;          // next Improve sweeps every vertex
-    unsigned wave_levels;         // levels run by the last top-down Evaluate
-    unsigned wave_t;              // top-down Evaluate: level reached by a one-CTA tail walk
+    unsigned wave_levels;         // grid steps run by the last top-down Evaluate
     unsigned wave_incomplete;     // the top-down Evaluate stopped at its level cap
     // Iteration state kept on the device so that one captured loop body (and
     // the host loop alike) serves every iteration:
@@ -155,6 +158,16 @@ struct DevCounters {
     unsigned last_switched, last_dg, last_levels, last_next, last_dense, last_rounds, last_jumped;
     // whole-exploit totals
     unsigned cum_wave_levels, cum_dense, cum_jump_rounds, cum_jump_evals;
+    // Level trace, kept while profiling is on (lvl_trace = 1) and left alone
+    // by a reset of the graph: the top-down Evaluate's levels by size bucket,
+    // the vertices they held and CTA 0's SM cycles over them (each level's
+    // grid barrier included); the cycles of a wave launch before its first
+    // level (Improve from offers and its barrier), after its last, and in a
+    // pointer-jumping finish; and the launches traced.  Only thread 0 of CTA 0
+    // writes them.
+    unsigned lvl_trace;
+    unsigned long long lvl_n[kLevelBuckets], lvl_items[kLevelBuckets], lvl_cyc[kLevelBuckets];
+    unsigned long long ph_pre_cyc, ph_post_cyc, ph_jump_cyc, ph_calls;
 };
 
 // Block-wide sum of one value per thread, added to *counter by one atomic.

@@ -848,9 +848,10 @@ struct WaveArgs {
     const CT *pc;
     double *g;
     float *g32;
-    const int32_t *switched;  // level 0: vertices whose parent changed
-    int32_t *lvl[2];          // vertices of levels t (mod 2), their g already lowered
-    double *lvg[2];           // ... and the lowered g they carry
+    const int32_t *switched;  // step 0: vertices whose parent changed
+    int32_t *lvl[2];          // vertices of grid step t (mod 2), their g already lowered
+    double *lvg[2];           // ... the lowered g they carry
+    int32_t *lvd[2];          // ... and their depth below the switched vertex they came from
     int32_t *dg;              // vertices whose g changed (each once)
     unsigned *wstamp;         // first-change stamps (tag = wave_epoch)
     unsigned *stamp;          // Improve-list stamps
@@ -858,22 +859,25 @@ struct WaveArgs {
     DevCounters *ctr;
     int32_t root;
     unsigned dense_limit;     // |changed| above this -> dense sweep next, stop marking
-    unsigned max_levels;      // give up (wave_incomplete) after this many levels
+    unsigned max_levels;      // a vertex this deep is lowered, not expanded (wave_incomplete)
     int32_t push;             // offer g(u) + c(u, w) to every neighbour w of a changed u
     unsigned long long *cand;
-    unsigned tail_max;        // levels of at most this many vertices: one CTA, no grid barrier
-    int64_t list_cap;         // capacity of lvl[] / lvg[]
+    unsigned tail_max;        // steps of at most this many vertices: one CTA, no grid barrier
+    unsigned local_levels;    // tree levels a CTA walks on its own within a grid step
+    unsigned local_max;       // ... while its local list holds at most this many vertices,
+    unsigned local_step;      // ... in grid steps of at most this many vertices
+    int64_t list_cap;         // capacity of lvl[] / lvg[] / lvd[]
     const float *h;           // goal-directed Replan: heuristic h(v); null = goal-free
     int64_t n;                // vertex count (bulk refresh of the FP32 shadow)
 };
 
-// Level 0 holds the switched vertices: each takes g(s) = g(p(s)) + c(p(s), s).
+// Step 0 holds the switched vertices: each takes g(s) = g(p(s)) + c(p(s), s).
 // A vertex whose g was lowered is expanded: its row is scanned once, every
 // neighbour joins the next Improve list (only neighbours of changed vertices
 // can find a better parent) and is offered its candidate through it, and
 // every child w (p(w) = u) is lowered at once to g(u) + c(u, w) -- one FP64
 // addition per tree edge, root to leaf, as in Alg. 2's Evaluate -- and, if
-// that lowered it, joins level t + 1 carrying the value.  A vertex whose g
+// that lowered it, is expanded in turn carrying the value.  A vertex whose g
 // does not drop prunes its subtree.
 //
 // Improve only switches to strictly cheaper parents, so no cost-to-come rises
@@ -881,212 +885,361 @@ struct WaveArgs {
 // not yet final, when switched vertices lie below one another) is at least
 // its final value, and g is lowered by an atomic minimum on its bit pattern
 // (non-negative doubles order like unsigned integers).  A stale value can
-// never overwrite a smaller one, and each vertex is reached again one level
-// after its parent's last drop, so the result is the root-to-leaf sum
-// whatever the scheduling.  The FP32 shadow is refreshed once at the end
-// from the final g of every vertex that changed.
+// never overwrite a smaller one, and each vertex is reached again right after
+// its parent's last drop, so the result is the root-to-leaf sum whatever the
+// order in which vertices are expanded.
 //
-// A level is split evenly over the CTAs, with a grid barrier between levels.
-// A CTA takes up to kWaveThreads vertices at a time, one per thread, then
-// streams the concatenated rows with every thread (the loads of a whole tile
-// in flight at once), locating each entry's row by binary search over the
-// tile's prefix sums in shared memory.  Levels of at most tail_max vertices
-// (the thin tails of most Evaluates) are walked by CTA 0 alone with CTA
-// barriers, while the other CTAs wait at one grid barrier.
+// Work is organised in grid steps separated by a grid barrier.  A step's
+// global list is split evenly over the CTAs.  A CTA takes up to kWaveThreads
+// vertices at a time, one per thread, then streams the concatenated rows with
+// every thread (the loads of a whole tile in flight at once), locating each
+// entry's row by binary search over the tile's prefix sums in shared memory.
+// The children a CTA lowers go to its local list in shared memory, with their
+// row extents (loaded beside the atomic minimum that lowered them), and the
+// CTA walks that list on its own, one tree level per tile, for up to
+// local_levels levels while the list holds at most local_max vertices: such a
+// level costs a few dependent memory round trips and a CTA barrier instead of
+// a grid-wide step.  Local walks run only in steps of at most local_step
+// vertices: a step ends when its slowest CTA does, so in a wide step a CTA
+// walking on alone would hold back every other CTA's share of the next step.  A longer list means a subtree wide enough to be worth
+// sharing: it goes to the global list of the next step, where every CTA takes
+// a part, and so do children beyond the local list's room and whatever the
+// list holds when the walk stops.  A step of at most tail_max
+// vertices is walked by CTA 0 alone with no level limit, while the other CTAs
+// wait at one grid barrier.
 constexpr int kWaveThreads = 512;
 constexpr int kWaveUnroll = 4;
+constexpr int kWaveStage = 64;  // Improve-list appends staged per warp
+
+template <typename CT>
+struct WaveStepCtx;
 
 template <typename CT>
 struct WaveShared {
+    // the tile being expanded
     int32_t u[kWaveThreads];
     double gu[kWaveThreads];
     long long base[kWaveThreads];
+    int32_t dep[kWaveThreads];
     int32_t seg[kWaveThreads + 1];
     unsigned long long scan[kWaveThreads / 32 + 2];
+    // the CTA's local list: lowered children and their row extents
+    int32_t lu[kWaveThreads];
+    double lg[kWaveThreads];
+    long long lb[kWaveThreads];
+    int32_t ll[kWaveThreads];
+    int32_t ld[kWaveThreads];
+    unsigned lcnt;     // local slots taken (beyond kWaveThreads: spilled to the global list)
+    unsigned nfirst;   // first changes counted by this CTA in the current step
+    unsigned fl[kWaveThreads / 32 + 1];
+    int32_t stage[kWaveThreads / 32][kWaveStage];  // Improve-list appends
+    int32_t dstage[kWaveThreads / 32][kWaveStage]; // changed-list appends (without offers)
 };
 
-// Vertices [lo, hi) of level t.  Every thread of the CTA calls this.
+// Where a tile's vertices come from.
+enum WaveSource { kFromSwitched = 0, kFromGlobal = 1, kFromLocal = 2 };
+
+// Per-step view of the lists and flags, the same for every tile of the step.
 template <typename CT>
-__device__ __forceinline__ void wave_level(const WaveArgs<CT> &a, WaveShared<CT> &sh, unsigned t,
-                                           int64_t lo, int64_t hi, unsigned tag, unsigned epoch,
-                                           int32_t *next, unsigned long long gpol,
-                                           unsigned long long &recomputed,
-                                           unsigned long long &offers, bool children,
-                                           bool over_limit = false) {
+struct WaveStepCtx {
+    const int32_t *in;
+    const double *ing;
+    const int32_t *ind;
+    int32_t *out;
+    double *outg;
+    int32_t *outd;
+    unsigned *out_cnt;
+    int32_t *next;
+    unsigned tag, epoch;
+    unsigned long long gpol;
+    double bound;
+    bool marking, offering, stop;
+    bool local_ok;  // local walks in this step (and row extents fetched for them)
+};
+
+// One tile of nv vertices (src: kFromSwitched / kFromGlobal read entries
+// [s0, s0 + nv) of the switched or global list; kFromLocal takes the local
+// list, which the tile empties and its children refill).  Every thread of the
+// CTA calls this.
+template <typename CT>
+__device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> &sh,
+                                          const WaveStepCtx<CT> &x, int src, int64_t s0, int nv,
+                                          WarpStage<kWaveStage> &mq, WarpStage<kWaveStage> &dq,
+                                          unsigned long long &recomputed,
+                                          unsigned long long &offers) {
     DevCounters *c = a.ctr;
     const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
-    const int32_t *in = ((t & 1u) != 0u) ? a.lvl[1] : a.lvl[0];
-    const double *ing = ((t & 1u) != 0u) ? a.lvg[1] : a.lvg[0];
-    int32_t *out = ((t & 1u) != 0u) ? a.lvl[0] : a.lvl[1];
-    double *outg = ((t & 1u) != 0u) ? a.lvg[0] : a.lvg[1];
-    unsigned *out_cnt = &c->wave_cnt[(t + 1) % 3];
-    // over_limit: with offers the caller counts the wave's changes itself
-    // (see wave_evaluate_kernel) and stops the marking past the dense limit
-    const bool marking = !over_limit && *(volatile unsigned *)&c->dense_next == 0u;
-    const bool offering = a.push && marking;
-    const double bound = goal_bound(c, a.h);
-    for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
-        const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
-        int deg = 0;
-        int32_t u = -1;
-        double gu = 0.0;
-        bool first = false;
-        if (tid < nv) {
-            if (t == 0u) {
-                const int32_t s = __ldcg(&a.switched[s0 + tid]);
-                const int32_t ps = __ldcg(&a.p[s]);
-                const double gs = ld_g_cg(&a.g[ps], gpol) + widen(__ldcg(&a.pc[s]));
-                ++recomputed;
-                const unsigned long long b = (unsigned long long)__double_as_longlong(gs);
-                if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[s]), b) > b) {
-                    u = s;
-                    gu = gs;
-                }
-            } else {
-                u = __ldcg(&in[s0 + tid]);
-                gu = __ldcg(&ing[s0 + tid]);
+    int deg = 0;
+    int32_t u = -1, d = 0;
+    double gu = 0.0;
+    long long beg = 0;
+    bool first = false;
+    if (tid < nv) {
+        if (src == kFromSwitched) {
+            const int32_t s = __ldcg(&a.switched[s0 + tid]);
+            const int32_t ps = __ldcg(&a.p[s]);
+            const double gs = ld_g_cg(&a.g[ps], x.gpol) + widen(__ldcg(&a.pc[s]));
+            ++recomputed;
+            const unsigned long long b = (unsigned long long)__double_as_longlong(gs);
+            if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[s]), b) > b) {
+                u = s;
+                gu = gs;
             }
-            if (u >= 0) {
-                // each changed vertex is counted once; without offers the wave
-                // also lists it (its FP32 shadow is refreshed from the list),
-                // with offers it keeps only the count (the shadow is refreshed
-                // in bulk when a dense sweep is next, see wave_evaluate_kernel)
-                first = atomicExch(&a.wstamp[u], tag) != tag;
-                // a vertex that is not promising keeps its lowered g but is
-                // not expanded: its subtree and neighbours are left as they are
-                if (promising(a.h, u, gu, bound)) {
-                    int64_t b, e;
-                    row_range(a.rows, u, b, e);
-                    deg = (int)(e - b);
-                    sh.base[tid] = b;
+        } else if (src == kFromGlobal) {
+            u = __ldcg(&x.in[s0 + tid]);
+            gu = __ldcg(&x.ing[s0 + tid]);
+            d = __ldcg(&x.ind[s0 + tid]);
+        } else {
+            u = sh.lu[tid];
+            gu = sh.lg[tid];
+            d = sh.ld[tid];
+            beg = sh.lb[tid];
+            deg = sh.ll[tid];
+        }
+    }
+    if (src == kFromLocal) {
+        __syncthreads();  // every entry of the local list is read: it refills from 0
+        if (tid == 0) sh.lcnt = 0u;
+    }
+    if (u >= 0) {
+        // each changed vertex is counted once (the result is used at the end
+        // of the tile, off the critical path)
+        first = atomicExch(&a.wstamp[u], x.tag) != x.tag;
+        // a vertex that is not promising keeps its lowered g but is not
+        // expanded: its subtree and neighbours are left as they are
+        if (promising(a.h, u, gu, x.bound)) {
+            if (src != kFromLocal) {
+                int64_t b, e;
+                row_range(a.rows, u, b, e);
+                beg = b;
+                deg = (int)(e - b);
+            }
+        } else {
+            deg = 0;
+        }
+        // this deep, the vertex is lowered but not expanded: pointer jumping
+        // finishes the values below it
+        if (x.stop || (unsigned)d >= a.max_levels) *(volatile unsigned *)&c->wave_incomplete = 1u;
+    }
+    sh.u[tid] = u;
+    sh.gu[tid] = gu;
+    sh.base[tid] = beg;
+    sh.dep[tid] = (x.stop || (unsigned)d >= a.max_levels) ? -1 : d;  // -1: no children
+    // one block scan of the row lengths: the tile's row offsets
+    constexpr int NW = kWaveThreads / 32;
+    int incl = deg;
+#pragma unroll
+    for (int off = 1; off < 32; off <<= 1) {
+        const int y = __shfl_up_sync(0xffffffffu, incl, off);
+        if (lane >= off) incl += y;
+    }
+    if (lane == 31) sh.scan[warp] = (unsigned long long)incl;
+    __syncthreads();
+    if (tid == 0) {
+        unsigned long long run = 0;
+        for (int w = 0; w < NW; ++w) {
+            const unsigned long long v = sh.scan[w];
+            sh.scan[w] = run;
+            run += v;
+        }
+        sh.seg[kWaveThreads] = (int)run;
+    }
+    __syncthreads();
+    sh.seg[tid] = (int)sh.scan[warp] + incl - deg;
+    __syncthreads();
+    const int total = sh.seg[kWaveThreads];
+    for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
+        int32_t xv[kWaveUnroll], own[kWaveUnroll];
+        double gx[kWaveUnroll];
+#pragma unroll
+        for (int j = 0; j < kWaveUnroll; ++j) {
+            const int pos = p0 + tid + j * kWaveThreads;
+            own[j] = -1;
+            xv[j] = 0;
+            gx[j] = 0.0;
+            if (pos < total) {
+                int l = 0, h = kWaveThreads;  // last k with seg[k] <= pos
+                while (h - l > 1) {
+                    const int mid = (l + h) >> 1;
+                    if (sh.seg[mid] <= pos) l = mid; else h = mid;
                 }
+                own[j] = l;
+                const Entry<CT> en = ld_stream(&a.adj[sh.base[l] + (pos - sh.seg[l])]);
+                xv[j] = en.col;
+                // c(u, w) of this entry; with parallel edges the cheaper one
+                // wins the minimum, as Improve chose it
+                gx[j] = sh.gu[l] + widen(en.w);
+                if (x.offering && en.col != a.root) ++offers;
             }
         }
-        sh.u[tid] = u;
-        sh.gu[tid] = gu;
-        // one block scan of (first change, row length): the row offsets of
-        // the tile, and the slots of its first changes in the changed list
-        // (one atomic per tile)
-        constexpr int NW = kWaveThreads / 32;
-        const unsigned long long xv = ((unsigned long long)(first ? 1u : 0u) << 32) | (unsigned)deg;
-        unsigned long long incl = xv;
+        // every load of this batch in flight at once: the parent of each
+        // neighbour and, for the offers, its current g
+        int32_t px[kWaveUnroll];
+        double gold[kWaveUnroll];
+#pragma unroll
+        for (int j = 0; j < kWaveUnroll; ++j) {
+            px[j] = -1;
+            gold[j] = 0.0;
+            if (own[j] >= 0) {
+                px[j] = __ldcg(&a.p[xv[j]]);
+                if (x.offering) gold[j] = ld_g_cg(&a.g[xv[j]], x.gpol);
+            }
+        }
+        // then every atomic of the batch.  A child is lowered, and its row
+        // extent is loaded beside the atomic for its own expansion.  With
+        // offers, a neighbour w that is not a child is offered g(u) + c(u, w)
+        // and joins the next Improve list only if that beats its g now: g only
+        // falls within an Evaluate and cur(w) = g(p(w)) + c(p(w), w) <= g(w)
+        // once it ends, so an offer not below g(w) can never win (and a
+        // child's offer equals its own cost).  Without offers every neighbour
+        // is marked.
+        unsigned childm = 0, markm = 0;
+        // a child's row extent is fetched with its atomic only while the
+        // local list is short enough to be walked (entries added later make
+        // it too long, and it goes to the global list, extents unused)
+        const bool want_ext = x.local_ok && sh.lcnt < a.local_max;
+        longlong2 ext[kWaveUnroll];
+#pragma unroll
+        for (int j = 0; j < kWaveUnroll; ++j) {
+            ext[j] = make_longlong2(0, 0);
+            if (own[j] >= 0) {
+                const bool child = sh.dep[own[j]] >= 0 && px[j] == sh.u[own[j]];
+                if (child) {
+                    if (want_ext) ext[j] = __ldg(reinterpret_cast<const longlong2 *>(a.rows) + xv[j]);
+                    const unsigned long long b = (unsigned long long)__double_as_longlong(gx[j]);
+                    if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[xv[j]]), b) > b)
+                        childm |= 1u << j;
+                } else if (x.offering) {
+                    if (xv[j] != a.root && gx[j] < gold[j]) {
+                        offer(a.cand, xv[j], gx[j]);
+                        if (atomicExch(&a.stamp[xv[j]], x.epoch) != x.epoch) markm |= 1u << j;
+                    }
+                }
+                if (x.marking && !a.push && xv[j] != a.root &&
+                    __ldcg(&a.stamp[xv[j]]) != x.epoch &&
+                    atomicExch(&a.stamp[xv[j]], x.epoch) != x.epoch)
+                    markm |= 1u << j;
+            }
+        }
+        recomputed += (unsigned long long)__popc(childm);
+        // lowered children: one block scan; the local list takes what fits,
+        // the rest goes to the next step's global list (one atomic per CTA)
+        const unsigned nmine = (unsigned)__popc(childm);
+        unsigned wincl = nmine;
 #pragma unroll
         for (int off = 1; off < 32; off <<= 1) {
-            const unsigned long long y = __shfl_up_sync(0xffffffffu, incl, off);
-            if (lane >= off) incl += y;
+            const unsigned y = __shfl_up_sync(0xffffffffu, wincl, off);
+            if (lane >= off) wincl += y;
         }
-        if (lane == 31) sh.scan[warp] = incl;
+        if (lane == 31) sh.scan[warp] = wincl;
         __syncthreads();
         if (tid == 0) {
-            unsigned long long run = 0;
+            unsigned run = 0;
             for (int w = 0; w < NW; ++w) {
-                const unsigned long long x = sh.scan[w];
+                const unsigned v = (unsigned)sh.scan[w];
                 sh.scan[w] = run;
-                run += x;
+                run += v;
             }
-            const unsigned nf = (unsigned)(run >> 32);
-            unsigned base = 0;
-            if (nf) {
-                if (a.push) {
-                    atomicAdd(&c->n_dg, nf);  // count only: no slot is needed, no wait
-                } else {
-                    base = atomicAdd(&c->n_dg, nf);
-                    if (base + nf > a.dense_limit) *(volatile unsigned *)&c->dense_next = 1u;
-                }
-            }
-            sh.scan[NW] = base;
-            sh.seg[kWaveThreads] = (int)(run & 0xffffffffull);
+            const unsigned lbase = sh.lcnt;
+            const unsigned room = lbase < (unsigned)kWaveThreads ? kWaveThreads - lbase : 0u;
+            const unsigned loc = run < room ? run : room;
+            sh.scan[NW] = lbase;
+            sh.scan[NW + 1] = ((unsigned long long)loc << 32) |
+                              (run > loc ? atomicAdd(x.out_cnt, run - loc) : 0u);
+            sh.lcnt = lbase + loc;
         }
         __syncthreads();
         {
-            const unsigned long long ex = sh.scan[warp] + incl - xv;
-            sh.seg[tid] = (int)(ex & 0xffffffffull);
-            if (first && !a.push) a.dg[(unsigned)sh.scan[NW] + (unsigned)(ex >> 32)] = u;
-        }
-        __syncthreads();
-        const int total = sh.seg[kWaveThreads];
-        for (int p0 = 0; p0 < total; p0 += kWaveThreads * kWaveUnroll) {
-            int32_t x[kWaveUnroll], own[kWaveUnroll];
-            double gx[kWaveUnroll];
-#pragma unroll
-            for (int j = 0; j < kWaveUnroll; ++j) {
-                const int pos = p0 + tid + j * kWaveThreads;
-                own[j] = -1;
-                x[j] = 0;
-                gx[j] = 0.0;
-                if (pos < total) {
-                    int l = 0, h = kWaveThreads;  // last k with seg[k] <= pos
-                    while (h - l > 1) {
-                        const int mid = (l + h) >> 1;
-                        if (sh.seg[mid] <= pos) l = mid; else h = mid;
-                    }
-                    own[j] = l;
-                    const Entry<CT> en = ld_stream(&a.adj[sh.base[l] + (pos - sh.seg[l])]);
-                    x[j] = en.col;
-                    // c(u, w) of this entry; with parallel edges the cheaper one
-                    // wins the minimum, as Improve chose it
-                    gx[j] = sh.gu[l] + widen(en.w);
-                    if (offering && en.col != a.root) ++offers;
-                }
-            }
-            // every load of this batch in flight at once: the parent of each
-            // neighbour and, for the offers, its current g
-            int32_t px[kWaveUnroll];
-            double gold[kWaveUnroll];
-#pragma unroll
-            for (int j = 0; j < kWaveUnroll; ++j) {
-                px[j] = -1;
-                gold[j] = 0.0;
-                if (own[j] >= 0) {
-                    if (children || offering) px[j] = __ldcg(&a.p[x[j]]);
-                    if (offering) gold[j] = ld_g_cg(&a.g[x[j]], gpol);
-                }
-            }
-            // then every atomic of the batch.  A child is lowered.  With offers,
-            // a neighbour w that is not a child is offered g(u) + c(u, w) and
-            // joins the next Improve list only if that beats its g now: g only
-            // falls within an Evaluate and cur(w) = g(p(w)) + c(p(w), w) <= g(w)
-            // once it ends, so an offer not below g(w) can never win (and a
-            // child's offer equals its own cost).  Without offers every
-            // neighbour is marked.
-            unsigned childm = 0, markm = 0;
-#pragma unroll
-            for (int j = 0; j < kWaveUnroll; ++j) {
-                if (own[j] >= 0) {
-                    const bool child = children && px[j] == sh.u[own[j]];
-                    if (child) {
-                        const unsigned long long b = (unsigned long long)__double_as_longlong(gx[j]);
-                        if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[x[j]]), b) > b)
-                            childm |= 1u << j;
-                    } else if (offering) {
-                        if (x[j] != a.root && gx[j] < gold[j]) {
-                            offer(a.cand, x[j], gx[j]);
-                            if (atomicExch(&a.stamp[x[j]], epoch) != epoch) markm |= 1u << j;
-                        }
-                    }
-                    if (marking && !a.push && x[j] != a.root && __ldcg(&a.stamp[x[j]]) != epoch &&
-                        atomicExch(&a.stamp[x[j]], epoch) != epoch)
-                        markm |= 1u << j;
-                }
-            }
-            recomputed += (unsigned long long)__popc(childm);
-            unsigned bc, bm;
-            block_reserve2<kWaveThreads>(__popc(childm), __popc(markm), out_cnt, &c->n_next,
-                                         sh.scan, bc, bm);
+            const unsigned lbase = (unsigned)sh.scan[NW];
+            const unsigned loc = (unsigned)(sh.scan[NW + 1] >> 32);
+            const unsigned gbase = (unsigned)(sh.scan[NW + 1] & 0xffffffffull);
+            unsigned idx = (unsigned)sh.scan[warp] + wincl - nmine;
 #pragma unroll
             for (int j = 0; j < kWaveUnroll; ++j) {
                 if (childm & (1u << j)) {
-                    if (bc < a.list_cap) {  // else the level overflows: see the caller
-                        out[bc] = x[j];
-                        outg[bc] = gx[j];
+                    const int dd = sh.dep[own[j]] + 1;
+                    if (idx < loc) {
+                        const unsigned slot = lbase + idx;
+                        sh.lu[slot] = xv[j];
+                        sh.lg[slot] = gx[j];
+                        sh.lb[slot] = ext[j].x;
+                        sh.ll[slot] = (int32_t)(unsigned)((unsigned long long)ext[j].y & 0xffffffffull);
+                        sh.ld[slot] = dd;
+                    } else {
+                        const unsigned long long k = (unsigned long long)gbase + (idx - loc);
+                        if (k < (unsigned long long)a.list_cap) {  // else: see the caller
+                            x.out[k] = xv[j];
+                            x.outg[k] = gx[j];
+                            x.outd[k] = dd;
+                        }
                     }
-                    ++bc;
+                    ++idx;
                 }
-                if (markm & (1u << j)) next[bm++] = x[j];
             }
         }
-        __syncthreads();  // u / gu / base / seg are rewritten by the next tile
+        __syncthreads();  // sh.scan is rewritten by the next batch
+#pragma unroll
+        for (int j = 0; j < kWaveUnroll; ++j)
+            mq.push((markm >> j) & 1u, xv[j], x.next, &c->n_next);
     }
+    // the first changes of the tile: counted (offers) or listed (no offers)
+    if (a.push) {
+        const unsigned nf = (unsigned)__popc(__ballot_sync(0xffffffffu, first));
+        if (lane == 0 && nf) atomicAdd(&sh.nfirst, nf);
+    } else {
+        dq.push(first, u, a.dg, &c->n_dg);
+    }
+    __syncthreads();  // u / gu / base / dep / seg are rewritten by the next tile
+}
+
+// One CTA's part of grid step t: the share [lo, hi) of the step's list (the
+// switched vertices at step 0), then its local walk; at the end the local list
+// and the step's first changes go to the global counters.  Every thread of
+// the CTA calls this.
+template <typename CT>
+__device__ void wave_step(const WaveArgs<CT> &a, WaveShared<CT> &sh, const WaveStepCtx<CT> &x,
+                          bool from_switched, int64_t lo, int64_t hi, unsigned local_levels,
+                          WarpStage<kWaveStage> &mq, WarpStage<kWaveStage> &dq,
+                          unsigned long long &recomputed, unsigned long long &offers) {
+    DevCounters *c = a.ctr;
+    const int tid = threadIdx.x;
+    if (tid == 0) {
+        sh.lcnt = 0u;
+        sh.nfirst = 0u;
+    }
+    __syncthreads();
+    for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
+        const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
+        wave_tile<CT>(a, sh, x, from_switched ? kFromSwitched : kFromGlobal, s0, nv, mq, dq,
+                      recomputed, offers);
+    }
+    for (unsigned l = 0;; ++l) {
+        __syncthreads();
+        const unsigned taken = sh.lcnt;
+        const int nl = taken < (unsigned)kWaveThreads ? (int)taken : kWaveThreads;
+        if (nl == 0) break;
+        if (l >= local_levels || (unsigned)nl > a.local_max) {
+            // the walk stops here: the local list joins the next step's list
+            __shared__ unsigned s_gb;
+            if (tid == 0) s_gb = atomicAdd(x.out_cnt, (unsigned)nl);
+            __syncthreads();
+            const unsigned long long k = (unsigned long long)s_gb + (unsigned)tid;
+            if (tid < nl && k < (unsigned long long)a.list_cap) {
+                x.out[k] = sh.lu[tid];
+                x.outg[k] = sh.lg[tid];
+                x.outd[k] = sh.ld[tid];
+            }
+            break;
+        }
+        wave_tile<CT>(a, sh, x, kFromLocal, 0, nl, mq, dq, recomputed, offers);
+    }
+    if (a.push) {
+        __syncthreads();
+        if (tid == 0 && sh.nfirst != 0u) atomicAdd(&c->n_dg, sh.nfirst);
+    } else {
+        dq.flush_block(a.dg, &c->n_dg, sh.fl);
+    }
+    __syncthreads();
 }
 
 // Clear the per-iteration fields (not the current list or the dense flag).

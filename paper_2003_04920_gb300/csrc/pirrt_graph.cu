@@ -101,12 +101,13 @@ struct pirrt_graph {
         int cur = -1;
         unsigned dense_limit = 0, max_levels = 0;
         int push = -1;
-        unsigned tail_max = 0;
+        unsigned tail_max = 0, local_levels = 0, local_max = 0, local_step = 0;
         const float *h = nullptr;
         bool operator==(const ArgsKey &o) const {
             return n == o.n && cur == o.cur && dense_limit == o.dense_limit &&
                    max_levels == o.max_levels && push == o.push && tail_max == o.tail_max &&
-                   h == o.h;
+                   local_levels == o.local_levels && local_max == o.local_max &&
+                   local_step == o.local_step && h == o.h;
         }
     } args_key;
     std::map<unsigned long long, cudaGraphExec_t> loops;  // captured Replan loops
@@ -187,7 +188,8 @@ pirrt_status ensure_stage(pirrt_graph *G, size_t bytes) {
 // argument block (stream-ordered; skipped when nothing changed).
 template <typename CT>
 pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_levels, int push,
-                        unsigned tail_max) {
+                        unsigned tail_max, unsigned local_levels = 0, unsigned local_max = 0,
+                        unsigned local_step = 0) {
     pirrt_graph::ArgsKey key;
     key.n = G->n;
     key.cur = G->cur;
@@ -195,6 +197,9 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     key.max_levels = max_levels;
     key.push = push;
     key.tail_max = tail_max;
+    key.local_levels = local_levels;
+    key.local_max = local_max;
+    key.local_step = local_step;
     key.h = G->goal >= 0 ? G->h : nullptr;
     if (key == G->args_key) return PIRRT_OK;
     // the pinned staging is rewritten only after its last copy has been
@@ -250,9 +255,14 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->lvl[1] = G->wl[1];
     wa->lvg[0] = G->acc[0];
     wa->lvg[1] = G->acc[1];
+    wa->lvd[0] = G->anc[0];  // pointer-jumping scratch, free during the wave
+    wa->lvd[1] = G->anc[1];
     wa->dg = G->dg;
     wa->list_cap = G->cap_n;
     wa->tail_max = tail_max;
+    wa->local_levels = local_levels;
+    wa->local_max = local_max;
+    wa->local_step = local_step;
     wa->wstamp = G->wstamp;
     wa->stamp = G->stamp;
     wa->list[0] = G->list[0];
@@ -727,7 +737,8 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         !(o.tile == 0 || o.tile == 1 || o.tile == 2 || o.tile == 3) ||
         !(o.group == 0 || o.group == 2 || o.group == 4 || o.group == 8 || o.group == 16 ||
           o.group == 32) ||
-        o.wave_ctas < 0 || o.wave_ctas > 2)
+        o.wave_ctas < 0 || o.wave_ctas > 2 || o.wave_local_max < 0 || o.wave_local_max > 512 ||
+        o.wave_local_step < 0)
         return fail(G, PIRRT_ERR_INVALID_ARG, "exploit: invalid option");
     if (G->recover) {
         // the last exploit stopped on a device timeout part-way through an
@@ -777,7 +788,15 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     // one CTA walks levels of at most this many vertices (~34 CSR entries each
     // on the 6-D roadmaps, a few passes of the CTA's threads)
     const unsigned tail_max = o.wave_tail < 0 ? 0u : (o.wave_tail > 0 ? (unsigned)o.wave_tail : 64u);
-    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0, tail_max);
+    // tree levels a CTA walks on its own from the children it lowered, before
+    // they join the next grid step
+    // (while its local list is short: a wide subtree is shared by the grid)
+    const unsigned local_levels =
+        o.wave_local < 0 ? 0u : (o.wave_local > 0 ? (unsigned)o.wave_local : 8u);
+    const unsigned local_max = o.wave_local_max > 0 ? (unsigned)o.wave_local_max : 128u;
+    const unsigned local_step = o.wave_local_step > 0 ? (unsigned)o.wave_local_step : 4096u;
+    pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0, tail_max,
+                                     local_levels, local_max, local_step);
     if (rc) return rc;
     const int wave_ctas = o.wave_ctas > 0 ? std::min(o.wave_ctas, G->wave_occ) : G->wave_occ;
     G->wave_blocks = G->num_sms * wave_ctas;
@@ -1292,7 +1311,9 @@ pirrt_status pirrt_graph_reset(pirrt_graph *G) {
     CK(cudaMemsetAsync(G->stamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->wstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
     CK(cudaMemsetAsync(G->swstamp, 0, sizeof(unsigned) * (size_t)G->cap_n, G->stream));
-    CK(cudaMemsetAsync(G->ctr, 0, sizeof(DevCounters), G->stream));
+    // the level trace (the tail of the counter block) survives a reset, like
+    // the rest of the profile
+    CK(cudaMemsetAsync(G->ctr, 0, offsetof(DevCounters, lvl_trace), G->stream));
     // insertions count into deg and leave it all zero
     CK(cudaMemsetAsync(G->deg, 0, sizeof(int32_t) * (size_t)(G->cap_n + 1), G->stream));
     // stamps start at 0, so the first list uses stamp value 1
@@ -1516,6 +1537,11 @@ pirrt_status pirrt_graph_set_profiling(pirrt_graph *G, int enable) {
     G->prof = pirrt_profile{};
     G->trace.clear();
     CK(cudaStreamSynchronize(G->stream));
+    // the device-side level trace starts afresh, on while profiling
+    const size_t lvl_off = offsetof(DevCounters, lvl_trace);
+    CK(cudaMemset(reinterpret_cast<char *>(G->ctr) + lvl_off, 0, sizeof(DevCounters) - lvl_off));
+    const unsigned on = enable ? 1u : 0u;
+    CK(cudaMemcpy(&G->ctr->lvl_trace, &on, sizeof(on), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(&G->copied_seen, &G->ctr->insert_copied, sizeof(G->copied_seen),
                   cudaMemcpyDeviceToHost));
     return PIRRT_OK;
@@ -1528,9 +1554,26 @@ int64_t pirrt_graph_get_trace(const pirrt_graph *G, pirrt_trace_record *out, int
     return n;
 }
 
-pirrt_status pirrt_graph_get_profile(const pirrt_graph *G, pirrt_profile *out) {
-    if (!G || !out) return PIRRT_ERR_INVALID_ARG;
+pirrt_status pirrt_graph_get_profile(const pirrt_graph *Gc, pirrt_profile *out) {
+    if (!Gc || !out) return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = const_cast<pirrt_graph *>(Gc);  // for the error text only
     *out = G->prof;
+    CK(cudaSetDevice(G->cfg.device));
+    CK(cudaStreamSynchronize(G->stream));
+    DevCounters h;
+    const size_t lvl_off = offsetof(DevCounters, lvl_trace);
+    CK(cudaMemcpy(reinterpret_cast<char *>(&h) + lvl_off,
+                  reinterpret_cast<const char *>(G->ctr) + lvl_off, sizeof(DevCounters) - lvl_off,
+                  cudaMemcpyDeviceToHost));
+    for (int b = 0; b < kLevelBuckets; ++b) {
+        out->level_count[b] = (int64_t)h.lvl_n[b];
+        out->level_vertices[b] = (int64_t)h.lvl_items[b];
+        out->level_cycles[b] = (int64_t)h.lvl_cyc[b];
+    }
+    out->wave_pre_cycles = (int64_t)h.ph_pre_cyc;
+    out->wave_post_cycles = (int64_t)h.ph_post_cyc;
+    out->wave_jump_cycles = (int64_t)h.ph_jump_cyc;
+    out->wave_calls = (int64_t)h.ph_calls;
     return PIRRT_OK;
 }
 

@@ -8,11 +8,53 @@
 
 namespace pirrt {
 
+// Level trace of one wave launch (thread 0 of CTA 0 only, while profiling):
+// each level's cycles run from its start to the next level's start, so its
+// grid barrier counts with it.  state: -1 off, -2 before the first level,
+// -3 after the last, b >= 0 the bucket of the running level.
+struct LevelClock {
+    long long t;
+    int state;
+};
+
+__device__ __forceinline__ void lc_start(const DevCounters *c, LevelClock &lc) {
+    lc.state = (blockIdx.x == 0 && threadIdx.x == 0 && c->lvl_trace != 0u) ? -2 : -1;
+    lc.t = clock64();
+}
+
+// A level of `count` vertices starts now (count 0: the levels are over).
+__device__ __forceinline__ void lc_level(DevCounters *c, LevelClock &lc, long long count) {
+    if (lc.state == -1) return;
+    const long long now = clock64();
+    const unsigned long long d = (unsigned long long)(now - lc.t);
+    if (lc.state == -2) c->ph_pre_cyc += d;
+    else if (lc.state >= 0) c->lvl_cyc[lc.state] += d;
+    else c->ph_post_cyc += d;
+    lc.t = now;
+    if (count > 0) {
+        int b = 64 - __clzll((unsigned long long)count);
+        if (b >= kLevelBuckets) b = kLevelBuckets - 1;
+        c->lvl_n[b] += 1ull;
+        c->lvl_items[b] += (unsigned long long)count;
+        lc.state = b;
+    } else {
+        lc.state = -3;
+    }
+}
+
+__device__ __forceinline__ void lc_end(DevCounters *c, LevelClock &lc) {
+    if (lc.state == -1) return;
+    lc_level(c, lc, 0);
+    c->ph_calls += 1ull;
+}
+
 // One Replan iteration in one launch: Improve from offers (when `ip` is
 // given; the dense-sweep kernel runs before this one), a grid barrier, the
-// top-down wave; if it stopped at its level cap, pointer jumping and the
-// frontier marking of its changes; then the end of the iteration
-// (advance_iteration), which in a captured loop sets the WHILE condition.
+// top-down wave in grid steps (each CTA walking the subtrees it reaches on
+// its own for a few levels, see wave_step); if a vertex was too deep to
+// expand, pointer jumping and the frontier marking of its changes; then the
+// end of the iteration (advance_iteration), which in a captured loop sets the
+// WHILE condition.
 template <typename CT>
 __global__ void __launch_bounds__(kWaveThreads, 2)
 wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT> *__restrict__ ep,
@@ -20,94 +62,97 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
                      cudaGraphConditionalHandle cond, int use_cond) {
     const WaveArgs<CT> a = *ap;
     __shared__ WaveShared<CT> sh;
-    __shared__ unsigned s_t;
     DevCounters *c = a.ctr;
+    LevelClock lc;
+    lc_start(c, lc);
     if (ip != nullptr) {
         improve_push_body<CT, 8>(*ip);
         grid_barrier(c, gridDim.x);  // a timeout is in the status word; the iteration still ends
     }
     const unsigned n_sw = *(volatile unsigned *)&c->n_switched;
     if (n_sw == 0u) {
-        if (blockIdx.x == 0 && threadIdx.x == 0) advance_iteration(c, cond, use_cond);
+        if (blockIdx.x == 0 && threadIdx.x == 0) {
+            lc_end(c, lc);
+            advance_iteration(c, cond, use_cond);
+        }
         return;
     }
-    const unsigned epoch = c->epoch + 1u;  // stamp of the list being built
-    const unsigned tag = c->wave_epoch;    // first-change stamp of this Evaluate
-    int32_t *next = ((c->la & 1u) ^ 1u) ? a.list[1] : a.list[0];
     const unsigned nblocks = gridDim.x;
     const int tid = threadIdx.x;
-    const unsigned long long gpol = policy_evict_last();
+    // the step's lists and flags, the same for every thread: kept in shared
+    // memory (thread 0 writes them each step) rather than in registers
+    __shared__ WaveStepCtx<CT> x;
+    if (tid == 0) {
+        x.epoch = c->epoch + 1u;  // stamp of the list being built
+        x.tag = c->wave_epoch;    // first-change stamp of this Evaluate
+        x.next = ((c->la & 1u) ^ 1u) ? a.list[1] : a.list[0];
+        x.gpol = policy_evict_last();
+        x.bound = goal_bound(c, a.h);
+    }
+    WarpStage<kWaveStage> mq{sh.stage[tid >> 5], 0u};   // Improve-list appends
+    WarpStage<kWaveStage> dq{sh.dstage[tid >> 5], 0u};  // changed-list appends (no offers)
     unsigned long long recomputed = 0, offers = 0;
-    // With offers the wave keeps no changed list, only its size n_dg (each
-    // changed vertex counted once): after every level barrier each CTA reads it
-    // with the next level's size, and past the dense limit the marking stops
-    // and the next sweep is dense (whichever way this Evaluate ends).
+    // The changed vertices are counted once each (and listed without offers):
+    // after every step barrier each CTA reads the count with the next step's
+    // size, and past the dense limit the marking stops and the next sweep is
+    // dense (whichever way this Evaluate ends).
     const bool push = a.push != 0;
     unsigned t = 0;
     for (;;) {
         int64_t count =
             t == 0 ? (int64_t)n_sw : (int64_t)(*(volatile unsigned *)&c->wave_cnt[t % 3]);
-        const unsigned ndg = push ? *(volatile unsigned *)&c->n_dg : 0u;
+        const unsigned ndg = *(volatile unsigned *)&c->n_dg;
+        lc_level(c, lc, count);
         if (count == 0) break;
-        const bool over = push && ndg > a.dense_limit;
-        if (over && tid == 0) *(volatile unsigned *)&c->dense_next = 1u;
-        if (t >= a.max_levels || count > a.list_cap) {
-            // Stop: this level's vertices were lowered but not expanded.  Scan
-            // their rows for the frontier and the offers only; pointer jumping
-            // finishes the values below them.  (Children beyond the list's
-            // capacity -- parallel edges -- were lost: the next sweep is dense.)
-            if (blockIdx.x == 0 && tid == 0) {
-                c->wave_incomplete = 1u;
-                if (count > a.list_cap) c->dense_next = 1u;
-            }
-            if (count > a.list_cap) count = a.list_cap;
+        const bool over = ndg > a.dense_limit;
+        const bool stop = count > a.list_cap;
+        __syncthreads();  // the previous step's readers of x are done
+        if (tid == 0) {
+            if (over) *(volatile unsigned *)&c->dense_next = 1u;
+            x.marking = !over && *(volatile unsigned *)&c->dense_next == 0u;
+            x.offering = push && x.marking;
+            x.in = (t & 1u) ? a.lvl[1] : a.lvl[0];
+            x.ing = (t & 1u) ? a.lvg[1] : a.lvg[0];
+            x.ind = (t & 1u) ? a.lvd[1] : a.lvd[0];
+            x.out = (t & 1u) ? a.lvl[0] : a.lvl[1];
+            x.outg = (t & 1u) ? a.lvg[0] : a.lvg[1];
+            x.outd = (t & 1u) ? a.lvd[0] : a.lvd[1];
+            x.out_cnt = &c->wave_cnt[(t + 1) % 3];
+            x.stop = stop;
+            x.local_ok = !stop && (count <= (int64_t)a.tail_max || count <= (int64_t)a.local_step);
+        }
+        __syncthreads();
+        if (stop) {
+            // The step's list overflowed (children lost -- parallel edges):
+            // its vertices were lowered; scan their rows for the frontier and
+            // the offers only; pointer jumping finishes every value and the
+            // next sweep is dense.
+            if (blockIdx.x == 0 && tid == 0) c->dense_next = 1u;
+            count = a.list_cap;
             const int64_t per = (count + nblocks - 1) / nblocks;
             const int64_t lo = (int64_t)blockIdx.x * per;
             const int64_t hi = lo + per < count ? lo + per : count;
-            wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, false, over);
+            wave_step<CT>(a, sh, x, t == 0, lo, hi, 0u, mq, dq, recomputed, offers);
+            ++t;
             grid_barrier(c, nblocks);
             break;
         }
-        if (count <= (int64_t)a.tail_max) {
-            // a thin level: CTA 0 walks on alone while the levels stay thin
-            if (blockIdx.x == 0) {
-                bool over_t = over;
-                for (;;) {
-                    if (tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
-                    __syncthreads();
-                    wave_level<CT>(a, sh, t, 0, count, tag, epoch, next, gpol, recomputed, offers,
-                                   true, over_t);
-                    ++t;
-                    if (tid == 0) s_t = *(volatile unsigned *)&c->wave_cnt[t % 3];
-                    __syncthreads();
-                    count = (int64_t)s_t;
-                    __syncthreads();
-                    if (count == 0 || count > (int64_t)a.tail_max || count > a.list_cap ||
-                        t >= a.max_levels)
-                        break;
-                    if (push) {
-                        // n_dg holds this CTA's own additions (same thread)
-                        if (tid == 0) s_t = *(volatile unsigned *)&c->n_dg;
-                        __syncthreads();
-                        over_t = s_t > a.dense_limit;
-                        __syncthreads();
-                        if (over_t && tid == 0) *(volatile unsigned *)&c->dense_next = 1u;
-                    }
-                }
-                if (tid == 0) c->wave_t = t;
-            }
-            if (!grid_barrier(c, nblocks)) break;
-            t = *(volatile unsigned *)&c->wave_t;
-            continue;
-        }
         if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
-        const int64_t per = (count + nblocks - 1) / nblocks;
-        const int64_t lo = (int64_t)blockIdx.x * per;
-        const int64_t hi = lo + per < count ? lo + per : count;
-        wave_level<CT>(a, sh, t, lo, hi, tag, epoch, next, gpol, recomputed, offers, true, over);
+        if (count <= (int64_t)a.tail_max) {
+            // a thin step: CTA 0 walks it on alone, with no level limit
+            if (blockIdx.x == 0)
+                wave_step<CT>(a, sh, x, t == 0, 0, count, 0xffffffffu, mq, dq, recomputed, offers);
+        } else {
+            const int64_t per = (count + nblocks - 1) / nblocks;
+            const int64_t lo = (int64_t)blockIdx.x * per;
+            const int64_t hi = lo + per < count ? lo + per : count;
+            wave_step<CT>(a, sh, x, t == 0, lo, hi, count <= (int64_t)a.local_step ? a.local_levels : 0u,
+                          mq, dq, recomputed, offers);
+        }
         ++t;
         if (!grid_barrier(c, nblocks)) break;
     }
+    mq.flush_block(x.next, &c->n_next, sh.fl);
     if (!push) {
         // the FP32 shadow of every changed vertex, from its final g
         const unsigned n_dg = *(volatile unsigned *)&c->n_dg;
@@ -137,8 +182,10 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     // the same branch.  A grid barrier that timed out raised kStatusTimeout:
     // the iteration still ends, which stops the loop.
     if (*(volatile unsigned *)&c->wave_incomplete != 0u) {
-        // stopped at the level cap: pointer jumping finishes the values and
-        // its changes are marked; the wave's changed list gives way
+        // a vertex was too deep to expand: pointer jumping finishes the
+        // values and its changes are marked; the wave's changed list gives way
+        lc_level(c, lc, 0);
+        const long long t_jump = clock64();
         bool ok = grid_barrier(c, nblocks) && *(volatile unsigned *)&c->status == 0u;
         if (ok && blockIdx.x == 0 && tid == 0) {
             c->n_dg = 0u;
@@ -150,10 +197,15 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
         if (ok) ok = grid_barrier(c, nblocks);
         if (ok) mark_changed<CT>(*mp);
         grid_barrier(c, nblocks);
-        if (blockIdx.x == 0 && tid == 0) advance_iteration(c, cond, use_cond);
+        if (blockIdx.x == 0 && tid == 0) {
+            if (lc.state != -1) c->ph_jump_cyc += (unsigned long long)(clock64() - t_jump);
+            lc_end(c, lc);
+            advance_iteration(c, cond, use_cond);
+        }
         return;
     }
     // otherwise the last CTA to finish ends the iteration (no grid barrier)
+    lc_end(c, lc);
     __syncthreads();
     if (tid == 0) {
         __threadfence();

@@ -981,7 +981,17 @@ def level_profile(prof: dict, clocks: dict) -> dict:
                          "vertices": items, "us_total": round(to_us(cyc), 1),
                          "us_per_level": round(to_us(cyc) / n, 2)})
     calls = prof["wave_calls"]
+
+    def tiles(kind):
+        out = []
+        for b, (n, items, cyc) in enumerate(zip(prof[f"{kind}_tiles"], prof[f"{kind}_vertices"],
+                                                prof[f"{kind}_cycles"])):
+            if n:
+                out.append({"vertices_lo": 1 << (b - 1) if b > 0 else 0, "tiles": n,
+                            "vertices": items, "us_per_tile": round(to_us(cyc) / n, 2)})
+        return out
     return {"sm_mhz": mhz, "wave_launches": calls, "buckets": rows,
+            "cta0_share_tiles": tiles("share"), "cta0_local_tiles": tiles("local"),
             "levels_us_total": round(to_us(sum(prof["level_cycles"])), 1),
             "pre_us_total": round(to_us(prof["wave_pre_cycles"]), 1),
             "post_us_total": round(to_us(prof["wave_post_cycles"]), 1),

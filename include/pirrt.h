@@ -319,6 +319,11 @@ typedef struct {
      * traced.  Cycles are of the SM clock; divide by it for time. */
     int64_t level_count[24], level_vertices[24], level_cycles[24];
     int64_t wave_pre_cycles, wave_post_cycles, wave_jump_cycles, wave_calls;
+    /* The same CTA's own tiles of up to 512 vertices, by tile size (same
+     * buckets): its share of a grid step, and the tree levels it walked on its
+     * own from the children it lowered. */
+    int64_t share_tiles[24], share_vertices[24], share_cycles[24];
+    int64_t local_tiles[24], local_vertices[24], local_cycles[24];
 } pirrt_profile;
 
 /* Clear the profile and turn event timing on (enable = 1) or off (0). */

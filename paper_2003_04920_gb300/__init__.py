@@ -85,7 +85,10 @@ class pirrt_profile(ctypes.Structure):
                 ("level_count", ctypes.c_int64 * 24), ("level_vertices", ctypes.c_int64 * 24),
                 ("level_cycles", ctypes.c_int64 * 24), ("wave_pre_cycles", ctypes.c_int64),
                 ("wave_post_cycles", ctypes.c_int64), ("wave_jump_cycles", ctypes.c_int64),
-                ("wave_calls", ctypes.c_int64)]
+                ("wave_calls", ctypes.c_int64),
+                ("share_tiles", ctypes.c_int64 * 24), ("share_vertices", ctypes.c_int64 * 24),
+                ("share_cycles", ctypes.c_int64 * 24), ("local_tiles", ctypes.c_int64 * 24),
+                ("local_vertices", ctypes.c_int64 * 24), ("local_cycles", ctypes.c_int64 * 24)]
 
     def as_dict(self) -> dict:
         out = {}

@@ -167,6 +167,10 @@ struct DevCounters {
     // writes them.
     unsigned lvl_trace;
     unsigned long long lvl_n[kLevelBuckets], lvl_items[kLevelBuckets], lvl_cyc[kLevelBuckets];
+    // CTA 0's own tiles, by tile size: its share of a grid step (shr_*) and
+    // the levels it walked on its own (loc_*), with their cycles
+    unsigned long long shr_n[kLevelBuckets], shr_items[kLevelBuckets], shr_cyc[kLevelBuckets];
+    unsigned long long loc_n[kLevelBuckets], loc_items[kLevelBuckets], loc_cyc[kLevelBuckets];
     unsigned long long ph_pre_cyc, ph_post_cyc, ph_jump_cyc, ph_calls;
 };
 
@@ -385,6 +389,44 @@ __device__ __forceinline__ bool grid_barrier(DevCounters *c, unsigned nblocks,
         int ok = 1;
         unsigned long long spins = 0;
         while (((old ^ *word) & 0x80000000u) == 0u) {
+            if (++spins > spin_limit) {
+                atomicOr(&c->status, kStatusTimeout);
+                ok = 0;
+                break;
+            }
+            __nanosleep(32);
+        }
+        __threadfence();
+        s_ok = ok;
+    }
+    __syncthreads();
+    return s_ok != 0;
+}
+
+// The same barrier for a kernel whose CTAs know its phase: thread 0 of every
+// CTA reads the phase bit once at kernel start (barrier_phase; no CTA can
+// complete a barrier before every CTA has arrived, so all read the same bit)
+// and passes it to each barrier, which toggles it.  The arrival is then an
+// atomic whose result nobody waits for.  Use it for every grid barrier of the
+// kernel up to the first grid_barrier, which does not keep the phase.
+__device__ __forceinline__ unsigned barrier_phase(const DevCounters *c) {
+    return *reinterpret_cast<const volatile unsigned *>(&c->bar_count) & 0x80000000u;
+}
+
+__device__ __forceinline__ bool grid_barrier_phased(DevCounters *c, unsigned nblocks,
+                                                    unsigned &phase,
+                                                    unsigned long long spin_limit = kBarrierSpinLimit) {
+    __shared__ int s_ok;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        const unsigned inc = blockIdx.x == 0 ? 0x80000000u - (nblocks - 1u) : 1u;
+        __threadfence();
+        atomicAdd(&c->bar_count, inc);  // result unused: a reduction, no round trip to wait for
+        phase ^= 0x80000000u;
+        volatile unsigned *word = &c->bar_count;
+        int ok = 1;
+        unsigned long long spins = 0;
+        while ((*word & 0x80000000u) != phase) {
             if (++spins > spin_limit) {
                 atomicOr(&c->status, kStatusTimeout);
                 ok = 0;

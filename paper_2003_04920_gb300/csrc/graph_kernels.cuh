@@ -499,6 +499,7 @@ template <typename CT, int G>
 __global__ void __launch_bounds__(kThreads)
 improve_kernel(const ImproveArgs<CT> *__restrict__ ap) {
     const ImproveArgs<CT> a = *ap;
+
     const int32_t *active = a.list[a.ctr->la & 1u];
     constexpr int kUnroll = 4;
     const int lane_g = threadIdx.x & (G - 1);
@@ -851,7 +852,8 @@ struct WaveArgs {
     const int32_t *switched;  // step 0: vertices whose parent changed
     int32_t *lvl[2];          // vertices of grid step t (mod 2), their g already lowered
     double *lvg[2];           // ... the lowered g they carry
-    int32_t *lvd[2];          // ... and their depth below the switched vertex they came from
+    longlong2 *lvx[2];        // ... and their row extent and depth below the switched vertex
+                              // they came from: {beg, (depth << 32) | len}
     int32_t *dg;              // vertices whose g changed (each once)
     unsigned *wstamp;         // first-change stamps (tag = wave_epoch)
     unsigned *stamp;          // Improve-list stamps
@@ -866,7 +868,7 @@ struct WaveArgs {
     unsigned local_levels;    // tree levels a CTA walks on its own within a grid step
     unsigned local_max;       // ... while its local list holds at most this many vertices,
     unsigned local_step;      // ... in grid steps of at most this many vertices
-    int64_t list_cap;         // capacity of lvl[] / lvg[] / lvd[]
+    int64_t list_cap;         // capacity of lvl[] / lvg[] / lvx[]
     const float *h;           // goal-directed Replan: heuristic h(v); null = goal-free
     int64_t n;                // vertex count (bulk refresh of the FP32 shadow)
 };
@@ -944,17 +946,16 @@ template <typename CT>
 struct WaveStepCtx {
     const int32_t *in;
     const double *ing;
-    const int32_t *ind;
+    const longlong2 *inx;
     int32_t *out;
     double *outg;
-    int32_t *outd;
+    longlong2 *outx;
     unsigned *out_cnt;
     int32_t *next;
     unsigned tag, epoch;
     unsigned long long gpol;
     double bound;
     bool marking, offering, stop;
-    bool local_ok;  // local walks in this step (and row extents fetched for them)
 };
 
 // One tile of nv vertices (src: kFromSwitched / kFromGlobal read entries
@@ -988,7 +989,10 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
         } else if (src == kFromGlobal) {
             u = __ldcg(&x.in[s0 + tid]);
             gu = __ldcg(&x.ing[s0 + tid]);
-            d = __ldcg(&x.ind[s0 + tid]);
+            const longlong2 e = __ldcg(&x.inx[s0 + tid]);
+            beg = e.x;
+            deg = (int)(unsigned)((unsigned long long)e.y & 0xffffffffull);
+            d = (int)((unsigned long long)e.y >> 32);
         } else {
             u = sh.lu[tid];
             gu = sh.lg[tid];
@@ -1008,7 +1012,7 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
         // a vertex that is not promising keeps its lowered g but is not
         // expanded: its subtree and neighbours are left as they are
         if (promising(a.h, u, gu, x.bound)) {
-            if (src != kFromLocal) {
+            if (src == kFromSwitched) {
                 int64_t b, e;
                 row_range(a.rows, u, b, e);
                 beg = b;
@@ -1094,10 +1098,8 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
         // child's offer equals its own cost).  Without offers every neighbour
         // is marked.
         unsigned childm = 0, markm = 0;
-        // a child's row extent is fetched with its atomic only while the
-        // local list is short enough to be walked (entries added later make
-        // it too long, and it goes to the global list, extents unused)
-        const bool want_ext = x.local_ok && sh.lcnt < a.local_max;
+        // a child's row extent is fetched with its atomic: the child is
+        // expanded from the local or the global list without another load
         longlong2 ext[kWaveUnroll];
 #pragma unroll
         for (int j = 0; j < kWaveUnroll; ++j) {
@@ -1105,7 +1107,7 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
             if (own[j] >= 0) {
                 const bool child = sh.dep[own[j]] >= 0 && px[j] == sh.u[own[j]];
                 if (child) {
-                    if (want_ext) ext[j] = __ldg(reinterpret_cast<const longlong2 *>(a.rows) + xv[j]);
+                    ext[j] = __ldg(reinterpret_cast<const longlong2 *>(a.rows) + xv[j]);
                     const unsigned long long b = (unsigned long long)__double_as_longlong(gx[j]);
                     if (atomicMin(reinterpret_cast<unsigned long long *>(&a.g[xv[j]]), b) > b)
                         childm |= 1u << j;
@@ -1170,7 +1172,9 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
                         if (k < (unsigned long long)a.list_cap) {  // else: see the caller
                             x.out[k] = xv[j];
                             x.outg[k] = gx[j];
-                            x.outd[k] = dd;
+                            x.outx[k] = make_longlong2(
+                                ext[j].x, (long long)(((unsigned long long)(unsigned)dd << 32) |
+                                                      ((unsigned long long)ext[j].y & 0xffffffffull)));
                         }
                     }
                     ++idx;
@@ -1197,12 +1201,22 @@ __device__ __forceinline__ void wave_tile(const WaveArgs<CT> &a, WaveShared<CT> 
 // and the step's first changes go to the global counters.  Every thread of
 // the CTA calls this.
 template <typename CT>
-__device__ void wave_step(const WaveArgs<CT> &a, WaveShared<CT> &sh, const WaveStepCtx<CT> &x,
+__device__ void wave_step(const WaveArgs<CT> &a, WaveShared<CT> &sh, WaveStepCtx<CT> &x,
                           bool from_switched, int64_t lo, int64_t hi, unsigned local_levels,
                           WarpStage<kWaveStage> &mq, WarpStage<kWaveStage> &dq,
-                          unsigned long long &recomputed, unsigned long long &offers) {
+                          unsigned long long &recomputed, unsigned long long &offers,
+                          unsigned ndg, bool trace = false) {
     DevCounters *c = a.ctr;
     const int tid = threadIdx.x;
+    // trace (thread 0 of CTA 0 while profiling): cycles of each tile, by size
+    auto tile_trace = [&](unsigned long long *n, unsigned long long *items,
+                          unsigned long long *cyc, int nv, long long t0) {
+        int b = 32 - __clz((unsigned)nv);
+        if (b >= kLevelBuckets) b = kLevelBuckets - 1;
+        n[b] += 1ull;
+        items[b] += (unsigned long long)nv;
+        cyc[b] += (unsigned long long)(clock64() - t0);
+    };
     if (tid == 0) {
         sh.lcnt = 0u;
         sh.nfirst = 0u;
@@ -1210,8 +1224,10 @@ __device__ void wave_step(const WaveArgs<CT> &a, WaveShared<CT> &sh, const WaveS
     __syncthreads();
     for (int64_t s0 = lo; s0 < hi; s0 += kWaveThreads) {
         const int nv = (hi - s0) < (int64_t)kWaveThreads ? (int)(hi - s0) : kWaveThreads;
+        const long long t0 = trace ? clock64() : 0;
         wave_tile<CT>(a, sh, x, from_switched ? kFromSwitched : kFromGlobal, s0, nv, mq, dq,
                       recomputed, offers);
+        if (trace) tile_trace(c->shr_n, c->shr_items, c->shr_cyc, nv, t0);
     }
     for (unsigned l = 0;; ++l) {
         __syncthreads();
@@ -1227,11 +1243,31 @@ __device__ void wave_step(const WaveArgs<CT> &a, WaveShared<CT> &sh, const WaveS
             if (tid < nl && k < (unsigned long long)a.list_cap) {
                 x.out[k] = sh.lu[tid];
                 x.outg[k] = sh.lg[tid];
-                x.outd[k] = sh.ld[tid];
+                x.outx[k] = make_longlong2(
+                    sh.lb[tid], (long long)(((unsigned long long)(unsigned)sh.ld[tid] << 32) |
+                                            (unsigned long long)(unsigned)sh.ll[tid]));
             }
             break;
         }
+        if (tid == 0 && a.push && x.marking) {
+            // past the dense limit the next sweep is dense and this CTA stops
+            // offering and marking: publish this CTA's first changes so far
+            // and take the count as last read (one local level behind)
+            if (ndg > a.dense_limit) {
+                x.marking = false;
+                x.offering = false;
+                *(volatile unsigned *)&c->dense_next = 1u;
+            } else {
+                if (sh.nfirst != 0u) {
+                    atomicAdd(&c->n_dg, sh.nfirst);
+                    sh.nfirst = 0u;
+                }
+                ndg = *(volatile unsigned *)&c->n_dg;
+            }
+        }
+        const long long t0 = trace ? clock64() : 0;
         wave_tile<CT>(a, sh, x, kFromLocal, 0, nl, mq, dq, recomputed, offers);
+        if (trace) tile_trace(c->loc_n, c->loc_items, c->loc_cyc, nl, t0);
     }
     if (a.push) {
         __syncthreads();

@@ -74,6 +74,7 @@ struct pirrt_graph {
     int32_t *dg = nullptr;
     int32_t *anc[2] = {nullptr, nullptr};
     double *acc[2] = {nullptr, nullptr};
+    longlong2 *wx[2] = {nullptr, nullptr};  // wave lists: row extent and depth of each entry
     int32_t *done = nullptr;
     int32_t *wl[2] = {nullptr, nullptr};  // jump work lists; also the wave's level lists
     unsigned *wstamp = nullptr;           // first-change stamps of an Evaluate
@@ -255,8 +256,8 @@ pirrt_status write_args(pirrt_graph *G, unsigned dense_limit, unsigned max_level
     wa->lvl[1] = G->wl[1];
     wa->lvg[0] = G->acc[0];
     wa->lvg[1] = G->acc[1];
-    wa->lvd[0] = G->anc[0];  // pointer-jumping scratch, free during the wave
-    wa->lvd[1] = G->anc[1];
+    wa->lvx[0] = G->wx[0];
+    wa->lvx[1] = G->wx[1];
     wa->dg = G->dg;
     wa->list_cap = G->cap_n;
     wa->tail_max = tail_max;
@@ -792,7 +793,7 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
     // they join the next grid step
     // (while its local list is short: a wide subtree is shared by the grid)
     const unsigned local_levels =
-        o.wave_local < 0 ? 0u : (o.wave_local > 0 ? (unsigned)o.wave_local : 8u);
+        o.wave_local < 0 ? 0u : (o.wave_local > 0 ? (unsigned)o.wave_local : 32u);
     const unsigned local_max = o.wave_local_max > 0 ? (unsigned)o.wave_local_max : 128u;
     const unsigned local_step = o.wave_local_step > 0 ? (unsigned)o.wave_local_step : 4096u;
     pirrt_status rc = write_args<CT>(G, dense_limit, max_levels, tile == 0 ? 1 : 0, tail_max,
@@ -1035,7 +1036,7 @@ void free_all(pirrt_graph *G) {
     if (G->hargs) cudaFreeHost(G->hargs);
     void *bufs[] = {G->dargs, G->pexport, G->rows, G->ralloc, G->touched, G->roff, G->adj[0], G->adj[1], G->g, G->g32, G->p, G->pc,
                     G->deg, G->tile_sums, G->stamp, G->list[0], G->list[1], G->switched,
-                    G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->done, G->wl[0],
+                    G->dg, G->anc[0], G->anc[1], G->acc[0], G->acc[1], G->wx[0], G->wx[1], G->done, G->wl[0],
                     G->wl[1], G->wstamp, G->swstamp, G->cand, G->aq, G->aring, G->ctr, G->stage, G->h};
     for (void *q : bufs)
         if (q) cudaFree(q);
@@ -1228,6 +1229,8 @@ pirrt_status pirrt_graph_create(const pirrt_config *cfg, pirrt_graph **out) {
     ALLOC(G->anc[1], sizeof(int32_t) * nv);
     ALLOC(G->acc[0], sizeof(double) * nv);
     ALLOC(G->acc[1], sizeof(double) * nv);
+    ALLOC(G->wx[0], sizeof(longlong2) * nv);
+    ALLOC(G->wx[1], sizeof(longlong2) * nv);
     ALLOC(G->done, sizeof(int32_t) * nv);
     ALLOC(G->wl[0], sizeof(int32_t) * nv);
     ALLOC(G->wl[1], sizeof(int32_t) * nv);
@@ -1569,6 +1572,12 @@ pirrt_status pirrt_graph_get_profile(const pirrt_graph *Gc, pirrt_profile *out) 
         out->level_count[b] = (int64_t)h.lvl_n[b];
         out->level_vertices[b] = (int64_t)h.lvl_items[b];
         out->level_cycles[b] = (int64_t)h.lvl_cyc[b];
+        out->share_tiles[b] = (int64_t)h.shr_n[b];
+        out->share_vertices[b] = (int64_t)h.shr_items[b];
+        out->share_cycles[b] = (int64_t)h.shr_cyc[b];
+        out->local_tiles[b] = (int64_t)h.loc_n[b];
+        out->local_vertices[b] = (int64_t)h.loc_items[b];
+        out->local_cycles[b] = (int64_t)h.loc_cyc[b];
     }
     out->wave_pre_cycles = (int64_t)h.ph_pre_cyc;
     out->wave_post_cycles = (int64_t)h.ph_post_cyc;

@@ -65,9 +65,12 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     DevCounters *c = a.ctr;
     LevelClock lc;
     lc_start(c, lc);
+    unsigned phase = 0;  // thread 0: phase bit of the grid barrier
+    if (threadIdx.x == 0) phase = barrier_phase(c);
     if (ip != nullptr) {
         improve_push_body<CT, 8>(*ip);
-        grid_barrier(c, gridDim.x);  // a timeout is in the status word; the iteration still ends
+        // a timeout is in the status word; the iteration still ends
+        grid_barrier_phased(c, gridDim.x, phase);
     }
     const unsigned n_sw = *(volatile unsigned *)&c->n_switched;
     if (n_sw == 0u) {
@@ -113,13 +116,12 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
             x.offering = push && x.marking;
             x.in = (t & 1u) ? a.lvl[1] : a.lvl[0];
             x.ing = (t & 1u) ? a.lvg[1] : a.lvg[0];
-            x.ind = (t & 1u) ? a.lvd[1] : a.lvd[0];
+            x.inx = (t & 1u) ? a.lvx[1] : a.lvx[0];
             x.out = (t & 1u) ? a.lvl[0] : a.lvl[1];
             x.outg = (t & 1u) ? a.lvg[0] : a.lvg[1];
-            x.outd = (t & 1u) ? a.lvd[0] : a.lvd[1];
+            x.outx = (t & 1u) ? a.lvx[0] : a.lvx[1];
             x.out_cnt = &c->wave_cnt[(t + 1) % 3];
             x.stop = stop;
-            x.local_ok = !stop && (count <= (int64_t)a.tail_max || count <= (int64_t)a.local_step);
         }
         __syncthreads();
         if (stop) {
@@ -132,25 +134,28 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
             const int64_t per = (count + nblocks - 1) / nblocks;
             const int64_t lo = (int64_t)blockIdx.x * per;
             const int64_t hi = lo + per < count ? lo + per : count;
-            wave_step<CT>(a, sh, x, t == 0, lo, hi, 0u, mq, dq, recomputed, offers);
+            wave_step<CT>(a, sh, x, t == 0, lo, hi, 0u, mq, dq, recomputed, offers, ndg,
+                          lc.state != -1);
             ++t;
-            grid_barrier(c, nblocks);
+            grid_barrier_phased(c, nblocks, phase);
             break;
         }
         if (blockIdx.x == 0 && tid == 0) c->wave_cnt[(t + 2) % 3] = 0u;
         if (count <= (int64_t)a.tail_max) {
             // a thin step: CTA 0 walks it on alone, with no level limit
             if (blockIdx.x == 0)
-                wave_step<CT>(a, sh, x, t == 0, 0, count, 0xffffffffu, mq, dq, recomputed, offers);
+                wave_step<CT>(a, sh, x, t == 0, 0, count, 0xffffffffu, mq, dq, recomputed, offers,
+                              ndg, lc.state != -1);
         } else {
             const int64_t per = (count + nblocks - 1) / nblocks;
             const int64_t lo = (int64_t)blockIdx.x * per;
             const int64_t hi = lo + per < count ? lo + per : count;
-            wave_step<CT>(a, sh, x, t == 0, lo, hi, count <= (int64_t)a.local_step ? a.local_levels : 0u,
-                          mq, dq, recomputed, offers);
+            wave_step<CT>(a, sh, x, t == 0, lo, hi,
+                          count <= (int64_t)a.local_step ? a.local_levels : 0u, mq, dq, recomputed,
+                          offers, ndg, lc.state != -1);
         }
         ++t;
-        if (!grid_barrier(c, nblocks)) break;
+        if (!grid_barrier_phased(c, nblocks, phase)) break;
     }
     mq.flush_block(x.next, &c->n_next, sh.fl);
     if (!push) {

@@ -471,6 +471,10 @@ def run_ours(args) -> None:
                      "bytes_per_launch": round(dom_bytes / launches, 1),
                      "avg_launch_ms": round(dom_ms_avg, 5)},
         "kernels": kernels,
+        # the whole step against the same peak: every phase's algorithmic bytes
+        # (scaled from the profiled step to the timed ones by their relaxations)
+        # over the timed step time
+        "step_roofline": step_roofline(kbytes, max(1, len(prof_times)), ms_per_step, peak),
         "wave_level_profile": level_profile(prof, clocks),
         "e2e": {"value": round(e2e_relax / e2e_s, 1) if e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
@@ -963,6 +967,17 @@ def run_reference(args) -> None:
                 "d2h_bytes_per_step": 0},
     }
     print(json.dumps(line), flush=True)
+
+
+def step_roofline(kbytes: dict, prof_steps: int, ms_per_step: float, peak: float) -> dict:
+    """Algorithmic bytes of one step (Improve, Evaluate and insertion, counted
+    over the profiled steps, which run the same schedule to the same trees)
+    divided by the timed step time."""
+    total = float(sum(v for v in kbytes.values() if v is not None)) / prof_steps
+    gbs = total / (ms_per_step / 1e3) / 1e9 if ms_per_step > 0 else 0.0
+    return {"algorithmic_bytes": int(total), "achieved": round(gbs, 1), "peak": peak,
+            "unit": "GB/s", "frac": round(gbs / peak, 4),
+            "note": "every phase's algorithmic bytes of one step over ms_per_step"}
 
 
 def level_profile(prof: dict, clocks: dict) -> dict:

@@ -9,7 +9,7 @@
 // the counter block, the kernel's argument block) lives in kScratchBytes of
 // static device memory that every GPU loading this library keeps until the
 // process exits.  The call reads a status word back and synchronises its
-// stream, so it is meant for plain streams, not for recording into a graph.
+// stream before it returns.
 #include <cuda_runtime.h>
 
 #include <cfloat>

@@ -607,13 +607,12 @@ def run_batch(args) -> None:
             B.insert(i, u, v, c)
 
     fill()
-    # Improve from offers (tile 0) or full screened scans (tile 2), lane
-    # counts, the dense threshold and the Evaluate form
-    cands = [dict(group=2), dict(group=4), dict(group=8), dict(group=4, dense_fraction=0.1),
-             dict(group=4, dense_fraction=0.7), dict(group=2, tile=2), dict(group=4, tile=2),
-             dict(group=4, evaluate="wave"), dict(group=4, evaluate="jump"),
-             dict(group=4, wave_ctas=1)]
-    best, idx, _ = B.autotune(cands)
+    # the library's searching autotuner: coordinate descent over the Improve
+    # kernel and its lanes, the dense threshold, the Evaluate form and the
+    # wave's shape, every trial from the same merged state
+    t_tune = time.perf_counter()
+    best, best_ms, trials = B.autotune_search(max_trials=args.tune_trials)
+    tune_s = time.perf_counter() - t_tune
 
     def timed(fn, k):
         ts = []
@@ -657,7 +656,7 @@ def run_batch(args) -> None:
     # one profiled pass for the per-kernel split
     fill()
     B.set_profiling(True)
-    B.exploit(**best, host_loop=True)
+    B.exploit(**{**best, "host_loop": True})
     prof = B.get_profile()
     B.set_profiling(False)
     peak, peak_src = measured_peaks()
@@ -674,7 +673,10 @@ def run_batch(args) -> None:
                                "dimension in {2,3,4,6,7}, k=ceil(2e ln N), FP32 costs; one exploit "
                                "of all members to a fixpoint per step",
                    "vertices": sum(r.n for r in rms), "undirected_edges": sum(r.m for r in rms),
-                   "autotuned_options": best, "autotune_candidates": cands,
+                   "autotuned_options": best,
+                   "autotune": {"kind": "coordinate descent (pirrt_batch_autotune_search)",
+                                "trials": trials, "best_trial_ms": round(best_ms, 3),
+                                "seconds": round(tune_s, 2)},
                    "separate_graphs_ms_per_step": round(ms2, 3),
                    "batched_speedup_vs_separate": round(ms2 / ms, 3),
                    "iterations": st["iterations"], "graph_launch": st["graph_launch"],
@@ -686,8 +688,6 @@ def run_batch(args) -> None:
         "gpu_launches": int(timed_launches),
         "clocks": clocks,
     }
-    if traffic_window:
-        line["traffic_window"] = traffic_window
     for G in solos:
         G.close()
     B.close()
@@ -1024,6 +1024,8 @@ def main():
     ap.add_argument("--workload", choices=sorted(WORKLOADS) + ["c4", "sweep", "explore"],
                     default="c3")
     ap.add_argument("--graphs", type=int, default=512, help="members of the batched workload")
+    ap.add_argument("--tune-trials", type=int, default=40,
+                    help="batched workload: exploits the searching autotuner may run")
     ap.add_argument("--n", type=int, default=None, help="override the vertex count")
     ap.add_argument("--block", type=int, default=None, help="override the block size S")
     ap.add_argument("--trial", type=int, default=0)

@@ -451,6 +451,22 @@ pirrt_status pirrt_batch_autotune(pirrt_batch *b, const pirrt_exploit_opts *cand
                                   int32_t n, pirrt_exploit_opts *best, int32_t *best_index,
                                   float *best_ms);
 
+/* Searching autotuner: the same trials (same starting state, restored after
+ * each), chosen by coordinate descent from `start` (NULL = the defaults) over
+ * the Improve kernel (tile 0 or 2) and its lanes per vertex, the dense-sweep
+ * fraction (0.1 .. 0.8), the Evaluate mode (AUTO or WAVE), the wave's CTAs
+ * per SM, its CTA-local walk (levels, list size, step size) and its one-CTA
+ * tail: each option in turn takes each of its values with the others held,
+ * and keeps a value that is more than 1% faster; passes repeat until one
+ * changes nothing or max_trials (>= 1) exploits have run.  Returns the
+ * fastest set in *best (with every tuned field written out), its time in
+ * *best_ms and the trials run in *trials (either may be NULL).  The batch is
+ * left as it was before the call.  Errors: PIRRT_ERR_INVALID_ARG, and those of
+ * pirrt_batch_exploit. */
+pirrt_status pirrt_batch_autotune_search(pirrt_batch *b, const pirrt_exploit_opts *start,
+                                         int32_t max_trials, pirrt_exploit_opts *best,
+                                         float *best_ms, int32_t *trials);
+
 /* Member `graph`'s g / parents (member-local ids, -1 for the root and for
  * unreached vertices) for its first n vertices (n <= max_vertices[graph]). */
 pirrt_status pirrt_batch_get_costs(const pirrt_batch *b, int32_t graph, double *g_out, int64_t n,

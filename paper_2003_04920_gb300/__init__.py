@@ -157,6 +157,10 @@ def load_library(path: str = LIB_PATH):
         "pirrt_batch_autotune": (st, [vp, ctypes.POINTER(pirrt_exploit_opts), ctypes.c_int32,
                                       ctypes.POINTER(pirrt_exploit_opts),
                                       ctypes.POINTER(ctypes.c_int32), ctypes.POINTER(ctypes.c_float)]),
+        "pirrt_batch_autotune_search": (st, [vp, ctypes.POINTER(pirrt_exploit_opts), ctypes.c_int32,
+                                             ctypes.POINTER(pirrt_exploit_opts),
+                                             ctypes.POINTER(ctypes.c_float),
+                                             ctypes.POINTER(ctypes.c_int32)]),
         "pirrt_batch_get_costs": (st, [vp, ctypes.c_int32, vp, i64, i32]),
         "pirrt_batch_get_parents": (st, [vp, ctypes.c_int32, vp, i64, i32]),
         "pirrt_batch_graph": (vp, [vp]),
@@ -442,6 +446,16 @@ def pirrt_selftest_wait(which: int, limit: int, stream=None) -> int:
     return int(lib.pirrt_selftest_wait(int(which), int(limit), stream))
 
 
+def opts_dict(o: pirrt_exploit_opts) -> dict:
+    """The keyword arguments of exploit_opts that give `o`."""
+    modes = {v: k for k, v in EVALUATE_MODES.items()}
+    return {"eps": o.eps, "max_iters": o.max_iters, "group": o.group, "tile": o.tile,
+            "dense_fraction": o.dense_fraction, "evaluate": modes[o.evaluate],
+            "wave_levels": o.wave_levels, "host_loop": bool(o.host_loop),
+            "wave_tail": o.wave_tail, "wave_ctas": o.wave_ctas, "wave_local": o.wave_local,
+            "wave_local_max": o.wave_local_max, "wave_local_step": o.wave_local_step}
+
+
 def exploit_opts(eps: float = 0.0, max_iters: int = 0, group: int = 0, tile: int = 0,
                  dense_fraction: float = 0.0, evaluate: str = "auto", wave_levels: int = 0,
                  host_loop: bool = False, wave_tail: int = 0,
@@ -534,6 +548,20 @@ class Batch:
                     self._lib.pirrt_batch_autotune(self._h, arr, len(candidates), ctypes.byref(best),
                                                    ctypes.byref(idx), ctypes.byref(ms)))
         return candidates[idx.value], idx.value, ms.value
+
+    def autotune_search(self, max_trials: int = 40, start: dict | None = None):
+        """Coordinate-descent search of the exploit options from the current
+        state (restored after each trial); returns (best options dict, ms,
+        trials run)."""
+        st = exploit_opts(**start) if start else None
+        best = pirrt_exploit_opts()
+        ms = ctypes.c_float(0)
+        n = ctypes.c_int32(0)
+        self._check("pirrt_batch_autotune_search",
+                    self._lib.pirrt_batch_autotune_search(
+                        self._h, ctypes.byref(st) if st is not None else None, int(max_trials),
+                        ctypes.byref(best), ctypes.byref(ms), ctypes.byref(n)))
+        return opts_dict(best), ms.value, n.value
 
     def get_costs(self, graph: int, n: int, out=None) -> np.ndarray:
         if out is None:

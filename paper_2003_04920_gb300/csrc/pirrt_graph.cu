@@ -1946,51 +1946,181 @@ pirrt_status pirrt_batch_exploit(pirrt_batch *B, const pirrt_exploit_opts *opts,
     return pirrt_graph_exploit(G, opts, stats);
 }
 
+// Trials of the autotuners: every trial starts from the state saved when the
+// tuner began and the batch is left in that state at the end.
+struct TrialRunner {
+    pirrt_batch *B;
+    pirrt_graph *G;
+    StateSnapshot snap;
+    int deep0 = 0, expl0 = 0;
+    unsigned wave_epoch_max = 0;
+    int trials = 0;
+
+    explicit TrialRunner(pirrt_batch *b) : B(b), G(b->G) {}
+
+    pirrt_status begin() {
+        pirrt_status rc = batch_flush(B);
+        if (rc) return rc;
+        if ((rc = snapshot_io(G, snap, true))) return rc;
+        deep0 = G->deep_hint;
+        expl0 = G->exploits;
+        return PIRRT_OK;
+    }
+
+    // One exploit with `o` from the saved state; its time in *ms.
+    pirrt_status run(const pirrt_exploit_opts &o, float *ms) {
+        pirrt_status rc;
+        if (trials > 0) {
+            if ((rc = snapshot_io(G, snap, false))) return rc;
+            // wave stamps written by earlier trials stay below this value
+            CK(cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
+                               cudaMemcpyHostToDevice, G->stream));
+        }
+        ++trials;
+        G->deep_hint = deep0;
+        G->exploits = expl0;
+        pirrt_exploit_stats st{};
+        rc = pirrt_graph_exploit(G, &o, &st);
+        if (rc == PIRRT_OK) {
+            wave_epoch_max = std::max(wave_epoch_max, G->ctr_host->wave_epoch + 1u);
+            *ms = st.ms_exploit;
+        }
+        return rc;
+    }
+
+    // Back to the saved state.
+    pirrt_status end() {
+        pirrt_status rc = PIRRT_OK;
+        if (trials > 0) {
+            rc = snapshot_io(G, snap, false);
+            if (rc == PIRRT_OK && wave_epoch_max &&
+                cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
+                                cudaMemcpyHostToDevice, G->stream) != cudaSuccess)
+                rc = PIRRT_ERR_CUDA;
+        }
+        cudaStreamSynchronize(G->stream);
+        G->deep_hint = deep0;
+        G->exploits = expl0;
+        if (snap.buf) cudaFree(snap.buf);
+        snap.buf = nullptr;
+        return rc;
+    }
+};
+
 pirrt_status pirrt_batch_autotune(pirrt_batch *B, const pirrt_exploit_opts *cand, int32_t n,
                                   pirrt_exploit_opts *best, int32_t *best_index, float *best_ms) {
     if (!B || !cand || n <= 0 || !best) return PIRRT_ERR_INVALID_ARG;
     pirrt_graph *G = B->G;
     CK(cudaSetDevice(G->cfg.device));
-    pirrt_status rc = batch_flush(B);
-    if (rc) return rc;
-    StateSnapshot snap;
-    if ((rc = snapshot_io(G, snap, true))) return rc;
-    const int deep0 = G->deep_hint, expl0 = G->exploits;
-    unsigned wave_epoch_max = 0;
+    TrialRunner tr(B);
+    pirrt_status rc = tr.begin();
     float tbest = 0.f;
     int ibest = -1;
     for (int32_t i = 0; i < n && rc == PIRRT_OK; ++i) {
-        if (i > 0 && (rc = snapshot_io(G, snap, false))) break;
-        if (i > 0) {  // wave stamps written by earlier trials stay below this value
-            CK(cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
-                               cudaMemcpyHostToDevice, G->stream));
-        }
-        G->deep_hint = deep0;
-        G->exploits = expl0;
-        pirrt_exploit_stats st{};
-        rc = pirrt_graph_exploit(G, &cand[i], &st);
-        if (rc == PIRRT_OK) {
-            wave_epoch_max = std::max(wave_epoch_max, G->ctr_host->wave_epoch + 1u);
-            if (ibest < 0 || st.ms_exploit < tbest) {
-                tbest = st.ms_exploit;
-                ibest = i;
-            }
+        float ms = 0.f;
+        rc = tr.run(cand[i], &ms);
+        if (rc == PIRRT_OK && (ibest < 0 || ms < tbest)) {
+            tbest = ms;
+            ibest = i;
         }
     }
-    pirrt_status rc2 = snapshot_io(G, snap, false);
-    if (rc2 == PIRRT_OK && wave_epoch_max)
-        rc2 = cudaMemcpyAsync(&G->ctr->wave_epoch, &wave_epoch_max, sizeof(unsigned),
-                              cudaMemcpyHostToDevice, G->stream) == cudaSuccess ? PIRRT_OK
-                                                                                 : PIRRT_ERR_CUDA;
-    cudaStreamSynchronize(G->stream);
-    G->deep_hint = deep0;
-    G->exploits = expl0;
-    if (snap.buf) cudaFree(snap.buf);
+    const pirrt_status rc2 = tr.end();
     if (rc) return rc;
     if (rc2) return rc2;
     *best = cand[ibest];
     if (best_index) *best_index = ibest;
     if (best_ms) *best_ms = tbest;
+    return PIRRT_OK;
+}
+
+namespace {
+// The option space of the searching autotuner: one list of values per
+// option, searched one coordinate at a time.
+struct TuneDim {
+    const char *name;
+    std::vector<double> values;
+    void (*set)(pirrt_exploit_opts &, double);
+};
+
+std::vector<TuneDim> tune_dims(int32_t cost_dtype) {
+    std::vector<TuneDim> d;
+    d.push_back({"tile", {0, 2}, [](pirrt_exploit_opts &o, double v) { o.tile = (int32_t)v; }});
+    d.push_back({"group",
+                 cost_dtype == PIRRT_COST_F32 ? std::vector<double>{2, 4, 8}
+                                              : std::vector<double>{4, 8, 16},
+                 [](pirrt_exploit_opts &o, double v) { o.group = (int32_t)v; }});
+    d.push_back({"dense_fraction", {0.1, 0.2, 0.35, 0.5, 0.8},
+                 [](pirrt_exploit_opts &o, double v) { o.dense_fraction = v; }});
+    d.push_back({"evaluate", {PIRRT_EVAL_AUTO, PIRRT_EVAL_WAVE},
+                 [](pirrt_exploit_opts &o, double v) { o.evaluate = (int32_t)v; }});
+    d.push_back({"wave_ctas", {1, 2}, [](pirrt_exploit_opts &o, double v) { o.wave_ctas = (int32_t)v; }});
+    d.push_back({"wave_local", {-1, 4, 32},
+                 [](pirrt_exploit_opts &o, double v) { o.wave_local = (int32_t)v; }});
+    d.push_back({"wave_local_max", {32, 128, 512},
+                 [](pirrt_exploit_opts &o, double v) { o.wave_local_max = (int32_t)v; }});
+    d.push_back({"wave_local_step", {1024, 4096, 16384},
+                 [](pirrt_exploit_opts &o, double v) { o.wave_local_step = (int32_t)v; }});
+    d.push_back({"wave_tail", {-1, 64, 256},
+                 [](pirrt_exploit_opts &o, double v) { o.wave_tail = (int32_t)v; }});
+    return d;
+}
+
+bool same_opts(const pirrt_exploit_opts &a, const pirrt_exploit_opts &b) {
+    return std::memcmp(&a, &b, sizeof(a)) == 0;
+}
+}  // namespace
+
+pirrt_status pirrt_batch_autotune_search(pirrt_batch *B, const pirrt_exploit_opts *start,
+                                         int32_t max_trials, pirrt_exploit_opts *best,
+                                         float *best_ms, int32_t *trials) {
+    if (!B || !best || max_trials < 1) return PIRRT_ERR_INVALID_ARG;
+    pirrt_graph *G = B->G;
+    CK(cudaSetDevice(G->cfg.device));
+    pirrt_exploit_opts cur{};
+    if (start) cur = *start;
+    // the defaults, written out, so that each coordinate starts from a value
+    // of its list
+    if (cur.group == 0) cur.group = 4;
+    if (cur.dense_fraction == 0.0) cur.dense_fraction = 0.35;
+    if (cur.wave_ctas == 0) cur.wave_ctas = 2;
+    if (cur.wave_local == 0) cur.wave_local = 32;
+    if (cur.wave_local_max == 0) cur.wave_local_max = 128;
+    if (cur.wave_local_step == 0) cur.wave_local_step = 4096;
+    if (cur.wave_tail == 0) cur.wave_tail = 64;
+    const std::vector<TuneDim> dims = tune_dims(G->cfg.cost_dtype);
+    TrialRunner tr(B);
+    pirrt_status rc = tr.begin();
+    float tcur = 0.f;
+    if (rc == PIRRT_OK) rc = tr.run(cur, &tcur);
+    // coordinate descent: a value replaces the current one only if it is
+    // faster by more than 1% (trial times vary by a fraction of that), and
+    // the passes stop when one changes nothing or the trials run out
+    bool improved = true;
+    while (rc == PIRRT_OK && improved && tr.trials < max_trials) {
+        improved = false;
+        for (const TuneDim &dim : dims) {
+            for (double v : dim.values) {
+                if (rc != PIRRT_OK || tr.trials >= max_trials) break;
+                pirrt_exploit_opts o = cur;
+                dim.set(o, v);
+                if (same_opts(o, cur)) continue;
+                float ms = 0.f;
+                rc = tr.run(o, &ms);
+                if (rc == PIRRT_OK && ms < 0.99f * tcur) {
+                    cur = o;
+                    tcur = ms;
+                    improved = true;
+                }
+            }
+        }
+    }
+    const int32_t n_trials = tr.trials;
+    const pirrt_status rc2 = tr.end();
+    if (rc) return rc;
+    if (rc2) return rc2;
+    *best = cur;
+    if (best_ms) *best_ms = tcur;
+    if (trials) *trials = n_trials;
     return PIRRT_OK;
 }
 

@@ -84,6 +84,36 @@ def test_autotune_restores_state_and_picks_a_candidate(members):
         np.testing.assert_array_equal(p, p0)
 
 
+def test_autotune_search_restores_state_and_keeps_results(members):
+    """The searching autotuner runs at most max_trials exploits from the same
+    state, returns a complete option set no slower than where it started, and
+    leaves the batch as it found it; exploiting with the options it picked gives
+    the wave's trees (bit for bit when it picked the wave; when AUTO hands deep
+    changes to pointer jumping, whose sums are reassociated, g within 1e-12 and
+    the unambiguous parents equal)."""
+    with P.Batch([rm.n for rm in members], [rm.m for rm in members]) as B:
+        for i, rm in enumerate(members):
+            B.insert(i, rm.u, rm.v, rm.cost)
+        best, ms, trials = B.autotune_search(max_trials=12)
+        assert 1 <= trials <= 12 and ms > 0
+        assert best["tile"] in (0, 2) and best["group"] in (2, 4, 8)
+        assert 0.1 <= best["dense_fraction"] <= 0.8 and best["wave_ctas"] in (1, 2)
+        assert best["evaluate"] in ("auto", "wave")
+        st = B.exploit(**best)
+        got = [(B.get_costs(i, rm.n), B.get_parents(i, rm.n)) for i, rm in enumerate(members)]
+    assert st["converged"] == 1
+    ref, _ = _batch_run(members, evaluate="wave")
+    for (g, p), (g0, p0), rm in zip(got, ref, members):
+        if best["evaluate"] == "wave":
+            np.testing.assert_array_equal(g, g0)
+            np.testing.assert_array_equal(p, p0)
+        else:
+            np.testing.assert_allclose(g, g0, rtol=1e-12)
+            A = O.CSR(rm.n, rm.u, rm.v, rm.cost.astype(np.float64))
+            mask, _ = A.unambiguous(g0)
+            np.testing.assert_array_equal(p[mask], p0[mask])
+
+
 def test_batch_incremental_inserts_and_errors():
     rms = [W.random_graph(900 + i, 40 + 10 * i, 120) for i in range(5)]
     with P.Batch([rm.n for rm in rms], [rm.m + 8 for rm in rms], cost_dtype=np.float64) as B:

@@ -350,6 +350,12 @@ def run_ours(args) -> None:
         prof = G.get_profile()
         if args.trace:
             np.save(args.trace, G.get_trace())
+        # one more step with every exploit a single CUDA-graph launch and only
+        # the device-side trace on: how long the wave launches run, and the
+        # time between one launch's end and the next one's start
+        G.set_profiling(2)
+        graph_trace_ms, _, _ = timed_steps(1)
+        gprof = G.get_profile()
         G.set_profiling(False)
         prof_on[0] = False
     barrier()
@@ -476,6 +482,14 @@ def run_ours(args) -> None:
         # over the timed step time
         "step_roofline": step_roofline(kbytes, max(1, len(prof_times)), ms_per_step, peak),
         "wave_level_profile": level_profile(prof, clocks),
+        "graph_launch_trace": {
+            "step_ms": round(graph_trace_ms[0], 3), "wave_launches": gprof["wave_spans"],
+            "wave_span_ms": round(gprof["wave_span_ns"] / 1e6, 3),
+            "gaps": gprof["wave_gaps"], "gap_ms": round(gprof["wave_gap_ns"] / 1e6, 3),
+            "note": "one step of captured loops: wave launches from CTA 0's start to the end of "
+                    "their iteration, and the time from one launch's end to the next one's start "
+                    "within an exploit (the dense-sweep kernel between them and the launch "
+                    "latency), on the global timer"},
         "e2e": {"value": round(e2e_relax / e2e_s, 1) if e2e_steps else None, "unit": UNIT,
                 "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
                 "prefetch": not args.no_prefetch},

@@ -324,9 +324,18 @@ typedef struct {
      * own from the children it lowered. */
     int64_t share_tiles[24], share_vertices[24], share_cycles[24];
     int64_t local_tiles[24], local_vertices[24], local_cycles[24];
+    /* Wave launches on the global timer, in ns: from the start of CTA 0 to
+     * the end of the iteration (wave_span_ns over wave_spans launches), and
+     * from the end of one launch to the start of the next within an exploit
+     * (wave_gap_ns over wave_gaps: the kernels in between and the launch
+     * latency). */
+    int64_t wave_span_ns, wave_spans, wave_gap_ns, wave_gaps;
 } pirrt_profile;
 
-/* Clear the profile and turn event timing on (enable = 1) or off (0). */
+/* Clear the profile and turn event timing on (enable = 1) or off (0).
+ * enable = 2 keeps only the device-side wave trace (the level_*, share_*,
+ * local_* and wave_* fields) and leaves every exploit a single CUDA-graph
+ * launch, with no host loop and no events. */
 pirrt_status pirrt_graph_set_profiling(pirrt_graph *g, int enable);
 
 /* Copy the profile accumulated since the last pirrt_graph_set_profiling

@@ -88,7 +88,9 @@ class pirrt_profile(ctypes.Structure):
                 ("wave_calls", ctypes.c_int64),
                 ("share_tiles", ctypes.c_int64 * 24), ("share_vertices", ctypes.c_int64 * 24),
                 ("share_cycles", ctypes.c_int64 * 24), ("local_tiles", ctypes.c_int64 * 24),
-                ("local_vertices", ctypes.c_int64 * 24), ("local_cycles", ctypes.c_int64 * 24)]
+                ("local_vertices", ctypes.c_int64 * 24), ("local_cycles", ctypes.c_int64 * 24),
+                ("wave_span_ns", ctypes.c_int64), ("wave_spans", ctypes.c_int64),
+                ("wave_gap_ns", ctypes.c_int64), ("wave_gaps", ctypes.c_int64)]
 
     def as_dict(self) -> dict:
         out = {}
@@ -331,9 +333,12 @@ class Graph:
             self._check("pirrt_graph_exploit", rc)
         return out
 
-    def set_profiling(self, enable: bool = True):
+    def set_profiling(self, enable=True):
+        """True: event timing (host loop); False: off; 2: the device-side wave
+        trace alone, every exploit still one CUDA-graph launch."""
+        mode = 2 if enable == 2 else (1 if enable else 0)
         self._check("pirrt_graph_set_profiling",
-                    self._lib.pirrt_graph_set_profiling(self._h, 1 if enable else 0))
+                    self._lib.pirrt_graph_set_profiling(self._h, mode))
 
     def get_profile(self) -> dict:
         pr = pirrt_profile()

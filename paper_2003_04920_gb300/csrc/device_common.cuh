@@ -171,6 +171,10 @@ struct DevCounters {
     // the levels it walked on its own (loc_*), with their cycles
     unsigned long long shr_n[kLevelBuckets], shr_items[kLevelBuckets], shr_cyc[kLevelBuckets];
     unsigned long long loc_n[kLevelBuckets], loc_items[kLevelBuckets], loc_cyc[kLevelBuckets];
+    // Wave launches on the global timer (ns): from CTA 0's start to the end of
+    // the iteration (span), and from one launch's end to the next one's start
+    // within an exploit (gap: the launches in between and the launch latency)
+    unsigned long long t_enter, t_last_exit, span_ns, spans, gap_ns, gaps;
     unsigned long long ph_pre_cyc, ph_post_cyc, ph_jump_cyc, ph_calls;
 };
 

@@ -1387,6 +1387,7 @@ static __global__ void begin_exploit_kernel(DevCounters *c, unsigned max_iters,
     c->cum_dense = 0u;
     c->cum_jump_rounds = 0u;
     c->cum_jump_evals = 0u;
+    c->t_last_exit = 0ull;  // no gap is counted across exploits
     c->bound_bits = c->goal_g != nullptr
                         ? *reinterpret_cast<const unsigned long long *>(c->goal_g)
                         : 0x7ff0000000000000ull;

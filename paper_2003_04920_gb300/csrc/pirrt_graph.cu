@@ -1536,14 +1536,14 @@ pirrt_status pirrt_graph_get_parents(const pirrt_graph *Gc, int32_t *p_out, int6
 pirrt_status pirrt_graph_set_profiling(pirrt_graph *G, int enable) {
     if (!G) return PIRRT_ERR_INVALID_ARG;
     CK(cudaSetDevice(G->cfg.device));
-    G->profiling = enable ? 1 : 0;
+    G->profiling = enable == 1 ? 1 : 0;  // 2: the device-side trace alone
     G->prof = pirrt_profile{};
     G->trace.clear();
     CK(cudaStreamSynchronize(G->stream));
     // the device-side level trace starts afresh, on while profiling
     const size_t lvl_off = offsetof(DevCounters, lvl_trace);
     CK(cudaMemset(reinterpret_cast<char *>(G->ctr) + lvl_off, 0, sizeof(DevCounters) - lvl_off));
-    const unsigned on = enable ? 1u : 0u;
+    const unsigned on = enable != 0 ? 1u : 0u;
     CK(cudaMemcpy(&G->ctr->lvl_trace, &on, sizeof(on), cudaMemcpyHostToDevice));
     CK(cudaMemcpy(&G->copied_seen, &G->ctr->insert_copied, sizeof(G->copied_seen),
                   cudaMemcpyDeviceToHost));
@@ -1583,6 +1583,10 @@ pirrt_status pirrt_graph_get_profile(const pirrt_graph *Gc, pirrt_profile *out) 
     out->wave_post_cycles = (int64_t)h.ph_post_cyc;
     out->wave_jump_cycles = (int64_t)h.ph_jump_cyc;
     out->wave_calls = (int64_t)h.ph_calls;
+    out->wave_span_ns = (int64_t)h.span_ns;
+    out->wave_spans = (int64_t)h.spans;
+    out->wave_gap_ns = (int64_t)h.gap_ns;
+    out->wave_gaps = (int64_t)h.gaps;
     return PIRRT_OK;
 }
 

@@ -17,9 +17,36 @@ struct LevelClock {
     int state;
 };
 
-__device__ __forceinline__ void lc_start(const DevCounters *c, LevelClock &lc) {
+__device__ __forceinline__ unsigned long long global_ns() {
+    unsigned long long t;
+    asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+    return t;
+}
+
+__device__ __forceinline__ void lc_start(DevCounters *c, LevelClock &lc) {
     lc.state = (blockIdx.x == 0 && threadIdx.x == 0 && c->lvl_trace != 0u) ? -2 : -1;
     lc.t = clock64();
+    if (lc.state != -1) {
+        const unsigned long long now = global_ns();
+        c->t_enter = now;
+        const unsigned long long last = __ldcg(&c->t_last_exit);
+        if (last != 0ull && now > last) {
+            c->gap_ns += now - last;
+            c->gaps += 1ull;
+        }
+    }
+}
+
+// The thread that ends the iteration: the launch's span (traced launches).
+__device__ __forceinline__ void trace_exit(DevCounters *c) {
+    if (c->lvl_trace == 0u) return;
+    const unsigned long long now = global_ns();
+    const unsigned long long t0 = __ldcg(&c->t_enter);
+    if (t0 != 0ull && now > t0) {
+        c->span_ns += now - t0;
+        c->spans += 1ull;
+    }
+    c->t_last_exit = now;
 }
 
 // A level of `count` vertices starts now (count 0: the levels are over).
@@ -76,6 +103,7 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     if (n_sw == 0u) {
         if (blockIdx.x == 0 && threadIdx.x == 0) {
             lc_end(c, lc);
+            trace_exit(c);
             advance_iteration(c, cond, use_cond);
         }
         return;
@@ -205,6 +233,7 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
         if (blockIdx.x == 0 && tid == 0) {
             if (lc.state != -1) c->ph_jump_cyc += (unsigned long long)(clock64() - t_jump);
             lc_end(c, lc);
+            trace_exit(c);
             advance_iteration(c, cond, use_cond);
         }
         return;
@@ -216,6 +245,7 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
         __threadfence();
         if (atomicAdd(&c->wave_ticket, 1u) == nblocks - 1u) {
             c->wave_ticket = 0u;
+            trace_exit(c);
             advance_iteration(c, cond, use_cond);
         }
     }

@@ -24,20 +24,21 @@ __device__ __forceinline__ float ld_g32f(const float *p, unsigned long long pol)
 // the FP32 argmin alone, unless another candidate lies within the screening
 // margin, in which case the group rescans the row exactly.  No shared memory,
 // no CTA barriers, no FP64 arithmetic per entry.
-template <int G, int kU>
-__global__ void __launch_bounds__(256)
-improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
-    const ImproveArgs<float> a = *ap;
+// The body, for blocks of THREADS threads (every thread of the block calls
+// it): the kernel below, and the wave's launch, which runs the dense sweeps
+// itself (replan_iteration.cuh).
+template <int G, int kU, int THREADS>
+__device__ void improve_screen_body(const ImproveArgs<float> &a) {
     const int32_t *active = a.list[a.ctr->la & 1u];
     constexpr unsigned long long kInfBits = 0x7ff0000000000000ull;
     constexpr int kStageCap = 128;
-    __shared__ int32_t s_sw[256 / 32][kStageCap];
+    __shared__ int32_t s_sw[THREADS / 32][kStageCap];
     WarpStage<kStageCap> swq{s_sw[threadIdx.x >> 5], 0u};
     const unsigned long long gpol = policy_evict_last();
     const int lane = threadIdx.x & 31, gl = threadIdx.x & (G - 1);
     const unsigned gmask = G == 32 ? 0xffffffffu : (((1u << G) - 1u) << (lane & ~(G - 1)));
     (void)gmask;
-    const int gpb = 256 / G;
+    const int gpb = THREADS / G;
     const int64_t gstride = (int64_t)gridDim.x * gpb;
     const bool dense = a.ctr->dense != 0u;
     if (a.push && !dense) return;  // list sweeps run from offers
@@ -184,12 +185,19 @@ improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
         (void)warp_span;
     }
     // one atomic per block and counter (thousands of warps end together)
-    __shared__ unsigned s_fl[256 / 32 + 1];
-    __shared__ unsigned long long s_red[256 / 32];
+    __shared__ unsigned s_fl[THREADS / 32 + 1];
+    __shared__ unsigned long long s_red[THREADS / 32];
     swq.flush_block(a.switched, &a.ctr->n_switched, s_fl);
     block_max(djmax, &a.ctr->dj_bits, s_red);
     block_add(relax, &a.ctr->relax, s_red);
     block_add(improved, &a.ctr->improved, s_red);
+}
+
+template <int G, int kU>
+__global__ void __launch_bounds__(256)
+improve_screen_kernel(const ImproveArgs<float> *__restrict__ ap) {
+    const ImproveArgs<float> a = *ap;
+    improve_screen_body<G, kU, 256>(a);
 }
 
 }  // namespace pirrt

@@ -460,7 +460,7 @@ pirrt_status launch_evaluate(pirrt_graph *G, cudaStream_t st, size_t off) {
 // when fused_improve is set.
 template <typename CT>
 pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st, cudaGraphConditionalHandle cond,
-                         int use_cond, bool fused_improve = false) {
+                         int use_cond, bool fused_improve = false, bool fuse_dense = false) {
     cudaLaunchConfig_t cfg{};
     cfg.gridDim = dim3(G->wave_blocks);
     cfg.blockDim = dim3(kWaveThreads);
@@ -474,17 +474,26 @@ pirrt_status launch_wave(pirrt_graph *G, cudaStream_t st, cudaGraphConditionalHa
     const ImproveArgs<CT> *ip = fused_improve ? dev_arg<ImproveArgs<CT>>(G, kArgImprove) : nullptr;
     CK(cudaLaunchKernelEx(&cfg, wave_evaluate_kernel<CT>, dev_arg<WaveArgs<CT>>(G, kArgWave),
                           dev_arg<EvaluateArgs<CT>>(G, kArgEvalFallback),
-                          dev_arg<MarkArgs<CT>>(G, kArgMarkFallback), ip, cond, use_cond));
+                          dev_arg<MarkArgs<CT>>(G, kArgMarkFallback), ip, cond, use_cond,
+                          fuse_dense ? 1 : 0));
     return PIRRT_OK;
 }
 
+// A captured iteration with offers whose dense sweeps run inside the wave's
+// launch too (FP32 costs, the default 4 lanes): one launch per iteration.
+bool fuses_dense(int cost_dtype, int tile, int gs) {
+    return cost_dtype == PIRRT_COST_F32 && tile == 0 && (gs == 0 || gs == 4);
+}
+
 // Kernel launches of one Replan iteration (host loop; a captured wave
-// iteration with offers runs the offer Improve inside the wave's launch).
-int iteration_launches(int tile, bool jump, bool async, bool graph) {
+// iteration with offers runs the offer Improve inside the wave's launch, and
+// with FP32 costs the dense sweep as well).
+int iteration_launches(int tile, bool jump, bool async, bool graph, bool fused_dense = false) {
     const int improve = tile == 0 ? 2 : 1;
     if (jump) return improve + 3;
     if (async) return improve + 5;
-    return (graph && tile == 0) ? 2 : improve + 1;
+    if (graph && tile == 0) return fused_dense ? 1 : 2;
+    return improve + 1;
 }
 
 constexpr size_t kAsyncSmem = (size_t)kAsyncLocal * (sizeof(double) + 2 * sizeof(int32_t));
@@ -522,7 +531,10 @@ pirrt_status launch_iteration(pirrt_graph *G, cudaStream_t st, int gs, int tile,
                               bool async, cudaGraphConditionalHandle cond, int use_cond) {
     pirrt_status rc;
     if (!jump && !async && tile == 0) {
-        // the dense-sweep kernel, then Improve from offers and the wave in one launch
+        // the dense-sweep kernel, then Improve from offers and the wave in one
+        // launch; with FP32 costs that launch also runs the dense sweeps
+        if (fuses_dense(G->cfg.cost_dtype, tile, gs))
+            return launch_wave<CT>(G, st, cond, use_cond, true, true);
         if ((rc = launch_improve<CT>(G, st, gs, tile, false))) return rc;
         return launch_wave<CT>(G, st, cond, use_cond, true);
     }
@@ -934,7 +946,9 @@ pirrt_status exploit_impl(pirrt_graph *G, const pirrt_exploit_opts *opts, pirrt_
         const bool saw_deep = h.cum_jump_evals > 0;
         if (saw_deep || !jump || (G->exploits % 8) == 1) G->deep_hint = saw_deep ? 1 : 0;
     }
-    if (graph_ran) P.launches += (int64_t)h.iter * iteration_launches(tile, jump, async, true);
+    if (graph_ran)
+        P.launches += (int64_t)h.iter * iteration_launches(tile, jump, async, true,
+                                                            fuses_dense(G->cfg.cost_dtype, tile, gs));
     s.iterations = (int32_t)h.iter;
     s.converged = h.converged ? 1 : 0;
     s.relaxations = (int64_t)(h.relax + h.offers);

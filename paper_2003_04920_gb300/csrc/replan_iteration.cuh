@@ -3,8 +3,11 @@
 // improve_push.cuh the Improve from candidate offers).
 #pragma once
 
+#include <type_traits>
+
 #include "graph_kernels.cuh"
 #include "improve_push.cuh"
+#include "improve_screen.cuh"
 
 namespace pirrt {
 
@@ -86,7 +89,7 @@ template <typename CT>
 __global__ void __launch_bounds__(kWaveThreads, 2)
 wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT> *__restrict__ ep,
                      const MarkArgs<CT> *__restrict__ mp, const ImproveArgs<CT> *__restrict__ ip,
-                     cudaGraphConditionalHandle cond, int use_cond) {
+                     cudaGraphConditionalHandle cond, int use_cond, int fuse_dense) {
     const WaveArgs<CT> a = *ap;
     __shared__ WaveShared<CT> sh;
     DevCounters *c = a.ctr;
@@ -95,7 +98,13 @@ wave_evaluate_kernel(const WaveArgs<CT> *__restrict__ ap, const EvaluateArgs<CT>
     unsigned phase = 0;  // thread 0: phase bit of the grid barrier
     if (threadIdx.x == 0) phase = barrier_phase(c);
     if (ip != nullptr) {
-        improve_push_body<CT, 8>(*ip);
+        // fuse_dense (FP32 costs): the dense sweeps run here too, by the same
+        // screened 4-lane body as the dense-sweep kernel, so that a captured
+        // iteration is this one launch
+        if constexpr (std::is_same<CT, float>::value) {
+            if (fuse_dense && __ldcg(&c->dense) != 0u) improve_screen_body<4, 4, kWaveThreads>(*ip);
+        }
+        improve_push_body<CT, 8>(*ip);  // the list sweep, or the offers' reset before a dense one
         // a timeout is in the status word; the iteration still ends
         grid_barrier_phased(c, gridDim.x, phase);
     }

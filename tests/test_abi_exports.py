@@ -123,3 +123,45 @@ def test_library_links_no_driver_library():
     import subprocess
     out = subprocess.run(["ldd", path], capture_output=True, text=True).stdout
     assert "libcuda.so" not in out
+
+
+def test_binding_structs_match_the_header(tmp_path):
+    """The ctypes mirrors of the header's structs have the C layout: the same
+    size and the same offset for every field (a C program compiled against
+    include/pirrt.h prints them; nothing calls the library)."""
+    import subprocess
+    import paper_2003_04920_gb300 as P
+    structs = {"pirrt_config": P.pirrt_config, "pirrt_exploit_opts": P.pirrt_exploit_opts,
+               "pirrt_exploit_stats": P.pirrt_exploit_stats, "pirrt_profile": P.pirrt_profile,
+               "pirrt_trace_record": P.pirrt_trace_record}
+    lines = ["#include <stddef.h>", "#include <stdio.h>", '#include "pirrt.h"', "int main(void) {"]
+    for name, cls in structs.items():
+        lines.append(f'    printf("{name} size %zu\\n", sizeof({name}));')
+        for field, _ in cls._fields_:
+            lines.append(f'    printf("{name} {field} %zu\\n", offsetof({name}, {field}));')
+    lines += ["    return 0;", "}"]
+    src = tmp_path / "layout.c"
+    src.write_text("\n".join(lines) + "\n")
+    exe = tmp_path / "layout"
+    subprocess.run(["gcc", "-std=c11", "-Wall", "-Werror", f"-I{HEADER_DIR}", str(src), "-o",
+                    str(exe)], check=True)
+    out = subprocess.run([str(exe)], check=True, capture_output=True, text=True).stdout
+    got = {}
+    for line in out.splitlines():
+        name, field, value = line.split()
+        got[(name, field)] = int(value)
+    for name, cls in structs.items():
+        assert got[(name, "size")] == ctypes.sizeof(cls), name
+        for field, _ in cls._fields_:
+            assert got[(name, field)] == getattr(cls, field).offset, (name, field)
+
+
+def test_option_dicts_round_trip():
+    """The searching autotuner's result comes back as exploit() keywords that
+    rebuild the same option struct."""
+    import paper_2003_04920_gb300 as P
+    o = P.exploit_opts(eps=0.5, max_iters=7, group=8, tile=2, dense_fraction=0.2,
+                       evaluate="wave", wave_levels=40, host_loop=True, wave_tail=-1,
+                       wave_ctas=1, wave_local=4, wave_local_max=32, wave_local_step=1024)
+    back = P.exploit_opts(**P.opts_dict(o))
+    assert bytes(back) == bytes(o)

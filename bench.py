@@ -522,13 +522,18 @@ KERNEL_FILES = {"improve": ("improve_push.cuh", "improve_screen.cuh", "graph_ker
 
 
 def kernel_hash(kernel: str) -> str:
-    """Hash of the sources a kernel is built from: a stored DRAM traffic
-    figure is used only while it matches."""
+    """Hash of the code a kernel is built from (its sources with comments and
+    whitespace removed): a stored DRAM traffic figure is used only while it
+    matches."""
     import hashlib
+    import re
     h = hashlib.sha1()
     for f in KERNEL_FILES[kernel]:
-        with open(os.path.join(ROOT, "paper_2003_04920_gb300", "csrc", f), "rb") as fh:
-            h.update(fh.read())
+        with open(os.path.join(ROOT, "paper_2003_04920_gb300", "csrc", f)) as fh:
+            text = fh.read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        text = re.sub(r"//[^\n]*", "", text)
+        h.update("".join(text.split()).encode())
     return h.hexdigest()[:12]
 
 

@@ -903,12 +903,12 @@ struct WaveArgs {
 // level costs a few dependent memory round trips and a CTA barrier instead of
 // a grid-wide step.  Local walks run only in steps of at most local_step
 // vertices: a step ends when its slowest CTA does, so in a wide step a CTA
-// walking on alone would hold back every other CTA's share of the next step.  A longer list means a subtree wide enough to be worth
-// sharing: it goes to the global list of the next step, where every CTA takes
-// a part, and so do children beyond the local list's room and whatever the
-// list holds when the walk stops.  A step of at most tail_max
-// vertices is walked by CTA 0 alone with no level limit, while the other CTAs
-// wait at one grid barrier.
+// walking on alone would hold back every other CTA's share of the next step.
+// A longer list means a subtree wide enough to be worth sharing: it goes to
+// the global list of the next step, where every CTA takes a part, and so do
+// children beyond the local list's room and whatever the list holds when the
+// walk stops.  A step of at most tail_max vertices is walked by CTA 0 alone
+// with no level limit, while the other CTAs wait at one grid barrier.
 constexpr int kWaveThreads = 512;
 constexpr int kWaveUnroll = 4;
 constexpr int kWaveStage = 64;  // Improve-list appends staged per warp

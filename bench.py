@@ -537,12 +537,13 @@ def kernel_hash(kernel: str) -> str:
     return h.hexdigest()[:12]
 
 
-def oracle_prefix(rm, seconds: float, goal=None, h=None) -> dict:
+def oracle_prefix(rm, seconds: float, goal=None, h=None, lib=None, max_blocks=None) -> dict:
     """Serial policy iteration (the oracle, Alg. 2) on a prefix of the same
     Batched-Extension schedule, block by block, until `seconds` have passed
-    (goal-directed, Sec. IV-C, when `goal` is given)."""
+    or `max_blocks` blocks are done (goal-directed, Sec. IV-C, when `goal` is
+    given); `lib` picks another build of the oracle."""
     import oracle as O
-    G = O.OracleGraph(rm.n)
+    G = O.OracleGraph(rm.n, lib=lib)
     if goal is not None:
         G.set_goal(goal, np.asarray(h, dtype=np.float64))
     relax = 0
@@ -556,7 +557,7 @@ def oracle_prefix(rm, seconds: float, goal=None, h=None) -> dict:
         t_exploit += time.perf_counter() - t
         relax += st["relaxations"]
         blocks += 1
-        if time.perf_counter() - t0 > seconds:
+        if time.perf_counter() - t0 > seconds or (max_blocks is not None and blocks >= max_blocks):
             break
     G.close()
     return dict(relax=relax, blocks=blocks, seconds=t_exploit, n_present=min(rm.n, blocks * rm.block))
@@ -599,7 +600,29 @@ def cpu_baseline(rm, seconds: float, goal=None, h=None, gpu_block_ms=None,
                                   f"{k} blocks, CUDA events, one step")
     if dijkstra:
         out["dijkstra"] = dijkstra_baseline(rm)
+    out["openmp"] = openmp_baseline(rm, r, goal, h)
     return out
+
+
+def openmp_baseline(rm, serial: dict, goal=None, h=None) -> dict:
+    """The oracle built with OpenMP (its Jacobi Improve sweep over the host's
+    cores, results identical to the serial build) on the same block prefix as
+    the serial run: an all-core CPU baseline beside the one-core one."""
+    import oracle as O
+    try:
+        lib = O.load_parallel()
+        if lib is None:
+            return {"unavailable": "the compiler has no OpenMP"}
+        r = oracle_prefix(rm, 10.0 * serial["seconds"] + 60.0, goal, h, lib=lib,
+                          max_blocks=serial["blocks"])
+    except Exception as e:  # a baseline beside the measurement, never a reason to fail it
+        return {"unavailable": f"{type(e).__name__}: {e}"}
+    return {"kind": "oracle built with OpenMP: the Jacobi Improve sweep shared over the host's "
+                    "cores, Evaluate's walk serial; the serial build's results bit for bit",
+            "cores": O.threads(lib), "value": round(r["relax"] / r["seconds"], 1), "unit": UNIT,
+            "ms_per_batch": round(1e3 * r["seconds"] / r["blocks"], 3),
+            "sample": f"the first {r['blocks']} blocks, as the one-core run; {r['relax']} "
+                      f"relaxations in {r['seconds']:.2f} s (exploitation only)"}
 
 
 def run_batch(args) -> None:

@@ -31,6 +31,7 @@ import numpy as np
 _HERE = os.path.dirname(os.path.abspath(__file__))
 SOURCE = os.path.join(_HERE, "pirrt_oracle.c")
 LIB_PATH = os.path.join(_HERE, "liboracle.so")
+LIB_OMP_PATH = os.path.join(_HERE, "liboracle_omp.so")
 
 OK, ERR_ARG, ERR_CAPACITY, ERR_OOM, ERR_BAD_INPUT, ERR_NOT_CONVERGED = range(6)
 
@@ -54,6 +55,38 @@ def build(force: bool = False) -> str:
     return LIB_PATH
 
 
+def build_parallel(force: bool = False) -> str | None:
+    """The same source built with OpenMP: the Jacobi Improve sweep shared
+    over the host's cores, results identical to the plain build.  None if
+    the compiler has no OpenMP (nothing else depends on it)."""
+    try:
+        if force or not os.path.exists(LIB_OMP_PATH) or \
+                os.path.getmtime(LIB_OMP_PATH) < os.path.getmtime(SOURCE):
+            compile_oracle(out=LIB_OMP_PATH, extra=("-fopenmp",))
+    except (subprocess.CalledProcessError, OSError):
+        return None
+    return LIB_OMP_PATH
+
+
+_lib_omp = None
+
+
+def load_parallel():
+    """The OpenMP build (built first if needed), or None without OpenMP."""
+    global _lib_omp
+    if _lib_omp is None:
+        path = build_parallel()
+        if path is None:
+            return None
+        _lib_omp = _declare(ctypes.CDLL(path))
+    return _lib_omp
+
+
+def threads(lib) -> int:
+    """Threads a build's Improve sweep runs on (1 for the plain build)."""
+    return int(lib.or_threads())
+
+
 def _declare(lib):
     vp, i64, i32, f64 = ctypes.c_void_p, ctypes.c_int64, ctypes.c_int32, ctypes.c_double
     sig = {
@@ -75,6 +108,7 @@ def _declare(lib):
         "or_check_bellman": (i64, [vp, vp, f64, vp]),
         "or_check_consistency": (i64, [vp, i32, vp, vp, f64, vp]),
         "or_unambiguous": (i64, [vp, i32, vp, f64, vp, vp]),
+        "or_threads": (ctypes.c_int, []),
     }
     for name, (res, args) in sig.items():
         fn = getattr(lib, name)

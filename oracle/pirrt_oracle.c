@@ -13,6 +13,10 @@
  *     correctness argument of Sec. IV ("Correctness", Batched-Extension),
  *     Replan reaches the optimal policy from any initial policy, so the O1
  *     fixpoint must equal single-source shortest paths.
+ * Built a second time with OpenMP (liboracle_omp.so), the Jacobi Improve
+ *     sweep is shared over the host's cores: each vertex reads only the g of
+ *     the last Evaluate and writes only its own parent, so the results are
+ *     those of the serial build, bit for bit (a CPU baseline on all cores).
  * Checkers: Bellman inequality on every edge, tree consistency
  *     g(v) = g(p(v)) + c(p(v), v), acyclic parent tree rooted at x_init,
  *     reachable set = component of x_init, and the "unambiguous" mask
@@ -61,6 +65,9 @@
 #include <stdint.h>
 #include <stdlib.h>
 #include <string.h>
+#ifdef _OPENMP
+#include <omp.h>
+#endif
 
 #define OR_OK 0
 #define OR_ERR_ARG 1
@@ -279,6 +286,11 @@ static double improve(or_graph *G, int64_t *relax, int64_t *switched)
 {
     double dJ = 0.0;
     const double bound = goal_cost(G);
+    int64_t relax_sum = 0, switched_sum = 0;
+#ifdef _OPENMP
+#pragma omp parallel for schedule(dynamic, 4096) reduction(+ : relax_sum, switched_sum) \
+    reduction(max : dJ)
+#endif
     for (int64_t x = 0; x < G->n; ++x) {
         if (x == G->root) continue;
         const or_list *L = &G->adj[x];
@@ -294,16 +306,28 @@ static double improve(or_graph *G, int64_t *relax, int64_t *switched)
                 best_c = L->c[i];
             }
         }
-        *relax += L->len;
+        relax_sum += L->len;
         if (best >= 0 && ghat + G->h[x] < bound) {
             G->pi[x] = best;
             G->pc[x] = best_c;
-            ++*switched;
+            ++switched_sum;
             double d = cur - ghat;
             if (d > dJ) dJ = d;
         }
     }
+    *relax += relax_sum;
+    *switched += switched_sum;
     return dJ;
+}
+
+/* Threads the Improve sweep runs on: 1 in the plain build. */
+int or_threads(void)
+{
+#ifdef _OPENMP
+    return omp_get_max_threads();
+#else
+    return 1;
+#endif
 }
 
 /* Replace the policy with parent[] (-1 = none) and evaluate it.  Every
